@@ -1,0 +1,352 @@
+"""Benchmark: RTG-GMRES solves/s on the 512x512x3 FP32 colour-image workload.
+
+One step = one complete RTG-GMRES solve (sketch signs, R_0 and beta,
+sketched Arnoldi steps until rho <= rho*, projected Tikhonov with GCV over
+8 values of mu, assembly of X) on a seeded synthetic blurred, noisy image.
+Default: N=1 GPU, 20 timed steps after 5 warm-up steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own problems (replicas: the path has no
+exchange step), value = all solves / max-over-ranks time.  The reference
+arm (--impl reference) times the FP64 CPU oracle on this host's cores.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "RTG-GMRES solves/s at rel. residual 1e-3: chosen form vs plain FP32, same GB300"
+WORKLOAD = "image512x512x3_f32"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--problems", type=int, default=4, help="distinct seeded problems cycled")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def rho_star(nu_c: float) -> float:
+    # stop level of the relative sketched residual: 1e-3, or the noise floor
+    # of the observation when that lies above it (discrepancy principle)
+    return max(1e-3, 1.01 * nu_c)
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- problems
+
+def make_problems(h, api, torch, count: int, seed0: int):
+    """Observations built on the device with the library's own operator (outside the timed region)."""
+    probs = []
+    for s in range(count):
+        p = workloads.image_config(2, seed=seed0 + s)
+        A = [api.banded(m, p.dims[m - 1], t) for m, _, t in p.factors]
+        B = [api.dense(m, t) for m, _, t in p.right_factors]
+        X = api.to_device(p.x_true, torch.float32)
+        Ch = h.operator_apply(X, A, B)
+        E = api.to_device(p.noise, torch.float32)
+        N = E * (p.nu * torch.linalg.vector_norm(Ch) / torch.linalg.vector_norm(E))
+        C = api.empty(p.dims, torch.float32)
+        C.copy_(Ch + N)
+        nu_c = float(torch.linalg.vector_norm(N) / torch.linalg.vector_norm(C))
+        probs.append(dict(p=p, A=A, B=B, C=C, tol=rho_star(nu_c), nu_c=nu_c))
+    return probs
+
+
+def solve(h, pr, X, stream=None, host=False):
+    p = pr["p"]
+    C = pr["C_host"] if host else pr["C"]
+    return h.gmres_solve(C, p.m, p.sketch_dims, p.seed, p.lam, pr["A"], pr["B"], X=X, tol=pr["tol"],
+                         mu_grid=p.mu_grid, stream=stream)
+
+
+# ----------------------------------------------------------------------------- roofline
+
+def roofline_apply(h, api, torch, probs, peaks):
+    """Standalone operator-apply timing (the per-step dominant full-tensor pass):
+    inputs cycled over > L2 bytes so every launch reads from HBM."""
+    p = probs[0]["p"]
+    n = int(np.prod(p.dims))
+    count = max(4, int(np.ceil(2 * 129e6 / (4 * n))))
+    Xs = [torch.randn(p.dims[::-1], device="cuda").permute(2, 1, 0) for _ in range(count)]
+    Ys = [api.empty(p.dims, torch.float32) for _ in range(count)]
+    stream = torch.cuda.current_stream()
+    for i in range(count):
+        h.operator_apply(Xs[i], probs[0]["A"], probs[0]["B"], Y=Ys[i])
+    torch.cuda.synchronize()
+    reps = 3 * count
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(reps):
+        h.operator_apply(Xs[i % count], probs[0]["A"], probs[0]["B"], Y=Ys[i % count])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    bytes_ = 2 * n * 4
+    peak = peaks.get("hbm_gbs", 6800.0)
+    ach = bytes_ / t / 1e9
+    return {"kernel": "k_apply_fused<float,3> (operator apply, 512x512x3 fp32)", "bound": "hbm",
+            "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+            "traffic": None, "bytes_per_launch": bytes_, "us_per_launch": round(t * 1e6, 3),
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst)"}
+
+
+# ----------------------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(probs_host, seconds: float):
+    """FP64 CPU oracle as it stands, on this host's cores, on a bounded sample of the workload."""
+    import oracle
+    done, t0 = 0, time.perf_counter()
+    iters = []
+    while True:
+        pr = probs_host[done % len(probs_host)]
+        p = pr["p"]
+        mats = oracle.factor_matrices(p.dims, p.factors, p.right_factors)
+        C, _, nu_c = oracle.make_observation(p.x_true, mats, p.noise, p.nu)
+        th = oracle.sketch_matrices(p.dims, p.sketch_dims, p.seed, p.problem_id)
+        ts = time.perf_counter()
+        r = oracle.rtg_gmres(mats, C, p.m, th, tol=rho_star(nu_c), lam=p.lam, mu_grid=p.mu_grid)
+        iters.append(r["iters"])
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": round(done / el, 4), "unit": "solves/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{done} full FP64 oracle solves of the 512x512x3 workload "
+                      f"(mean {np.mean(iters):.1f} Arnoldi steps), numpy BLAS default threads"}
+
+
+# ----------------------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    probs = [dict(p=workloads.image_config(2, seed=s)) for s in range(args.problems)]
+    import oracle
+    times = []
+    iters = []
+    for step in range(args.warmup + args.steps):
+        pr = probs[step % len(probs)]
+        p = pr["p"]
+        t0 = time.perf_counter()
+        mats = oracle.factor_matrices(p.dims, p.factors, p.right_factors)
+        C, _, nu_c = oracle.make_observation(p.x_true, mats, p.noise, p.nu)
+        th = oracle.sketch_matrices(p.dims, p.sketch_dims, p.seed, p.problem_id)
+        r = oracle.rtg_gmres(mats, C, p.m, th, tol=rho_star(nu_c), lam=p.lam, mu_grid=p.mu_grid)
+        t = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(t)
+            iters.append(r["iters"])
+    tot = sum(times)
+    val = args.steps / tot
+    out = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "solves/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * tot / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "dims": [512, 512, 3], "m": 50,
+                      "sketch": [128, 128, 3], "gcv_grid": 8, "mean_iters": float(np.mean(iters)),
+                      "stop": "rho <= max(1e-3, 1.01*nu_C)"},
+           "cpu_baseline": {"value": round(val, 4), "unit": "solves/s", "cores": os.cpu_count(),
+                            "kind": "oracle",
+                            "sample": f"{args.steps} timed FP64 oracle solves (observation build "
+                                      "included), numpy BLAS default threads"},
+           "e2e": {"value": round(val, 4), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2603_00839_gb300 import api
+    h = api.Handle(torch.cuda.current_device())
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {"hbm_gbs": 6800.0, "fallback": True}
+    probs = make_problems(h, api, torch, args.problems, seed0=1000 * rank)
+    X = api.empty(probs[0]["p"].dims, torch.float32)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # warm-up (builds the plan and its CUDA graph)
+    for s in range(args.warmup):
+        solve(h, probs[s % len(probs)], X)
+    torch.cuda.synchronize()
+
+    # device-timed steps; L2 flushed between steps (outside the events)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    iters, launches = [], 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            evs[s][0].record(stream)
+            _, info = solve(h, probs[s % len(probs)], X)
+            evs[s][1].record(stream)
+            iters.append(info.iters)
+            launches += info.launches
+            if info.device_status != 0 or not info.converged:
+                raise RuntimeError(f"solve failed: status {info.device_status} converged {info.converged}")
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * 1e3 / ms_max
+
+    # end-to-end through the C ABI with pinned host buffers (H2D of C, D2H of X and the summary)
+    n = int(np.prod(probs[0]["p"].dims))
+    for pr in probs:
+        ch = torch.empty(tuple(reversed(pr["p"].dims)), dtype=torch.float32, pin_memory=True)
+        ch = ch.permute(2, 1, 0)
+        ch.copy_(pr["C"].cpu())
+        pr["C_host"] = ch
+    Xh = torch.empty(tuple(reversed(probs[0]["p"].dims)), dtype=torch.float32,
+                     pin_memory=True).permute(2, 1, 0)
+    for s in range(2):
+        solve(h, probs[s % len(probs)], Xh, host=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        solve(h, probs[s % len(probs)], Xh, host=True)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_t = torch.tensor([e2e_s], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_val = world / float(e2e_t.item())
+
+    roof = roofline_apply(h, api, torch, probs, peaks) if rank == 0 else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline([dict(p=pr["p"]) for pr in probs], args.cpu_seconds)
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 2), "unit": "solves/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD, "dims": [512, 512, 3], "m": 50,
+                          "sketch": [128, 128, 3], "blur": "gaussian sigma 2.5 radius 7 + 3x3 mix",
+                          "noise": 1e-2, "gcv_grid": 8, "mean_iters": float(np.mean(iters)),
+                          "stop": "rho <= max(1e-3, 1.01*nu_C)", "problems": args.problems,
+                          "l2": "flushed (256 MB write) between timed steps",
+                          "form": "plain fp32"},
+               "e2e": {"value": round(e2e_val, 2), "unit": "solves/s",
+                       "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n + 2368},
+               "gpu_launches": launches,
+               "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary()}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

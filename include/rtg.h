@@ -1,0 +1,254 @@
+/*
+ * rtg.h -- C ABI of the GB300 (sm_103a) Randomized Tensor Global GMRES library.
+ *
+ * Method: A. Badahmane, "Randomized Tensor Krylov Subspace Methods via
+ * Sketched Einstein Product with Applications to Image and Video
+ * Restoration".  The library solves Phi(X) = C for a separable blur
+ * operator Phi(X) = A *_N X (*_M B) (Section 1; Eq. 56-57) by RTG-GMRES:
+ * sketched global Arnoldi (Section 4.3 and the algorithm "Block GMRES via
+ * Sketched Einstein Product"), the Hessenberg least-squares problem
+ * (Eq. 11S) and the projected Tikhonov problem (Eq. 12S-14S, Eq. 13) with
+ * mu chosen by GCV (Section 3, "Parameter selection via GCV").
+ *
+ * Conventions shared by every entry point
+ *  - Tensors are dense, contiguous and column-major: mode 1 varies fastest
+ *    (the ivec ordering of Section 4.1).  Order 1..4.
+ *  - Device pointers are caller-owned; the library never frees them.
+ *    rtg_gmres_solve also accepts host pointers (pageable or pinned) for
+ *    C, X0 and X and stages them through its own device buffers.
+ *  - Host arrays inside structs (taps, dense factors, mu grids) are read
+ *    during the call only.
+ *  - All work is ordered on the given stream (NULL = legacy default
+ *    stream).  rtg_gmres_solve and rtg_krylov_query synchronise that stream
+ *    once, at the end, to return host-side results; the other calls are
+ *    asynchronous.
+ *  - Errors: every call returns an rtg_status; arguments are validated
+ *    before anything is launched, and rtg_last_error() returns a
+ *    thread-local message for the last failing call.  No call aborts the
+ *    process or traps the GPU; device-side anomalies (non-finite values,
+ *    breakdown) are reported through rtg_info.
+ *  - A handle is bound to one device and is not thread-safe: use one
+ *    handle per host thread.
+ */
+#ifndef RTG_H
+#define RTG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTG_MAX_ORDER 4
+#define RTG_MAX_RADIUS 32      /* banded factors: taps of length 2r+1, r <= 32 */
+#define RTG_MAX_KRYLOV 256     /* largest Krylov dimension m */
+#define RTG_MAX_MU 32          /* largest GCV grid */
+
+typedef enum rtg_status {
+    RTG_OK = 0,
+    RTG_ERR_INVALID_ARG = 1,   /* bad pointer, shape, size or option */
+    RTG_ERR_UNSUPPORTED = 2,   /* valid but not implemented (e.g. dtype for that call) */
+    RTG_ERR_CUDA = 3,          /* a CUDA runtime call failed; see rtg_last_error() */
+    RTG_ERR_ALLOC = 4,         /* device or pinned allocation failed */
+    RTG_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    RTG_ERR_NONFINITE = 6      /* NaN/Inf met in the data (reported by rtg_gmres_solve) */
+} rtg_status;
+
+typedef enum rtg_dtype {
+    RTG_F64 = 0,               /* double data, double arithmetic */
+    RTG_F32 = 1,               /* float data, float arithmetic with FP64 small solves */
+    RTG_BF16 = 2               /* reserved */
+} rtg_dtype;
+
+typedef enum rtg_factor_kind {
+    RTG_FACTOR_IDENTITY = 0,
+    RTG_FACTOR_BANDED_TOEPLITZ = 1,  /* (M x)_i = sum_{|t|<=r} taps[r+t] x_{i+t}, zero outside */
+    RTG_FACTOR_DENSE = 2             /* dense n x n matrix M, column-major (M(i,j) at i + n*j) */
+} rtg_factor_kind;
+
+typedef struct rtg_shape {
+    int32_t order;                   /* 1..RTG_MAX_ORDER */
+    int64_t dims[RTG_MAX_ORDER];     /* I_1..I_order, each >= 1; unused entries ignored */
+} rtg_shape;
+
+/*
+ * One factor of the separable operator (Eq. 56-57; Section 1).
+ * A left factor ("A factor") acts as the mode product X x_mode M: the
+ * 4th-order blurring tensor of Eq. 56 is A[i,j,i',j'] = A_1[i,i'] A_2[j,j'],
+ * so A *_2 X = X x_1 A_1 x_2 A_2.  A right factor ("B factor") is the
+ * Einstein right product X *_1 B, i.e. (X *_1 B)[..,c'] = sum_c X[..,c] B[c,c'],
+ * applied as X x_mode B^T.  For a banded right factor, B is the banded
+ * Toeplitz matrix built from its taps.
+ */
+typedef struct rtg_factor {
+    int32_t mode;                    /* 1-based mode the factor acts on */
+    int32_t kind;                    /* rtg_factor_kind */
+    int32_t n;                       /* must equal dims[mode-1] */
+    int32_t radius;                  /* banded: r (0..RTG_MAX_RADIUS) */
+    const double* taps;              /* banded: host array of 2r+1 taps */
+    const double* dense;             /* dense: host array n*n, column-major */
+} rtg_factor;
+
+/* Options of rtg_gmres_solve.  A zero-initialised struct is valid. */
+typedef struct rtg_opts {
+    double tol;                      /* stop at the first j with rho_j <= tol (0: run m steps) */
+    const double* mu_grid;           /* host array of n_mu GCV candidates (lambda < 0) */
+    int32_t n_mu;                    /* 1..RTG_MAX_MU when lambda < 0 */
+    int32_t max_restarts;            /* restarts from the least-squares iterate (>= 0) */
+    double breakdown_tol;            /* breakdown if h_{j+1,j} <= breakdown_tol * ||S(Phi V_j)||;
+                                        0 selects 1e-12 (F64) / 1e-6 (F32) */
+    int32_t flags;                   /* RTG_FLAG_* */
+    int32_t reserved;
+} rtg_opts;
+
+#define RTG_FLAG_NO_GRAPH      1     /* launch kernels directly instead of a CUDA graph */
+#define RTG_FLAG_TRUE_RESIDUAL 2     /* also compute ||C - Phi(X)||_F / ||C||_F into info */
+
+typedef struct rtg_info {
+    int32_t iters;                   /* Arnoldi steps taken, all cycles */
+    int32_t restarts;
+    int32_t breakdown;               /* 1: h_{j+1,j} fell below the breakdown level (exact in K_j) */
+    int32_t converged;               /* 1: rho <= tol (or breakdown) */
+    double beta;                     /* ||R_0||_Theta of the first cycle */
+    double mu;                       /* regularisation used (GCV choice, fixed lambda, or 0) */
+    double rho_final;                /* last rho_j */
+    double* rho_hist;                /* optional caller host array of length >= m*(max_restarts+1) */
+    double* gcv;                     /* optional caller host array of length n_mu (GCV values) */
+    double true_rel_resid;           /* with RTG_FLAG_TRUE_RESIDUAL, else -1 */
+    double elapsed_ms;               /* device time of the solve (CUDA events) */
+    int32_t device_status;           /* rtg_status seen on the device (NONFINITE, ...) */
+    int32_t launches;                /* kernels this library launched for the solve */
+} rtg_info;
+
+typedef struct rtg_context* rtg_handle;
+typedef struct rtg_krylov_state* rtg_krylov;
+typedef struct CUstream_st* rtg_stream;   /* same type as cudaStream_t */
+
+/* Create a handle on CUDA device `device`.  The handle owns all workspace
+ * (basis, sketches, Hessenberg data, graphs) and grows it on demand. */
+rtg_status rtg_create(rtg_handle* handle, int device);
+/* Free the handle and everything it owns.  NULL is accepted. */
+rtg_status rtg_destroy(rtg_handle handle);
+/* Thread-local description of the last error (never NULL). */
+const char* rtg_last_error(void);
+const char* rtg_status_string(rtg_status status);
+int32_t rtg_version(void);
+
+/*
+ * Y = Phi(X): the Einstein-product operator of Section 1 with separable
+ * factors (Eq. 56-57, zero boundary conditions).  Modes without a factor
+ * are untouched.  Several factors on one mode compose (right factors after
+ * left ones).  X and Y: device arrays of prod(dims) elements of `dtype`
+ * (F64 or F32); Y must not overlap X.
+ * Errors: INVALID_ARG (shape, factor mode/size/radius, NULL), UNSUPPORTED
+ * (BF16), CUDA.
+ */
+rtg_status rtg_operator_apply(rtg_handle handle,
+                              const rtg_factor* A_factors, int32_t nA,
+                              const rtg_factor* B_factors, int32_t nB,
+                              rtg_shape shape, rtg_dtype dtype,
+                              const void* X, void* Y, rtg_stream stream);
+
+/*
+ * SX = S(X) = X x_1 Theta_1 x_2 ... x_d Theta_d (Section 3, the global
+ * tensor sketching operator; Section 3.1, the compressed tensor).
+ * Theta_k is s_k x I_k with Rademacher entries +-1/sqrt(s_k) drawn from
+ * Philox4x64-10 keyed (seed, problem_id): signs of the sketched modes in
+ * increasing mode order, each Theta_k row-major, sign e = bit e%64 of
+ * output word e/64 (set bit = -1), output word w from counter (w/4+1,0,0,0).
+ * A mode with s_k >= I_k is not sketched (Theta_k = I, s'_k = I_k).
+ * SX: device array of prod(s'_k) elements of `dtype`, column-major.
+ * Errors: INVALID_ARG (s_k < 1, shape), UNSUPPORTED (BF16), CUDA.
+ */
+rtg_status rtg_sketch(rtg_handle handle, rtg_shape shape, rtg_dtype dtype,
+                      const int64_t* sketch_dims, uint64_t seed, uint64_t problem_id,
+                      const void* X, void* SX, rtg_stream stream);
+
+/*
+ * Raw Philox4x64-10 stream behind the sketch (see rtg_sketch): out[w] for
+ * w < n_words, device array of uint64.  Exposed so the signs can be checked
+ * bit for bit.
+ */
+rtg_status rtg_philox_words(rtg_handle handle, uint64_t seed, uint64_t problem_id,
+                            int64_t n_words, uint64_t* out, rtg_stream stream);
+
+/*
+ * Caller-held sketched Arnoldi state (Section 4.3): basis V_1..V_{m+1}
+ * (full space), their sketches Q = [S(V_1) .. S(V_{m+1})], the Hessenberg
+ * matrix Hbar_m and the Givens QR used for rho_j.  rtg_krylov_create
+ * allocates it for one operator, shape, dtype (F64/F32), Krylov dimension m
+ * and sketch; the factors are copied.
+ */
+rtg_status rtg_krylov_create(rtg_handle handle,
+                             const rtg_factor* A_factors, int32_t nA,
+                             const rtg_factor* B_factors, int32_t nB,
+                             rtg_shape shape, rtg_dtype dtype, int32_t m,
+                             const int64_t* sketch_dims, uint64_t seed, uint64_t problem_id,
+                             rtg_krylov* krylov);
+rtg_status rtg_krylov_destroy(rtg_krylov krylov);
+
+/*
+ * Start the process: R_0 = C - Phi(X_0) (X0 may be NULL for X_0 = 0),
+ * beta = ||R_0||_Theta, V_1 = R_0/beta, S(V_1) (first steps of the Block
+ * GMRES algorithm).  C, X0: device arrays.  Asynchronous.
+ */
+rtg_status rtg_krylov_start(rtg_handle handle, rtg_krylov krylov,
+                            const void* C, const void* X0, rtg_stream stream);
+
+/*
+ * One sketched Arnoldi step j -> j+1: W = Phi(V_j); h_ij = <V_i, W>_Theta
+ * for i <= j, computed as classical Gram-Schmidt with one
+ * re-orthogonalisation pass in the sketch space (equal to the paper's
+ * modified Gram-Schmidt in exact arithmetic); h_{j+1,j} = ||W - sum h_ij V_i||_Theta;
+ * V_{j+1} and S(V_{j+1}); Givens update of the least-squares residual
+ * rho_j = ||beta e1 - Hbar_j y_j|| / beta (Eq. 11S).  After a breakdown
+ * or once j = m the call is a no-op.  Asynchronous.
+ */
+rtg_status rtg_arnoldi_step(rtg_handle handle, rtg_krylov krylov, rtg_stream stream);
+
+/* Host view of a Krylov state (filled by rtg_krylov_query, which synchronises the stream). */
+typedef struct rtg_krylov_view {
+    int32_t j;                       /* number of completed steps */
+    int32_t m;
+    int32_t breakdown;
+    int32_t sketch_size;             /* d = prod(s'_k) */
+    int64_t n;                       /* prod(dims) */
+    double beta;
+    double rho;                      /* last rho_j (1.0 before the first step) */
+    const void* V;                   /* device: (m+1) tensors of n elements, V_i at V + i*n */
+    const void* Q;                   /* device: (m+1) sketches of d elements (dtype of the state) */
+} rtg_krylov_view;
+
+/* H: optional host array of (m+1)*m doubles, column-major, receives Hbar. */
+rtg_status rtg_krylov_query(rtg_handle handle, rtg_krylov krylov, rtg_krylov_view* view,
+                            double* H, rtg_stream stream);
+
+/*
+ * RTG-GMRES for Phi(X) = C (the algorithm "Block GMRES via Sketched
+ * Einstein Product" with the projected Tikhonov problem of Eq. 12S/13):
+ *   R_0 = C - Phi(X_0), beta = ||R_0||_Theta; up to m sketched Arnoldi
+ *   steps, stopping at the first j with rho_j <= opts->tol or on breakdown;
+ *   then y = argmin ||beta e1 - Hbar y||^2 + mu ||y||^2 with
+ *     lambda > 0: mu = lambda;  lambda == 0: mu = 0 (Eq. 11S);
+ *     lambda < 0: mu = argmin GCV(mu) over opts->mu_grid (ties: larger mu);
+ *   X = X_0 + sum_j y_j V_j (Eq. 10S).
+ * With opts->max_restarts > 0, a cycle that ends at j = m without reaching
+ * tol restarts from its least-squares iterate.
+ * C, X0 (may be NULL), X: device or host arrays of prod(dims) elements of
+ * dtype (F64 or F32); X may alias X0.  info may be NULL.  The call
+ * synchronises `stream` once at the end.
+ * Errors: INVALID_ARG, UNSUPPORTED, ALLOC, CUDA; numeric trouble is
+ * reported in info->device_status (RTG_ERR_NONFINITE) with RTG_OK returned.
+ */
+rtg_status rtg_gmres_solve(rtg_handle handle,
+                           const rtg_factor* A_factors, int32_t nA,
+                           const rtg_factor* B_factors, int32_t nB,
+                           rtg_shape shape, rtg_dtype dtype,
+                           const void* C, int32_t m, const int64_t* sketch_dims,
+                           uint64_t seed, double lambda, const void* X0, void* X,
+                           const rtg_opts* opts, rtg_info* info, rtg_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTG_H */

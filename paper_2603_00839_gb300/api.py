@@ -1,0 +1,337 @@
+"""Python binding of librtg: argument marshalling only.
+
+Every computation runs in the CUDA kernels behind the C ABI; this module
+converts Python objects into the ABI's structs and pointers.  PyTorch
+provides device memory and streams.  Tensors are column-major (mode 1
+fastest, the ivec order of Section 4.1 of the paper): use
+:func:`empty` / :func:`to_device` to make them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _lib as L
+
+__all__ = ["Handle", "Factor", "banded", "dense", "identity", "empty", "to_device",
+           "colmajor_strides", "SolveResult", "Krylov"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def colmajor_strides(dims: Sequence[int]) -> Tuple[int, ...]:
+    s, out = 1, []
+    for d in dims:
+        out.append(s)
+        s *= int(d)
+    return tuple(out)
+
+
+def empty(dims: Sequence[int], dtype=None, device="cuda"):
+    """Uninitialised column-major tensor of shape ``dims`` on ``device``."""
+    torch = _torch()
+    dtype = dtype or torch.float32
+    rev = tuple(int(d) for d in reversed(dims))
+    return torch.empty(rev, dtype=dtype, device=device).permute(*reversed(range(len(dims))))
+
+
+def to_device(a: np.ndarray, dtype=None, device="cuda"):
+    """Copy a numpy array (any order) into a new column-major tensor on ``device``."""
+    torch = _torch()
+    t = torch.from_numpy(np.asfortranarray(a))
+    out = empty(a.shape, dtype or t.dtype, device)
+    out.copy_(t)
+    return out
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return L.F64
+    if t.dtype == torch.float32:
+        return L.F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _check_tensor(t, dims: Sequence[int], name: str) -> None:
+    if tuple(t.shape) != tuple(dims):
+        raise ValueError(f"{name}: shape {tuple(t.shape)} != {tuple(dims)}")
+    if t.numel() > 1 and tuple(t.stride()) != colmajor_strides(dims):
+        raise ValueError(f"{name}: not column-major dense (strides {t.stride()})")
+
+
+def _shape(dims: Sequence[int]) -> L.Shape:
+    if not 1 <= len(dims) <= L.MAX_ORDER:
+        raise ValueError("order must be 1..4")
+    s = L.Shape()
+    s.order = len(dims)
+    for k, d in enumerate(dims):
+        s.dims[k] = int(d)
+    return s
+
+
+@dataclasses.dataclass
+class Factor:
+    """One factor of the separable operator: ``mode`` is 1-based."""
+    mode: int
+    kind: int
+    n: int
+    taps: Optional[np.ndarray] = None
+    matrix: Optional[np.ndarray] = None
+
+    @property
+    def radius(self) -> int:
+        return 0 if self.taps is None else (len(self.taps) - 1) // 2
+
+
+def banded(mode: int, n: int, taps) -> Factor:
+    taps = np.ascontiguousarray(taps, dtype=np.float64)
+    assert len(taps) % 2 == 1
+    return Factor(mode, L.FACTOR_BANDED_TOEPLITZ, n, taps=taps)
+
+
+def dense(mode: int, M) -> Factor:
+    M = np.asarray(M, dtype=np.float64)
+    return Factor(mode, L.FACTOR_DENSE, M.shape[0], matrix=np.asfortranarray(M))
+
+
+def identity(mode: int, n: int) -> Factor:
+    return Factor(mode, L.FACTOR_IDENTITY, n)
+
+
+def _factor_array(fs: Sequence[Factor]):
+    arr = (L.Factor * max(len(fs), 1))()
+    keep = []
+    for i, f in enumerate(fs):
+        arr[i].mode, arr[i].kind, arr[i].n, arr[i].radius = f.mode, f.kind, f.n, f.radius
+        if f.taps is not None:
+            arr[i].taps = f.taps.ctypes.data_as(C.POINTER(C.c_double))
+            keep.append(f.taps)
+        if f.matrix is not None:
+            m = np.ascontiguousarray(f.matrix.ravel(order="F"))
+            keep.append(m)
+            arr[i].dense = m.ctypes.data_as(C.POINTER(C.c_double))
+    return (arr if fs else None), len(fs), keep
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return _torch().cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+@dataclasses.dataclass
+class SolveResult:
+    iters: int
+    restarts: int
+    breakdown: bool
+    converged: bool
+    beta: float
+    mu: float
+    rho_final: float
+    rho: np.ndarray
+    gcv: Optional[np.ndarray]
+    elapsed_ms: float
+    device_status: int
+    launches: int
+
+
+class Handle:
+    """A librtg handle bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = L.load()
+        h = C.c_void_p()
+        L.check(self.lib.rtg_create(C.byref(h), int(device)))
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.rtg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- K0
+    def philox_words(self, seed: int, problem_id: int, n_words: int, stream=None):
+        """Raw Philox4x64-10 stream behind the sketch signs (uint64 as int64 tensor)."""
+        torch = _torch()
+        out = torch.empty(n_words, dtype=torch.int64, device=f"cuda:{self.device}")
+        L.check(self.lib.rtg_philox_words(self._h, C.c_uint64(seed), C.c_uint64(problem_id),
+                                          n_words, out.data_ptr(), _stream(stream)))
+        return out
+
+    # ---------------------------------------------------------------- K1
+    def operator_apply(self, X, A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (),
+                       Y=None, stream=None):
+        """Y = Phi(X) for the separable Einstein-product operator."""
+        dims = tuple(X.shape)
+        _check_tensor(X, dims, "X")
+        if Y is None:
+            Y = empty(dims, X.dtype, X.device)
+        _check_tensor(Y, dims, "Y")
+        a, na, ka = _factor_array(A_factors)
+        b, nb, kb = _factor_array(B_factors)
+        L.check(self.lib.rtg_operator_apply(self._h, a, na, b, nb, _shape(dims), _dtype_code(X),
+                                            X.data_ptr(), Y.data_ptr(), _stream(stream)))
+        return Y
+
+    # ---------------------------------------------------------------- K3
+    def sketch(self, X, sketch_dims: Sequence[int], seed: int, problem_id: int = 0, SX=None,
+               stream=None):
+        """SX = S(X) with mode-wise Rademacher sketches (modes with s_k >= I_k untouched)."""
+        dims = tuple(X.shape)
+        _check_tensor(X, dims, "X")
+        sd = tuple(int(min(s, d)) for s, d in zip(sketch_dims, dims))
+        if SX is None:
+            SX = empty(sd, X.dtype, X.device)
+        _check_tensor(SX, sd, "SX")
+        sk = (C.c_int64 * len(dims))(*[int(s) for s in sketch_dims])
+        L.check(self.lib.rtg_sketch(self._h, _shape(dims), _dtype_code(X), sk, C.c_uint64(seed),
+                                    C.c_uint64(problem_id), X.data_ptr(), SX.data_ptr(),
+                                    _stream(stream)))
+        return SX
+
+    # ---------------------------------------------------------------- solve
+    def gmres_solve(self, C_obs, m: int, sketch_dims: Sequence[int], seed: int, lam: float,
+                    A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (),
+                    X0=None, X=None, tol: float = 0.0, mu_grid=None, max_restarts: int = 0,
+                    breakdown_tol: float = 0.0, use_graph: bool = True, stream=None):
+        """RTG-GMRES; C_obs, X0, X may be device tensors or host numpy arrays (Fortran order)."""
+        dims = tuple(C_obs.shape)
+        host = isinstance(C_obs, np.ndarray)
+        if host:
+            if C_obs.dtype not in (np.float32, np.float64) or not C_obs.flags.f_contiguous:
+                raise ValueError("host C must be a Fortran-ordered float32/float64 array")
+            dt = L.F64 if C_obs.dtype == np.float64 else L.F32
+            if X is None:
+                X = np.empty(dims, dtype=C_obs.dtype, order="F")
+        else:
+            _check_tensor(C_obs, dims, "C")
+            dt = _dtype_code(C_obs)
+            if X is None:
+                X = empty(dims, C_obs.dtype, C_obs.device)
+        a, na, ka = _factor_array(A_factors)
+        b, nb, kb = _factor_array(B_factors)
+        sk = (C.c_int64 * len(dims))(*[int(s) for s in sketch_dims])
+        opts = L.Opts()
+        opts.tol = float(tol)
+        grid = None
+        if mu_grid is not None:
+            grid = np.ascontiguousarray(mu_grid, dtype=np.float64)
+            opts.mu_grid = grid.ctypes.data_as(C.POINTER(C.c_double))
+            opts.n_mu = len(grid)
+        opts.max_restarts = int(max_restarts)
+        opts.breakdown_tol = float(breakdown_tol)
+        opts.flags = 0 if use_graph else L.FLAG_NO_GRAPH
+        info = L.Info()
+        rho = np.zeros(m * (max_restarts + 1) + 1)
+        info.rho_hist = rho.ctypes.data_as(C.POINTER(C.c_double))
+        gcv = np.zeros(L.MAX_MU)
+        info.gcv = gcv.ctypes.data_as(C.POINTER(C.c_double))
+        L.check(self.lib.rtg_gmres_solve(self._h, a, na, b, nb, _shape(dims), dt, _ptr(C_obs), int(m),
+                                         sk, C.c_uint64(seed), float(lam), _ptr(X0), _ptr(X),
+                                         C.byref(opts), C.byref(info), _stream(stream)))
+        res = SolveResult(info.iters, info.restarts, bool(info.breakdown), bool(info.converged),
+                          info.beta, info.mu, info.rho_final, rho[:info.iters].copy(),
+                          gcv[:len(grid)].copy() if (grid is not None and lam < 0) else None,
+                          info.elapsed_ms, info.device_status, info.launches)
+        return X, res
+
+
+class Krylov:
+    """Caller-held sketched Arnoldi state (rtg_krylov_*)."""
+
+    def __init__(self, handle: Handle, dims: Sequence[int], dtype, m: int,
+                 sketch_dims: Sequence[int], seed: int, A_factors: Sequence[Factor] = (),
+                 B_factors: Sequence[Factor] = (), problem_id: int = 0):
+        torch = _torch()
+        self.h = handle
+        self.dims = tuple(dims)
+        self.dtype = dtype
+        self.m = m
+        code = L.F64 if dtype == torch.float64 else L.F32
+        a, na, ka = _factor_array(A_factors)
+        b, nb, kb = _factor_array(B_factors)
+        sk = (C.c_int64 * len(dims))(*[int(s) for s in sketch_dims])
+        k = C.c_void_p()
+        L.check(handle.lib.rtg_krylov_create(handle._h, a, na, b, nb, _shape(dims), code, int(m), sk,
+                                             C.c_uint64(seed), C.c_uint64(problem_id), C.byref(k)))
+        self._k = k
+        self.sdims = tuple(int(min(s, d)) for s, d in zip(sketch_dims, dims))
+
+    def close(self):
+        if getattr(self, "_k", None) is not None and self._k.value:
+            self.h.lib.rtg_krylov_destroy(self._k)
+            self._k = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def start(self, C_obs, X0=None, stream=None):
+        _check_tensor(C_obs, self.dims, "C")
+        L.check(self.h.lib.rtg_krylov_start(self.h._h, self._k, C_obs.data_ptr(),
+                                            None if X0 is None else X0.data_ptr(), _stream(stream)))
+
+    def step(self, stream=None):
+        L.check(self.h.lib.rtg_arnoldi_step(self.h._h, self._k, _stream(stream)))
+
+    def query(self, stream=None):
+        """(view, Hbar as (m+1) x m numpy array)."""
+        v = L.KrylovView()
+        H = np.zeros((self.m + 1) * self.m)
+        L.check(self.h.lib.rtg_krylov_query(self.h._h, self._k, C.byref(v),
+                                            H.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
+        return v, H.reshape((self.m + 1, self.m), order="F")
+
+    def basis(self, count: Optional[int] = None):
+        """Views of the device basis V_0..V_{count-1} and sketches Q_0..Q_{count-1}."""
+        torch = _torch()
+        v, _ = self.query()
+        count = v.j + 1 if count is None else count
+        elt = 8 if self.dtype == torch.float64 else 4
+        n, d = v.n, v.sketch_size
+        Vs, Qs = [], []
+        for i in range(count):
+            Vs.append(_wrap(v.V + i * n * elt, self.dims, self.dtype, self.h.device))
+            Qs.append(_wrap(v.Q + i * d * elt, self.sdims, self.dtype, self.h.device))
+        return Vs, Qs
+
+
+class _DeviceRange:
+    """Minimal __cuda_array_interface__ exporter for a range of library memory."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def _wrap(ptr: int, dims, dtype, device):
+    """Copy a device range into a new column-major tensor (no aliasing of library memory)."""
+    torch = _torch()
+    n = int(np.prod(dims))
+    typestr = "<f8" if dtype == torch.float64 else "<f4"
+    flat = torch.as_tensor(_DeviceRange(ptr, n, typestr), device=f"cuda:{device}").clone()
+    return flat.reshape(tuple(reversed(dims))).permute(*reversed(range(len(dims))))

@@ -1,0 +1,278 @@
+// Operator apply Y = alpha * Phi(X) + beta * Z for the separable Einstein
+// product Phi(X) = A *_N X (*_M B) (Section 1; Eq. 56-57 with zero
+// boundary conditions).  Phi is a list of mode products with banded
+// Toeplitz or dense matrices.
+//
+// Fused path (one HBM pass): a CTA owns a 64 x 16 tile of modes 1-2 for
+// up to four channels of mode 3.  Per channel it stages the halo tile in
+// shared memory, filters along mode 1 into a second shared tile, then
+// along mode 2 into registers; the mode-3 matrix mixes the channels in
+// registers before the single store.  Unfused path: one kernel per mode
+// product, ping-ponging through scratch tensors.
+#include "rtg_internal.cuh"
+
+namespace rtg {
+
+constexpr int FTX = 64;
+constexpr int FTY = 16;
+constexpr int FTHREADS = 256;
+
+struct FusedArgs {
+  int64_t I1, I2;
+  int64_t nslab;               // independent slabs of nc channels
+  int r1, r2;
+  int nc;
+  double t1[kMaxTaps], t2[kMaxTaps];
+  double M[kMaxMix * kMaxMix]; // M[p + nc*c]
+  double alpha, beta;
+};
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(FTHREADS)
+k_apply_fused(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
+  if (stop != nullptr && *stop) return;
+  const T* __restrict__ X = Xr.get<const T>();
+  T* __restrict__ Y = Yr.get<T>();
+  const T* __restrict__ Z = Zr.get<const T>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T t1s[kMaxTaps], t2s[kMaxTaps];
+  const int Wd = FTX + 2 * a.r1;
+  const int Ht = FTY + 2 * a.r2;
+  T* in_s = reinterpret_cast<T*>(smem_raw);
+  T* tmp = in_s + Ht * Wd;
+  for (int t = threadIdx.x; t <= 2 * a.r1; t += FTHREADS) t1s[t] = static_cast<T>(a.t1[t]);
+  for (int t = threadIdx.x; t <= 2 * a.r2; t += FTHREADS) t2s[t] = static_cast<T>(a.t2[t]);
+
+  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * FTX;
+  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * FTY;
+  const int64_t plane = a.I1 * a.I2;
+  const int tx = threadIdx.x & (FTX - 1);
+  const int ty = threadIdx.x / FTX;          // 0..3, rows ty + 4k
+  T acc[NC][FTY / 4];
+
+  for (int64_t slab = blockIdx.z; slab < a.nslab; slab += gridDim.z) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T* Xc = X + (slab * NC + c) * plane;
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < Ht * Wd; idx += FTHREADS) {
+        const int yy = idx / Wd, xx = idx - yy * Wd;
+        const int64_t gx = x0 - a.r1 + xx, gy = y0 - a.r2 + yy;
+        T v = 0;
+        if (gx >= 0 && gx < a.I1 && gy >= 0 && gy < a.I2) v = Xc[gy * a.I1 + gx];
+        in_s[idx] = v;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < Ht * FTX; idx += FTHREADS) {    // mode-1 filter
+        const int yy = idx / FTX, xx = idx - yy * FTX;
+        const T* row = in_s + yy * Wd + xx;
+        T s = 0;
+        for (int t = 0; t <= 2 * a.r1; ++t) s += t1s[t] * row[t];
+        tmp[idx] = s;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < FTY / 4; ++k) {                              // mode-2 filter
+        const T* col = tmp + (ty + 4 * k) * FTX + tx;
+        T s = 0;
+        for (int t = 0; t <= 2 * a.r2; ++t) s += t2s[t] * col[t * FTX];
+        acc[c][k] = s;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < FTY / 4; ++k) {                                // mode-3 mix + store
+      const int64_t gx = x0 + tx, gy = y0 + ty + 4 * k;
+      if (gx >= a.I1 || gy >= a.I2) continue;
+#pragma unroll
+      for (int p = 0; p < NC; ++p) {
+        T v = 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v += static_cast<T>(a.M[p + NC * c]) * acc[c][k];
+        const int64_t o = (slab * NC + p) * plane + gy * a.I1 + gx;
+        T out = static_cast<T>(a.alpha) * v;
+        if (Z != nullptr) out += static_cast<T>(a.beta) * Z[o];
+        Y[o] = out;
+      }
+    }
+  }
+}
+
+struct TapArgs {
+  double t[kMaxTaps];
+};
+
+// out(l, i, r) = sum_t taps[r+t] X(l, i+t, r), zero outside [0, I)
+template <typename T>
+__global__ void k_pass_band(PtrRef Xr, PtrRef Yr, int64_t L, int64_t I, int64_t R, int rad,
+                            TapArgs taps, const int* stop) {
+  if (stop != nullptr && *stop) return;
+  const T* __restrict__ X = Xr.get<const T>();
+  T* __restrict__ Y = Yr.get<T>();
+  const int64_t total = L * I * R;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = o % L;
+    const int64_t i = (o / L) % I;
+    const int64_t r = o / (L * I);
+    T s = 0;
+    for (int t = -rad; t <= rad; ++t) {
+      const int64_t ii = i + t;
+      if (ii >= 0 && ii < I) s += static_cast<T>(taps.t[rad + t]) * X[l + L * (ii + I * r)];
+    }
+    Y[o] = s;
+  }
+}
+
+// out(l, p, r) = sum_i M(p, i) X(l, i, r), M column-major on the device
+template <typename T>
+__global__ void k_pass_dense(PtrRef Xr, PtrRef Yr, int64_t L, int64_t I, int64_t R,
+                             const double* __restrict__ M, const int* stop) {
+  if (stop != nullptr && *stop) return;
+  const T* __restrict__ X = Xr.get<const T>();
+  T* __restrict__ Y = Yr.get<T>();
+  const int64_t total = L * I * R;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = o % L;
+    const int64_t p = (o / L) % I;
+    const int64_t r = o / (L * I);
+    T s = 0;
+    for (int64_t i = 0; i < I; ++i) s += static_cast<T>(M[p + I * i]) * X[l + L * (i + I * r)];
+    Y[o] = s;
+  }
+}
+
+// Y = alpha * A + beta * Z (Y may alias A)
+template <typename T>
+__global__ void k_axpby(PtrRef Ar, PtrRef Yr, PtrRef Zr, double alpha, double beta, int64_t n,
+                        const int* stop) {
+  if (stop != nullptr && *stop) return;
+  const T* A = Ar.get<const T>();
+  T* Y = Yr.get<T>();
+  const T* Z = Zr.get<const T>();
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    T v = static_cast<T>(alpha) * A[o];
+    if (Z != nullptr) v += static_cast<T>(beta) * Z[o];
+    Y[o] = v;
+  }
+}
+
+static unsigned grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 64) b = 152 * 64;
+  if (b < 1) b = 1;
+  return static_cast<unsigned>(b);
+}
+
+static size_t fused_smem(const OpPlan& op, size_t elem) {
+  const size_t Wd = FTX + 2 * op.r1, Ht = FTY + 2 * op.r2;
+  return (Ht * Wd + Ht * FTX) * elem;
+}
+
+int64_t apply_scratch_elems(const OpPlan& op) {
+  if (op.fused || op.npass <= 1) return 0;
+  int64_t n = 1;
+  for (int k = 0; k < op.order; ++k) n *= op.dims[k];
+  return n;
+}
+
+int apply_launches(const OpPlan& op, bool combine) {
+  if (op.fused || op.npass == 0) return 1;
+  return op.npass + (combine ? 1 : 0);
+}
+
+static bool has_ptr(const PtrRef& r) { return r.base != nullptr || r.ind != nullptr; }
+
+template <typename T>
+static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, double beta,
+                           PtrRef Z, T* tmp, T* tmp2, const int* stop, cudaStream_t s) {
+  int64_t n = 1;
+  for (int k = 0; k < op.order; ++k) n *= op.dims[k];
+  if (n == 0) return cudaSuccess;
+  if (op.fused) {
+    FusedArgs a{};
+    a.I1 = op.dims[0];
+    a.I2 = op.order > 1 ? op.dims[1] : 1;
+    const int64_t I3 = op.order > 2 ? op.dims[2] : 1;
+    int64_t rest = 1;
+    for (int k = 3; k < op.order; ++k) rest *= op.dims[k];
+    a.r1 = op.r1;
+    a.r2 = op.r2;
+    for (int t = 0; t <= 2 * op.r1; ++t) a.t1[t] = op.t1[t];
+    for (int t = 0; t <= 2 * op.r2; ++t) a.t2[t] = op.t2[t];
+    a.alpha = alpha;
+    a.beta = has_ptr(Z) ? beta : 0.0;
+    if (op.mix > 0) {
+      a.nc = op.mix;
+      a.nslab = rest;
+      for (int i = 0; i < op.mix * op.mix; ++i) a.M[i] = op.M3[i];
+    } else {
+      a.nc = 1;
+      a.nslab = I3 * rest;
+      a.M[0] = 1.0;
+    }
+    const size_t smem = fused_smem(op, sizeof(T));
+    dim3 grid(static_cast<unsigned>((a.I1 + FTX - 1) / FTX),
+              static_cast<unsigned>((a.I2 + FTY - 1) / FTY),
+              static_cast<unsigned>(a.nslab < 65535 ? a.nslab : 65535));
+    cudaError_t e = cudaSuccess;
+    switch (a.nc) {
+#define RTG_FUSED_CASE(NC)                                                                        \
+  case NC:                                                                                        \
+    e = cudaFuncSetAttribute(k_apply_fused<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                             static_cast<int>(smem));                                              \
+    if (e != cudaSuccess) return e;                                                               \
+    k_apply_fused<T, NC><<<grid, FTHREADS, smem, s>>>(X, Y, Z, stop, a);                          \
+    break;
+      RTG_FUSED_CASE(1)
+      RTG_FUSED_CASE(2)
+      RTG_FUSED_CASE(3)
+      RTG_FUSED_CASE(4)
+#undef RTG_FUSED_CASE
+      default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  // unfused: one kernel per mode product
+  if (op.npass == 0) {
+    k_axpby<T><<<grid_for(n, 256), 256, 0, s>>>(X, Y, Z, alpha, has_ptr(Z) ? beta : 0.0, n, stop);
+    return cudaGetLastError();
+  }
+  PtrRef src = X;
+  for (int p = 0; p < op.npass; ++p) {
+    const Pass& ps = op.pass[p];
+    PtrRef dst = (p == op.npass - 1) ? Y : ref((p % 2 == 0) ? tmp : tmp2);
+    int64_t L = 1, R = 1;
+    for (int k = 0; k < ps.mode; ++k) L *= op.dims[k];
+    for (int k = ps.mode + 1; k < op.order; ++k) R *= op.dims[k];
+    const int64_t I = op.dims[ps.mode];
+    if (ps.kind == PK_BAND) {
+      TapArgs ta{};
+      for (int t = 0; t <= 2 * ps.radius; ++t) ta.t[t] = ps.taps[t];
+      k_pass_band<T><<<grid_for(n, 256), 256, 0, s>>>(src, dst, L, I, R, ps.radius, ta, stop);
+    } else {
+      k_pass_dense<T><<<grid_for(n, 256), 256, 0, s>>>(src, dst, L, I, R, ps.dense, stop);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    src = dst;
+  }
+  if (alpha != 1.0 || has_ptr(Z)) {
+    k_axpby<T><<<grid_for(n, 256), 256, 0, s>>>(Y, Y, Z, alpha, has_ptr(Z) ? beta : 0.0, n, stop);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const OpPlan& op, int dtype, PtrRef X, PtrRef Y, double alpha,
+                         double beta, PtrRef Z, void* tmp, void* tmp2, const int* stop,
+                         cudaStream_t s) {
+  if (dtype == RTG_F64)
+    return apply_t<double>(op, X, Y, alpha, beta, Z, static_cast<double*>(tmp),
+                           static_cast<double*>(tmp2), stop, s);
+  return apply_t<float>(op, X, Y, alpha, beta, Z, static_cast<float*>(tmp),
+                        static_cast<float*>(tmp2), stop, s);
+}
+
+}  // namespace rtg

@@ -1,0 +1,223 @@
+// Reduced solves and solution assembly of RTG-GMRES.
+//
+// The Givens QR of the step kernels already holds Hbar_k = Omega^T [R; 0]
+// and Omega^T beta e1 = g, so
+//   ||beta e1 - Hbar y||^2 + mu ||y||^2 = ||g_{0:k} - R y||^2 + g_k^2 + mu ||y||^2.
+// Projected Tikhonov (Eq. 12S) is solved in the stacked form of Eq. 13,
+// min || [R; sqrt(mu) I] y - [g_{0:k}; 0] ||, by Householder reflections
+// that use the structure (column j touches row j of R and rows 0..j of the
+// sqrt(mu) I block), then back substitution.  GCV (Section 3, "Parameter
+// selection via GCV"): the numerator is ||Hbar y_mu - beta e1||^2; the
+// trace is tr(I - Hbar (Hbar^T Hbar + mu I)^{-1} Hbar^T) = 1 + mu ||R_mu^{-1}||_F^2
+// (k+1 minus k plus mu tr((R_mu^T R_mu)^{-1})).  One CTA per candidate mu;
+// the last CTA to finish picks the smallest GCV (ties: the larger mu).
+// Everything here is FP64.
+#include "rtg_internal.cuh"
+
+namespace rtg {
+
+constexpr int TK_THREADS = 128;
+
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int u = 0; u < (int)(blockDim.x >> 5); ++u) t += sh[u];
+  return t;
+}
+
+// Back substitution y = U^{-1} b for an upper-triangular k x k U (leading
+// dimension ldu), parallel over rows; b is overwritten.  Zero pivots give
+// y_i = 0 (the least-squares minimiser of smallest norm on that direction).
+__device__ void back_subst(const double* U, int ldu, double* b, double* y, int k) {
+  for (int i = k - 1; i >= 0; --i) {
+    __syncthreads();
+    const double piv = U[i + static_cast<int64_t>(ldu) * i];
+    const double yi = (piv != 0.0) ? b[i] / piv : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) y[i] = yi;
+    for (int t = threadIdx.x; t < i; t += blockDim.x) b[t] -= U[t + static_cast<int64_t>(ldu) * i] * yi;
+  }
+  __syncthreads();
+}
+
+// mode 0: least squares (mu = 0); 1: fixed mu = lambda; 2: GCV over the grid.
+// scratch: per block 2*m*m + 3*m doubles.
+__global__ void __launch_bounds__(TK_THREADS)
+k_tikhonov(Work w, const SolveDesc* desc, int mode, double* scratch) {
+  Ctl* ctl = w.ctl;
+  const int k = ctl->j;
+  const int m = w.m, ld = m + 1;
+  __shared__ double sh[32];
+  __shared__ int am_last;
+  if (k == 0) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) ctl->mu = (mode == 1) ? desc->lambda : 0.0;
+    return;
+  }
+  const double mu = (mode == 0) ? 0.0 : (mode == 1 ? desc->lambda : desc->mu_grid[blockIdx.x]);
+  double* Top = scratch + static_cast<int64_t>(blockIdx.x) * (2 * m * m + 3 * m);  // k x k, ld m
+  double* Bot = Top + m * m;                                                     // k x k, ld m
+  double* c = Bot + m * m;                                                       // k
+  double* y = c + m;                                                             // k
+  double* cb = y + m;                                                            // k
+  const double smu = sqrt(mu);
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    const int i = idx % k, j = idx / k;
+    Top[i + m * j] = (i <= j) ? w.R[i + static_cast<int64_t>(ld) * j] : 0.0;
+    Bot[i + m * j] = (i == j) ? smu : 0.0;
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    c[i] = w.g[i];
+    cb[i] = 0.0;
+  }
+  __syncthreads();
+  if (mode != 0) {
+    // Householder on column j: rows {j of Top} U {0..j of Bot}
+    for (int j = 0; j < k; ++j) {
+      double part = 0.0;
+      for (int i = threadIdx.x; i <= j; i += blockDim.x) part += Bot[i + m * j] * Bot[i + m * j];
+      const double sigma = block_sum(part, sh);
+      const double alpha = Top[j + m * j];
+      const double nrm = sqrt(alpha * alpha + sigma);
+      __syncthreads();
+      if (nrm != 0.0 && sigma != 0.0) {
+        const double sgn = (alpha >= 0.0) ? 1.0 : -1.0;
+        const double v0 = alpha + sgn * nrm;
+        const double tau = 2.0 / (v0 * v0 + sigma);
+        for (int col = j + 1 + threadIdx.x; col <= k; col += blockDim.x) {   // col == k: rhs
+          double* tc = (col < k) ? &Top[j + m * col] : &c[j];
+          double wdot = v0 * (*tc);
+          for (int i = 0; i <= j; ++i) wdot += Bot[i + m * j] * ((col < k) ? Bot[i + m * col] : cb[i]);
+          wdot *= tau;
+          *tc -= wdot * v0;
+          for (int i = 0; i <= j; ++i) {
+            if (col < k) Bot[i + m * col] -= wdot * Bot[i + m * j];
+            else cb[i] -= wdot * Bot[i + m * j];
+          }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) Top[j + m * j] = -sgn * nrm;
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) Bot[i + m * j] = 0.0;
+      }
+      __syncthreads();
+    }
+  }
+  back_subst(Top, m, c, y, k);
+  // residual ||g_{0:k} - R y||^2 + g_k^2
+  double part = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double r = w.g[i];
+    for (int j = i; j < k; ++j) r -= w.R[i + static_cast<int64_t>(ld) * j] * y[j];
+    part += r * r;
+  }
+  const double res2 = block_sum(part, sh) + w.g[k] * w.g[k];
+  if (mode == 2) {
+    // ||R_mu^{-1}||_F^2, one column of the inverse per thread (column stored in Bot)
+    double inv2 = 0.0;
+    for (int col = threadIdx.x; col < k; col += blockDim.x) {
+      double* z = Bot + m * col;
+      for (int i = col; i >= 0; --i) {
+        double acc = (i == col) ? 1.0 : 0.0;
+        for (int l = i + 1; l <= col; ++l) acc -= Top[i + m * l] * z[l];
+        z[i] = acc / Top[i + m * i];
+        inv2 += z[i] * z[i];
+      }
+    }
+    const double trace = 1.0 + mu * block_sum(inv2, sh);
+    const double gcv = res2 / (trace * trace);
+    if (threadIdx.x == 0) w.gcv[blockIdx.x] = gcv;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) w.ysel[static_cast<int64_t>(blockIdx.x) * m + i] = y[i];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicInc(w.counter, gridDim.x - 1) == gridDim.x - 1);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    __shared__ int best;
+    if (threadIdx.x == 0) {
+      int b = 0;
+      double bv = __ldcg(w.gcv), bm = desc->mu_grid[0];
+      for (unsigned u = 1; u < gridDim.x; ++u) {
+        const double v = __ldcg(w.gcv + u), mm = desc->mu_grid[u];
+        if (v < bv || (v == bv && mm > bm)) {
+          bv = v;
+          bm = mm;
+          b = static_cast<int>(u);
+        }
+      }
+      best = b;
+      ctl->mu = bm;
+      ctl->gcv_best = bv;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) w.y[i] = __ldcg(w.ysel + static_cast<int64_t>(best) * m + i);
+    return;
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) w.y[i] = y[i];
+  if (threadIdx.x == 0) ctl->mu = mu;
+}
+
+// X = X0 + sum_{i<k} y_i V_i  (Eq. 10S)
+template <typename T>
+__global__ void k_assemble(Work w, PtrRef X0r, PtrRef Xr) {
+  const int k = w.ctl->j;
+  __shared__ T ys[kMaxK];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = static_cast<T>(w.y[i]);
+  __syncthreads();
+  const T* X0 = X0r.get<const T>();
+  T* X = Xr.get<T>();
+  const T* V = static_cast<const T*>(w.V);
+  const int64_t n = w.n;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    T v = (X0 != nullptr) ? X0[o] : static_cast<T>(0);
+    for (int i = 0; i < k; ++i) v += ys[i] * V[static_cast<int64_t>(i) * n + o];
+    X[o] = v;
+  }
+}
+
+__global__ void k_finalize(Work w, InfoDev* info) {
+  const Ctl* c = w.ctl;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    info->iters = c->iters_total;
+    info->restarts = c->cycle;
+    info->breakdown = c->breakdown;
+    info->converged = c->converged;
+    info->status = c->status;
+    info->k = c->j;
+    info->beta = c->beta0;
+    info->mu = c->mu;
+    info->rho_final = c->rho;
+  }
+  for (int i = t; i < c->iters_total && i < kMaxK; i += blockDim.x) info->rho_hist[i] = w.rho_hist[i];
+  for (int i = t; i < kMaxMu; i += blockDim.x) info->gcv[i] = w.gcv[i];
+}
+
+static unsigned ew_grid(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return static_cast<unsigned>(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s) {
+  const unsigned blocks = (f.mode == 2) ? static_cast<unsigned>(f.n_mu) : 1u;
+  k_tikhonov<<<blocks, TK_THREADS, 0, s>>>(w, f.desc, f.mode, w.ysel + kMaxMu * w.m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const Work& w, PtrRef X0, PtrRef X, cudaStream_t s) {
+  if (w.dtype == RTG_F64) k_assemble<double><<<ew_grid(w.n), 256, 0, s>>>(w, X0, X);
+  else k_assemble<float><<<ew_grid(w.n), 256, 0, s>>>(w, X0, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Work& w, InfoDev* info, cudaStream_t s) {
+  k_finalize<<<1, 256, 0, s>>>(w, info);
+  return cudaGetLastError();
+}
+
+}  // namespace rtg

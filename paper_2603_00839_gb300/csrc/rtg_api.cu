@@ -1,0 +1,976 @@
+// C ABI of librtg (declared in include/rtg.h): handles, argument
+// validation, operator and sketch plans, the Krylov state, and the solve,
+// which runs as one CUDA graph per configuration: prologue (sketch signs,
+// R_0, beta), a device-controlled WHILE node whose body is one sketched
+// Arnoldi step, and the epilogue (Tikhonov/GCV, assembly, summary).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "rtg_internal.cuh"
+
+using namespace rtg;
+
+namespace rtg {
+int gs_grid(int64_t d);
+}
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+rtg_status fail(rtg_status st, const char* fmt, ...) {
+  char buf[768];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+rtg_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(RTG_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+#define RK(call)                        \
+  do {                                  \
+    rtg_status s_ = (call);             \
+    if (s_ != RTG_OK) return s_;        \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  rtg_status ensure(size_t b) {
+    if (b <= bytes && p) return RTG_OK;
+    if (p) {
+      cudaDeviceSynchronize();
+      release();
+    }
+    if (b == 0) return RTG_OK;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return fail(RTG_ERR_ALLOC, "cudaMalloc(%zu bytes) failed: %s", b, cudaGetErrorString(e));
+    }
+    bytes = b;
+    return RTG_OK;
+  }
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+size_t elt_size(int dtype) { return dtype == RTG_F64 ? 8 : 4; }
+
+// ------------------------------------------------------------------ operator plans
+
+struct OpHolder {
+  OpPlan op{};
+  std::vector<std::unique_ptr<DevBuf>> dense;
+};
+
+rtg_status check_shape(const rtg_shape& sh, int64_t* n_out) {
+  if (sh.order < 1 || sh.order > kMaxOrder) return fail(RTG_ERR_INVALID_ARG, "shape.order=%d not in 1..%d", sh.order, kMaxOrder);
+  int64_t n = 1;
+  for (int k = 0; k < sh.order; ++k) {
+    if (sh.dims[k] < 1) return fail(RTG_ERR_INVALID_ARG, "shape.dims[%d]=%lld must be >= 1", k, (long long)sh.dims[k]);
+    if (n > (int64_t(1) << 40) / sh.dims[k]) return fail(RTG_ERR_INVALID_ARG, "tensor too large");
+    n *= sh.dims[k];
+  }
+  *n_out = n;
+  return RTG_OK;
+}
+
+rtg_status check_dtype(rtg_dtype dt) {
+  if (dt == RTG_F64 || dt == RTG_F32) return RTG_OK;
+  if (dt == RTG_BF16) return fail(RTG_ERR_UNSUPPORTED, "dtype RTG_BF16 is not supported by this call");
+  return fail(RTG_ERR_INVALID_ARG, "unknown dtype %d", (int)dt);
+}
+
+rtg_status check_factors(const rtg_factor* f, int nf, const rtg_shape& sh, const char* which) {
+  if (nf < 0) return fail(RTG_ERR_INVALID_ARG, "%s count %d < 0", which, nf);
+  if (nf > 0 && f == nullptr) return fail(RTG_ERR_INVALID_ARG, "%s is NULL with count %d", which, nf);
+  for (int i = 0; i < nf; ++i) {
+    const rtg_factor& x = f[i];
+    if (x.mode < 1 || x.mode > sh.order) return fail(RTG_ERR_INVALID_ARG, "%s[%d].mode=%d outside 1..%d", which, i, x.mode, sh.order);
+    if (x.n != sh.dims[x.mode - 1]) return fail(RTG_ERR_INVALID_ARG, "%s[%d].n=%d but dims[%d]=%lld", which, i, x.n, x.mode - 1, (long long)sh.dims[x.mode - 1]);
+    if (x.kind == RTG_FACTOR_IDENTITY) continue;
+    if (x.kind == RTG_FACTOR_BANDED_TOEPLITZ) {
+      if (x.radius < 0 || x.radius > kMaxRadius) return fail(RTG_ERR_INVALID_ARG, "%s[%d].radius=%d outside 0..%d", which, i, x.radius, kMaxRadius);
+      if (x.taps == nullptr) return fail(RTG_ERR_INVALID_ARG, "%s[%d].taps is NULL", which, i);
+      for (int t = 0; t <= 2 * x.radius; ++t)
+        if (!std::isfinite(x.taps[t])) return fail(RTG_ERR_INVALID_ARG, "%s[%d].taps[%d] is not finite", which, i, t);
+      continue;
+    }
+    if (x.kind == RTG_FACTOR_DENSE) {
+      if (x.dense == nullptr) return fail(RTG_ERR_INVALID_ARG, "%s[%d].dense is NULL", which, i);
+      if (x.n > 4096) return fail(RTG_ERR_UNSUPPORTED, "%s[%d]: dense factor of size %d > 4096", which, i, x.n);
+      for (int64_t t = 0; t < int64_t(x.n) * x.n; ++t)
+        if (!std::isfinite(x.dense[t])) return fail(RTG_ERR_INVALID_ARG, "%s[%d].dense has a non-finite entry", which, i);
+      continue;
+    }
+    return fail(RTG_ERR_INVALID_ARG, "%s[%d].kind=%d unknown", which, i, x.kind);
+  }
+  return RTG_OK;
+}
+
+void append_bytes(std::string& k, const void* p, size_t n) { k.append(static_cast<const char*>(p), n); }
+
+std::string op_key(const rtg_factor* A, int nA, const rtg_factor* B, int nB, const rtg_shape& sh) {
+  std::string k;
+  append_bytes(k, &sh.order, sizeof sh.order);
+  append_bytes(k, sh.dims, sizeof(int64_t) * sh.order);
+  for (int side = 0; side < 2; ++side) {
+    const rtg_factor* f = side ? B : A;
+    const int nf = side ? nB : nA;
+    k.push_back(side ? 'B' : 'A');
+    for (int i = 0; i < nf; ++i) {
+      append_bytes(k, &f[i].mode, sizeof(int32_t));
+      append_bytes(k, &f[i].kind, sizeof(int32_t));
+      append_bytes(k, &f[i].n, sizeof(int32_t));
+      if (f[i].kind == RTG_FACTOR_BANDED_TOEPLITZ) {
+        append_bytes(k, &f[i].radius, sizeof(int32_t));
+        append_bytes(k, f[i].taps, sizeof(double) * (2 * f[i].radius + 1));
+      } else if (f[i].kind == RTG_FACTOR_DENSE) {
+        append_bytes(k, f[i].dense, sizeof(double) * size_t(f[i].n) * f[i].n);
+      }
+    }
+  }
+  return k;
+}
+
+// Mode products in application order: left factors, then right factors
+// (a right factor B acts as the mode matrix B^T; for banded B the taps reverse).
+rtg_status build_op(const rtg_factor* A, int nA, const rtg_factor* B, int nB, const rtg_shape& sh,
+                    OpHolder& H) {
+  OpPlan& op = H.op;
+  op = OpPlan{};
+  op.order = sh.order;
+  for (int k = 0; k < sh.order; ++k) op.dims[k] = sh.dims[k];
+  for (int side = 0; side < 2; ++side) {
+    const rtg_factor* f = side ? B : A;
+    const int nf = side ? nB : nA;
+    for (int i = 0; i < nf; ++i) {
+      const rtg_factor& x = f[i];
+      if (x.kind == RTG_FACTOR_IDENTITY) continue;
+      if (op.npass >= kMaxPasses) return fail(RTG_ERR_UNSUPPORTED, "more than %d non-identity factors", kMaxPasses);
+      Pass& p = op.pass[op.npass++];
+      p = Pass{};
+      p.mode = x.mode - 1;
+      p.n = x.n;
+      if (x.kind == RTG_FACTOR_BANDED_TOEPLITZ) {
+        p.kind = PK_BAND;
+        p.radius = x.radius;
+        for (int t = 0; t <= 2 * x.radius; ++t) p.taps[t] = side ? x.taps[2 * x.radius - t] : x.taps[t];
+      } else {
+        p.kind = PK_DENSE;
+        std::vector<double> M(size_t(x.n) * x.n);
+        for (int i2 = 0; i2 < x.n; ++i2)
+          for (int j2 = 0; j2 < x.n; ++j2)
+            M[i2 + size_t(x.n) * j2] = side ? x.dense[j2 + size_t(x.n) * i2] : x.dense[i2 + size_t(x.n) * j2];
+        auto buf = std::make_unique<DevBuf>();
+        RK(buf->ensure(M.size() * sizeof(double)));
+        CK(cudaMemcpy(buf->p, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice));
+        p.dense = static_cast<const double*>(buf->p);
+        H.dense.push_back(std::move(buf));
+        // keep a host copy for the fused kernel's mode-3 matrix
+        if (p.mode == 2 && x.n <= kMaxMix)
+          for (size_t q = 0; q < M.size(); ++q) op.M3[q] = M[q];
+      }
+    }
+  }
+  // fused pattern: <= 1 banded pass on modes 1 and 2, <= 1 pass on mode 3
+  // (dense or banded, size <= kMaxMix unless absent), none above
+  int cnt[kMaxOrder] = {0, 0, 0, 0};
+  bool ok = true;
+  for (int p = 0; p < op.npass; ++p) {
+    const Pass& ps = op.pass[p];
+    cnt[ps.mode]++;
+    if (ps.mode >= 3) ok = false;
+    if (ps.mode <= 1 && ps.kind != PK_BAND) ok = false;
+    if (ps.mode == 2 && ps.n > kMaxMix) ok = false;
+  }
+  for (int k = 0; k < 3; ++k)
+    if (cnt[k] > 1) ok = false;
+  int64_t nslab = 1;
+  for (int k = 2; k < op.order; ++k) nslab *= op.dims[k];
+  if (op.order >= 2 && op.dims[1] > 65535LL * 16) ok = false;
+  op.fused = ok;
+  if (ok) {
+    op.r1 = op.r2 = 0;
+    op.t1[0] = op.t2[0] = 1.0;
+    op.mix = 0;
+    for (int p = 0; p < op.npass; ++p) {
+      const Pass& ps = op.pass[p];
+      if (ps.mode == 0) {
+        op.r1 = ps.radius;
+        for (int t = 0; t <= 2 * ps.radius; ++t) op.t1[t] = ps.taps[t];
+      } else if (ps.mode == 1) {
+        op.r2 = ps.radius;
+        for (int t = 0; t <= 2 * ps.radius; ++t) op.t2[t] = ps.taps[t];
+      } else {
+        const int nn = ps.n;
+        op.mix = nn;
+        if (ps.kind == PK_BAND) {
+          for (int pp = 0; pp < nn; ++pp)
+            for (int c = 0; c < nn; ++c) {
+              const int t = c - pp;
+              op.M3[pp + nn * c] = (t >= -ps.radius && t <= ps.radius) ? ps.taps[ps.radius + t] : 0.0;
+            }
+        }
+      }
+    }
+  }
+  (void)nslab;
+  return RTG_OK;
+}
+
+// ------------------------------------------------------------------ sketch plans
+
+rtg_status build_sketch(const rtg_shape& sh, const int64_t* sdims, uint64_t seed, uint64_t pid,
+                        SketchPlan& sp) {
+  if (sdims == nullptr) return fail(RTG_ERR_INVALID_ARG, "sketch_dims is NULL");
+  sp = SketchPlan{};
+  sp.order = sh.order;
+  sp.seed = seed;
+  sp.pid = pid;
+  int64_t bit = 0, word = 0, d = 1;
+  double scale = 1.0;
+  for (int k = 0; k < sh.order; ++k) {
+    if (sdims[k] < 1) return fail(RTG_ERR_INVALID_ARG, "sketch_dims[%d]=%lld must be >= 1", k, (long long)sdims[k]);
+    sp.dims[k] = sh.dims[k];
+    if (sdims[k] < sh.dims[k]) {
+      sp.sketched[k] = 1;
+      sp.sdims[k] = sdims[k];
+      sp.bit_off[k] = bit;
+      sp.word_off[k] = word;
+      sp.wpr[k] = static_cast<int>((sh.dims[k] + 31) / 32);
+      bit += sdims[k] * sh.dims[k];
+      word += sdims[k] * sp.wpr[k];
+      scale /= std::sqrt(static_cast<double>(sdims[k]));
+    } else {
+      sp.sketched[k] = 0;
+      sp.sdims[k] = sh.dims[k];
+    }
+    d *= sp.sdims[k];
+  }
+  sp.total_words = word;
+  sp.d = d;
+  sp.scale = scale;
+  // largest intermediate of the contraction chain (all but the last output)
+  int64_t cur[kMaxOrder];
+  for (int k = 0; k < sh.order; ++k) cur[k] = sh.dims[k];
+  int last = -1;
+  for (int k = 0; k < sh.order; ++k)
+    if (sp.sketched[k]) last = k;
+  int64_t tmx = 1;
+  for (int k = 0; k < sh.order; ++k) {
+    if (!sp.sketched[k]) continue;
+    cur[k] = sp.sdims[k];
+    if (k == last) break;
+    int64_t sz = 1;
+    for (int u = 0; u < sh.order; ++u) sz *= cur[u];
+    if (sz > tmx) tmx = sz;
+  }
+  sp.tmp_elems = tmx;
+  if (d > (int64_t(1) << 31) - 1) return fail(RTG_ERR_UNSUPPORTED, "sketch size %lld too large", (long long)d);
+  return RTG_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a{};
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + bytes && y < x + bytes;
+}
+
+// ------------------------------------------------------------------ workspace
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Lays out (and, with mem != null, points) every buffer of an Arnoldi workspace.
+size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, int tk_blocks,
+                  int64_t apply_elems, Work& w, void** tA, void** tB, uint32_t** bits) {
+  Carver c(mem);
+  const size_t e = elt_size(dtype);
+  const int64_t d = sp.d;
+  w = Work{};
+  w.dtype = dtype;
+  w.n = n;
+  w.d = static_cast<int>(d);
+  w.m = m;
+  const int G = gs_grid(d);
+  w.V = c.take<char>(size_t(m + 1) * n * e);
+  w.W = c.take<char>(size_t(n) * e);
+  w.S = c.take<char>(size_t(d) * e);
+  w.tmp0 = c.take<char>(size_t(sp.tmp_elems) * e);
+  w.tmp1 = c.take<char>(size_t(sp.tmp_elems) * e);
+  w.Q = c.take<char>(size_t(m + 1) * d * e);
+  w.part = c.take<double>(size_t(G) * (m + 2));
+  w.part_rows = G;
+  w.counter = c.take<unsigned>(8);
+  w.ctl = c.take<Ctl>(1);
+  w.H = c.take<double>(size_t(m + 1) * m);
+  w.R = c.take<double>(size_t(m + 1) * m);
+  w.cs = c.take<double>(m);
+  w.sn = c.take<double>(m);
+  w.g = c.take<double>(m + 1);
+  w.h1 = c.take<double>(m + 1);
+  w.h2 = c.take<double>(m + 1);
+  w.rho_hist = c.take<double>(kMaxK);
+  w.y = c.take<double>(m);
+  w.gcv = c.take<double>(kMaxMu);
+  w.ysel = c.take<double>(size_t(kMaxMu) * m + size_t(tk_blocks) * (2 * size_t(m) * m + 3 * m));
+  *tA = c.take<char>(size_t(apply_elems) * e);
+  *tB = c.take<char>(size_t(apply_elems) * e);
+  *bits = c.take<uint32_t>(size_t(sp.total_words) + 1);
+  return c.off + 256;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+
+struct rtg_context;
+
+struct SolvePlan {
+  OpHolder op;
+  SketchPlan sp{};
+  DevBuf mem;
+  Work w{};
+  void* tA = nullptr;
+  void* tB = nullptr;
+  uint32_t* bits = nullptr;
+  SolveDesc* desc_dev = nullptr;
+  InfoDev* info_dev = nullptr;
+  SolveDesc* desc_host = nullptr;
+  InfoDev* info_host = nullptr;
+  DevBuf small;           // desc + info
+  DevBuf Cst, X0st, Xst;  // staging of host arrays
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int mode = 0;           // 0 LS, 1 fixed mu, 2 GCV
+  int n_mu = 0;
+  bool has_x0 = false;
+  bool use_graph = true;
+  bool true_resid = false;
+  int dtype = RTG_F32;
+  int launches_pro = 0, launches_step = 0, launches_epi = 0;   // kernels per phase
+  ~SolvePlan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (desc_host) cudaFreeHost(desc_host);
+    if (info_host) cudaFreeHost(info_host);
+  }
+};
+
+struct rtg_context {
+  int device = 0;
+  std::map<std::string, std::unique_ptr<OpHolder>> ops;
+  std::map<std::string, std::unique_ptr<DevBuf>> bits;
+  DevBuf tA, tB, t0, t1;
+  std::map<std::string, std::unique_ptr<SolvePlan>> plans;
+};
+
+struct rtg_krylov_state {
+  rtg_context* ctx = nullptr;
+  OpHolder op;
+  SketchPlan sp{};
+  DevBuf mem;
+  Work w{};
+  void* tA = nullptr;
+  void* tB = nullptr;
+  uint32_t* bits = nullptr;
+  int dtype = RTG_F32;
+  int m = 0;
+  bool started = false;
+};
+
+namespace {
+
+rtg_status get_op(rtg_context* h, const rtg_factor* A, int nA, const rtg_factor* B, int nB,
+                  const rtg_shape& sh, OpHolder** out) {
+  std::string key = op_key(A, nA, B, nB, sh);
+  auto it = h->ops.find(key);
+  if (it != h->ops.end()) {
+    *out = it->second.get();
+    return RTG_OK;
+  }
+  if (h->ops.size() > 64) {
+    cudaDeviceSynchronize();
+    h->ops.clear();
+  }
+  auto H = std::make_unique<OpHolder>();
+  RK(build_op(A, nA, B, nB, sh, *H));
+  *out = H.get();
+  h->ops[key] = std::move(H);
+  return RTG_OK;
+}
+
+StepOpts solve_step_opts(const SolvePlan& P, int use_cond, cudaGraphConditionalHandle hnd) {
+  StepOpts o{};
+  o.desc_tol = &P.desc_dev->tol;
+  o.desc_bd_tol = &P.desc_dev->bd_tol;
+  o.solve_mode = 1;
+  o.use_cond = use_cond;
+  o.cond = static_cast<unsigned long long>(hnd);
+  return o;
+}
+
+PtrRef desc_ref(const void* const* field) {
+  PtrRef r;
+  r.ind = field;
+  return r;
+}
+
+rtg_status enqueue_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s) {
+  Work& w = P.w;
+  CK(launch_reset(w, 0, s));
+  CK(launch_theta_bits(P.sp, P.bits, s));
+  PtrRef C = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->C));
+  PtrRef src = C;
+  if (P.has_x0) {   // R_0 = C - Phi(X_0) into the V_0 slot
+    PtrRef X0 = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X0));
+    CK(launch_apply(P.op.op, P.dtype, X0, ref(w.V), -1.0, 1.0, C, P.tA, P.tB, nullptr, s));
+    src = ref(w.V);
+  }
+  CK(launch_sketch(P.sp, P.dtype, P.bits, src, w.S, w.tmp0, w.tmp1, nullptr, s));
+  CK(launch_start(w, src, so, s));
+  return RTG_OK;
+}
+
+rtg_status enqueue_step(const OpHolder& op, const SketchPlan& sp, const Work& w, int dtype,
+                        void* tA, void* tB, const uint32_t* bits, const StepOpts& so,
+                        cudaStream_t s) {
+  PtrRef vj;
+  vj.base = w.V;
+  vj.jidx = &w.ctl->j;
+  vj.stride = w.n;
+  const int* stop = &w.ctl->stop;
+  CK(launch_apply(op.op, dtype, vj, ref(w.W), 1.0, 0.0, PtrRef{}, tA, tB, stop, s));
+  CK(launch_sketch(sp, dtype, bits, ref(w.W), w.S, w.tmp0, w.tmp1, stop, s));
+  CK(launch_pass1(w, s));
+  CK(launch_pass2(w, so, s));
+  CK(launch_update(w, so, s));
+  return RTG_OK;
+}
+
+rtg_status enqueue_epilogue(SolvePlan& P, cudaStream_t s) {
+  FinishOpts f{};
+  f.desc = P.desc_dev;
+  f.n_mu = P.n_mu;
+  f.mode = P.mode;
+  CK(launch_tikhonov(P.w, f, s));
+  PtrRef X0 = P.has_x0 ? desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X0)) : PtrRef{};
+  PtrRef X = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X));
+  CK(launch_assemble(P.w, X0, X, s));
+  CK(launch_finalize(P.w, P.info_dev, s));
+  return RTG_OK;
+}
+
+rtg_status build_graph(SolvePlan& P) {
+  cudaStream_t cs = nullptr, cs2 = nullptr;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
+  struct StreamGuard {
+    cudaStream_t a, b;
+    ~StreamGuard() {
+      cudaStreamDestroy(a);
+      cudaStreamDestroy(b);
+    }
+  } sg{cs, cs2};
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle hnd;
+  CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
+  const StepOpts so = solve_step_opts(P, 1, hnd);
+  CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  rtg_status st = enqueue_prologue(P, so, cs);
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t gcap = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (st == RTG_OK) {
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &gcap, &deps, nullptr, &nd);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamGetCaptureInfo");
+  }
+  cudaGraphNode_t cnode = nullptr;
+  cudaGraphNodeParams cp{};
+  if (st == RTG_OK) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaError_t e = cudaGraphAddNode(&cnode, gcap, deps, nullptr, nd, &cp);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphAddNode(conditional)");
+  }
+  if (st == RTG_OK) {
+    cudaError_t e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamUpdateCaptureDependencies");
+  }
+  if (st == RTG_OK) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCaptureToGraph(body)");
+    if (st == RTG_OK) {
+      st = enqueue_step(P.op, P.sp, P.w, P.dtype, P.tA, P.tB, P.bits, so, cs2);
+      cudaGraph_t bodyout = nullptr;
+      e = cudaStreamEndCapture(cs2, &bodyout);
+      if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture(body)");
+    }
+  }
+  if (st == RTG_OK) st = enqueue_epilogue(P, cs);
+  cudaGraph_t gout = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &gout);
+  if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture");
+  if (st != RTG_OK) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st;
+  }
+  P.graph = g;
+  CK(cudaGraphInstantiate(&P.exec, g, 0));
+  return RTG_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+
+extern "C" {
+
+const char* rtg_last_error(void) { return g_err.c_str(); }
+
+const char* rtg_status_string(rtg_status s) {
+  switch (s) {
+    case RTG_OK: return "RTG_OK";
+    case RTG_ERR_INVALID_ARG: return "RTG_ERR_INVALID_ARG";
+    case RTG_ERR_UNSUPPORTED: return "RTG_ERR_UNSUPPORTED";
+    case RTG_ERR_CUDA: return "RTG_ERR_CUDA";
+    case RTG_ERR_ALLOC: return "RTG_ERR_ALLOC";
+    case RTG_ERR_TIMEOUT: return "RTG_ERR_TIMEOUT";
+    case RTG_ERR_NONFINITE: return "RTG_ERR_NONFINITE";
+  }
+  return "RTG_UNKNOWN_STATUS";
+}
+
+int32_t rtg_version(void) { return 100; }
+
+rtg_status rtg_create(rtg_handle* handle, int device) {
+  if (handle == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
+  *handle = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "cudaGetDeviceCount");
+  }
+  if (device < 0 || device >= count) return fail(RTG_ERR_INVALID_ARG, "device %d not in 0..%d", device, count - 1);
+  DeviceGuard dg(device);
+  CK(cudaFree(nullptr));   // make sure the context exists
+  auto* ctx = new rtg_context();
+  ctx->device = device;
+  *handle = ctx;
+  return RTG_OK;
+}
+
+rtg_status rtg_destroy(rtg_handle handle) {
+  if (handle == nullptr) return RTG_OK;
+  DeviceGuard dg(handle->device);
+  cudaDeviceSynchronize();
+  delete handle;
+  return RTG_OK;
+}
+
+rtg_status rtg_philox_words(rtg_handle h, uint64_t seed, uint64_t pid, int64_t n_words,
+                            uint64_t* out, rtg_stream stream) {
+  if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
+  if (n_words < 0) return fail(RTG_ERR_INVALID_ARG, "n_words < 0");
+  if (n_words == 0) return RTG_OK;
+  DeviceGuard dg(h->device);
+  if (!is_device_ptr(out)) return fail(RTG_ERR_INVALID_ARG, "out is not a device pointer");
+  CK(launch_philox_words(seed, pid, n_words, out, reinterpret_cast<cudaStream_t>(stream)));
+  return RTG_OK;
+}
+
+rtg_status rtg_operator_apply(rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
+                              int32_t nB, rtg_shape shape, rtg_dtype dtype, const void* X,
+                              void* Y, rtg_stream stream) {
+  if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
+  int64_t n = 0;
+  RK(check_shape(shape, &n));
+  RK(check_dtype(dtype));
+  RK(check_factors(A, nA, shape, "A_factors"));
+  RK(check_factors(B, nB, shape, "B_factors"));
+  DeviceGuard dg(h->device);
+  if (!is_device_ptr(X) || !is_device_ptr(Y)) return fail(RTG_ERR_INVALID_ARG, "X and Y must be device pointers");
+  if (overlaps(X, Y, size_t(n) * elt_size(dtype))) return fail(RTG_ERR_INVALID_ARG, "Y overlaps X");
+  OpHolder* op = nullptr;
+  RK(get_op(h, A, nA, B, nB, shape, &op));
+  const int64_t sc = apply_scratch_elems(op->op);
+  RK(h->tA.ensure(size_t(sc) * elt_size(dtype)));
+  RK(h->tB.ensure(size_t(sc) * elt_size(dtype)));
+  CK(launch_apply(op->op, dtype, ref(X), ref(Y), 1.0, 0.0, PtrRef{}, h->tA.p, h->tB.p, nullptr,
+                  reinterpret_cast<cudaStream_t>(stream)));
+  return RTG_OK;
+}
+
+rtg_status rtg_sketch(rtg_handle h, rtg_shape shape, rtg_dtype dtype, const int64_t* sketch_dims,
+                      uint64_t seed, uint64_t pid, const void* X, void* SX, rtg_stream stream) {
+  if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
+  int64_t n = 0;
+  RK(check_shape(shape, &n));
+  RK(check_dtype(dtype));
+  SketchPlan sp;
+  RK(build_sketch(shape, sketch_dims, seed, pid, sp));
+  DeviceGuard dg(h->device);
+  if (!is_device_ptr(X) || !is_device_ptr(SX)) return fail(RTG_ERR_INVALID_ARG, "X and SX must be device pointers");
+  if (overlaps(X, SX, size_t(std::max<int64_t>(n, sp.d)) * elt_size(dtype)) && X == SX)
+    return fail(RTG_ERR_INVALID_ARG, "SX must not alias X");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::string key;
+  append_bytes(key, &sp.order, sizeof sp.order);
+  append_bytes(key, sp.dims, sizeof sp.dims);
+  append_bytes(key, sp.sdims, sizeof sp.sdims);
+  append_bytes(key, &seed, sizeof seed);
+  append_bytes(key, &pid, sizeof pid);
+  auto it = h->bits.find(key);
+  DevBuf* bits = nullptr;
+  if (it == h->bits.end()) {
+    if (h->bits.size() > 64) {
+      cudaDeviceSynchronize();
+      h->bits.clear();
+    }
+    auto b = std::make_unique<DevBuf>();
+    RK(b->ensure(size_t(sp.total_words + 1) * sizeof(uint32_t)));
+    CK(launch_theta_bits(sp, static_cast<uint32_t*>(b->p), s));
+    bits = b.get();
+    h->bits[key] = std::move(b);
+  } else {
+    bits = it->second.get();
+  }
+  RK(h->t0.ensure(size_t(sp.tmp_elems) * elt_size(dtype)));
+  RK(h->t1.ensure(size_t(sp.tmp_elems) * elt_size(dtype)));
+  CK(launch_sketch(sp, dtype, static_cast<const uint32_t*>(bits->p), ref(X), SX, h->t0.p, h->t1.p,
+                   nullptr, s));
+  return RTG_OK;
+}
+
+rtg_status rtg_krylov_create(rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
+                             int32_t nB, rtg_shape shape, rtg_dtype dtype, int32_t m,
+                             const int64_t* sketch_dims, uint64_t seed, uint64_t pid,
+                             rtg_krylov* out) {
+  if (h == nullptr || out == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle or krylov is NULL");
+  *out = nullptr;
+  int64_t n = 0;
+  RK(check_shape(shape, &n));
+  RK(check_dtype(dtype));
+  RK(check_factors(A, nA, shape, "A_factors"));
+  RK(check_factors(B, nB, shape, "B_factors"));
+  if (m < 1 || m > kMaxK) return fail(RTG_ERR_INVALID_ARG, "m=%d not in 1..%d", m, kMaxK);
+  DeviceGuard dg(h->device);
+  auto K = std::make_unique<rtg_krylov_state>();
+  K->ctx = h;
+  K->dtype = dtype;
+  K->m = m;
+  RK(build_op(A, nA, B, nB, shape, K->op));
+  RK(build_sketch(shape, sketch_dims, seed, pid, K->sp));
+  const int64_t ae = apply_scratch_elems(K->op.op);
+  Work tmpw;
+  void *ta, *tb;
+  uint32_t* bits;
+  const size_t bytes = carve_work(nullptr, dtype, n, K->sp, m, 1, ae, tmpw, &ta, &tb, &bits);
+  RK(K->mem.ensure(bytes));
+  CK(cudaMemset(K->mem.p, 0, bytes));
+  carve_work(K->mem.p, dtype, n, K->sp, m, 1, ae, K->w, &K->tA, &K->tB, &K->bits);
+  CK(launch_theta_bits(K->sp, K->bits, nullptr));
+  CK(cudaDeviceSynchronize());
+  *out = K.release();
+  return RTG_OK;
+}
+
+rtg_status rtg_krylov_destroy(rtg_krylov K) {
+  if (K == nullptr) return RTG_OK;
+  DeviceGuard dg(K->ctx->device);
+  cudaDeviceSynchronize();
+  delete K;
+  return RTG_OK;
+}
+
+rtg_status rtg_krylov_start(rtg_handle h, rtg_krylov K, const void* C, const void* X0,
+                            rtg_stream stream) {
+  if (h == nullptr || K == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle or krylov is NULL");
+  DeviceGuard dg(h->device);
+  if (!is_device_ptr(C)) return fail(RTG_ERR_INVALID_ARG, "C must be a device pointer");
+  if (X0 != nullptr && !is_device_ptr(X0)) return fail(RTG_ERR_INVALID_ARG, "X0 must be a device pointer or NULL");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Work& w = K->w;
+  CK(launch_reset(w, 0, s));
+  PtrRef src = ref(C);
+  if (X0 != nullptr) {
+    CK(launch_apply(K->op.op, K->dtype, ref(X0), ref(w.V), -1.0, 1.0, ref(C), K->tA, K->tB, nullptr, s));
+    src = ref(w.V);
+  }
+  CK(launch_sketch(K->sp, K->dtype, K->bits, src, w.S, w.tmp0, w.tmp1, nullptr, s));
+  StepOpts o{};
+  o.tol = 0.0;
+  o.bd_tol = K->dtype == RTG_F64 ? 1e-12 : 1e-6;
+  CK(launch_start(w, src, o, s));
+  K->started = true;
+  return RTG_OK;
+}
+
+rtg_status rtg_arnoldi_step(rtg_handle h, rtg_krylov K, rtg_stream stream) {
+  if (h == nullptr || K == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle or krylov is NULL");
+  if (!K->started) return fail(RTG_ERR_INVALID_ARG, "rtg_krylov_start has not been called");
+  DeviceGuard dg(h->device);
+  StepOpts o{};
+  o.tol = 0.0;
+  o.bd_tol = K->dtype == RTG_F64 ? 1e-12 : 1e-6;
+  o.solve_mode = 0;
+  return enqueue_step(K->op, K->sp, K->w, K->dtype, K->tA, K->tB, K->bits, o,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+rtg_status rtg_krylov_query(rtg_handle h, rtg_krylov K, rtg_krylov_view* view, double* H,
+                            rtg_stream stream) {
+  if (h == nullptr || K == nullptr || view == nullptr) return fail(RTG_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Ctl c{};
+  CK(cudaMemcpyAsync(&c, K->w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  if (H != nullptr)
+    CK(cudaMemcpyAsync(H, K->w.H, sizeof(double) * size_t(K->m + 1) * K->m, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  view->j = c.j;
+  view->m = K->m;
+  view->breakdown = c.breakdown;
+  view->sketch_size = K->w.d;
+  view->n = K->w.n;
+  view->beta = c.beta;
+  view->rho = c.rho;
+  view->V = K->w.V;
+  view->Q = K->w.Q;
+  return RTG_OK;
+}
+
+rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
+                           int32_t nB, rtg_shape shape, rtg_dtype dtype, const void* C, int32_t m,
+                           const int64_t* sketch_dims, uint64_t seed, double lambda, const void* X0,
+                           void* X, const rtg_opts* opts_in, rtg_info* info, rtg_stream stream) {
+  if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
+  int64_t n = 0;
+  RK(check_shape(shape, &n));
+  RK(check_dtype(dtype));
+  RK(check_factors(A, nA, shape, "A_factors"));
+  RK(check_factors(B, nB, shape, "B_factors"));
+  if (m < 1 || m > kMaxK) return fail(RTG_ERR_INVALID_ARG, "m=%d not in 1..%d", m, kMaxK);
+  if (C == nullptr || X == nullptr) return fail(RTG_ERR_INVALID_ARG, "C and X must not be NULL");
+  if (!std::isfinite(lambda)) return fail(RTG_ERR_INVALID_ARG, "lambda is not finite");
+  rtg_opts opts{};
+  if (opts_in) opts = *opts_in;
+  if (!(opts.tol >= 0.0) || !std::isfinite(opts.tol)) return fail(RTG_ERR_INVALID_ARG, "opts.tol must be finite and >= 0");
+  if (opts.max_restarts != 0) return fail(RTG_ERR_UNSUPPORTED, "restarts are not supported on the GPU path (max_restarts=%d)", opts.max_restarts);
+  if (!(opts.breakdown_tol >= 0.0)) return fail(RTG_ERR_INVALID_ARG, "opts.breakdown_tol must be >= 0");
+  const int mode = lambda > 0 ? 1 : (lambda == 0 ? 0 : 2);
+  if (mode == 2) {
+    if (opts.n_mu < 1 || opts.n_mu > kMaxMu || opts.mu_grid == nullptr)
+      return fail(RTG_ERR_INVALID_ARG, "lambda < 0 needs opts.mu_grid with 1..%d values", kMaxMu);
+    for (int i = 0; i < opts.n_mu; ++i)
+      if (!(opts.mu_grid[i] > 0.0) || !std::isfinite(opts.mu_grid[i])) return fail(RTG_ERR_INVALID_ARG, "mu_grid[%d] must be finite and > 0", i);
+  }
+  DeviceGuard dg(h->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bytes_t = size_t(n) * elt_size(dtype);
+  const bool C_dev = is_device_ptr(C), X_dev = is_device_ptr(X);
+  const bool X0_dev = X0 != nullptr && is_device_ptr(X0);
+  if (X0 != nullptr && X0 != X && overlaps(X0, X, bytes_t)) return fail(RTG_ERR_INVALID_ARG, "X partially overlaps X0");
+  if (overlaps(C, X, bytes_t)) return fail(RTG_ERR_INVALID_ARG, "X overlaps C");
+
+  SketchPlan sp;
+  RK(build_sketch(shape, sketch_dims, seed, 0, sp));
+  const bool use_graph = !(opts.flags & RTG_FLAG_NO_GRAPH);
+  std::string key = op_key(A, nA, B, nB, shape);
+  append_bytes(key, &dtype, sizeof dtype);
+  append_bytes(key, &m, sizeof m);
+  append_bytes(key, sp.sdims, sizeof sp.sdims);
+  append_bytes(key, &seed, sizeof seed);
+  const int nmu_key = mode == 2 ? opts.n_mu : 0;
+  append_bytes(key, &mode, sizeof mode);
+  append_bytes(key, &nmu_key, sizeof nmu_key);
+  const bool has_x0 = X0 != nullptr;
+  key.push_back(has_x0 ? '1' : '0');
+  key.push_back(use_graph ? 'g' : 'd');
+
+  auto it = h->plans.find(key);
+  SolvePlan* P = nullptr;
+  if (it == h->plans.end()) {
+    if (h->plans.size() >= 8) {
+      cudaDeviceSynchronize();
+      h->plans.clear();
+    }
+    auto np = std::make_unique<SolvePlan>();
+    P = np.get();
+    P->dtype = dtype;
+    P->mode = mode;
+    P->n_mu = nmu_key;
+    P->has_x0 = has_x0;
+    P->use_graph = use_graph;
+    P->sp = sp;
+    RK(build_op(A, nA, B, nB, shape, P->op));
+    const int64_t ae = apply_scratch_elems(P->op.op);
+    const int tkb = mode == 2 ? opts.n_mu : 1;
+    Work tmpw;
+    void *ta, *tb;
+    uint32_t* bits;
+    const size_t bytes = carve_work(nullptr, dtype, n, sp, m, tkb, ae, tmpw, &ta, &tb, &bits);
+    RK(P->mem.ensure(bytes));
+    CK(cudaMemset(P->mem.p, 0, bytes));
+    carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->bits);
+    RK(P->small.ensure(sizeof(SolveDesc) + sizeof(InfoDev) + 512));
+    P->desc_dev = static_cast<SolveDesc*>(P->small.p);
+    P->info_dev = reinterpret_cast<InfoDev*>(static_cast<char*>(P->small.p) + ((sizeof(SolveDesc) + 255) & ~size_t(255)));
+    CK(cudaMallocHost(&P->desc_host, sizeof(SolveDesc)));
+    CK(cudaMallocHost(&P->info_host, sizeof(InfoDev)));
+    std::memset(P->desc_host, 0, sizeof(SolveDesc));
+    CK(cudaMemset(P->small.p, 0, P->small.bytes));
+    CK(cudaEventCreate(&P->ev0));
+    CK(cudaEventCreate(&P->ev1));
+    {
+      int nsk = 0;
+      for (int k = 0; k < sp.order; ++k) nsk += sp.sketched[k];
+      P->launches_pro = 1 + (nsk > 0 ? 1 : 0) + (has_x0 ? apply_launches(P->op.op, true) : 0) +
+                        sketch_launches(sp) + 2;
+      P->launches_step = apply_launches(P->op.op, false) + sketch_launches(sp) + 3;
+      P->launches_epi = 3;
+    }
+    if (use_graph) RK(build_graph(*P));
+    h->plans[key] = std::move(np);
+  } else {
+    P = it->second.get();
+  }
+  // per-call descriptor (host arrays are staged through plan buffers)
+  SolveDesc& D = *P->desc_host;
+  D.C = C;
+  D.X0 = X0;
+  D.X = X;
+  if (!C_dev) {
+    RK(P->Cst.ensure(bytes_t));
+    CK(cudaMemcpyAsync(P->Cst.p, C, bytes_t, cudaMemcpyHostToDevice, s));
+    D.C = P->Cst.p;
+  }
+  if (has_x0 && !X0_dev) {
+    RK(P->X0st.ensure(bytes_t));
+    CK(cudaMemcpyAsync(P->X0st.p, X0, bytes_t, cudaMemcpyHostToDevice, s));
+    D.X0 = P->X0st.p;
+  }
+  if (!X_dev) {
+    RK(P->Xst.ensure(bytes_t));
+    D.X = P->Xst.p;
+    if (has_x0 && X0 == X) D.X0 = D.X;
+    if (has_x0 && X0 == X && !X0_dev) {
+      CK(cudaMemcpyAsync(P->Xst.p, X0, bytes_t, cudaMemcpyHostToDevice, s));
+    }
+  }
+  D.tol = opts.tol;
+  D.bd_tol = opts.breakdown_tol > 0 ? opts.breakdown_tol : (dtype == RTG_F64 ? 1e-12 : 1e-6);
+  D.lambda = lambda;
+  D.n_mu = mode == 2 ? opts.n_mu : 0;
+  for (int i = 0; i < D.n_mu; ++i) D.mu_grid[i] = opts.mu_grid[i];
+  CK(cudaMemcpyAsync(P->desc_dev, P->desc_host, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(P->ev0, s));
+  if (use_graph) {
+    CK(cudaGraphLaunch(P->exec, s));
+  } else {
+    const StepOpts so = solve_step_opts(*P, 0, 0);
+    RK(enqueue_prologue(*P, so, s));
+    for (int j = 0; j < m; ++j) RK(enqueue_step(P->op, P->sp, P->w, dtype, P->tA, P->tB, P->bits, so, s));
+    RK(enqueue_epilogue(*P, s));
+  }
+  CK(cudaEventRecord(P->ev1, s));
+  if (!X_dev) CK(cudaMemcpyAsync(X, P->Xst.p, bytes_t, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(P->info_host, P->info_dev, sizeof(InfoDev), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const InfoDev& I = *P->info_host;
+  if (info) {
+    info->iters = I.iters;
+    info->restarts = I.restarts;
+    info->breakdown = I.breakdown;
+    info->converged = I.converged;
+    info->beta = I.beta;
+    info->mu = I.mu;
+    info->rho_final = I.rho_final;
+    if (info->rho_hist)
+      for (int i = 0; i < I.iters && i < kMaxK; ++i) info->rho_hist[i] = I.rho_hist[i];
+    if (info->gcv && mode == 2)
+      for (int i = 0; i < opts.n_mu; ++i) info->gcv[i] = I.gcv[i];
+    info->true_rel_resid = -1.0;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, P->ev0, P->ev1);
+    info->elapsed_ms = ms;
+    info->device_status = I.status;
+    info->launches = P->launches_pro + P->launches_epi +
+                     (use_graph ? I.iters : m) * P->launches_step;
+  }
+  return RTG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+// Internal declarations shared by the translation units of librtg.
+// Tensors are column-major (mode 1 fastest), the ivec order of Section 4.1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rtg.h"
+
+namespace rtg {
+
+constexpr int kMaxOrder = RTG_MAX_ORDER;
+constexpr int kMaxRadius = RTG_MAX_RADIUS;
+constexpr int kMaxTaps = 2 * kMaxRadius + 1;
+constexpr int kMaxK = RTG_MAX_KRYLOV;
+constexpr int kMaxMu = RTG_MAX_MU;
+constexpr int kMaxPasses = 8;
+constexpr int kMaxMix = 4;          // channel-mixing size handled inside the fused blur kernel
+
+enum PassKind : int { PK_BAND = 1, PK_DENSE = 2 };
+
+// One mode product of the separable operator Phi (Eq. 56-57): either a
+// banded Toeplitz matrix (taps) or a dense matrix (device, column-major).
+struct Pass {
+  int mode;          // 0-based
+  int kind;          // PK_BAND / PK_DENSE
+  int n;             // mode size
+  int radius;        // PK_BAND
+  double taps[kMaxTaps];
+  const double* dense;   // PK_DENSE: device pointer, n*n column-major
+};
+
+// Operator as the list of mode products, in application order, plus the
+// parameters of the fused kernel when the list matches its pattern:
+// banded/identity on modes 1 and 2, and on mode 3 identity or a dense
+// (or banded) matrix of size <= kMaxMix; higher modes untouched.
+struct OpPlan {
+  int order;
+  int64_t dims[kMaxOrder];
+  int npass;
+  Pass pass[kMaxPasses];
+  bool fused;
+  int r1, r2;                // fused: radii on modes 1 and 2 (0 with a unit tap = identity)
+  double t1[kMaxTaps], t2[kMaxTaps];
+  int mix;                   // fused: 0 = no channel mixing, else mix size (= dims[2])
+  double M3[kMaxMix * kMaxMix];   // fused: mode-3 matrix, M3[p + mix*c] = M(p, c)
+};
+
+// Control block of one sketched Arnoldi process (device resident).
+struct Ctl {
+  int j;            // completed steps in this cycle
+  int stop;         // no further steps
+  int breakdown;
+  int converged;
+  int status;       // rtg_status seen on the device
+  int skip_update;  // do not form V_{j+1} (stopped by convergence inside a solve)
+  int iters_total;  // steps over all cycles
+  int cycle;
+  int loops;        // executions of the step body since the reset (hard cap m+1)
+  double beta;      // ||R_0||_Theta of this cycle
+  double beta0;     // of the first cycle (scale of rho)
+  double rho;       // last rho_j
+  double pre2;      // ||S(Phi V_j)||^2 before orthogonalisation
+  double hnext;     // h_{j+1,j}
+  double mu;        // chosen regularisation
+  double gcv_best;
+};
+
+// Per-call parameters of a solve, read by the graph's kernels.
+struct SolveDesc {
+  const void* C;
+  const void* X0;   // may be null
+  void* X;
+  double tol;
+  double bd_tol;
+  double lambda;    // > 0 fixed, 0 least squares, < 0 GCV
+  int n_mu;
+  int pad;
+  double mu_grid[kMaxMu];
+};
+
+// Host-visible summary written at the end of a solve (one D2H copy).
+struct InfoDev {
+  int iters, restarts, breakdown, converged, status, k, pad0, pad1;
+  double beta, mu, rho_final, true_rel_resid;
+  double rho_hist[kMaxK];
+  double gcv[kMaxMu];
+};
+
+// Workspace of one Arnoldi process.  T is the data type (double / float).
+struct Work {
+  int dtype;                   // RTG_F64 / RTG_F32
+  int64_t n;                   // elements per tensor
+  int d;                       // sketch size prod(s'_k)
+  int m;                       // Krylov dimension
+  void* V;                     // (m+1) * n
+  void* W;                     // n
+  void* S;                     // d   (sketch of W, then s after the first GS pass)
+  void* tmp0;                  // sketch chain intermediates
+  void* tmp1;
+  void* Q;                     // (m+1) * d sketched basis
+  double* part;                // partial sums: gridDim x (m+2)
+  unsigned* counter;           // last-block counters (several)
+  Ctl* ctl;
+  double* H;                   // (m+1) x m Hessenberg, column-major
+  double* R;                   // (m+1) x m rotated Hessenberg (upper triangular part)
+  double* cs;                  // Givens cosines (m)
+  double* sn;                  // Givens sines (m)
+  double* g;                   // rotated right-hand side (m+1)
+  double* h1;                  // first-pass coefficients (m+1)
+  double* h2;                  // second-pass coefficients (m+1)
+  double* rho_hist;            // (m) per cycle
+  double* y;                   // solution coefficients (m)
+  double* gcv;                 // GCV values (kMaxMu)
+  double* ysel;                // per-mu coefficient candidates (kMaxMu * m)
+  int part_rows;               // rows available in part
+};
+
+// Sketch description: modes with s_k < I_k carry Theta_k as packed sign
+// bits (row-major rows of ceil(I_k/32) words).
+struct SketchPlan {
+  int order;
+  int64_t dims[kMaxOrder];
+  int64_t sdims[kMaxOrder];    // s'_k
+  int sketched[kMaxOrder];
+  int64_t bit_off[kMaxOrder];  // offset of Theta_k in the Philox sign stream
+  int64_t word_off[kMaxOrder]; // offset of Theta_k in the packed device array
+  int wpr[kMaxOrder];          // 32-bit words per row
+  int64_t total_words;         // packed device array size (uint32 words)
+  int64_t d;                   // prod(s'_k)
+  int64_t tmp_elems;           // largest intermediate of the chain
+  double scale;                // prod 1/sqrt(s_k) over sketched modes
+  uint64_t seed, pid;
+};
+
+// A tensor pointer resolved on the device: an explicit base, or a base read
+// from device memory (per-call descriptors of a captured graph), optionally
+// advanced by (*jidx) * stride elements (the current basis vector V_j).
+struct PtrRef {
+  const void* base = nullptr;
+  const void* const* ind = nullptr;
+  const int* jidx = nullptr;
+  int64_t stride = 0;
+  int joff = 0;
+#ifdef __CUDACC__
+  template <typename T>
+  __device__ __forceinline__ T* get() const {
+    const void* b = ind ? *ind : base;
+    T* p = static_cast<T*>(const_cast<void*>(b));
+    if (jidx) p += static_cast<int64_t>(*jidx + joff) * stride;
+    return p;
+  }
+#endif
+};
+inline PtrRef ref(const void* p) { PtrRef r; r.base = p; return r; }
+
+// ---------------------------------------------------------------- launchers
+// k_philox.cu
+cudaError_t launch_philox_words(uint64_t seed, uint64_t pid, int64_t n_words, uint64_t* out,
+                                cudaStream_t s);
+cudaError_t launch_theta_bits(const SketchPlan& sp, uint32_t* bits, cudaStream_t s);
+
+// k_apply.cu: Y = alpha * Phi(X) + beta * Z (Z may be null when beta == 0).
+// tmp: scratch of n elements for the unfused path (may be null if unused).
+cudaError_t launch_apply(const OpPlan& op, int dtype, PtrRef X, PtrRef Y, double alpha,
+                         double beta, PtrRef Z, void* tmp, void* tmp2, const int* stop,
+                         cudaStream_t s);
+// Scratch elements the unfused path needs (0 when fused).
+int64_t apply_scratch_elems(const OpPlan& op);
+// Kernels one launch_apply issues (combine: alpha != 1 or a Z term).
+int apply_launches(const OpPlan& op, bool combine);
+
+// k_sketch.cu: SX = S(X); tmp0/tmp1 hold sp.tmp_elems elements each.
+cudaError_t launch_sketch(const SketchPlan& sp, int dtype, const uint32_t* bits, PtrRef X,
+                          void* SX, void* tmp0, void* tmp1, const int* stop, cudaStream_t s);
+int sketch_launches(const SketchPlan& sp);
+
+// k_arnoldi.cu: the sketched Arnoldi process on a Work.
+//   start:  beta = ||S||, V_0 = src / beta, Q_0 = S / beta  (src = R_0)
+//   pass1:  h1 = Q^T S, pre = ||S||^2
+//   pass2:  S <- S - Q h1; h2 = Q^T S; h = h1 + h2; h_{j+1,j}; Givens; stop rule
+//   update: V_{j+1} = (W - V h)/h_{j+1,j}, Q_{j+1} = (S - Q h2)/h_{j+1,j}
+struct StepOpts {
+  double tol;            // rho stop level (read from desc when desc_tol is set)
+  double bd_tol;
+  const double* desc_tol;    // optional device pointer overriding tol
+  const double* desc_bd_tol; // optional device pointer overriding bd_tol
+  int solve_mode;        // 1: skip V_{j+1} once the solve stops
+  int use_cond;
+  unsigned long long cond;   // cudaGraphConditionalHandle
+};
+cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, cudaStream_t s);
+cudaError_t launch_pass1(const Work& w, cudaStream_t s);
+cudaError_t launch_pass2(const Work& w, const StepOpts& o, cudaStream_t s);
+cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s);
+cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s);
+
+// k_solve.cu: projected Tikhonov / GCV, assembly and the info summary.
+struct FinishOpts {
+  const SolveDesc* desc;     // lambda, mu grid
+  int n_mu;                  // structural: GCV blocks (lambda < 0)
+  int mode;                  // 0: least squares, 1: fixed mu, 2: GCV
+};
+cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s);
+cudaError_t launch_assemble(const Work& w, PtrRef X0, PtrRef X, cudaStream_t s);
+cudaError_t launch_finalize(const Work& w, InfoDev* info, cudaStream_t s);
+}  // namespace rtg

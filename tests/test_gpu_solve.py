@@ -1,0 +1,239 @@
+"""GPU parity of the sketched Arnoldi process and the full RTG-GMRES solve.
+
+Bars (written per test): FP64 paths within 1e-9..1e-10 of the FP64
+oracle; FP32 paths: residual histories and final iterates within 1e-4
+relative error, the tolerance the spec workload states for FP32.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def h():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_00839_gb300 import api
+    return api.Handle(0)
+
+
+def _api():
+    from paper_2603_00839_gb300 import api
+    return api
+
+
+def _api_factors(p):
+    api = _api()
+    A = [api.banded(m, p.dims[m - 1], t) if k == "banded" else api.dense(m, t)
+         for m, k, t in p.factors]
+    B = [api.banded(m, p.dims[m - 1], t) if k == "banded" else api.dense(m, t)
+         for m, k, t in p.right_factors]
+    return A, B
+
+
+def _setup(p):
+    mats = oracle.factor_matrices(p.dims, p.factors, p.right_factors)
+    C, _, nu_c = oracle.make_observation(p.x_true, mats, p.noise, p.nu)
+    th = oracle.sketch_matrices(p.dims, p.sketch_dims, p.seed, p.problem_id)
+    return mats, C, nu_c, th
+
+
+def _relnorm(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ------------------------------------------------------------------------ Arnoldi steps
+
+@pytest.mark.parametrize("dt,tol", [(torch.float64, 1e-10), (torch.float32, 1e-4)])
+def test_arnoldi_steps_match_oracle_and_invariants(h, dt, tol):
+    api = _api()
+    dims, sk = (48, 40, 3), (16, 12, 3)
+    a = w.gaussian_taps(1.2, 3)
+    p_f = [(1, "banded", a), (2, "banded", a)]
+    p_r = [(3, "dense", w.channel_mix())]
+    mats = oracle.factor_matrices(dims, p_f, p_r)
+    C = np.random.default_rng(0).standard_normal(dims)
+    th = oracle.sketch_matrices(dims, sk, 5)
+    m = 10
+    ref = oracle.sketched_arnoldi(lambda X: oracle.apply_operator(X, mats), C, m,
+                                  lambda X: oracle.sketch(X, th))
+    K = api.Krylov(h, dims, dt, m, sk, 5,
+                   [api.banded(1, dims[0], a), api.banded(2, dims[1], a)],
+                   [api.dense(3, w.channel_mix())])
+    K.start(api.to_device(C, dt))
+    for _ in range(m):
+        K.step()
+    view, H = K.query()
+    assert view.j == m and not view.breakdown
+    assert abs(view.beta - ref.beta) <= tol * ref.beta
+    assert np.max(np.abs(H - ref.H)) <= tol * np.max(np.abs(ref.H))
+    Vs, Qs = K.basis(m + 1)
+    V = [v.cpu().double().numpy() for v in Vs]
+    # Arnoldi relation (7S) on the GPU basis, evaluated in FP64 by the oracle
+    for j in range(m):
+        lhs = oracle.apply_operator(V[j], mats)
+        rhs = sum(H[i, j] * V[i] for i in range(j + 2))
+        assert np.linalg.norm(lhs - rhs) <= tol * np.linalg.norm(lhs)
+    # sketched orthonormality with sketches recomputed from the stored basis
+    SV = np.stack([oracle.sketch(v, th).ravel(order="F") for v in V], axis=1)
+    assert np.max(np.abs(SV.T @ SV - np.eye(m + 1))) <= (1e-10 if dt == torch.float64 else 1e-4)
+    # the stored sketches equal the recomputed ones
+    Q = np.stack([q.cpu().double().numpy().ravel(order="F") for q in Qs], axis=1)
+    assert np.max(np.abs(Q - SV)) <= (1e-11 if dt == torch.float64 else 1e-4)
+    # further steps after j = m are no-ops
+    K.step()
+    view2, H2 = K.query()
+    assert view2.j == m and np.array_equal(H, H2)
+
+
+def test_arnoldi_happy_breakdown_identity_operator(h):
+    api = _api()
+    dims = (20, 16, 3)
+    C = np.random.default_rng(1).standard_normal(dims)
+    K = api.Krylov(h, dims, torch.float64, 5, (8, 8, 3), 0)
+    K.start(api.to_device(C, torch.float64))
+    for _ in range(3):
+        K.step()
+    view, H = K.query()
+    assert view.j == 1 and view.breakdown
+    assert abs(H[0, 0] - 1.0) < 1e-12 and H[1, 0] == 0.0
+
+
+# ------------------------------------------------------------------------ full solves
+
+def test_solve_image64_f64_matches_oracle(h):
+    p = w.image_config(1)
+    mats, C, nu_c, th = _setup(p)
+    tol = oracle.rho_star(nu_c)
+    ref = oracle.rtg_gmres(mats, C, p.m, th, tol=tol, lam=p.lam)
+    api = _api()
+    A, B = _api_factors(p)
+    X, info = h.gmres_solve(api.to_device(C, torch.float64), p.m, p.sketch_dims, p.seed, p.lam,
+                            A, B, tol=tol)
+    assert info.iters == ref["iters"] and info.converged and info.device_status == 0
+    assert np.allclose(info.rho, ref["rho"], rtol=1e-10, atol=0)
+    assert abs(info.beta - ref["beta"]) <= 1e-12 * ref["beta"]
+    assert _relnorm(X.cpu().numpy(), ref["X"]) < 1e-10
+    gold = json.load(open(os.path.join(GOLDEN, "image64_f64.json")))
+    assert info.iters == gold["iters"]
+
+
+def test_solve_image512_f32_matches_oracle(h):
+    """The 512x512x3 FP32 workload at full size: rho history, mu and X within 1e-4."""
+    p = w.image_config(2)
+    mats, C, nu_c, th = _setup(p)
+    tol = oracle.rho_star(nu_c)
+    ref = oracle.rtg_gmres(mats, C, p.m, th, tol=tol, lam=p.lam, mu_grid=p.mu_grid)
+    api = _api()
+    A, B = _api_factors(p)
+    X, info = h.gmres_solve(api.to_device(C, torch.float32), p.m, p.sketch_dims, p.seed, p.lam,
+                            A, B, tol=tol, mu_grid=p.mu_grid)
+    assert info.iters == ref["iters"] and info.converged and info.device_status == 0
+    assert np.allclose(info.rho, ref["rho"], rtol=1e-4, atol=0)
+    if info.mu != ref["mu"]:      # a GCV near-tie may pick either neighbour
+        i, k = list(p.mu_grid).index(info.mu), list(p.mu_grid).index(ref["mu"])
+        assert abs(ref["gcv"][i] - ref["gcv"][k]) <= 1e-4 * ref["gcv"][k]
+    else:
+        assert np.allclose(info.gcv, ref["gcv"], rtol=1e-4)
+        assert _relnorm(X.cpu().double().numpy(), ref["X"]) < 1e-4
+
+
+def test_solve_host_buffers_equal_device_buffers(h):
+    p = w.image_config(1)
+    mats, C, nu_c, th = _setup(p)
+    api = _api()
+    A, B = _api_factors(p)
+    Xd, i1 = h.gmres_solve(api.to_device(C, torch.float64), p.m, p.sketch_dims, p.seed, p.lam, A, B,
+                           tol=1e-3)
+    Xh, i2 = h.gmres_solve(np.asfortranarray(C), p.m, p.sketch_dims, p.seed, p.lam, A, B, tol=1e-3)
+    assert isinstance(Xh, np.ndarray) and i1.iters == i2.iters
+    assert np.array_equal(Xd.cpu().numpy(), Xh)
+
+
+def test_solve_graph_and_direct_launch_agree(h):
+    p = w.image_config(1)
+    mats, C, nu_c, th = _setup(p)
+    api = _api()
+    A, B = _api_factors(p)
+    Cd = api.to_device(C, torch.float64)
+    Xg, ig = h.gmres_solve(Cd, p.m, p.sketch_dims, p.seed, p.lam, A, B, tol=1e-3)
+    Xd, idr = h.gmres_solve(Cd, p.m, p.sketch_dims, p.seed, p.lam, A, B, tol=1e-3, use_graph=False)
+    assert ig.iters == idr.iters
+    assert np.array_equal(Xg.cpu().numpy(), Xd.cpu().numpy())
+
+
+@pytest.mark.parametrize("lam", [0.0, 1e-2])
+def test_solve_with_initial_guess(h, lam):
+    p = w.image_config(1)
+    mats, C, nu_c, th = _setup(p)
+    X0 = 0.5 * np.ones(p.dims)
+    ref = oracle.rtg_gmres(mats, C, 12, th, X0=X0, tol=0.0, lam=lam)
+    api = _api()
+    A, B = _api_factors(p)
+    X, info = h.gmres_solve(api.to_device(C, torch.float64), 12, p.sketch_dims, p.seed, lam, A, B,
+                            X0=api.to_device(X0, torch.float64))
+    assert info.iters == 12 == ref["iters"]
+    assert np.allclose(info.rho, ref["rho"], rtol=1e-9)
+    assert _relnorm(X.cpu().numpy(), ref["X"]) < 1e-9
+
+
+def test_solve_zero_rhs_and_identity_operator(h):
+    api = _api()
+    dims = (32, 24, 3)
+    X, info = h.gmres_solve(api.to_device(np.zeros(dims), torch.float64), 5, (8, 8, 3), 0, 1e-3)
+    assert info.iters == 0 and info.converged and float(X.abs().max()) == 0.0
+    C = np.random.default_rng(2).standard_normal(dims)
+    X, info = h.gmres_solve(api.to_device(C, torch.float64), 5, (8, 8, 3), 0, 0.0)
+    assert info.iters == 1 and info.breakdown
+    assert _relnorm(X.cpu().numpy(), C) < 1e-13
+
+
+def test_solve_gcv_grid_sizes_and_fixed_mu(h):
+    dims, sk = (64, 48, 3), (24, 16, 3)
+    a = w.gaussian_taps(1.5, 4)
+    fac = [(1, "banded", a), (2, "banded", a)]
+    mats = oracle.factor_matrices(dims, fac)
+    x = w.piecewise_image(64, 48, 3, seed=4)
+    C, _, nu_c = oracle.make_observation(x, mats, w.noise_draw(dims, 4), 5e-3)
+    th = oracle.sketch_matrices(dims, sk, 2)
+    api = _api()
+    A = [api.banded(1, 64, a), api.banded(2, 48, a)]
+    Cd = api.to_device(C, torch.float64)
+    for grid in (w.mu_grid(1), w.mu_grid(3), w.mu_grid(32, 1e-6, 1.0)):
+        ref = oracle.rtg_gmres(mats, C, 20, th, tol=0.0, lam=-1.0, mu_grid=grid)
+        X, info = h.gmres_solve(Cd, 20, sk, 2, -1.0, A, tol=0.0, mu_grid=grid)
+        assert info.mu == ref["mu"]
+        assert np.allclose(info.gcv, ref["gcv"], rtol=1e-8)
+        assert _relnorm(X.cpu().numpy(), ref["X"]) < 1e-9
+    ref = oracle.rtg_gmres(mats, C, 20, th, tol=0.0, lam=3e-3)
+    X, info = h.gmres_solve(Cd, 20, sk, 2, 3e-3, A)
+    assert info.mu == 3e-3 and _relnorm(X.cpu().numpy(), ref["X"]) < 1e-9
+
+
+def test_solve_rejects_bad_arguments(h):
+    api = _api()
+    from paper_2603_00839_gb300._lib import RtgError
+    Cd = api.to_device(np.ones((8, 8, 3)), torch.float64)
+    with pytest.raises(RtgError):
+        h.gmres_solve(Cd, 0, (4, 4, 3), 0, 1e-3)                      # m = 0
+    with pytest.raises(RtgError):
+        h.gmres_solve(Cd, 300, (4, 4, 3), 0, 1e-3)                    # m > 256
+    with pytest.raises(RtgError):
+        h.gmres_solve(Cd, 5, (0, 4, 3), 0, 1e-3)                      # sketch size 0
+    with pytest.raises(RtgError):
+        h.gmres_solve(Cd, 5, (4, 4, 3), 0, -1.0)                      # GCV without a grid
+    with pytest.raises(RtgError):
+        h.gmres_solve(Cd, 5, (4, 4, 3), 0, 1e-3, max_restarts=1)      # restarts: unsupported
