@@ -248,6 +248,30 @@ rtg_status rtg_gmres_solve(rtg_handle handle,
                            uint64_t seed, double lambda, const void* X0, void* X,
                            const rtg_opts* opts, rtg_info* info, rtg_stream stream);
 
+/*
+ * rtg_sketch_noalloc -- the paper has no counterpart; this is a service of
+ * the library.  Same result as rtg_sketch (same kernels, same Philox
+ * signs) for callers that cannot call cudaMalloc: code that runs next to a
+ * framework which has already reserved the device memory for its own pool,
+ * or latency-critical code that cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  It takes no handle and
+ * allocates nothing: its scratch (packed signs and the contraction
+ * intermediates) lives in one 4 MiB array of the library's static device
+ * memory, which every GPU that loads the library holds until the process
+ * exits.  Sizes whose scratch (bits + two intermediates) exceeds 4 MiB are
+ * rejected with RTG_ERR_INVALID_ARG and a message in rtg_last_error().
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents (each call writes every scratch byte it reads,
+ * so nothing needs clearing); calls that overlap on the GPU (different
+ * streams, or different host threads) race on it.  X, SX: device arrays as
+ * for rtg_sketch; the call is asynchronous on `stream`.
+ */
+rtg_status rtg_sketch_noalloc(rtg_shape shape, rtg_dtype dtype, const int64_t* sketch_dims,
+                              uint64_t seed, uint64_t problem_id, const void* X, void* SX,
+                              rtg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,8 @@ _SIGS = {
                                   C.c_int32, Shape, C.c_int, C.c_void_p, C.c_int32,
                                   C.POINTER(C.c_int64), C.c_uint64, C.c_double, C.c_void_p,
                                   C.c_void_p, C.POINTER(Opts), C.POINTER(Info), C.c_void_p]),
+    "rtg_sketch_noalloc": (C.c_int, [Shape, C.c_int, C.POINTER(C.c_int64), C.c_uint64, C.c_uint64,
+                                     C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 SYMBOLS = tuple(_SIGS)

@@ -384,6 +384,8 @@ size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, 
 
 }  // namespace
 
+void rtg::record_error(const char* msg) { g_err = msg; }
+
 // ------------------------------------------------------------------ handle
 
 struct rtg_context;

@@ -154,6 +154,9 @@ struct PtrRef {
 };
 inline PtrRef ref(const void* p) { PtrRef r; r.base = p; return r; }
 
+// Sets the thread-local message rtg_last_error() returns (rtg_api.cu).
+void record_error(const char* msg);
+
 // ---------------------------------------------------------------- launchers
 // k_philox.cu
 cudaError_t launch_philox_words(uint64_t seed, uint64_t pid, int64_t n_words, uint64_t* out,
