@@ -256,10 +256,10 @@ rtg_status rtg_gmres_solve(rtg_handle handle,
  * or latency-critical code that cannot afford the implicit device
  * synchronisation of cudaMalloc/cudaFree.  It takes no handle and
  * allocates nothing: its scratch (packed signs and the contraction
- * intermediates) lives in one 4 MiB array of the library's static device
+ * intermediates) lives in one 16 MiB array of the library's static device
  * memory, which every GPU that loads the library holds until the process
- * exits.  Sizes whose scratch (bits + two intermediates) exceeds 4 MiB are
- * rejected with RTG_ERR_INVALID_ARG and a message in rtg_last_error().
+ * exits.  Sizes whose scratch (signs, Theta fragments and two partial-sum
+ * intermediates) exceeds 16 MiB are rejected with RTG_ERR_INVALID_ARG and a message in rtg_last_error().
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  All calls share the one array and it keeps

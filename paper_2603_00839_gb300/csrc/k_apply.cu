@@ -97,6 +97,132 @@ k_apply_fused(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
   }
 }
 
+// Register-blocked variant for a compile-time radius RR (taps zero-padded
+// to 2*RR+1) and NC jointly mixed channels.  Tile 64 x 16 of modes 1-2,
+// 256 threads.  All NC halo tiles are staged in shared memory at once with
+// cp.async (zero fill outside the tensor: the zero boundary of Eq. 57), so
+// the CTA waits on global memory once.  Mode-1 pass: a thread filters 8
+// consecutive outputs of a row from a register window of 8+2RR values;
+// mode-2 pass: a thread filters 4 consecutive rows of one column.
+constexpr int RTX = 64;
+constexpr int RTY = 16;
+constexpr int RSEG = 8;    // mode-1 outputs per thread
+constexpr int VSEG = 4;    // mode-2 outputs per thread
+
+__device__ __forceinline__ void cp_async4z(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int sz = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async8z(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int sz = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+
+template <typename T, int NC, int RR>
+__global__ void __launch_bounds__(FTHREADS)
+k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
+  if (stop != nullptr && *stop) return;
+  const T* __restrict__ X = Xr.get<const T>();
+  T* __restrict__ Y = Yr.get<T>();
+  const T* __restrict__ Z = Zr.get<const T>();
+  constexpr int NT = 2 * RR + 1;
+  constexpr int Wd = RTX + 2 * RR;
+  constexpr int Ht = RTY + 2 * RR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* in_s = reinterpret_cast<T*>(smem_raw);      // NC x Ht x Wd
+  T* tmp = in_s + NC * Ht * Wd;                  // Ht x RTX
+  T t1[NT], t2[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int u1 = t - (RR - a.r1), u2 = t - (RR - a.r2);
+    t1[t] = (u1 >= 0 && u1 <= 2 * a.r1) ? static_cast<T>(a.t1[u1]) : static_cast<T>(0);
+    t2[t] = (u2 >= 0 && u2 <= 2 * a.r2) ? static_cast<T>(a.t2[u2]) : static_cast<T>(0);
+  }
+  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * RTX;
+  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * RTY;
+  const int64_t plane = a.I1 * a.I2;
+  const int vx = threadIdx.x & (RTX - 1);        // mode-2 pass: column
+  const int vy = (threadIdx.x / RTX) * VSEG;     // mode-2 pass: first of 4 rows
+  for (int64_t slab = blockIdx.z; slab < a.nslab; slab += gridDim.z) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NC * Ht * Wd; idx += FTHREADS) {
+      const int c = idx / (Ht * Wd), rem = idx - c * (Ht * Wd);
+      const int yy = rem / Wd, xx = rem - yy * Wd;
+      const int64_t gx = x0 - RR + xx, gy = y0 - RR + yy;
+      const bool v = gx >= 0 && gx < a.I1 && gy >= 0 && gy < a.I2;
+      const T* src = X + (slab * NC + c) * plane + (v ? gy * a.I1 + gx : 0);
+      if (sizeof(T) == 4) cp_async4z(&in_s[idx], src, v);
+      else cp_async8z(&in_s[idx], src, v);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    T acc[NC][VSEG];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T* ins = in_s + c * Ht * Wd;
+      // mode 1: Ht rows x 8 segments of 8 outputs
+      for (int task = threadIdx.x; task < Ht * (RTX / RSEG); task += FTHREADS) {
+        const int yy = task / (RTX / RSEG);
+        const int xs = (task - yy * (RTX / RSEG)) * RSEG;
+        const T* row = ins + yy * Wd + xs;
+        T win[RSEG + 2 * RR];
+#pragma unroll
+        for (int u = 0; u < RSEG + 2 * RR; ++u) win[u] = row[u];
+#pragma unroll
+        for (int o = 0; o < RSEG; ++o) {
+          T sacc = 0;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) sacc += t1[t] * win[o + t];
+          tmp[yy * RTX + xs + o] = sacc;
+        }
+      }
+      __syncthreads();
+      // mode 2: 4 rows of one column
+      {
+        T win[VSEG + 2 * RR];
+#pragma unroll
+        for (int u = 0; u < VSEG + 2 * RR; ++u) win[u] = tmp[(vy + u) * RTX + vx];
+#pragma unroll
+        for (int o = 0; o < VSEG; ++o) {
+          T sacc = 0;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) sacc += t2[t] * win[o + t];
+          acc[c][o] = sacc;
+        }
+      }
+      __syncthreads();
+    }
+    const int64_t gx = x0 + vx;
+    if (gx < a.I1) {
+#pragma unroll
+      for (int o = 0; o < VSEG; ++o) {
+        const int64_t gy = y0 + vy + o;
+        if (gy >= a.I2) break;
+#pragma unroll
+        for (int p = 0; p < NC; ++p) {
+          T v = 0;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v += static_cast<T>(a.M[p + NC * c]) * acc[c][o];
+          const int64_t idx = (slab * NC + p) * plane + gy * a.I1 + gx;
+          T out = static_cast<T>(a.alpha) * v;
+          if (Z != nullptr) out += static_cast<T>(a.beta) * Z[idx];
+          Y[idx] = out;
+        }
+      }
+    }
+  }
+}
+
+// Smallest compiled radius bucket that holds r (0 when none does).
+static int reg_bucket(int r) {
+  const int b[] = {3, 5, 7, 9, 12, 16};
+  for (int v : b)
+    if (r <= v) return v;
+  return 0;
+}
+
 struct TapArgs {
   double t[kMaxTaps];
 };
@@ -211,6 +337,24 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
       a.nc = 1;
       a.nslab = I3 * rest;
       a.M[0] = 1.0;
+    }
+    const int rr = reg_bucket(op.r1 > op.r2 ? op.r1 : op.r2);
+    if (rr > 0 && (a.nc == 1 || a.nc == 3)) {
+      const size_t smem = static_cast<size_t>(a.nc * (RTY + 2 * rr) * (RTX + 2 * rr) + (RTY + 2 * rr) * RTX) * sizeof(T);
+      dim3 grid(static_cast<unsigned>((a.I1 + RTX - 1) / RTX), static_cast<unsigned>((a.I2 + RTY - 1) / RTY),
+                static_cast<unsigned>(a.nslab < 65535 ? a.nslab : 65535));
+      cudaError_t e = cudaSuccess;
+#define RTG_REG_CASE(NC, RR)                                                                          \
+  if (a.nc == NC && rr == RR) {                                                                       \
+    e = cudaFuncSetAttribute(k_apply_reg<T, NC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                             static_cast<int>(smem));                                                  \
+    if (e != cudaSuccess) return e;                                                                   \
+    k_apply_reg<T, NC, RR><<<grid, FTHREADS, smem, s>>>(X, Y, Z, stop, a);                            \
+    return cudaGetLastError();                                                                        \
+  }
+      RTG_REG_CASE(1, 3) RTG_REG_CASE(1, 5) RTG_REG_CASE(1, 7) RTG_REG_CASE(1, 9) RTG_REG_CASE(1, 12) RTG_REG_CASE(1, 16)
+      RTG_REG_CASE(3, 3) RTG_REG_CASE(3, 5) RTG_REG_CASE(3, 7) RTG_REG_CASE(3, 9) RTG_REG_CASE(3, 12) RTG_REG_CASE(3, 16)
+#undef RTG_REG_CASE
     }
     const size_t smem = fused_smem(op, sizeof(T));
     dim3 grid(static_cast<unsigned>((a.I1 + FTX - 1) / FTX),

@@ -3,12 +3,526 @@
 //
 // Each sketched mode k is one contraction of the current tensor, viewed as
 // (L, I_k, R) column-major: Y(l, q, r) = sum_i Theta_k(q, i) X(l, i, r).
-// Theta_k is held as packed sign bits, so every product is an exact
-// sign flip; the scale prod_k 1/sqrt(s_k) is applied once, by the last
-// contraction.  Intermediates live in two scratch tensors.
-#include "rtg_internal.cuh"
+// The scale prod_k 1/sqrt(s_k) is applied once, by the last contraction.
+//
+// FP32 data: every contraction is a GEMM on the tensor cores
+// (mma.sync m16n8k16, BF16 in, FP32 accumulate).  Theta_k has entries
+// exactly +-1 in BF16; each FP32 value x is split into three BF16 limbs
+// h + m + l with h = bf16(x), m = bf16(x - h), l = bf16(x - h - m) (both
+// differences exact in FP32), so the three products per pair carry the
+// full 24-bit significand and the sum is accumulated in FP32.  The first
+// contraction on mode 1 (L = 1) is Theta (A operand, rows q) times the
+// columns of X (B operand); later ones multiply X (A operand, rows l) by
+// Theta^T (B operand).  Theta is expanded once per sketch into fragment
+// order.  A CTA stages its operands (fragments and the data block) in
+// shared memory with cp.async in one round trip, its 8 warps split K, and
+// their partial tiles are summed through shared memory, so every stage
+// writes final values.  The last contraction of a solve step also takes
+// the first Gram-Schmidt pass: each CTA holds a final tile of the sketch
+// and adds its dot products with every stored sketched basis vector.
+//
+// FP64 data: the same chain on CUDA cores with exact sign flips.
+#include <cuda_bf16.h>
+
+#include "gs_common.cuh"
 
 namespace rtg {
+
+// ------------------------------------------------------------------ plan
+
+const char* make_sketch_plan(int order, const int64_t* dims, const int64_t* sdims_in,
+                             uint64_t seed, uint64_t pid, int dtype, SketchPlan& sp) {
+  sp = SketchPlan{};
+  if (sdims_in == nullptr) return "sketch_dims is NULL";
+  sp.order = order;
+  sp.seed = seed;
+  sp.pid = pid;
+  sp.dtype = dtype;
+  int64_t bit = 0, word = 0, d = 1;
+  double scale = 1.0;
+  for (int k = 0; k < order; ++k) {
+    if (sdims_in[k] < 1) return "sketch_dims must be >= 1";
+    sp.dims[k] = dims[k];
+    if (sdims_in[k] < dims[k]) {
+      sp.sketched[k] = 1;
+      sp.sdims[k] = sdims_in[k];
+      sp.bit_off[k] = bit;
+      sp.word_off[k] = word;
+      sp.wpr[k] = static_cast<int>((dims[k] + 31) / 32);
+      bit += sdims_in[k] * dims[k];
+      word += sdims_in[k] * sp.wpr[k];
+      scale /= sqrt(static_cast<double>(sdims_in[k]));
+    } else {
+      sp.sketched[k] = 0;
+      sp.sdims[k] = dims[k];
+    }
+    d *= sp.sdims[k];
+  }
+  if (d > (int64_t(1) << 31) - 1) return "sketch size too large";
+  sp.total_words = word;
+  sp.d = d;
+  sp.scale = scale;
+  // contraction chain in increasing mode order
+  int64_t cur[kMaxOrder];
+  for (int k = 0; k < order; ++k) cur[k] = dims[k];
+  sp.nstage = 0;
+  int64_t frag = 0, part = 1;
+  for (int k = 0; k < order; ++k) {
+    if (!sp.sketched[k]) continue;
+    const int t = sp.nstage++;
+    int64_t L = 1, R = 1;
+    for (int u = 0; u < k; ++u) L *= cur[u];
+    for (int u = k + 1; u < order; ++u) R *= cur[u];
+    const int64_t I = cur[k], s = sp.sdims[k];
+    sp.stage_mode[t] = k;
+    sp.stage_L[t] = L;
+    sp.stage_I[t] = I;
+    sp.stage_R[t] = R;
+    sp.stage_s[t] = s;
+    sp.stage_first[t] = (L == 1) ? 1 : 0;
+    sp.stage_kt[t] = static_cast<int>((I + 15) / 16);
+    const int64_t out_elems = L * s * R;
+    sp.stage_out[t] = out_elems;
+    if (dtype == RTG_F32) {
+      sp.frag_off[t] = frag;
+      if (sp.stage_first[t]) {
+        sp.stage_ntile[t] = static_cast<int>((s + 15) / 16);          // m16 tiles of Theta rows
+        frag += int64_t(sp.stage_ntile[t]) * sp.stage_kt[t] * 32 * 4;   // uint4 per lane
+      } else {
+        sp.stage_ntile[t] = static_cast<int>((s + 7) / 8);           // n8 tiles of Theta rows
+        frag += int64_t(sp.stage_ntile[t]) * sp.stage_kt[t] * 32 * 2;   // uint2 per lane
+      }
+    }
+    sp.stage_split[t] = 1;
+    cur[k] = s;
+  }
+  sp.frag_words = frag;
+  for (int t = 0; t + 1 < sp.nstage; ++t)
+    if (sp.stage_out[t] > part) part = sp.stage_out[t];
+  sp.part_elems = part;
+  sp.last_split = 1;
+  sp.tmp_elems = part;
+  sp.fused_dots = (dtype == RTG_F32 && sp.nstage > 0 && !sp.stage_first[sp.nstage - 1]) ? 1 : 0;
+  sp.dots_blocks = 0;
+  if (sp.fused_dots) {
+    const int t = sp.nstage - 1;
+    sp.dots_blocks = ((sp.stage_L[t] + 15) / 16) * sp.stage_R[t] * ((sp.stage_ntile[t] + 3) / 4);
+  }
+  return nullptr;
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+size_t sketch_scratch_bytes(const SketchPlan& sp) {
+  const size_t elt = sp.dtype == RTG_F64 ? 8 : 4;
+  return al256((sp.total_words + 1) * 4) + al256((sp.frag_words + 1) * 4) +
+         2 * al256(size_t(sp.part_elems) * elt) + 256;
+}
+
+SketchScratch carve_sketch_scratch(const SketchPlan& sp, void* base) {
+  const size_t elt = sp.dtype == RTG_F64 ? 8 : 4;
+  char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) & ~uintptr_t(255));
+  SketchScratch sc;
+  sc.bits = reinterpret_cast<uint32_t*>(p);
+  p += al256((sp.total_words + 1) * 4);
+  sc.frags = reinterpret_cast<uint32_t*>(p);
+  p += al256((sp.frag_words + 1) * 4);
+  sc.tmp0 = p;
+  p += al256(size_t(sp.part_elems) * elt);
+  sc.tmp1 = p;
+  return sc;
+}
+
+// ------------------------------------------------------------------ Theta fragments
+
+__device__ __forceinline__ uint32_t pm1_pair(uint32_t b0, uint32_t b1, bool v0, bool v1) {
+  // packed bf16x2: +1 = 0x3F80, -1 = 0xBF80, padding = 0
+  const uint32_t lo = v0 ? (0x3F80u | (b0 << 15)) : 0u;
+  const uint32_t hi = v1 ? (0x3F80u | (b1 << 15)) : 0u;
+  return lo | (hi << 16);
+}
+
+__device__ __forceinline__ uint32_t theta_bit(const uint32_t* rowbits, int64_t i) {
+  return (rowbits[i >> 5] >> (i & 31)) & 1u;
+}
+
+struct FragArgs {
+  int nstage;
+  int first[kMaxOrder];
+  int64_t s[kMaxOrder], I[kMaxOrder], word_off[kMaxOrder], frag_off[kMaxOrder];
+  int wpr[kMaxOrder], kt[kMaxOrder], ntile[kMaxOrder];
+  int64_t total_lanes;
+  int64_t lane_off[kMaxOrder + 1];
+};
+
+// One thread per (tile, k-tile, lane) of every stage: the fragment
+// registers of mma.m16n8k16 for Theta (A operand, first stage) or
+// Theta^T (B operand, later stages).
+__global__ void k_theta_frags(FragArgs a, const uint32_t* __restrict__ bits, uint32_t* frags) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= a.total_lanes) return;
+  int t = 0;
+  while (t + 1 < a.nstage && g >= a.lane_off[t + 1]) ++t;
+  const int64_t local = g - a.lane_off[t];
+  const int lane = static_cast<int>(local & 31);
+  const int64_t tile_k = local >> 5;                 // kk * ntile + tile
+  const int64_t tile = tile_k % a.ntile[t];
+  const int kk = static_cast<int>(tile_k / a.ntile[t]);
+  const int gid = lane >> 2, tig = lane & 3;
+  const uint32_t* rows = bits + a.word_off[t];
+  const int64_t k0 = static_cast<int64_t>(kk) * 16 + tig * 2;
+  if (a.first[t]) {
+    // A (16 x 16, row-major): reg0 (r, k0..k0+1), reg1 (r+8, ..), reg2 (r, k0+8..), reg3 (r+8, k0+8..)
+    uint32_t reg[4];
+    for (int h = 0; h < 4; ++h) {
+      const int64_t q = tile * 16 + gid + ((h & 1) ? 8 : 0);
+      const int64_t i = k0 + ((h & 2) ? 8 : 0);
+      const bool rv = q < a.s[t];
+      const uint32_t* rb = rows + (rv ? q : 0) * a.wpr[t];
+      const bool v0 = rv && i < a.I[t], v1 = rv && (i + 1) < a.I[t];
+      reg[h] = pm1_pair(v0 ? theta_bit(rb, i) : 0u, v1 ? theta_bit(rb, i + 1) : 0u, v0, v1);
+    }
+    uint4* out = reinterpret_cast<uint4*>(frags + a.frag_off[t]);
+    out[tile_k * 32 + lane] = make_uint4(reg[0], reg[1], reg[2], reg[3]);
+  } else {
+    // B (16 x 8, "col"): reg0 (k0..k0+1, n), reg1 (k0+8.., n); B(k = i, n = q) = Theta(q, i)
+    const int64_t q = tile * 8 + gid;
+    const bool rv = q < a.s[t];
+    const uint32_t* rb = rows + (rv ? q : 0) * a.wpr[t];
+    uint32_t reg[2];
+    for (int h = 0; h < 2; ++h) {
+      const int64_t i = k0 + (h ? 8 : 0);
+      const bool v0 = rv && i < a.I[t], v1 = rv && (i + 1) < a.I[t];
+      reg[h] = pm1_pair(v0 ? theta_bit(rb, i) : 0u, v1 ? theta_bit(rb, i + 1) : 0u, v0, v1);
+    }
+    uint2* out = reinterpret_cast<uint2*>(frags + a.frag_off[t]);
+    out[tile_k * 32 + lane] = make_uint2(reg[0], reg[1]);
+  }
+}
+
+cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, cudaStream_t s) {
+  cudaError_t e = launch_theta_bits(sp, bits, s);
+  if (e != cudaSuccess || sp.dtype != RTG_F32 || sp.nstage == 0) return e;
+  FragArgs a{};
+  a.nstage = sp.nstage;
+  int64_t lanes = 0;
+  for (int t = 0; t < sp.nstage; ++t) {
+    const int k = sp.stage_mode[t];
+    a.first[t] = sp.stage_first[t];
+    a.s[t] = sp.stage_s[t];
+    a.I[t] = sp.stage_I[t];
+    a.word_off[t] = sp.word_off[k];
+    a.frag_off[t] = sp.frag_off[t];
+    a.wpr[t] = sp.wpr[k];
+    a.kt[t] = sp.stage_kt[t];
+    a.ntile[t] = sp.stage_ntile[t];
+    a.lane_off[t] = lanes;
+    lanes += int64_t(sp.stage_ntile[t]) * sp.stage_kt[t] * 32;
+  }
+  a.lane_off[sp.nstage] = lanes;
+  a.total_lanes = lanes;
+  k_theta_frags<<<static_cast<unsigned>((lanes + 255) / 256), 256, 0, s>>>(a, bits, frags);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ tensor-core contractions
+
+__device__ __forceinline__ void split3(float x, uint16_t& h, uint16_t& m, uint16_t& l) {
+  const __nv_bfloat16 bh = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(bh);
+  const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(bm);
+  const __nv_bfloat16 bl = __float2bfloat16_rn(r2);
+  h = __bfloat16_as_ushort(bh);
+  m = __bfloat16_as_ushort(bm);
+  l = __bfloat16_as_ushort(bl);
+}
+
+// pack limbs of (x0, x1) into three bf16x2 registers
+__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t out[3]) {
+  uint16_t h0, m0, l0, h1, m1, l1;
+  split3(x0, h0, m0, l0);
+  split3(x1, h1, m1, l1);
+  out[0] = uint32_t(h0) | (uint32_t(h1) << 16);
+  out[1] = uint32_t(m0) | (uint32_t(m1) << 16);
+  out[2] = uint32_t(l0) | (uint32_t(l1) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+// 4-byte copy; src_size 0 writes a zero and reads nothing
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int sz = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+constexpr int TC_THREADS = 256;   // 8 warps split K
+constexpr int F_COLS = 16;        // first stage: columns of X per CTA
+constexpr int F_MT = 8;           // first stage: m16 tiles (128 Theta rows) per CTA
+constexpr int N_NT = 4;           // later stages: n8 tiles (32 Theta rows) per CTA
+
+template <int CH>
+constexpr size_t first_smem() {
+  return size_t(CH) * F_MT * 32 * 16 + size_t(F_COLS) * (CH * 16 + 8) * 4 >
+                 size_t(8) * 128 * F_COLS * 4
+             ? size_t(CH) * F_MT * 32 * 16 + size_t(F_COLS) * (CH * 16 + 8) * 4
+             : size_t(8) * 128 * F_COLS * 4;
+}
+
+// First contraction (mode 1, L = 1): out[q + s*r] = scale * sum_i Theta(q, i) X(i, r).
+// CTA: 128 rows of Theta x 16 columns of X; K in chunks of CH tiles staged
+// in shared memory; warp w takes the K tiles w, w+8, ...
+template <int CH>
+__global__ void __launch_bounds__(TC_THREADS)
+k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t s, int kt_total,
+              const uint4* __restrict__ fragA, int mt_total, float scale, const int* stop) {
+  if (stop != nullptr && *stop) return;
+  const float* __restrict__ X = Xr.get<const float>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int XS = CH * 16 + 8;
+  uint4* fA = reinterpret_cast<uint4*>(smem);                                   // [CH][F_MT][32]
+  float* xs = reinterpret_cast<float*>(smem + size_t(CH) * F_MT * 32 * 16);       // [F_COLS][XS]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gid = lane >> 2, tig = lane & 3;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * F_COLS;
+  const int mb = blockIdx.y;
+  const int nmt = min(F_MT, mt_total - mb * F_MT);
+  float acc[F_MT][2][4];
+#pragma unroll
+  for (int a = 0; a < F_MT; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  const bool vec = (I % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  for (int kc0 = 0; kc0 < kt_total; kc0 += CH) {
+    const int nk = min(CH, kt_total - kc0);
+    for (int idx = tid; idx < nk * F_MT * 32; idx += TC_THREADS) {
+      const int kk = idx / (F_MT * 32), rem = idx - kk * F_MT * 32, mt = rem >> 5, ln = rem & 31;
+      if (mt < nmt)
+        cp_async16(&fA[idx], &fragA[(static_cast<int64_t>(kc0 + kk) * mt_total + mb * F_MT + mt) * 32 + ln]);
+      else
+        fA[idx] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const int64_t i0 = static_cast<int64_t>(kc0) * 16;
+    const int rows = nk * 16;
+    if (vec) {
+      for (int idx = tid; idx < F_COLS * rows / 4; idx += TC_THREADS) {
+        const int col = idx / (rows / 4), k4 = (idx - col * (rows / 4)) * 4;
+        const int64_t c = c0 + col, i = i0 + k4;
+        float* dst = &xs[col * XS + k4];
+        if (c < R && i + 3 < I) {
+          cp_async16(dst, X + c * I + i);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) dst[u] = (c < R && i + u < I) ? X[c * I + i + u] : 0.f;
+        }
+      }
+    } else {
+      for (int idx = tid; idx < F_COLS * rows; idx += TC_THREADS) {
+        const int col = idx / rows, k = idx - col * rows;
+        const int64_t c = c0 + col, i = i0 + k;
+        const bool v = c < R && i < I;
+        cp_async4(&xs[col * XS + k], v ? static_cast<const void*>(X + c * I + i) : static_cast<const void*>(X), v);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int kk = warp; kk < nk; kk += 8) {
+      uint32_t B[2][2][3];
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float2 v = *reinterpret_cast<const float2*>(&xs[(nt * 8 + gid) * XS + kk * 16 + tig * 2 + h * 8]);
+          split_pair(v.x, v.y, B[nt][h]);
+        }
+#pragma unroll
+      for (int mt = 0; mt < F_MT; ++mt) {
+        if (mt >= nmt) break;
+        const uint4 av = fA[(kk * F_MT + mt) * 32 + lane];
+        const uint32_t A[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int l = 0; l < 3; ++l) mma_bf16(acc[mt][nt], A, B[nt][0][l], B[nt][1][l]);
+      }
+    }
+    __syncthreads();
+  }
+  // sum the 8 warps' K partials through shared memory
+  float* red = reinterpret_cast<float*>(smem);                // [8][128][F_COLS]
+#pragma unroll
+  for (int mt = 0; mt < F_MT; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = mt * 16 + gid + h * 8, col = nt * 8 + tig * 2;
+        red[(warp * 128 + row) * F_COLS + col] = acc[mt][nt][2 * h];
+        red[(warp * 128 + row) * F_COLS + col + 1] = acc[mt][nt][2 * h + 1];
+      }
+  __syncthreads();
+  for (int idx = tid; idx < 128 * F_COLS; idx += TC_THREADS) {
+    const int row = idx & 127, col = idx >> 7;
+    float v = 0.f;
+#pragma unroll
+    for (int wv = 0; wv < 8; ++wv) v += red[(wv * 128 + row) * F_COLS + col];
+    const int64_t q = static_cast<int64_t>(mb) * 128 + row, c = c0 + col;
+    if (q < s && c < R) out[q + s * c] = v * scale;
+  }
+}
+
+template <int CH>
+constexpr size_t inner_smem() {
+  return size_t(CH) * N_NT * 32 * 8 + size_t(CH) * 16 * 20 * 4 > size_t(8) * 16 * N_NT * 8 * 4
+             ? size_t(CH) * N_NT * 32 * 8 + size_t(CH) * 16 * 20 * 4
+             : size_t(8) * 16 * N_NT * 8 * 4;
+}
+
+// Later contraction (L > 1): out[l + L*(q + s*r)] = scale * sum_i X(l, i, r) Theta(q, i).
+// CTA: 16 values of l x 32 values of q for one r; K in chunks of CH tiles
+// staged in shared memory; warp w takes the K tiles w, w+8, ...  With
+// dots_pass >= 0 the CTA then runs that Gram-Schmidt pass on its final
+// tile (block partials, last-block combine, scalar epilogue).
+template <int CH>
+__global__ void __launch_bounds__(TC_THREADS)
+k_sk_inner_tc(PtrRef Xr, float* __restrict__ out, int64_t L, int64_t I, int64_t R, int64_t s,
+              int kt_total, const uint2* __restrict__ fragB, int nt_total, float scale,
+              int dots_pass, Work w, StepOpts o, const int* stop) {
+  if (stop != nullptr && *stop) return;
+  const float* __restrict__ X = Xr.get<const float>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int XA = 20;                                                         // 16 l + 4 pad
+  uint2* fB = reinterpret_cast<uint2*>(smem);                                    // [CH][N_NT][32]
+  float* xa = reinterpret_cast<float*>(smem + size_t(CH) * N_NT * 32 * 8);        // [CH*16][XA]
+  __shared__ double red2[GS_MAXW][kMaxK + 2];
+  __shared__ double tot[kMaxK + 2];
+  __shared__ int am_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gid = lane >> 2, tig = lane & 3;
+  const int64_t ltiles = (L + 15) / 16;
+  const int64_t lt = blockIdx.x % ltiles, r = blockIdx.x / ltiles;
+  const int64_t l0 = lt * 16;
+  const int nt0 = blockIdx.y * N_NT;
+  const int nnt = min(N_NT, nt_total - nt0);
+  const float* Xb = X + L * I * r;
+  float acc[N_NT][4];
+#pragma unroll
+  for (int a = 0; a < N_NT; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+  const bool vec = (L % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  for (int kc0 = 0; kc0 < kt_total; kc0 += CH) {
+    const int nk = min(CH, kt_total - kc0);
+    for (int idx = tid; idx < nk * N_NT * 32; idx += TC_THREADS) {
+      const int kk = idx / (N_NT * 32), rem = idx - kk * N_NT * 32, nt = rem >> 5, ln = rem & 31;
+      if (nt < nnt)
+        cp_async8(&fB[idx], &fragB[(static_cast<int64_t>(kc0 + kk) * nt_total + nt0 + nt) * 32 + ln]);
+      else
+        fB[idx] = make_uint2(0u, 0u);
+    }
+    const int64_t i0 = static_cast<int64_t>(kc0) * 16;
+    const int rows = nk * 16;
+    if (vec) {
+      for (int idx = tid; idx < rows * 4; idx += TC_THREADS) {
+        const int k = idx >> 2, part = idx & 3;
+        const int64_t i = i0 + k, l = l0 + part * 4;
+        float* dst = &xa[k * XA + part * 4];
+        if (i < I && l + 3 < L) {
+          cp_async16(dst, Xb + l + L * i);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) dst[u] = (i < I && l + u < L) ? Xb[l + u + L * i] : 0.f;
+        }
+      }
+    } else {
+      for (int idx = tid; idx < rows * 16; idx += TC_THREADS) {
+        const int k = idx >> 4, ll = idx & 15;
+        const int64_t i = i0 + k, l = l0 + ll;
+        const bool v = i < I && l < L;
+        cp_async4(&xa[k * XA + ll], v ? static_cast<const void*>(Xb + l + L * i) : static_cast<const void*>(X), v);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int kk = warp; kk < nk; kk += 8) {
+      uint32_t A[3][4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int l = gid + ((h & 1) ? 8 : 0);
+        const int k = kk * 16 + tig * 2 + ((h & 2) ? 8 : 0);
+        uint32_t lim[3];
+        split_pair(xa[k * XA + l], xa[(k + 1) * XA + l], lim);
+        A[0][h] = lim[0];
+        A[1][h] = lim[1];
+        A[2][h] = lim[2];
+      }
+#pragma unroll
+      for (int nt = 0; nt < N_NT; ++nt) {
+        if (nt >= nnt) break;
+        const uint2 bv = fB[(kk * N_NT + nt) * 32 + lane];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) mma_bf16(acc[nt], A[l], bv.x, bv.y);
+      }
+    }
+    __syncthreads();
+  }
+  float* red = reinterpret_cast<float*>(smem);               // [8][16][N_NT*8]
+  constexpr int TW = N_NT * 8;
+#pragma unroll
+  for (int nt = 0; nt < N_NT; ++nt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int l = gid + h * 8, q = nt * 8 + tig * 2;
+      red[(warp * 16 + l) * TW + q] = acc[nt][2 * h];
+      red[(warp * 16 + l) * TW + q + 1] = acc[nt][2 * h + 1];
+    }
+  __syncthreads();
+  constexpr int ITEMS = (16 * TW + TC_THREADS - 1) / TC_THREADS;
+  float vals[ITEMS];
+  int64_t ix[ITEMS];
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    vals[k] = 0.f;   // entries outside the tensor stay 0 and add nothing below
+    ix[k] = 0;
+    const int e = tid + k * TC_THREADS;
+    if (e >= 16 * TW) continue;
+    const int l = e & 15, q = e >> 4;
+    const int64_t gl = l0 + l, gq = static_cast<int64_t>(nt0) * 8 + q;
+    if (gl >= L || gq >= s) continue;
+    float v = 0.f;
+#pragma unroll
+    for (int wv = 0; wv < 8; ++wv) v += red[(wv * 16 + l) * TW + q];
+    v *= scale;
+    const int64_t g = gl + L * (gq + s * r);
+    out[g] = v;
+    vals[k] = v;
+    ix[k] = g;
+  }
+  const int cnt = ITEMS;
+  if (dots_pass < 0) return;
+  const int ncols = (dots_pass == 0) ? 0 : w.ctl->j + 1;
+  block_partials<float, ITEMS>(w, vals, ix, cnt, ncols, red2);
+  if (!last_block_combine(w, ncols, tot, &am_last)) return;
+  if (tid == 0) gs_finish(w, dots_pass, o, tot, ncols);
+}
+
+// ------------------------------------------------------------------ CUDA-core chain (FP64)
 
 // Y(l, q, r) = scale * sum_i (-1)^bit(q, i) X(l, i, r)
 template <typename T>
@@ -40,7 +554,7 @@ __global__ void k_sketch_mode(PtrRef Xr, T* __restrict__ Y, int64_t L, int64_t I
 }
 
 template <typename T>
-__global__ void k_copy_scale(PtrRef Xr, T* __restrict__ Y, int64_t n, const int* stop) {
+__global__ void k_copy(PtrRef Xr, T* __restrict__ Y, int64_t n, const int* stop) {
   if (stop != nullptr && *stop) return;
   const T* X = Xr.get<const T>();
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
@@ -54,56 +568,95 @@ static unsigned grid_for(int64_t n) {
   return static_cast<unsigned>(b < 1 ? 1 : b);
 }
 
-template <typename T>
-static cudaError_t sketch_t(const SketchPlan& sp, const uint32_t* bits, PtrRef X, T* SX, T* tmp0,
-                           T* tmp1, const int* stop, cudaStream_t s) {
-  int64_t cur[kMaxOrder];
-  int64_t n = 1;
-  for (int k = 0; k < sp.order; ++k) {
-    cur[k] = sp.dims[k];
-    n *= sp.dims[k];
-  }
-  int modes[kMaxOrder], nm = 0;
-  for (int k = 0; k < sp.order; ++k)
-    if (sp.sketched[k]) modes[nm++] = k;
-  if (nm == 0) {     // no sketched mode: S = identity
-    k_copy_scale<T><<<grid_for(n), 256, 0, s>>>(X, SX, n, stop);
-    return cudaGetLastError();
-  }
+int sketch_launches(const SketchPlan& sp) { return sp.nstage == 0 ? 1 : sp.nstage; }
+
+static cudaError_t sketch_f64(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, double* out,
+                              const int* stop, cudaStream_t s) {
   PtrRef src = X;
-  for (int t = 0; t < nm; ++t) {
-    const int k = modes[t];
-    int64_t L = 1, R = 1;
-    for (int u = 0; u < k; ++u) L *= cur[u];
-    for (int u = k + 1; u < sp.order; ++u) R *= cur[u];
-    const int64_t I = cur[k], sk = sp.sdims[k];
-    const bool last = (t == nm - 1);
-    T* dst = last ? SX : ((t % 2 == 0) ? tmp0 : tmp1);
-    const T scale = last ? static_cast<T>(sp.scale) : static_cast<T>(1);
-    k_sketch_mode<T><<<grid_for(L * sk * R), 256, 0, s>>>(src, dst, L, I, R, sk,
-                                                          bits + sp.word_off[k], sp.wpr[k], scale,
-                                                          stop);
+  for (int t = 0; t < sp.nstage; ++t) {
+    const int k = sp.stage_mode[t];
+    const bool last = (t == sp.nstage - 1);
+    double* dst = last ? out : static_cast<double*>((t % 2 == 0) ? sc.tmp0 : sc.tmp1);
+    const double scale = last ? sp.scale : 1.0;
+    k_sketch_mode<double><<<grid_for(sp.stage_out[t]), 256, 0, s>>>(
+        src, dst, sp.stage_L[t], sp.stage_I[t], sp.stage_R[t], sp.stage_s[t],
+        sc.bits + sp.word_off[k], sp.wpr[k], scale, stop);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    cur[k] = sk;
     src = ref(dst);
   }
   return cudaSuccess;
 }
 
-int sketch_launches(const SketchPlan& sp) {
-  int nm = 0;
-  for (int k = 0; k < sp.order; ++k) nm += sp.sketched[k] ? 1 : 0;
-  return nm == 0 ? 1 : nm;
+static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, float* out,
+                              const SketchDots* dots, const int* stop, cudaStream_t s) {
+  PtrRef src = X;
+  for (int t = 0; t < sp.nstage; ++t) {
+    const bool last = (t == sp.nstage - 1);
+    float* dst = last ? out : static_cast<float*>((t % 2 == 0) ? sc.tmp0 : sc.tmp1);
+    const float scale = last ? static_cast<float>(sp.scale) : 1.f;
+    const int kt = sp.stage_kt[t];
+    const uint32_t* fr = sc.frags + sp.frag_off[t];
+    cudaError_t e = cudaSuccess;
+    if (sp.stage_first[t]) {
+      dim3 grid(static_cast<unsigned>((sp.stage_R[t] + F_COLS - 1) / F_COLS),
+                static_cast<unsigned>((sp.stage_ntile[t] + F_MT - 1) / F_MT));
+      if (kt > 16) {
+        constexpr size_t sm = first_smem<32>();
+        e = cudaFuncSetAttribute(k_sk_first_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        k_sk_first_tc<32><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_I[t], sp.stage_R[t], sp.stage_s[t],
+                                                       kt, reinterpret_cast<const uint4*>(fr),
+                                                       sp.stage_ntile[t], scale, stop);
+      } else {
+        constexpr size_t sm = first_smem<16>();
+        e = cudaFuncSetAttribute(k_sk_first_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        k_sk_first_tc<16><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_I[t], sp.stage_R[t], sp.stage_s[t],
+                                                       kt, reinterpret_cast<const uint4*>(fr),
+                                                       sp.stage_ntile[t], scale, stop);
+      }
+    } else {
+      const int64_t ltiles = (sp.stage_L[t] + 15) / 16;
+      dim3 grid(static_cast<unsigned>(ltiles * sp.stage_R[t]),
+                static_cast<unsigned>((sp.stage_ntile[t] + N_NT - 1) / N_NT));
+      const int dpass = (last && dots != nullptr) ? dots->pass : -1;
+      const Work wk = (dots != nullptr) ? *dots->w : Work{};
+      const StepOpts so = (dots != nullptr) ? dots->o : StepOpts{};
+      if (kt > 16) {
+        constexpr size_t sm = inner_smem<32>();
+        e = cudaFuncSetAttribute(k_sk_inner_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        k_sk_inner_tc<32><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_L[t], sp.stage_I[t], sp.stage_R[t],
+                                                       sp.stage_s[t], kt, reinterpret_cast<const uint2*>(fr),
+                                                       sp.stage_ntile[t], scale, dpass, wk, so, stop);
+      } else {
+        constexpr size_t sm = inner_smem<16>();
+        e = cudaFuncSetAttribute(k_sk_inner_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        k_sk_inner_tc<16><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_L[t], sp.stage_I[t], sp.stage_R[t],
+                                                       sp.stage_s[t], kt, reinterpret_cast<const uint2*>(fr),
+                                                       sp.stage_ntile[t], scale, dpass, wk, so, stop);
+      }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    src = ref(dst);
+  }
+  return cudaSuccess;
 }
 
-cudaError_t launch_sketch(const SketchPlan& sp, int dtype, const uint32_t* bits, PtrRef X,
-                          void* SX, void* tmp0, void* tmp1, const int* stop, cudaStream_t s) {
-  if (dtype == RTG_F64)
-    return sketch_t<double>(sp, bits, X, static_cast<double*>(SX), static_cast<double*>(tmp0),
-                            static_cast<double*>(tmp1), stop, s);
-  return sketch_t<float>(sp, bits, X, static_cast<float*>(SX), static_cast<float*>(tmp0),
-                         static_cast<float*>(tmp1), stop, s);
+cudaError_t launch_sketch(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, void* out,
+                          const SketchDots* dots, const int* stop, cudaStream_t s) {
+  int64_t n = 1;
+  for (int k = 0; k < sp.order; ++k) n *= sp.dims[k];
+  if (sp.nstage == 0) {     // no sketched mode: S = identity
+    if (sp.dtype == RTG_F64) k_copy<double><<<grid_for(n), 256, 0, s>>>(X, static_cast<double*>(out), n, stop);
+    else k_copy<float><<<grid_for(n), 256, 0, s>>>(X, static_cast<float*>(out), n, stop);
+    return cudaGetLastError();
+  }
+  if (sp.dtype == RTG_F64) return sketch_f64(sp, sc, X, static_cast<double*>(out), stop, s);
+  return sketch_f32(sp, sc, X, static_cast<float*>(out), sp.fused_dots ? dots : nullptr, stop, s);
 }
 
 }  // namespace rtg

@@ -16,36 +16,34 @@
 
 namespace rtg {
 
-constexpr int TK_THREADS = 128;
+// One warp per candidate mu: FP64 on this GPU has a long dependent
+// latency, so the kernel keeps its chains short (reciprocal pivots computed
+// in parallel, warp shuffles instead of block barriers).
+constexpr int TK_THREADS = 32;
 
 __device__ double block_sum(double v, double* sh) {
+  (void)sh;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int u = 0; u < (int)(blockDim.x >> 5); ++u) t += sh[u];
-  return t;
+  return v;
 }
 
 // Back substitution y = U^{-1} b for an upper-triangular k x k U (leading
-// dimension ldu), parallel over rows; b is overwritten.  Zero pivots give
-// y_i = 0 (the least-squares minimiser of smallest norm on that direction).
-__device__ void back_subst(const double* U, int ldu, double* b, double* y, int k) {
+// dimension ldu) with precomputed reciprocal pivots rinv (0 for a zero
+// pivot: y_i = 0, the smallest-norm least-squares choice on that
+// direction); b is overwritten.
+__device__ void back_subst(const double* U, int ldu, const double* rinv, double* b, double* y,
+                           int k) {
   for (int i = k - 1; i >= 0; --i) {
-    __syncthreads();
-    const double piv = U[i + static_cast<int64_t>(ldu) * i];
-    const double yi = (piv != 0.0) ? b[i] / piv : 0.0;
-    __syncthreads();
+    __syncwarp();
+    const double yi = b[i] * rinv[i];
     if (threadIdx.x == 0) y[i] = yi;
     for (int t = threadIdx.x; t < i; t += blockDim.x) b[t] -= U[t + static_cast<int64_t>(ldu) * i] * yi;
   }
-  __syncthreads();
+  __syncwarp();
 }
 
 // mode 0: least squares (mu = 0); 1: fixed mu = lambda; 2: GCV over the grid.
-// scratch: per block 2*m*m + 3*m doubles.
+// scratch: per block 2*m*m + 4*m doubles.
 __global__ void __launch_bounds__(TK_THREADS)
 k_tikhonov(Work w, const SolveDesc* desc, int mode, double* scratch) {
   Ctl* ctl = w.ctl;
@@ -58,11 +56,12 @@ k_tikhonov(Work w, const SolveDesc* desc, int mode, double* scratch) {
     return;
   }
   const double mu = (mode == 0) ? 0.0 : (mode == 1 ? desc->lambda : desc->mu_grid[blockIdx.x]);
-  double* Top = scratch + static_cast<int64_t>(blockIdx.x) * (2 * m * m + 3 * m);  // k x k, ld m
+  double* Top = scratch + static_cast<int64_t>(blockIdx.x) * (2 * m * m + 4 * m);  // k x k, ld m
   double* Bot = Top + m * m;                                                     // k x k, ld m
   double* c = Bot + m * m;                                                       // k
   double* y = c + m;                                                             // k
   double* cb = y + m;                                                            // k
+  double* rinv = cb + m;                                                         // k
   const double smu = sqrt(mu);
   for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
     const int i = idx % k, j = idx / k;
@@ -105,7 +104,13 @@ k_tikhonov(Work w, const SolveDesc* desc, int mode, double* scratch) {
       __syncthreads();
     }
   }
-  back_subst(Top, m, c, y, k);
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double piv = Top[i + m * i];
+    rinv[i] = (piv != 0.0) ? 1.0 / piv : 0.0;
+  }
+  __syncthreads();
+  back_subst(Top, m, rinv, c, y, k);
   // residual ||g_{0:k} - R y||^2 + g_k^2
   double part = 0.0;
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
@@ -122,7 +127,7 @@ k_tikhonov(Work w, const SolveDesc* desc, int mode, double* scratch) {
       for (int i = col; i >= 0; --i) {
         double acc = (i == col) ? 1.0 : 0.0;
         for (int l = i + 1; l <= col; ++l) acc -= Top[i + m * l] * z[l];
-        z[i] = acc / Top[i + m * i];
+        z[i] = acc * rinv[i];
         inv2 += z[i] * z[i];
       }
     }

@@ -17,9 +17,6 @@
 
 using namespace rtg;
 
-namespace rtg {
-int gs_grid(int64_t d);
-}
 
 namespace {
 
@@ -262,52 +259,9 @@ rtg_status build_op(const rtg_factor* A, int nA, const rtg_factor* B, int nB, co
 // ------------------------------------------------------------------ sketch plans
 
 rtg_status build_sketch(const rtg_shape& sh, const int64_t* sdims, uint64_t seed, uint64_t pid,
-                        SketchPlan& sp) {
-  if (sdims == nullptr) return fail(RTG_ERR_INVALID_ARG, "sketch_dims is NULL");
-  sp = SketchPlan{};
-  sp.order = sh.order;
-  sp.seed = seed;
-  sp.pid = pid;
-  int64_t bit = 0, word = 0, d = 1;
-  double scale = 1.0;
-  for (int k = 0; k < sh.order; ++k) {
-    if (sdims[k] < 1) return fail(RTG_ERR_INVALID_ARG, "sketch_dims[%d]=%lld must be >= 1", k, (long long)sdims[k]);
-    sp.dims[k] = sh.dims[k];
-    if (sdims[k] < sh.dims[k]) {
-      sp.sketched[k] = 1;
-      sp.sdims[k] = sdims[k];
-      sp.bit_off[k] = bit;
-      sp.word_off[k] = word;
-      sp.wpr[k] = static_cast<int>((sh.dims[k] + 31) / 32);
-      bit += sdims[k] * sh.dims[k];
-      word += sdims[k] * sp.wpr[k];
-      scale /= std::sqrt(static_cast<double>(sdims[k]));
-    } else {
-      sp.sketched[k] = 0;
-      sp.sdims[k] = sh.dims[k];
-    }
-    d *= sp.sdims[k];
-  }
-  sp.total_words = word;
-  sp.d = d;
-  sp.scale = scale;
-  // largest intermediate of the contraction chain (all but the last output)
-  int64_t cur[kMaxOrder];
-  for (int k = 0; k < sh.order; ++k) cur[k] = sh.dims[k];
-  int last = -1;
-  for (int k = 0; k < sh.order; ++k)
-    if (sp.sketched[k]) last = k;
-  int64_t tmx = 1;
-  for (int k = 0; k < sh.order; ++k) {
-    if (!sp.sketched[k]) continue;
-    cur[k] = sp.sdims[k];
-    if (k == last) break;
-    int64_t sz = 1;
-    for (int u = 0; u < sh.order; ++u) sz *= cur[u];
-    if (sz > tmx) tmx = sz;
-  }
-  sp.tmp_elems = tmx;
-  if (d > (int64_t(1) << 31) - 1) return fail(RTG_ERR_UNSUPPORTED, "sketch size %lld too large", (long long)d);
+                        int dtype, SketchPlan& sp) {
+  const char* err = make_sketch_plan(sh.order, sh.dims, sdims, seed, pid, dtype, sp);
+  if (err != nullptr) return fail(RTG_ERR_INVALID_ARG, "%s", err);
   return RTG_OK;
 }
 
@@ -345,7 +299,7 @@ struct Carver {
 
 // Lays out (and, with mem != null, points) every buffer of an Arnoldi workspace.
 size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, int tk_blocks,
-                  int64_t apply_elems, Work& w, void** tA, void** tB, uint32_t** bits) {
+                  int64_t apply_elems, Work& w, void** tA, void** tB, SketchScratch* sk) {
   Carver c(mem);
   const size_t e = elt_size(dtype);
   const int64_t d = sp.d;
@@ -354,15 +308,20 @@ size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, 
   w.n = n;
   w.d = static_cast<int>(d);
   w.m = m;
-  const int G = gs_grid(d);
+  int64_t G = gs_grid(d);
+  if (sp.dots_blocks > G) G = sp.dots_blocks;
   w.V = c.take<char>(size_t(m + 1) * n * e);
   w.W = c.take<char>(size_t(n) * e);
   w.S = c.take<char>(size_t(d) * e);
-  w.tmp0 = c.take<char>(size_t(sp.tmp_elems) * e);
-  w.tmp1 = c.take<char>(size_t(sp.tmp_elems) * e);
+  w.Spart = c.take<char>(size_t(d) * e);
+  w.nparts = 1;
+  void* skmem = c.take<char>(sketch_scratch_bytes(sp));
+  *sk = carve_sketch_scratch(sp, skmem);
+  w.tmp0 = sk->tmp0;
+  w.tmp1 = sk->tmp1;
   w.Q = c.take<char>(size_t(m + 1) * d * e);
   w.part = c.take<double>(size_t(G) * (m + 2));
-  w.part_rows = G;
+  w.part_rows = static_cast<int>(G);
   w.counter = c.take<unsigned>(8);
   w.ctl = c.take<Ctl>(1);
   w.H = c.take<double>(size_t(m + 1) * m);
@@ -375,10 +334,10 @@ size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, 
   w.rho_hist = c.take<double>(kMaxK);
   w.y = c.take<double>(m);
   w.gcv = c.take<double>(kMaxMu);
-  w.ysel = c.take<double>(size_t(kMaxMu) * m + size_t(tk_blocks) * (2 * size_t(m) * m + 3 * m));
+  w.ysel = c.take<double>(size_t(kMaxMu) * m + size_t(tk_blocks) * (2 * size_t(m) * m + 4 * m));
   *tA = c.take<char>(size_t(apply_elems) * e);
   *tB = c.take<char>(size_t(apply_elems) * e);
-  *bits = c.take<uint32_t>(size_t(sp.total_words) + 1);
+  if (mem == nullptr) *sk = SketchScratch{};
   return c.off + 256;
 }
 
@@ -397,7 +356,7 @@ struct SolvePlan {
   Work w{};
   void* tA = nullptr;
   void* tB = nullptr;
-  uint32_t* bits = nullptr;
+  SketchScratch sk;
   SolveDesc* desc_dev = nullptr;
   InfoDev* info_dev = nullptr;
   SolveDesc* desc_host = nullptr;
@@ -427,8 +386,8 @@ struct SolvePlan {
 struct rtg_context {
   int device = 0;
   std::map<std::string, std::unique_ptr<OpHolder>> ops;
-  std::map<std::string, std::unique_ptr<DevBuf>> bits;
-  DevBuf tA, tB, t0, t1;
+  std::map<std::string, std::unique_ptr<DevBuf>> sketches;   // signs, fragments and scratch per sketch
+  DevBuf tA, tB;
   std::map<std::string, std::unique_ptr<SolvePlan>> plans;
 };
 
@@ -440,7 +399,7 @@ struct rtg_krylov_state {
   Work w{};
   void* tA = nullptr;
   void* tB = nullptr;
-  uint32_t* bits = nullptr;
+  SketchScratch sk;
   int dtype = RTG_F32;
   int m = 0;
   bool started = false;
@@ -486,7 +445,7 @@ PtrRef desc_ref(const void* const* field) {
 rtg_status enqueue_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s) {
   Work& w = P.w;
   CK(launch_reset(w, 0, s));
-  CK(launch_theta_bits(P.sp, P.bits, s));
+  CK(launch_theta(P.sp, P.sk.bits, P.sk.frags, s));
   PtrRef C = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->C));
   PtrRef src = C;
   if (P.has_x0) {   // R_0 = C - Phi(X_0) into the V_0 slot
@@ -494,13 +453,15 @@ rtg_status enqueue_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s) {
     CK(launch_apply(P.op.op, P.dtype, X0, ref(w.V), -1.0, 1.0, C, P.tA, P.tB, nullptr, s));
     src = ref(w.V);
   }
-  CK(launch_sketch(P.sp, P.dtype, P.bits, src, w.S, w.tmp0, w.tmp1, nullptr, s));
-  CK(launch_start(w, src, so, s));
+  const bool fused = P.sp.fused_dots != 0;
+  SketchDots dots{&w, 0, so};
+  CK(launch_sketch(P.sp, P.sk, src, fused ? w.S : w.Spart, fused ? &dots : nullptr, nullptr, s));
+  CK(launch_start(w, src, so, fused, s));
   return RTG_OK;
 }
 
 rtg_status enqueue_step(const OpHolder& op, const SketchPlan& sp, const Work& w, int dtype,
-                        void* tA, void* tB, const uint32_t* bits, const StepOpts& so,
+                        void* tA, void* tB, const SketchScratch& sk, const StepOpts& so,
                         cudaStream_t s) {
   PtrRef vj;
   vj.base = w.V;
@@ -508,8 +469,10 @@ rtg_status enqueue_step(const OpHolder& op, const SketchPlan& sp, const Work& w,
   vj.stride = w.n;
   const int* stop = &w.ctl->stop;
   CK(launch_apply(op.op, dtype, vj, ref(w.W), 1.0, 0.0, PtrRef{}, tA, tB, stop, s));
-  CK(launch_sketch(sp, dtype, bits, ref(w.W), w.S, w.tmp0, w.tmp1, stop, s));
-  CK(launch_pass1(w, s));
+  const bool fused = sp.fused_dots != 0;
+  SketchDots dots{&w, 1, so};
+  CK(launch_sketch(sp, sk, ref(w.W), fused ? w.S : w.Spart, fused ? &dots : nullptr, stop, s));
+  if (!fused) CK(launch_pass1(w, s));
   CK(launch_pass2(w, so, s));
   CK(launch_update(w, so, s));
   return RTG_OK;
@@ -573,7 +536,7 @@ rtg_status build_graph(SolvePlan& P) {
     cudaError_t e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCaptureToGraph(body)");
     if (st == RTG_OK) {
-      st = enqueue_step(P.op, P.sp, P.w, P.dtype, P.tA, P.tB, P.bits, so, cs2);
+      st = enqueue_step(P.op, P.sp, P.w, P.dtype, P.tA, P.tB, P.sk, so, cs2);
       cudaGraph_t bodyout = nullptr;
       e = cudaStreamEndCapture(cs2, &bodyout);
       if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture(body)");
@@ -682,11 +645,11 @@ rtg_status rtg_sketch(rtg_handle h, rtg_shape shape, rtg_dtype dtype, const int6
   RK(check_shape(shape, &n));
   RK(check_dtype(dtype));
   SketchPlan sp;
-  RK(build_sketch(shape, sketch_dims, seed, pid, sp));
+  RK(build_sketch(shape, sketch_dims, seed, pid, dtype, sp));
   DeviceGuard dg(h->device);
   if (!is_device_ptr(X) || !is_device_ptr(SX)) return fail(RTG_ERR_INVALID_ARG, "X and SX must be device pointers");
-  if (overlaps(X, SX, size_t(std::max<int64_t>(n, sp.d)) * elt_size(dtype)) && X == SX)
-    return fail(RTG_ERR_INVALID_ARG, "SX must not alias X");
+  if (overlaps(X, SX, size_t(std::min<int64_t>(n, sp.d)) * elt_size(dtype)))
+    return fail(RTG_ERR_INVALID_ARG, "SX must not overlap X");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::string key;
   append_bytes(key, &sp.order, sizeof sp.order);
@@ -694,25 +657,26 @@ rtg_status rtg_sketch(rtg_handle h, rtg_shape shape, rtg_dtype dtype, const int6
   append_bytes(key, sp.sdims, sizeof sp.sdims);
   append_bytes(key, &seed, sizeof seed);
   append_bytes(key, &pid, sizeof pid);
-  auto it = h->bits.find(key);
-  DevBuf* bits = nullptr;
-  if (it == h->bits.end()) {
-    if (h->bits.size() > 64) {
+  append_bytes(key, &sp.dtype, sizeof sp.dtype);
+  auto it = h->sketches.find(key);
+  DevBuf* buf = nullptr;
+  bool fresh = false;
+  if (it == h->sketches.end()) {
+    if (h->sketches.size() > 16) {
       cudaDeviceSynchronize();
-      h->bits.clear();
+      h->sketches.clear();
     }
     auto b = std::make_unique<DevBuf>();
-    RK(b->ensure(size_t(sp.total_words + 1) * sizeof(uint32_t)));
-    CK(launch_theta_bits(sp, static_cast<uint32_t*>(b->p), s));
-    bits = b.get();
-    h->bits[key] = std::move(b);
+    RK(b->ensure(sketch_scratch_bytes(sp)));
+    buf = b.get();
+    h->sketches[key] = std::move(b);
+    fresh = true;
   } else {
-    bits = it->second.get();
+    buf = it->second.get();
   }
-  RK(h->t0.ensure(size_t(sp.tmp_elems) * elt_size(dtype)));
-  RK(h->t1.ensure(size_t(sp.tmp_elems) * elt_size(dtype)));
-  CK(launch_sketch(sp, dtype, static_cast<const uint32_t*>(bits->p), ref(X), SX, h->t0.p, h->t1.p,
-                   nullptr, s));
+  const SketchScratch sc = carve_sketch_scratch(sp, buf->p);
+  if (fresh) CK(launch_theta(sp, sc.bits, sc.frags, s));
+  CK(launch_sketch(sp, sc, ref(X), SX, nullptr, nullptr, s));
   return RTG_OK;
 }
 
@@ -734,16 +698,16 @@ rtg_status rtg_krylov_create(rtg_handle h, const rtg_factor* A, int32_t nA, cons
   K->dtype = dtype;
   K->m = m;
   RK(build_op(A, nA, B, nB, shape, K->op));
-  RK(build_sketch(shape, sketch_dims, seed, pid, K->sp));
+  RK(build_sketch(shape, sketch_dims, seed, pid, dtype, K->sp));
   const int64_t ae = apply_scratch_elems(K->op.op);
   Work tmpw;
   void *ta, *tb;
-  uint32_t* bits;
-  const size_t bytes = carve_work(nullptr, dtype, n, K->sp, m, 1, ae, tmpw, &ta, &tb, &bits);
+  SketchScratch tsk;
+  const size_t bytes = carve_work(nullptr, dtype, n, K->sp, m, 1, ae, tmpw, &ta, &tb, &tsk);
   RK(K->mem.ensure(bytes));
   CK(cudaMemset(K->mem.p, 0, bytes));
-  carve_work(K->mem.p, dtype, n, K->sp, m, 1, ae, K->w, &K->tA, &K->tB, &K->bits);
-  CK(launch_theta_bits(K->sp, K->bits, nullptr));
+  carve_work(K->mem.p, dtype, n, K->sp, m, 1, ae, K->w, &K->tA, &K->tB, &K->sk);
+  CK(launch_theta(K->sp, K->sk.bits, K->sk.frags, nullptr));
   CK(cudaDeviceSynchronize());
   *out = K.release();
   return RTG_OK;
@@ -771,11 +735,13 @@ rtg_status rtg_krylov_start(rtg_handle h, rtg_krylov K, const void* C, const voi
     CK(launch_apply(K->op.op, K->dtype, ref(X0), ref(w.V), -1.0, 1.0, ref(C), K->tA, K->tB, nullptr, s));
     src = ref(w.V);
   }
-  CK(launch_sketch(K->sp, K->dtype, K->bits, src, w.S, w.tmp0, w.tmp1, nullptr, s));
   StepOpts o{};
   o.tol = 0.0;
   o.bd_tol = K->dtype == RTG_F64 ? 1e-12 : 1e-6;
-  CK(launch_start(w, src, o, s));
+  const bool fused = K->sp.fused_dots != 0;
+  SketchDots dots{&w, 0, o};
+  CK(launch_sketch(K->sp, K->sk, src, fused ? w.S : w.Spart, fused ? &dots : nullptr, nullptr, s));
+  CK(launch_start(w, src, o, fused, s));
   K->started = true;
   return RTG_OK;
 }
@@ -788,7 +754,7 @@ rtg_status rtg_arnoldi_step(rtg_handle h, rtg_krylov K, rtg_stream stream) {
   o.tol = 0.0;
   o.bd_tol = K->dtype == RTG_F64 ? 1e-12 : 1e-6;
   o.solve_mode = 0;
-  return enqueue_step(K->op, K->sp, K->w, K->dtype, K->tA, K->tB, K->bits, o,
+  return enqueue_step(K->op, K->sp, K->w, K->dtype, K->tA, K->tB, K->sk, o,
                       reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -848,7 +814,7 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
   if (overlaps(C, X, bytes_t)) return fail(RTG_ERR_INVALID_ARG, "X overlaps C");
 
   SketchPlan sp;
-  RK(build_sketch(shape, sketch_dims, seed, 0, sp));
+  RK(build_sketch(shape, sketch_dims, seed, 0, dtype, sp));
   const bool use_graph = !(opts.flags & RTG_FLAG_NO_GRAPH);
   std::string key = op_key(A, nA, B, nB, shape);
   append_bytes(key, &dtype, sizeof dtype);
@@ -882,11 +848,11 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
     const int tkb = mode == 2 ? opts.n_mu : 1;
     Work tmpw;
     void *ta, *tb;
-    uint32_t* bits;
-    const size_t bytes = carve_work(nullptr, dtype, n, sp, m, tkb, ae, tmpw, &ta, &tb, &bits);
+    SketchScratch tsk;
+    const size_t bytes = carve_work(nullptr, dtype, n, sp, m, tkb, ae, tmpw, &ta, &tb, &tsk);
     RK(P->mem.ensure(bytes));
     CK(cudaMemset(P->mem.p, 0, bytes));
-    carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->bits);
+    carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk);
     RK(P->small.ensure(sizeof(SolveDesc) + sizeof(InfoDev) + 512));
     P->desc_dev = static_cast<SolveDesc*>(P->small.p);
     P->info_dev = reinterpret_cast<InfoDev*>(static_cast<char*>(P->small.p) + ((sizeof(SolveDesc) + 255) & ~size_t(255)));
@@ -899,9 +865,10 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
     {
       int nsk = 0;
       for (int k = 0; k < sp.order; ++k) nsk += sp.sketched[k];
-      P->launches_pro = 1 + (nsk > 0 ? 1 : 0) + (has_x0 ? apply_launches(P->op.op, true) : 0) +
-                        sketch_launches(sp) + 2;
-      P->launches_step = apply_launches(P->op.op, false) + sketch_launches(sp) + 3;
+      const int gs = sp.fused_dots ? 0 : 1;
+      P->launches_pro = 1 + (nsk > 0 ? (dtype == RTG_F32 ? 2 : 1) : 0) +
+                        (has_x0 ? apply_launches(P->op.op, true) : 0) + sketch_launches(sp) + gs + 1;
+      P->launches_step = apply_launches(P->op.op, false) + sketch_launches(sp) + gs + 2;
       P->launches_epi = 3;
     }
     if (use_graph) RK(build_graph(*P));
@@ -944,7 +911,7 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
   } else {
     const StepOpts so = solve_step_opts(*P, 0, 0);
     RK(enqueue_prologue(*P, so, s));
-    for (int j = 0; j < m; ++j) RK(enqueue_step(P->op, P->sp, P->w, dtype, P->tA, P->tB, P->bits, so, s));
+    for (int j = 0; j < m; ++j) RK(enqueue_step(P->op, P->sp, P->w, dtype, P->tA, P->tB, P->sk, so, s));
     RK(enqueue_epilogue(*P, s));
   }
   CK(cudaEventRecord(P->ev1, s));

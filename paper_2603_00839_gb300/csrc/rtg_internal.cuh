@@ -96,6 +96,8 @@ struct Work {
   void* V;                     // (m+1) * n
   void* W;                     // n
   void* S;                     // d   (sketch of W, then s after the first GS pass)
+  void* Spart;                 // nparts * d partial sketches written by the chain
+  int nparts;
   void* tmp0;                  // sketch chain intermediates
   void* tmp1;
   void* Q;                     // (m+1) * d sketched basis
@@ -117,9 +119,11 @@ struct Work {
 };
 
 // Sketch description: modes with s_k < I_k carry Theta_k as packed sign
-// bits (row-major rows of ceil(I_k/32) words).
+// bits (row-major rows of ceil(I_k/32) words), and the contraction chain
+// (one stage per sketched mode, in increasing mode order).
 struct SketchPlan {
   int order;
+  int dtype;                   // data type of the chain (RTG_F64 / RTG_F32)
   int64_t dims[kMaxOrder];
   int64_t sdims[kMaxOrder];    // s'_k
   int sketched[kMaxOrder];
@@ -128,10 +132,39 @@ struct SketchPlan {
   int wpr[kMaxOrder];          // 32-bit words per row
   int64_t total_words;         // packed device array size (uint32 words)
   int64_t d;                   // prod(s'_k)
-  int64_t tmp_elems;           // largest intermediate of the chain
+  int64_t tmp_elems;           // elements of one scratch tensor
   double scale;                // prod 1/sqrt(s_k) over sketched modes
   uint64_t seed, pid;
+  // contraction stages
+  int nstage;
+  int stage_mode[kMaxOrder];
+  int stage_first[kMaxOrder];  // 1: L == 1 (first-mode tensor-core kernel)
+  int stage_split[kMaxOrder];  // K split (partial outputs)
+  int stage_kt[kMaxOrder];     // K tiles of 16
+  int stage_ntile[kMaxOrder];  // m16 (first) or n8 (later) tiles of the sketch size
+  int64_t stage_L[kMaxOrder], stage_I[kMaxOrder], stage_R[kMaxOrder], stage_s[kMaxOrder];
+  int64_t stage_out[kMaxOrder];   // elements of one stage output
+  int64_t frag_off[kMaxOrder];    // uint32 offset of the stage's Theta fragments
+  int64_t frag_words;
+  int64_t part_elems;             // elements of each scratch tensor
+  int last_split;                 // partial copies of the final sketch (1)
+  int fused_dots;                 // the last stage can run the first Gram-Schmidt pass
+  int64_t dots_blocks;            // CTAs of that last stage (rows of partial sums)
 };
+
+// Scratch of one sketch chain: signs, Theta fragments, two tensors.
+struct SketchScratch {
+  uint32_t* bits = nullptr;
+  uint32_t* frags = nullptr;
+  void* tmp0 = nullptr;
+  void* tmp1 = nullptr;
+};
+
+// Fills sp; returns an error message or nullptr (k_sketch.cu).
+const char* make_sketch_plan(int order, const int64_t* dims, const int64_t* sketch_dims,
+                             uint64_t seed, uint64_t pid, int dtype, SketchPlan& sp);
+size_t sketch_scratch_bytes(const SketchPlan& sp);
+SketchScratch carve_sketch_scratch(const SketchPlan& sp, void* base);
 
 // A tensor pointer resolved on the device: an explicit base, or a base read
 // from device memory (per-call descriptors of a captured graph), optionally
@@ -162,6 +195,8 @@ void record_error(const char* msg);
 cudaError_t launch_philox_words(uint64_t seed, uint64_t pid, int64_t n_words, uint64_t* out,
                                 cudaStream_t s);
 cudaError_t launch_theta_bits(const SketchPlan& sp, uint32_t* bits, cudaStream_t s);
+// signs, then (FP32 chain) the Theta fragments of every stage
+cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, cudaStream_t s);
 
 // k_apply.cu: Y = alpha * Phi(X) + beta * Z (Z may be null when beta == 0).
 // tmp: scratch of n elements for the unfused path (may be null if unused).
@@ -173,9 +208,14 @@ int64_t apply_scratch_elems(const OpPlan& op);
 // Kernels one launch_apply issues (combine: alpha != 1 or a Z term).
 int apply_launches(const OpPlan& op, bool combine);
 
-// k_sketch.cu: SX = S(X); tmp0/tmp1 hold sp.tmp_elems elements each.
-cudaError_t launch_sketch(const SketchPlan& sp, int dtype, const uint32_t* bits, PtrRef X,
-                          void* SX, void* tmp0, void* tmp1, const int* stop, cudaStream_t s);
+// k_sketch.cu: S(X) into `out` (d elements).  With dots != null and
+// sp.fused_dots, the last contraction also runs Gram-Schmidt pass
+// dots->pass (0: beta, 1: h1) on the sketch it writes (out must be w.S).
+struct Work;
+struct StepOpts;
+struct SketchDots;
+cudaError_t launch_sketch(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, void* out,
+                          const SketchDots* dots, const int* stop, cudaStream_t s);
 int sketch_launches(const SketchPlan& sp);
 
 // k_arnoldi.cu: the sketched Arnoldi process on a Work.
@@ -192,8 +232,15 @@ struct StepOpts {
   int use_cond;
   unsigned long long cond;   // cudaGraphConditionalHandle
 };
-cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, cudaStream_t s);
+struct SketchDots {
+  const Work* w;
+  int pass;
+  StepOpts o;
+};
+// pass 0 on w.Spart (unless the sketch already ran it) and the scaling V_0, Q_0
+cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fused, cudaStream_t s);
 cudaError_t launch_pass1(const Work& w, cudaStream_t s);
+int gs_grid(int64_t d);
 cudaError_t launch_pass2(const Work& w, const StepOpts& o, cudaStream_t s);
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s);
 cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s);

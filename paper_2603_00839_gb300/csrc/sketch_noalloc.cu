@@ -17,7 +17,7 @@
 
 namespace {
 
-constexpr size_t kNoAllocBytes = size_t(4) << 20;   // 4 MiB of static device scratch
+constexpr size_t kNoAllocBytes = size_t(16) << 20;  // 16 MiB of static device scratch
 
 // Shared by every call on a device; keeps the contents of the last call.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -68,53 +68,13 @@ extern "C" rtg_status rtg_sketch_noalloc(rtg_shape shape, rtg_dtype dtype,
   if (sketch_dims == nullptr || X == nullptr || SX == nullptr || X == SX)
     return noalloc_fail(RTG_ERR_INVALID_ARG, "sketch_dims, X and SX must be non-NULL and SX must not alias X");
   if (!on_device(X) || !on_device(SX)) return noalloc_fail(RTG_ERR_INVALID_ARG, "X and SX must be device pointers");
-  SketchPlan sp{};
-  sp.order = shape.order;
-  sp.seed = seed;
-  sp.pid = problem_id;
-  int64_t bit = 0, word = 0, d = 1;
-  double scale = 1.0;
-  for (int k = 0; k < shape.order; ++k) {
+  for (int k = 0; k < shape.order; ++k)
     if (shape.dims[k] < 1 || shape.dims[k] > (int64_t(1) << 31)) return noalloc_fail(RTG_ERR_INVALID_ARG, "shape.dims must be in 1..2^31");
-    if (sketch_dims[k] < 1) return noalloc_fail(RTG_ERR_INVALID_ARG, "sketch_dims must be >= 1");
-    sp.dims[k] = shape.dims[k];
-    if (sketch_dims[k] < shape.dims[k]) {
-      sp.sketched[k] = 1;
-      sp.sdims[k] = sketch_dims[k];
-      sp.bit_off[k] = bit;
-      sp.word_off[k] = word;
-      sp.wpr[k] = static_cast<int>((shape.dims[k] + 31) / 32);
-      bit += sketch_dims[k] * shape.dims[k];
-      word += sketch_dims[k] * sp.wpr[k];
-      scale /= sqrt(static_cast<double>(sketch_dims[k]));
-    } else {
-      sp.sdims[k] = shape.dims[k];
-    }
-    d *= sp.sdims[k];
-  }
-  sp.total_words = word;
-  sp.d = d;
-  sp.scale = scale;
-  int64_t cur[kMaxOrder], tmx = 1;
-  int last = -1;
-  for (int k = 0; k < shape.order; ++k) {
-    cur[k] = shape.dims[k];
-    if (sp.sketched[k]) last = k;
-  }
-  for (int k = 0; k < shape.order; ++k) {
-    if (!sp.sketched[k]) continue;
-    cur[k] = sp.sdims[k];
-    if (k == last) break;
-    int64_t sz = 1;
-    for (int u = 0; u < shape.order; ++u) sz *= cur[u];
-    if (sz > tmx) tmx = sz;
-  }
-  sp.tmp_elems = tmx;
-  // scratch layout: [sign bits | intermediate 0 | intermediate 1], 256-byte aligned
-  const size_t elt = dtype == RTG_F64 ? 8 : 4;
-  const size_t bits_bytes = ((size_t(word) + 1) * 4 + 255) & ~size_t(255);
-  const size_t tmp_bytes = (size_t(tmx) * elt + 255) & ~size_t(255);
-  const size_t need = bits_bytes + 2 * tmp_bytes;
+  SketchPlan sp;
+  const char* perr = make_sketch_plan(shape.order, shape.dims, sketch_dims, seed, problem_id, dtype, sp);
+  if (perr != nullptr) return noalloc_fail(RTG_ERR_INVALID_ARG, perr);
+  // scratch: packed signs, Theta fragments and two contraction intermediates
+  const size_t need = sketch_scratch_bytes(sp);
   if (need > kNoAllocBytes) {
     char msg[256];
     snprintf(msg, sizeof msg, "sketch needs %zu bytes of scratch; the static scratch holds %zu bytes",
@@ -127,15 +87,13 @@ extern "C" rtg_status rtg_sketch_noalloc(rtg_shape shape, rtg_dtype dtype,
   void* base = nullptr;
   cudaError_t e = scratch_address(device, &base);
   if (e != cudaSuccess) return noalloc_fail(RTG_ERR_CUDA, cudaGetErrorString(e));
-  uint32_t* bits = static_cast<uint32_t*>(base);
-  char* t0 = static_cast<char*>(base) + bits_bytes;
-  char* t1 = t0 + tmp_bytes;
+  const SketchScratch sc = carve_sketch_scratch(sp, base);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // every byte the chain reads is written first in this call: the signs by
-  // launch_theta_bits, the intermediates by the contraction that produces
-  // them, so nothing in the shared scratch needs clearing
-  e = launch_theta_bits(sp, bits, s);
-  if (e == cudaSuccess) e = launch_sketch(sp, dtype, bits, ref(X), SX, t0, t1, nullptr, s);
+  // every byte the chain reads is written first in this call: the signs and
+  // fragments by launch_theta, the intermediates by the contraction that
+  // produces them, so nothing in the shared scratch needs clearing
+  e = launch_theta(sp, sc.bits, sc.frags, s);
+  if (e == cudaSuccess) e = launch_sketch(sp, sc, ref(X), SX, nullptr, nullptr, s);
   if (e != cudaSuccess) return noalloc_fail(RTG_ERR_CUDA, cudaGetErrorString(e));
   return RTG_OK;
 }
