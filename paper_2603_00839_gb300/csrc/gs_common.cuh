@@ -10,6 +10,7 @@
 namespace rtg {
 
 constexpr int GS_MAXW = 8;   // warps per block of the reducing kernels (256 threads)
+constexpr int kRedCols = 2 * kMaxK + 4;   // columns of one reduction (see gs_ncols)
 
 template <typename A>
 __device__ __forceinline__ A warp_sum(A v) {
@@ -23,58 +24,122 @@ __device__ __forceinline__ void set_cond(const StepOpts& o, int keep_going) {
     cudaGraphSetConditional(static_cast<cudaGraphConditionalHandle>(o.cond), keep_going ? 1u : 0u);
 }
 
-// Givens update of column J of the rotated Hessenberg (Eq. 11S):
-// rotations 0..J-1 applied to R(:, J), a new rotation zeroes R(J+1, J),
-// g is rotated; |g[J+1]| is the least-squares residual.
-__device__ inline void givens_column(const Work& w, int J) {
-  const int ld = w.m + 1;
-  double* Rc = w.R + static_cast<int64_t>(ld) * J;
-  const double* Hc = w.H + static_cast<int64_t>(ld) * J;
-  for (int i = 0; i <= J + 1; ++i) Rc[i] = Hc[i];
-  for (int i = 0; i < J; ++i) {
-    const double a = Rc[i], b = Rc[i + 1];
-    Rc[i] = w.cs[i] * a + w.sn[i] * b;
-    Rc[i + 1] = -w.sn[i] * a + w.cs[i] * b;
+// Double-float ("float-float") accumulation for FP32 data: the FP64 pipe
+// of this GPU runs at 1/64 of the FP32 rate with a long dependent latency,
+// so sums of products of FP32 values are kept as unevaluated pairs
+// hi + lo of floats with error-free transformations (exact product by
+// FMA, Knuth's two-sum), about 48 significant bits.  IEEE intrinsics keep
+// the compiler from contracting or reassociating them.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  const FF s = ff_two_sum(x.hi, y.hi);
+  const float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return ff_two_sum(s.hi, e);
+}
+__device__ __forceinline__ FF ff_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_warp_sum(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    FF w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = ff_add(v, w);
   }
-  const double a = Rc[J], b = Rc[J + 1];
-  const double den = hypot(a, b);
-  double c = 1.0, s = 0.0;
-  if (den != 0.0) {
-    c = a / den;
-    s = b / den;
-  }
-  Rc[J] = den;
-  Rc[J + 1] = 0.0;
-  w.cs[J] = c;
-  w.sn[J] = s;
-  const double gJ = w.g[J];
-  w.g[J + 1] = -s * gJ;
-  w.g[J] = c * gJ;
+  return v;
+}
+__device__ __forceinline__ double ff_to_double(FF v) {
+  return static_cast<double>(v.hi) + static_cast<double>(v.lo);
 }
 
-// Per-block partial sums: column i < ncols is sum_e Q_i[e] * v[e] over the
-// entries this block holds, column ncols is sum_e v[e]^2.  Each thread
-// passes up to ITEMS entries (vals, idx; cnt valid).  Data-type products
-// and warp sums, FP64 across warps.  Writes row blockIdx.x of w.part.
-// red: shared scratch [GS_MAXW][kMaxK + 2].
+// Dot-product accumulator: float-float for FP32 data, FP64 for FP64 data.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<float> {
+  FF v{0.f, 0.f};
+  __device__ __forceinline__ void add(float a, float b) { v = ff_add(v, ff_prod(a, b)); }
+  __device__ __forceinline__ double warp_total() { return ff_to_double(ff_warp_sum(v)); }
+};
+template <>
+struct DotAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ double warp_total() { return warp_sum(v); }
+};
+
+// Columns of the per-block partial sums of one Gram-Schmidt reduction:
+// [0, J] s . Q_i, [J+1] s . s, [J+2, 2J+2] Q_J . Q_i (the new row of the
+// Gram matrix G = Q^T Q).  The start of a process (J = -1) has only s . s.
+__device__ __forceinline__ int gs_ncols(int J) { return J < 0 ? 1 : 2 * J + 3; }
+
+// Per-block partial sums of the columns above: products of the stored
+// values accumulated in double-float (FP32 data) or FP64 (FP64 data).
+// Each thread passes up to ITEMS entries (vals at sketch indices idx);
+// entries past cnt or with a negative index are ignored.  Writes row
+// (linear block id) of w.part.  red: shared [GS_MAXW][kRedCols].
 template <typename T, int ITEMS>
-__device__ void block_partials(const Work& w, const T* vals, const int64_t* idx, int cnt, int ncols,
-                               double (*red)[kMaxK + 2]) {
+__device__ void block_partials(const Work& w, const T* vals, const int64_t* idx, int cnt, int J,
+                               double (*red)[kRedCols]) {
   const T* Q = static_cast<const T*>(w.Q);
   const int64_t d = w.d;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  for (int i = 0; i <= ncols; ++i) {
-    T p = 0;
+  const int ncols = gs_ncols(J);
+  T sv[ITEMS], qJ[ITEMS];
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k)
-      if (k < cnt) p += vals[k] * ((i < ncols) ? Q[static_cast<int64_t>(i) * d + idx[k]] : vals[k]);
-    p = warp_sum(p);
-    if (lane == 0) red[warp][i] = static_cast<double>(p);
+  for (int k = 0; k < ITEMS; ++k) {
+    const bool ok = k < cnt && idx[k] >= 0;
+    sv[k] = ok ? vals[k] : static_cast<T>(0);
+    qJ[k] = (ok && J >= 0) ? Q[static_cast<int64_t>(J) * d + idx[k]] : static_cast<T>(0);
+  }
+  {   // s . s
+    DotAcc<T> a;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) a.add(sv[k], sv[k]);
+    const double t = a.warp_total();
+    if (lane == 0) red[warp][J + 1] = t;
+  }
+  // columns of Q in groups of 8: all loads of a group go out before any use
+  constexpr int GRP = 8;
+  for (int i0 = 0; i0 <= J; i0 += GRP) {
+    T qv[GRP][ITEMS];
+#pragma unroll
+    for (int g = 0; g < GRP; ++g)
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const bool ok = k < cnt && idx[k] >= 0 && i0 + g <= J;
+        qv[g][k] = ok ? Q[static_cast<int64_t>(i0 + g) * d + idx[k]] : static_cast<T>(0);
+      }
+#pragma unroll
+    for (int g = 0; g < GRP; ++g) {
+      if (i0 + g > J) break;
+      DotAcc<T> p, q;
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        p.add(sv[k], qv[g][k]);
+        q.add(qJ[k], qv[g][k]);
+      }
+      const double tp = p.warp_total(), tq = q.warp_total();
+      if (lane == 0) {
+        red[warp][i0 + g] = tp;
+        red[warp][J + 2 + i0 + g] = tq;
+      }
+    }
   }
   __syncthreads();
-  const int rowlen = w.m + 2;
-  for (int i = threadIdx.x; i <= ncols; i += blockDim.x) {
+  const int rowlen = 2 * w.m + 4;
+  for (int i = threadIdx.x; i < ncols; i += blockDim.x) {
     double acc = 0.0;
     for (int u = 0; u < nw; ++u) acc += red[u][i];
     w.part[static_cast<int64_t>(blockIdx.x + gridDim.x * blockIdx.y) * rowlen + i] = acc;
@@ -82,7 +147,7 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
 }
 
 // Ticket: returns true in every thread of the last block to finish, after
-// tot[0..ncols] holds the sum of all blocks' rows (one warp per column,
+// tot[0..ncols) holds the sum of all blocks' rows (one warp per column,
 // lanes striding over rows).  The counter wraps back to zero by itself.
 __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot, int* am_last) {
   __threadfence();
@@ -94,8 +159,8 @@ __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot,
   __threadfence();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  const int rowlen = w.m + 2;
-  for (int i = warp; i <= ncols; i += nw) {
+  const int rowlen = 2 * w.m + 4;
+  for (int i = warp; i < ncols; i += nw) {
     double a0 = 0.0, a1 = 0.0;
     unsigned b = lane;
     for (; b + 32 < nblk; b += 64) {
@@ -110,74 +175,148 @@ __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot,
   return true;
 }
 
-// Scalar epilogue (one thread).  pass 0: beta = ||R_0||_Theta; pass 1:
-// h1 and ||S(W)||^2; pass 2: h = h1 + h2, h_{j+1,j}, breakdown test,
-// Givens, rho_j and the stop rule.
-__device__ inline void gs_finish(const Work& w, int pass, const StepOpts& o, const double* tot,
-                                 int ncols) {
+// Start of a process (one thread): beta = ||R_0||_Theta = sqrt(s . s).
+__device__ inline void gs_finish_start(const Work& w, const StepOpts& o, const double* tot) {
   Ctl* ctl = w.ctl;
-  const int J = ctl->j;
   const double tol = o.desc_tol ? *o.desc_tol : o.tol;
-  const double bd_tol = o.desc_bd_tol ? *o.desc_bd_tol : o.bd_tol;
-  if (pass == 0) {
-    const double beta = sqrt(tot[0]);
-    if (!isfinite(beta)) {
-      ctl->status = RTG_ERR_NONFINITE;
-      ctl->stop = 1;
-    } else if (beta == 0.0) {
+  const double beta = sqrt(tot[0]);
+  if (!isfinite(beta)) {
+    ctl->status = RTG_ERR_NONFINITE;
+    ctl->stop = 1;
+  } else if (beta == 0.0) {
+    ctl->converged = 1;
+    ctl->stop = 1;
+  } else {
+    ctl->beta = beta;
+    if (ctl->cycle == 0) ctl->beta0 = beta;
+    w.g[0] = beta;
+    ctl->rho = beta / ctl->beta0;
+    if (ctl->rho <= tol && ctl->cycle > 0) {
       ctl->converged = 1;
       ctl->stop = 1;
-    } else {
-      ctl->beta = beta;
-      if (ctl->cycle == 0) ctl->beta0 = beta;
-      w.g[0] = beta;
-      ctl->rho = beta / ctl->beta0;
-      if (ctl->rho <= tol && ctl->cycle > 0) {
-        ctl->converged = 1;
-        ctl->stop = 1;
-      }
-      if (w.m == 0) ctl->stop = 1;
     }
-    set_cond(o, !ctl->stop);
-    return;
+    if (w.m == 0) ctl->stop = 1;
   }
-  if (pass == 1) {
-    for (int i = 0; i < ncols; ++i) w.h1[i] = tot[i];
-    ctl->pre2 = tot[ncols];
-    return;
-  }
-  double hh = 0.0;
+  set_cond(o, !ctl->stop);
+}
+
+// Step finish from one reduction (every thread of the last block).
+// Classical Gram-Schmidt with one re-orthogonalisation pass, written with
+// the Gram matrix G = Q^T Q of the stored sketched basis so that a single
+// pass over Q suffices: h1 = Q^T s, h2 = Q^T (s - Q h1) = h1 - G h1,
+// h = h1 + h2 and h_{j+1,j}^2 = ||s - Q h||^2 = s.s - 2 h.h1 + h.(G h), all
+// in FP64.  Then the Hessenberg column, breakdown test, Givens update
+// (Eq. 11S) and stop rule.  sh: shared scratch of >= 5 (kMaxK + 2) doubles.
+__device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const double* tot, double* sh) {
+  Ctl* ctl = w.ctl;
+  const int J = ctl->j;
   const int ld = w.m + 1;
-  double* Hc = w.H + static_cast<int64_t>(ld) * J;
-  bool finite = true;
-  for (int i = 0; i < ncols; ++i) {
-    w.h2[i] = tot[i];
-    hh += tot[i] * tot[i];
-    const double h = w.h1[i] + tot[i];
-    Hc[i] = h;
-    finite = finite && isfinite(h);
+  const double* h1 = tot;
+  const double s2 = tot[J + 1];
+  const double* grow = tot + J + 2;
+  double* col = sh;                    // h, then the rotated column
+  double* cs = col + (kMaxK + 2);
+  double* sn = cs + (kMaxK + 2);
+  double* red = sn + (kMaxK + 2);      // scalars, then one value per row
+  double* G = w.G;
+  // new row/column of G
+  for (int i = threadIdx.x; i <= J; i += blockDim.x) {
+    G[i + static_cast<int64_t>(ld) * J] = grow[i];
+    G[J + static_cast<int64_t>(ld) * i] = grow[i];
   }
-  const double hn2 = tot[ncols] - hh;
-  const double hn = sqrt(hn2 > 0.0 ? hn2 : 0.0);
-  finite = finite && isfinite(hn) && isfinite(ctl->pre2);
-  const bool breakdown = finite && (hn <= bd_tol * sqrt(ctl->pre2));
-  Hc[J + 1] = breakdown ? 0.0 : hn;
-  for (int i = J + 2; i < ld; ++i) Hc[i] = 0.0;
-  givens_column(w, J);
-  const double rho = fabs(w.g[J + 1]) / ctl->beta0;
-  ctl->rho = rho;
-  w.rho_hist[ctl->iters_total] = rho;
-  ctl->iters_total += 1;
-  ctl->hnext = hn;
-  ctl->j = J + 1;
-  if (!finite) ctl->status = RTG_ERR_NONFINITE;
-  if (breakdown) ctl->breakdown = 1;
-  const bool conv = finite && rho <= tol;
-  if (conv || breakdown) ctl->converged = 1;
-  const bool stop = !finite || breakdown || conv || (J + 1 >= w.m);
-  ctl->stop = stop ? 1 : 0;
-  ctl->skip_update = (!finite || breakdown || (o.solve_mode && stop)) ? 1 : 0;
-  set_cond(o, !stop);
+  for (int i = threadIdx.x; i < J; i += blockDim.x) {
+    cs[i] = w.cs[i];
+    sn[i] = w.sn[i];
+  }
+  __syncthreads();
+  // h = h1 + (h1 - G h1): one warp per row, lanes across the columns
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i <= J; i += nw) {
+    double gh = 0.0;
+    for (int k = lane; k <= J; k += 32) gh += G[i + static_cast<int64_t>(ld) * k] * h1[k];
+    gh = warp_sum(gh);
+    if (lane == 0) col[i] = 2.0 * h1[i] - gh;
+  }
+  __syncthreads();
+  // h.h1 and h.(G h)
+  double* hgh_row = red + 32;          // (G h)_i * h_i per row
+  for (int i = warp; i <= J; i += nw) {
+    double gh = 0.0;
+    for (int k = lane; k <= J; k += 32) gh += G[i + static_cast<int64_t>(ld) * k] * col[k];
+    gh = warp_sum(gh);
+    if (lane == 0) hgh_row[i] = gh * col[i];
+  }
+  __syncthreads();
+  double a = 0.0, b = 0.0;
+  if (warp == 0) {
+    for (int i = lane; i <= J; i += 32) {
+      a += col[i] * h1[i];
+      b += hgh_row[i];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+      red[0] = a;
+      red[1] = b;
+    }
+  }
+  __syncthreads();
+  const double hh1 = red[0];
+  const double hgh = red[1];
+  double* Hc = w.H + static_cast<int64_t>(ld) * J;
+  for (int i = threadIdx.x; i <= J; i += blockDim.x) Hc[i] = col[i];
+  for (int i = J + 2 + threadIdx.x; i < ld; i += blockDim.x) Hc[i] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double tol = o.desc_tol ? *o.desc_tol : o.tol;
+    const double bd_tol = o.desc_bd_tol ? *o.desc_bd_tol : o.bd_tol;
+    bool finite = isfinite(s2) && isfinite(hh1) && isfinite(hgh);
+    for (int i = 0; i <= J; ++i) finite = finite && isfinite(col[i]);
+    const double hn2 = s2 - 2.0 * hh1 + hgh;
+    const double hn = sqrt(hn2 > 0.0 ? hn2 : 0.0);
+    const bool breakdown = finite && (hn <= bd_tol * sqrt(s2));
+    col[J + 1] = breakdown ? 0.0 : hn;
+    Hc[J + 1] = col[J + 1];
+    // rotations 0..J-1 on the new column, then the new rotation
+    double x = col[0];
+    for (int i = 0; i < J; ++i) {
+      const double y = col[i + 1];
+      col[i] = cs[i] * x + sn[i] * y;
+      x = -sn[i] * x + cs[i] * y;
+    }
+    const double y = col[J + 1];
+    const double den = hypot(x, y);
+    double c = 1.0, sv = 0.0;
+    if (den != 0.0) {
+      c = x / den;
+      sv = y / den;
+    }
+    col[J] = den;
+    col[J + 1] = 0.0;
+    w.cs[J] = c;
+    w.sn[J] = sv;
+    const double gJ = w.g[J];
+    w.g[J + 1] = -sv * gJ;
+    w.g[J] = c * gJ;
+    const double rho = fabs(sv * gJ) / ctl->beta0;
+    ctl->rho = rho;
+    ctl->pre2 = s2;
+    w.rho_hist[ctl->iters_total] = rho;
+    ctl->iters_total += 1;
+    ctl->hnext = hn;
+    ctl->j = J + 1;
+    if (!finite) ctl->status = RTG_ERR_NONFINITE;
+    if (breakdown) ctl->breakdown = 1;
+    const bool conv = finite && rho <= tol;
+    if (conv || breakdown) ctl->converged = 1;
+    const bool stop = !finite || breakdown || conv || (J + 1 >= w.m);
+    ctl->stop = stop ? 1 : 0;
+    ctl->skip_update = (!finite || breakdown || (o.solve_mode && stop)) ? 1 : 0;
+    set_cond(o, !stop);
+  }
+  __syncthreads();
+  double* Rc = w.R + static_cast<int64_t>(ld) * J;
+  for (int i = threadIdx.x; i <= J + 1; i += blockDim.x) Rc[i] = col[i];
 }
 
 }  // namespace rtg

@@ -120,6 +120,16 @@ __device__ __forceinline__ void cp_async8z(void* smem, const void* gmem, bool va
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
 }
 
+template <int RR, typename T>
+struct RegGeom {
+  // FP32 rows start on a 16-byte boundary: the halo is widened to RA >= RR
+  // columns (a multiple of 4) and the filter window starts OFF = RA - RR in.
+  static constexpr int RA = (sizeof(T) == 4) ? ((RR + 3) / 4) * 4 : RR;
+  static constexpr int OFF = RA - RR;
+  static constexpr int Wd = RTX + 2 * RA;
+  static constexpr int Ht = RTY + 2 * RR;
+};
+
 template <typename T, int NC, int RR>
 __global__ void __launch_bounds__(FTHREADS)
 k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
@@ -127,9 +137,9 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
   const T* __restrict__ X = Xr.get<const T>();
   T* __restrict__ Y = Yr.get<T>();
   const T* __restrict__ Z = Zr.get<const T>();
+  using G = RegGeom<RR, T>;
   constexpr int NT = 2 * RR + 1;
-  constexpr int Wd = RTX + 2 * RR;
-  constexpr int Ht = RTY + 2 * RR;
+  constexpr int Wd = G::Wd, Ht = G::Ht, RA = G::RA, OFF = G::OFF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* in_s = reinterpret_cast<T*>(smem_raw);      // NC x Ht x Wd
   T* tmp = in_s + NC * Ht * Wd;                  // Ht x RTX
@@ -140,21 +150,37 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
     t1[t] = (u1 >= 0 && u1 <= 2 * a.r1) ? static_cast<T>(a.t1[u1]) : static_cast<T>(0);
     t2[t] = (u2 >= 0 && u2 <= 2 * a.r2) ? static_cast<T>(a.t2[u2]) : static_cast<T>(0);
   }
-  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * RTX;
-  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * RTY;
+  const int x0 = blockIdx.x * RTX;
+  const int y0 = blockIdx.y * RTY;
+  const int I1 = static_cast<int>(a.I1), I2 = static_cast<int>(a.I2);
   const int64_t plane = a.I1 * a.I2;
   const int vx = threadIdx.x & (RTX - 1);        // mode-2 pass: column
   const int vy = (threadIdx.x / RTX) * VSEG;     // mode-2 pass: first of 4 rows
   for (int64_t slab = blockIdx.z; slab < a.nslab; slab += gridDim.z) {
     __syncthreads();
-    for (int idx = threadIdx.x; idx < NC * Ht * Wd; idx += FTHREADS) {
-      const int c = idx / (Ht * Wd), rem = idx - c * (Ht * Wd);
-      const int yy = rem / Wd, xx = rem - yy * Wd;
-      const int64_t gx = x0 - RR + xx, gy = y0 - RR + yy;
-      const bool v = gx >= 0 && gx < a.I1 && gy >= 0 && gy < a.I2;
-      const T* src = X + (slab * NC + c) * plane + (v ? gy * a.I1 + gx : 0);
-      if (sizeof(T) == 4) cp_async4z(&in_s[idx], src, v);
-      else cp_async8z(&in_s[idx], src, v);
+    const T* Xs = X + slab * NC * plane;
+    if (sizeof(T) == 4 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+      // 16-byte copies; a float4 lies wholly inside or outside (I1 % 4 == 0)
+      constexpr int W4 = Wd / 4;
+      for (int idx = threadIdx.x; idx < NC * Ht * W4; idx += FTHREADS) {
+        const int row = idx / W4, f4 = idx - row * W4;
+        const int c = row / Ht, yy = row - c * Ht;
+        const int gy = y0 - RR + yy, gx = x0 - RA + 4 * f4;
+        const bool v = gy >= 0 && gy < I2 && gx >= 0 && gx < I1;
+        const T* src = v ? Xs + c * plane + static_cast<int64_t>(gy) * I1 + gx : X;
+        const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(&in_s[row * Wd + 4 * f4]));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(v ? 16 : 0));
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < NC * Ht * Wd; idx += FTHREADS) {
+        const int row = idx / Wd, xx = idx - row * Wd;
+        const int c = row / Ht, yy = row - c * Ht;
+        const int gy = y0 - RR + yy, gx = x0 - RA + xx;
+        const bool v = gy >= 0 && gy < I2 && gx >= 0 && gx < I1;
+        const T* src = v ? Xs + c * plane + static_cast<int64_t>(gy) * I1 + gx : X;
+        if (sizeof(T) == 8) cp_async8z(&in_s[idx], src, v);
+        else cp_async4z(&in_s[idx], src, v);
+      }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
@@ -166,10 +192,28 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
       for (int task = threadIdx.x; task < Ht * (RTX / RSEG); task += FTHREADS) {
         const int yy = task / (RTX / RSEG);
         const int xs = (task - yy * (RTX / RSEG)) * RSEG;
-        const T* row = ins + yy * Wd + xs;
         T win[RSEG + 2 * RR];
+        if (sizeof(T) == 4) {
+          // aligned 16-byte loads covering the window, which starts OFF & 3 floats in
+          constexpr int A0 = OFF & ~3, SH = OFF & 3;
+          constexpr int NV = (SH + RSEG + 2 * RR + 3) / 4;
+          const float4* rp = reinterpret_cast<const float4*>(ins + yy * Wd + xs + A0);
+          float buf[NV * 4];
 #pragma unroll
-        for (int u = 0; u < RSEG + 2 * RR; ++u) win[u] = row[u];
+          for (int v4 = 0; v4 < NV; ++v4) {
+            const float4 q = rp[v4];
+            buf[4 * v4] = q.x;
+            buf[4 * v4 + 1] = q.y;
+            buf[4 * v4 + 2] = q.z;
+            buf[4 * v4 + 3] = q.w;
+          }
+#pragma unroll
+          for (int u = 0; u < RSEG + 2 * RR; ++u) win[u] = static_cast<T>(buf[SH + u]);
+        } else {
+          const T* row = ins + yy * Wd + xs + OFF;
+#pragma unroll
+          for (int u = 0; u < RSEG + 2 * RR; ++u) win[u] = row[u];
+        }
 #pragma unroll
         for (int o = 0; o < RSEG; ++o) {
           T sacc = 0;
@@ -194,18 +238,18 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
       }
       __syncthreads();
     }
-    const int64_t gx = x0 + vx;
-    if (gx < a.I1) {
+    const int gx = x0 + vx;
+    if (gx < I1) {
 #pragma unroll
       for (int o = 0; o < VSEG; ++o) {
-        const int64_t gy = y0 + vy + o;
-        if (gy >= a.I2) break;
+        const int gy = y0 + vy + o;
+        if (gy >= I2) break;
 #pragma unroll
         for (int p = 0; p < NC; ++p) {
           T v = 0;
 #pragma unroll
           for (int c = 0; c < NC; ++c) v += static_cast<T>(a.M[p + NC * c]) * acc[c][o];
-          const int64_t idx = (slab * NC + p) * plane + gy * a.I1 + gx;
+          const int64_t idx = (slab * NC + p) * plane + static_cast<int64_t>(gy) * I1 + gx;
           T out = static_cast<T>(a.alpha) * v;
           if (Z != nullptr) out += static_cast<T>(a.beta) * Z[idx];
           Y[idx] = out;
@@ -339,13 +383,16 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
       a.M[0] = 1.0;
     }
     const int rr = reg_bucket(op.r1 > op.r2 ? op.r1 : op.r2);
-    if (rr > 0 && (a.nc == 1 || a.nc == 3)) {
-      const size_t smem = static_cast<size_t>(a.nc * (RTY + 2 * rr) * (RTX + 2 * rr) + (RTY + 2 * rr) * RTX) * sizeof(T);
+    const bool fits = a.I1 < (int64_t(1) << 30) && a.I2 < (int64_t(1) << 30) &&
+                      (sizeof(T) == 8 || (a.I1 % 4) == 0);
+    if (rr > 0 && fits && (a.nc == 1 || a.nc == 3)) {
       dim3 grid(static_cast<unsigned>((a.I1 + RTX - 1) / RTX), static_cast<unsigned>((a.I2 + RTY - 1) / RTY),
                 static_cast<unsigned>(a.nslab < 65535 ? a.nslab : 65535));
       cudaError_t e = cudaSuccess;
 #define RTG_REG_CASE(NC, RR)                                                                          \
   if (a.nc == NC && rr == RR) {                                                                       \
+    using Gm = RegGeom<RR, T>;                                                                        \
+    const size_t smem = static_cast<size_t>(NC * Gm::Ht * Gm::Wd + Gm::Ht * RTX) * sizeof(T);         \
     e = cudaFuncSetAttribute(k_apply_reg<T, NC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                              static_cast<int>(smem));                                                  \
     if (e != cudaSuccess) return e;                                                                   \

@@ -7,11 +7,13 @@
 // sketch of W after every subtraction.  Because S is linear,
 // S(W - h V_i) = S(W) - h S(V_i), so the whole process can run on the
 // sketch s = S(Phi V_j): classical Gram-Schmidt with one
-// re-orthogonalisation pass (h = h1 + h2), equal to MGS in exact
-// arithmetic.  h_{j+1,j} = ||s - Q h||, taken as sqrt(||s'||^2 - ||h2||^2)
-// with s' = s - Q h1 (Q has orthonormal columns).  The full-space
-// update then applies the total h once:
-//   V_{j+1} = (W - sum_i h_i V_i) / h_{j+1,j},  Q_{j+1} = (s' - Q h2) / h_{j+1,j}.
+// re-orthogonalisation pass, equal to MGS in exact arithmetic.  The second
+// pass is taken through the Gram matrix G = Q^T Q of the stored sketches
+// (kept one row per step): h2 = Q^T (s - Q h1) = h1 - G h1, so one
+// reduction over Q per step gives h = h1 + h2 and
+// h_{j+1,j}^2 = ||s - Q h||^2 = s.s - 2 h.h1 + h.G h, all in FP64.  The
+// update then applies h once:
+//   V_{j+1} = (W - sum_i h_i V_i) / h_{j+1,j},  Q_{j+1} = (s - Q h) / h_{j+1,j}.
 //
 // Reductions: each CTA reduces its slice (data-type partials, warp
 // shuffles, FP64 across warps) into a row of `part`; the last CTA to finish
@@ -34,61 +36,47 @@ int gs_grid(int64_t d) {
   return static_cast<int>(g < 1 ? 1 : g);
 }
 
-// pass 0: start (norm of the summed sketch -> beta); 1: h1 = Q^T S and
-// ||S||^2 (S summed from the chain's partial sketches); 2: S <- S - Q h1,
-// h2 = Q^T S, ||S||^2, then the step epilogue.
+// pass 0: start of the process, beta = ||S|| with S summed from the
+// chain's partial sketches; pass 1: one Arnoldi step's Gram-Schmidt
+// reduction on S (s . Q_i, s . s and the new Gram row) and its finish.
 template <typename T>
 __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(Work w, int pass, StepOpts o) {
   Ctl* ctl = w.ctl;
   if (ctl->stop) return;
-  const int J = ctl->j;
-  const int ncols = (pass == 0) ? 0 : J + 1;
+  const int J = (pass == 0) ? -1 : ctl->j;
   const int d = w.d;
   T* S = static_cast<T*>(w.S);
-  const T* Q = static_cast<const T*>(w.Q);
-  __shared__ T coef[kMaxK + 1];
-  __shared__ double red[GS_MAXW][kMaxK + 2];
-  __shared__ double tot[kMaxK + 2];
+  __shared__ double red[GS_MAXW][kRedCols];
+  __shared__ double tot[kRedCols];
   __shared__ int am_last;
-  if (pass == 2)
-    for (int i = threadIdx.x; i < ncols; i += GS_THREADS) coef[i] = static_cast<T>(w.h1[i]);
-  __syncthreads();
-
   const int64_t chunk = (d + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk;
   const int64_t hi = (lo + chunk < d) ? lo + chunk : d;
   T sv[GS_ITEMS];
   int64_t ix[GS_ITEMS];
   int cnt = 0;
+  const T* P = static_cast<const T*>(w.Spart);
 #pragma unroll
   for (int k = 0; k < GS_ITEMS; ++k) {
     ix[k] = lo + threadIdx.x + static_cast<int64_t>(k) * GS_THREADS;
-    if (ix[k] < hi) cnt = k + 1;
-  }
-  if (pass == 2) {
-#pragma unroll
-    for (int k = 0; k < GS_ITEMS; ++k) {
-      if (k >= cnt) break;
-      T v = S[ix[k]];
-      for (int i = 0; i < ncols; ++i) v -= coef[i] * Q[static_cast<int64_t>(i) * d + ix[k]];
-      sv[k] = v;
-      S[ix[k]] = v;
-    }
-  } else {
-    // sum the partial sketches of the contraction chain into S
-    const T* P = static_cast<const T*>(w.Spart);
-#pragma unroll
-    for (int k = 0; k < GS_ITEMS; ++k) {
-      if (k >= cnt) break;
+    sv[k] = 0;
+    if (ix[k] < hi) {
+      cnt = k + 1;
       T v = 0;
       for (int p = 0; p < w.nparts; ++p) v += P[static_cast<int64_t>(p) * d + ix[k]];
       S[ix[k]] = v;
       sv[k] = v;
+    } else {
+      ix[k] = -1;
     }
   }
-  block_partials<T, GS_ITEMS>(w, sv, ix, cnt, ncols, red);
-  if (!last_block_combine(w, ncols, tot, &am_last)) return;
-  if (threadIdx.x == 0) gs_finish(w, pass, o, tot, ncols);
+  block_partials<T, GS_ITEMS>(w, sv, ix, cnt, J, red);
+  if (!last_block_combine(w, gs_ncols(J), tot, &am_last)) return;
+  if (pass == 0) {
+    if (threadIdx.x == 0) gs_finish_start(w, o, tot);
+  } else {
+    gs_finish_gram(w, o, tot, &red[0][0]);
+  }
 }
 
 // V_0 = src / beta, Q_0 = S / beta
@@ -134,14 +122,14 @@ __global__ void k_update(Work w, StepOpts o) {
   }
   if (ctl->skip_update || ctl->j == 0) return;
   const int jj = ctl->j;
-  __shared__ T hs[kMaxK + 1], h2s[kMaxK + 1];
+  __shared__ T hs[kMaxK + 1];
+  __shared__ double hd[kMaxK + 1];
   const int ld = w.m + 1;
   for (int i = threadIdx.x; i < jj; i += blockDim.x) {
-    hs[i] = static_cast<T>(w.H[static_cast<int64_t>(ld) * (jj - 1) + i]);
-    h2s[i] = static_cast<T>(w.h2[i]);
+    const double h = w.H[static_cast<int64_t>(ld) * (jj - 1) + i];
+    hs[i] = static_cast<T>(h);
+    hd[i] = h;
   }
-  __syncthreads();
-  const T inv = static_cast<T>(1.0 / ctl->hnext);
   T* V = static_cast<T*>(w.V);
   T* Q = static_cast<T*>(w.Q);
   const T* W = static_cast<const T*>(w.W);
@@ -154,9 +142,34 @@ __global__ void k_update(Work w, StepOpts o) {
     const float4* W4 = reinterpret_cast<const float4*>(W);
     const float4* V4 = reinterpret_cast<const float4*>(V);
     float4* out = reinterpret_cast<float4*>(V) + static_cast<int64_t>(jj) * n4;
+    // the first element's data loads go out before the barrier that publishes h
+    constexpr int PRE = 8;
+    float4 pre[PRE];
+    float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t0 < n4) {
+      w0 = W4[t0];
+#pragma unroll
+      for (int i = 0; i < PRE; ++i)
+        if (i < jj) pre[i] = V4[static_cast<int64_t>(i) * n4 + t0];
+    }
+    __syncthreads();
+    const T inv = static_cast<T>(1.0 / ctl->hnext);
+    const float fi = static_cast<float>(inv);
     for (int64_t e = t0; e < n4; e += stride) {
-      float4 acc = W4[e];
+      float4 acc;
       int i = 0;
+      if (e == t0) {
+        acc = w0;
+#pragma unroll
+        for (int u = 0; u < PRE; ++u) {
+          if (u >= jj) break;
+          const float h0 = hs[u];
+          acc.x -= h0 * pre[u].x; acc.y -= h0 * pre[u].y; acc.z -= h0 * pre[u].z; acc.w -= h0 * pre[u].w;
+        }
+        i = jj < PRE ? jj : PRE;
+      } else {
+        acc = W4[e];
+      }
       for (; i + 4 <= jj; i += 4) {
         const float4 a = V4[static_cast<int64_t>(i) * n4 + e];
         const float4 b = V4[static_cast<int64_t>(i + 1) * n4 + e];
@@ -173,21 +186,24 @@ __global__ void k_update(Work w, StepOpts o) {
         const float h0 = hs[i];
         acc.x -= h0 * a.x; acc.y -= h0 * a.y; acc.z -= h0 * a.z; acc.w -= h0 * a.w;
       }
-      const float fi = static_cast<float>(inv);
       acc.x *= fi; acc.y *= fi; acc.z *= fi; acc.w *= fi;
       out[e] = acc;
     }
   } else {
+    __syncthreads();
+    const T inv = static_cast<T>(1.0 / ctl->hnext);
     for (int64_t e = t0; e < n; e += stride) {
       T v = W[e];
       for (int i = 0; i < jj; ++i) v -= hs[i] * V[static_cast<int64_t>(i) * n + e];
       V[static_cast<int64_t>(jj) * n + e] = v * inv;
     }
   }
+  // Q_{j} = (s - Q h) / h_{j,j-1}, accumulated in FP64 and rounded once
+  const double invd = 1.0 / ctl->hnext;
   for (int64_t e = t0; e < d; e += stride) {
-    T v = S[e];
-    for (int i = 0; i < jj; ++i) v -= h2s[i] * Q[static_cast<int64_t>(i) * d + e];
-    Q[static_cast<int64_t>(jj) * d + e] = v * inv;
+    double v = static_cast<double>(S[e]);
+    for (int i = 0; i < jj; ++i) v -= hd[i] * static_cast<double>(Q[static_cast<int64_t>(i) * d + e]);
+    Q[static_cast<int64_t>(jj) * d + e] = static_cast<T>(v * invd);
   }
 }
 
@@ -236,20 +252,14 @@ cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fuse
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass1(const Work& w, cudaStream_t s) {
-  StepOpts o{};
+cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s) {
   const int g = gs_grid(w.d);
   if (w.dtype == RTG_F64) k_gs_pass<double><<<g, GS_THREADS, 0, s>>>(w, 1, o);
   else k_gs_pass<float><<<g, GS_THREADS, 0, s>>>(w, 1, o);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass2(const Work& w, const StepOpts& o, cudaStream_t s) {
-  const int g = gs_grid(w.d);
-  if (w.dtype == RTG_F64) k_gs_pass<double><<<g, GS_THREADS, 0, s>>>(w, 2, o);
-  else k_gs_pass<float><<<g, GS_THREADS, 0, s>>>(w, 2, o);
-  return cudaGetLastError();
-}
+
 
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s) {
   if (w.dtype == RTG_F64) k_update<double><<<ew_grid(w.n), 256, 0, s>>>(w, o);

@@ -28,6 +28,12 @@
 
 namespace rtg {
 
+constexpr int TC_THREADS = 256;   // 8 warps split K
+constexpr int F_COLS = 16;        // first stage: columns of X per CTA
+constexpr int F_MT = 4;           // first stage: m16 tiles (64 Theta rows) per CTA
+constexpr int N_NT = 2;           // later stages: n8 tiles (16 Theta rows) per CTA
+constexpr int XA = 20;            // blocked row: 16 values of l + 4 pad (conflict-free A loads)
+
 // ------------------------------------------------------------------ plan
 
 const char* make_sketch_plan(int order, const int64_t* dims, const int64_t* sdims_in,
@@ -66,7 +72,7 @@ const char* make_sketch_plan(int order, const int64_t* dims, const int64_t* sdim
   int64_t cur[kMaxOrder];
   for (int k = 0; k < order; ++k) cur[k] = dims[k];
   sp.nstage = 0;
-  int64_t frag = 0, part = 1;
+  int64_t frag = 0;
   for (int k = 0; k < order; ++k) {
     if (!sp.sketched[k]) continue;
     const int t = sp.nstage++;
@@ -81,24 +87,44 @@ const char* make_sketch_plan(int order, const int64_t* dims, const int64_t* sdim
     sp.stage_s[t] = s;
     sp.stage_first[t] = (L == 1) ? 1 : 0;
     sp.stage_kt[t] = static_cast<int>((I + 15) / 16);
-    const int64_t out_elems = L * s * R;
-    sp.stage_out[t] = out_elems;
+    sp.stage_out[t] = L * s * R;
+    sp.stage_split[t] = 1;
     if (dtype == RTG_F32) {
       sp.frag_off[t] = frag;
       if (sp.stage_first[t]) {
-        sp.stage_ntile[t] = static_cast<int>((s + 15) / 16);          // m16 tiles of Theta rows
-        frag += int64_t(sp.stage_ntile[t]) * sp.stage_kt[t] * 32 * 4;   // uint4 per lane
+        sp.stage_ntile[t] = static_cast<int>((s + 15) / 16);            // m16 tiles of Theta rows
+        const int64_t blocks = (sp.stage_ntile[t] + F_MT - 1) / F_MT;   // F_MT tiles per CTA
+        frag += blocks * sp.stage_kt[t] * F_MT * 32 * 4;                // uint4 per lane
       } else {
-        sp.stage_ntile[t] = static_cast<int>((s + 7) / 8);           // n8 tiles of Theta rows
-        frag += int64_t(sp.stage_ntile[t]) * sp.stage_kt[t] * 32 * 2;   // uint2 per lane
+        sp.stage_ntile[t] = static_cast<int>((s + 7) / 8);             // n8 tiles of Theta rows
+        const int64_t blocks = (sp.stage_ntile[t] + N_NT - 1) / N_NT;   // N_NT tiles per CTA
+        frag += blocks * sp.stage_kt[t] * N_NT * 32 * 2;                // uint2 per lane
       }
     }
-    sp.stage_split[t] = 1;
     cur[k] = s;
   }
   sp.frag_words = frag;
-  for (int t = 0; t + 1 < sp.nstage; ++t)
-    if (sp.stage_out[t] > part) part = sp.stage_out[t];
+  // layouts between stages (FP32 chain)
+  int64_t part = 1;
+  for (int t = 0; t < sp.nstage; ++t)
+    sp.stage_in_blocked[t] = (dtype == RTG_F32 && t > 0 && !sp.stage_first[t]) ? 1 : 0;
+  for (int t = 0; t < sp.nstage; ++t) {
+    if (t + 1 < sp.nstage) {
+      const int k = sp.stage_mode[t], k2 = sp.stage_mode[t + 1];
+      int64_t M = 1;
+      for (int u = k + 1; u < k2; ++u) M *= dims[u];
+      sp.next_M[t] = M;
+      sp.next_L[t] = sp.stage_L[t + 1];
+      sp.next_I[t] = sp.stage_I[t + 1];
+      sp.next_LT[t] = (sp.stage_L[t + 1] + 15) / 16;
+      sp.stage_out_alloc[t] = sp.stage_in_blocked[t + 1]
+                                  ? sp.stage_R[t + 1] * sp.next_LT[t] * sp.stage_I[t + 1] * 20
+                                  : sp.stage_out[t];
+      if (sp.stage_out_alloc[t] > part) part = sp.stage_out_alloc[t];
+    } else {
+      sp.stage_out_alloc[t] = sp.stage_out[t];
+    }
+  }
   sp.part_elems = part;
   sp.last_split = 1;
   sp.tmp_elems = part;
@@ -106,7 +132,7 @@ const char* make_sketch_plan(int order, const int64_t* dims, const int64_t* sdim
   sp.dots_blocks = 0;
   if (sp.fused_dots) {
     const int t = sp.nstage - 1;
-    sp.dots_blocks = ((sp.stage_L[t] + 15) / 16) * sp.stage_R[t] * ((sp.stage_ntile[t] + 3) / 4);
+    sp.dots_blocks = ((sp.stage_L[t] + 15) / 16) * sp.stage_R[t] * ((sp.stage_ntile[t] + N_NT - 1) / N_NT);
   }
   return nullptr;
 }
@@ -116,7 +142,7 @@ static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 size_t sketch_scratch_bytes(const SketchPlan& sp) {
   const size_t elt = sp.dtype == RTG_F64 ? 8 : 4;
   return al256((sp.total_words + 1) * 4) + al256((sp.frag_words + 1) * 4) +
-         2 * al256(size_t(sp.part_elems) * elt) + 256;
+         2 * al256(size_t(sp.part_elems) * elt) + 256 + 256;
 }
 
 SketchScratch carve_sketch_scratch(const SketchPlan& sp, void* base) {
@@ -130,6 +156,8 @@ SketchScratch carve_sketch_scratch(const SketchPlan& sp, void* base) {
   sc.tmp0 = p;
   p += al256(size_t(sp.part_elems) * elt);
   sc.tmp1 = p;
+  p += al256(size_t(sp.part_elems) * elt);
+  sc.status = reinterpret_cast<int*>(p);
   return sc;
 }
 
@@ -165,9 +193,14 @@ __global__ void k_theta_frags(FragArgs a, const uint32_t* __restrict__ bits, uin
   while (t + 1 < a.nstage && g >= a.lane_off[t + 1]) ++t;
   const int64_t local = g - a.lane_off[t];
   const int lane = static_cast<int>(local & 31);
-  const int64_t tile_k = local >> 5;                 // kk * ntile + tile
-  const int64_t tile = tile_k % a.ntile[t];
-  const int kk = static_cast<int>(tile_k / a.ntile[t]);
+  // blocked layout: ((block * kt + kk) * per + tile_in_block) * 32 + lane, per = F_MT or N_NT
+  const int per = a.first[t] ? F_MT : N_NT;
+  const int64_t idx = local >> 5;
+  const int tin = static_cast<int>(idx % per);
+  const int kk = static_cast<int>((idx / per) % a.kt[t]);
+  const int64_t blk = idx / (static_cast<int64_t>(per) * a.kt[t]);
+  const int64_t tile = blk * per + tin;
+  const int64_t tile_k = idx;
   const int gid = lane >> 2, tig = lane & 3;
   const uint32_t* rows = bits + a.word_off[t];
   const int64_t k0 = static_cast<int64_t>(kk) * 16 + tig * 2;
@@ -217,7 +250,8 @@ cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, 
     a.kt[t] = sp.stage_kt[t];
     a.ntile[t] = sp.stage_ntile[t];
     a.lane_off[t] = lanes;
-    lanes += int64_t(sp.stage_ntile[t]) * sp.stage_kt[t] * 32;
+    const int per = sp.stage_first[t] ? F_MT : N_NT;
+    lanes += ((sp.stage_ntile[t] + per - 1) / per) * per * int64_t(sp.stage_kt[t]) * 32;
   }
   a.lane_off[sp.nstage] = lanes;
   a.total_lanes = lanes;
@@ -272,29 +306,79 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool val
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-constexpr int TC_THREADS = 256;   // 8 warps split K
-constexpr int F_COLS = 16;        // first stage: columns of X per CTA
-constexpr int F_MT = 8;           // first stage: m16 tiles (128 Theta rows) per CTA
-constexpr int N_NT = 4;           // later stages: n8 tiles (32 Theta rows) per CTA
+constexpr int F_RED = 17;         // padded row of the first stage's cross-warp reduction
+
+// ---- TMA bulk copies completing on an mbarrier (bounded waits)
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Waits for phase `parity`; gives up after a bounded number of polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
 
 template <int CH>
 constexpr size_t first_smem() {
   return size_t(CH) * F_MT * 32 * 16 + size_t(F_COLS) * (CH * 16 + 8) * 4 >
-                 size_t(8) * 128 * F_COLS * 4
+                 size_t(8) * F_MT * 16 * F_RED * 4
              ? size_t(CH) * F_MT * 32 * 16 + size_t(F_COLS) * (CH * 16 + 8) * 4
-             : size_t(8) * 128 * F_COLS * 4;
+             : size_t(8) * F_MT * 16 * F_RED * 4;
 }
 
-// First contraction (mode 1, L = 1): out[q + s*r] = scale * sum_i Theta(q, i) X(i, r).
-// CTA: 128 rows of Theta x 16 columns of X; K in chunks of CH tiles staged
-// in shared memory; warp w takes the K tiles w, w+8, ...
+// Output placement of a stage: natural column-major (last stage) or blocked
+// for the next stage (see SketchPlan).  e_r is the r-part of the natural
+// index, already split by the caller into (l-offset, i', r').
+struct OutMap {
+  int blocked;
+  int64_t L, s;           // this stage
+  int64_t M, I2, LT2;     // next stage
+};
+__device__ __forceinline__ int64_t out_pos(const OutMap& om, int64_t l, int64_t q, int64_t r) {
+  if (!om.blocked) return l + om.L * (q + om.s * r);
+  const int64_t rm = r % om.M, rq = r / om.M;
+  const int64_t l2 = l + om.L * q + om.L * om.s * rm;
+  const int64_t i2 = rq % om.I2, r2 = rq / om.I2;
+  return ((r2 * om.LT2 + l2 / 16) * om.I2 + i2) * XA + (l2 % 16);
+}
+
+// First contraction (mode 1, L = 1): out(q, r) = scale * sum_i Theta(q, i) X(i, r).
+// CTA: 64 rows of Theta x 16 columns of X.  Each K chunk (CH tiles) arrives
+// by TMA bulk copies: one for the Theta fragments, one per column of X.
+// Warp w takes the K tiles w, w+8, ...; the 8 partial tiles are summed in
+// shared memory.
 template <int CH>
 __global__ void __launch_bounds__(TC_THREADS)
 k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t s, int kt_total,
-              const uint4* __restrict__ fragA, int mt_total, float scale, const int* stop) {
+              const uint4* __restrict__ fragA, int mt_total, float scale, OutMap om,
+              int* status, const int* stop) {
   if (stop != nullptr && *stop) return;
   const float* __restrict__ X = Xr.get<const float>();
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
   constexpr int XS = CH * 16 + 8;
   uint4* fA = reinterpret_cast<uint4*>(smem);                                   // [CH][F_MT][32]
   float* xs = reinterpret_cast<float*>(smem + size_t(CH) * F_MT * 32 * 16);       // [F_COLS][XS]
@@ -302,6 +386,9 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
   const int64_t c0 = static_cast<int64_t>(blockIdx.x) * F_COLS;
   const int mb = blockIdx.y;
   const int nmt = min(F_MT, mt_total - mb * F_MT);
+  const bool bulk = (I % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  if (tid == 0) mbar_init(&bar);
+  __syncthreads();
   float acc[F_MT][2][4];
 #pragma unroll
   for (int a = 0; a < F_MT; ++a)
@@ -309,64 +396,69 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
     for (int b = 0; b < 2; ++b)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-  const bool vec = (I % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  bool ok = true;
+  uint32_t phase = 0;
   for (int kc0 = 0; kc0 < kt_total; kc0 += CH) {
     const int nk = min(CH, kt_total - kc0);
-    for (int idx = tid; idx < nk * F_MT * 32; idx += TC_THREADS) {
-      const int kk = idx / (F_MT * 32), rem = idx - kk * F_MT * 32, mt = rem >> 5, ln = rem & 31;
-      if (mt < nmt)
-        cp_async16(&fA[idx], &fragA[(static_cast<int64_t>(kc0 + kk) * mt_total + mb * F_MT + mt) * 32 + ln]);
-      else
-        fA[idx] = make_uint4(0u, 0u, 0u, 0u);
-    }
     const int64_t i0 = static_cast<int64_t>(kc0) * 16;
-    const int rows = nk * 16;
-    if (vec) {
-      for (int idx = tid; idx < F_COLS * rows / 4; idx += TC_THREADS) {
-        const int col = idx / (rows / 4), k4 = (idx - col * (rows / 4)) * 4;
-        const int64_t c = c0 + col, i = i0 + k4;
-        float* dst = &xs[col * XS + k4];
-        if (c < R && i + 3 < I) {
-          cp_async16(dst, X + c * I + i);
-        } else {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) dst[u] = (c < R && i + u < I) ? X[c * I + i + u] : 0.f;
-        }
-      }
-    } else {
-      for (int idx = tid; idx < F_COLS * rows; idx += TC_THREADS) {
-        const int col = idx / rows, k = idx - col * rows;
-        const int64_t c = c0 + col, i = i0 + k;
-        const bool v = c < R && i < I;
-        cp_async4(&xs[col * XS + k], v ? static_cast<const void*>(X + c * I + i) : static_cast<const void*>(X), v);
+    const int rows = static_cast<int>((static_cast<int64_t>(nk) * 16 < I - i0) ? static_cast<int64_t>(nk) * 16 : I - i0);   // valid rows of X
+    const int ncol = static_cast<int>((static_cast<int64_t>(F_COLS) < R - c0) ? static_cast<int64_t>(F_COLS) : R - c0);
+    if (tid == 0) {
+      const uint32_t fbytes = static_cast<uint32_t>(nk) * F_MT * 32 * 16;
+      const uint32_t xbytes = bulk ? static_cast<uint32_t>(ncol) * rows * 4 : 0u;
+      mbar_expect(&bar, fbytes + xbytes);
+      bulk_g2s(fA, fragA + (static_cast<int64_t>(mb) * kt_total + kc0) * F_MT * 32, fbytes, &bar);
+      if (bulk)
+        for (int col = 0; col < ncol; ++col)
+          bulk_g2s(&xs[col * XS], X + (c0 + col) * I + i0, static_cast<uint32_t>(rows) * 4, &bar);
+    }
+    // zero the rows and columns the copies do not cover; without bulk, plain loads
+    if (!bulk || ncol < F_COLS || rows < nk * 16) {
+      for (int idx = tid; idx < F_COLS * nk * 16; idx += TC_THREADS) {
+        const int col = idx / (nk * 16), k = idx - col * (nk * 16);
+        if (bulk && col < ncol && k < rows) continue;
+        xs[col * XS + k] = (col < ncol && k < rows) ? X[(c0 + col) * I + i0 + k] : 0.f;
       }
     }
-    cp_async_wait_all();
+    if (!mbar_wait(&bar, phase)) ok = false;
+    phase ^= 1u;
     __syncthreads();
-    for (int kk = warp; kk < nk; kk += 8) {
-      uint32_t B[2][2][3];
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const float2 v = *reinterpret_cast<const float2*>(&xs[(nt * 8 + gid) * XS + kk * 16 + tig * 2 + h * 8]);
-          split_pair(v.x, v.y, B[nt][h]);
-        }
-#pragma unroll
-      for (int mt = 0; mt < F_MT; ++mt) {
-        if (mt >= nmt) break;
-        const uint4 av = fA[(kk * F_MT + mt) * 32 + lane];
-        const uint32_t A[4] = {av.x, av.y, av.z, av.w};
+    if (ok) {
+      for (int kk = warp; kk < nk; kk += 8) {
+        uint32_t B[2][2][3];
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-          for (int l = 0; l < 3; ++l) mma_bf16(acc[mt][nt], A, B[nt][0][l], B[nt][1][l]);
+          for (int h = 0; h < 2; ++h) {
+            const float2 v = *reinterpret_cast<const float2*>(&xs[(nt * 8 + gid) * XS + kk * 16 + tig * 2 + h * 8]);
+            split_pair(v.x, v.y, B[nt][h]);
+          }
+        uint32_t A[F_MT][4];
+#pragma unroll
+        for (int mt = 0; mt < F_MT; ++mt) {
+          const uint4 av = fA[(kk * F_MT + mt) * 32 + lane];
+          A[mt][0] = av.x;
+          A[mt][1] = av.y;
+          A[mt][2] = av.z;
+          A[mt][3] = av.w;
+        }
+        // limb-outer order: consecutive MMAs update independent accumulators
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+          for (int mt = 0; mt < F_MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_bf16(acc[mt][nt], A[mt], B[nt][0][l], B[nt][1][l]);
       }
     }
     __syncthreads();
   }
-  // sum the 8 warps' K partials through shared memory
-  float* red = reinterpret_cast<float*>(smem);                // [8][128][F_COLS]
+  if (!ok) {
+    if (tid == 0 && status != nullptr) atomicExch(status, RTG_ERR_TIMEOUT);
+    return;
+  }
+  constexpr int ROWS = F_MT * 16;
+  float* red = reinterpret_cast<float*>(smem);                // [8][ROWS][F_RED]
 #pragma unroll
   for (int mt = 0; mt < F_MT; ++mt)
 #pragma unroll
@@ -374,113 +466,116 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int row = mt * 16 + gid + h * 8, col = nt * 8 + tig * 2;
-        red[(warp * 128 + row) * F_COLS + col] = acc[mt][nt][2 * h];
-        red[(warp * 128 + row) * F_COLS + col + 1] = acc[mt][nt][2 * h + 1];
+        red[(warp * ROWS + row) * F_RED + col] = acc[mt][nt][2 * h];
+        red[(warp * ROWS + row) * F_RED + col + 1] = acc[mt][nt][2 * h + 1];
       }
   __syncthreads();
-  for (int idx = tid; idx < 128 * F_COLS; idx += TC_THREADS) {
-    const int row = idx & 127, col = idx >> 7;
+  for (int idx = tid; idx < ROWS * F_COLS; idx += TC_THREADS) {
+    const int row = idx % ROWS, col = idx / ROWS;
+    const int64_t q = static_cast<int64_t>(mb) * ROWS + row, c = c0 + col;
+    if (q >= s || c >= R || row >= nmt * 16) continue;
     float v = 0.f;
 #pragma unroll
-    for (int wv = 0; wv < 8; ++wv) v += red[(wv * 128 + row) * F_COLS + col];
-    const int64_t q = static_cast<int64_t>(mb) * 128 + row, c = c0 + col;
-    if (q < s && c < R) out[q + s * c] = v * scale;
+    for (int wv = 0; wv < 8; ++wv) v += red[(wv * ROWS + row) * F_RED + col];
+    out[out_pos(om, 0, q, c)] = v * scale;
   }
 }
 
 template <int CH>
 constexpr size_t inner_smem() {
-  return size_t(CH) * N_NT * 32 * 8 + size_t(CH) * 16 * 20 * 4 > size_t(8) * 16 * N_NT * 8 * 4
-             ? size_t(CH) * N_NT * 32 * 8 + size_t(CH) * 16 * 20 * 4
+  return size_t(CH) * N_NT * 32 * 8 + size_t(CH) * 16 * XA * 4 > size_t(8) * 16 * N_NT * 8 * 4
+             ? size_t(CH) * N_NT * 32 * 8 + size_t(CH) * 16 * XA * 4
              : size_t(8) * 16 * N_NT * 8 * 4;
 }
 
-// Later contraction (L > 1): out[l + L*(q + s*r)] = scale * sum_i X(l, i, r) Theta(q, i).
-// CTA: 16 values of l x 32 values of q for one r; K in chunks of CH tiles
-// staged in shared memory; warp w takes the K tiles w, w+8, ...  With
-// dots_pass >= 0 the CTA then runs that Gram-Schmidt pass on its final
-// tile (block partials, last-block combine, scalar epilogue).
+// Later contraction (L > 1): out(l, q, r) = scale * sum_i X(l, i, r) Theta(q, i).
+// CTA: 16 values of l x 16 values of q for one r.  Input blocked for this
+// stage (one bulk copy of I rows x 20 floats per K chunk) or natural
+// (plain loads).  Warp w takes the K tiles w, w+8, ...  With dots_pass >= 0
+// the CTA then runs that Gram-Schmidt pass on its final tile.
 template <int CH>
 __global__ void __launch_bounds__(TC_THREADS)
-k_sk_inner_tc(PtrRef Xr, float* __restrict__ out, int64_t L, int64_t I, int64_t R, int64_t s,
-              int kt_total, const uint2* __restrict__ fragB, int nt_total, float scale,
-              int dots_pass, Work w, StepOpts o, const int* stop) {
+k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int64_t I, int64_t R,
+              int64_t s, int kt_total, const uint2* __restrict__ fragB, int nt_total, float scale,
+              OutMap om, int dots_pass, Work w, StepOpts o, int* status, const int* stop) {
   if (stop != nullptr && *stop) return;
   const float* __restrict__ X = Xr.get<const float>();
-  extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int XA = 20;                                                         // 16 l + 4 pad
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
   uint2* fB = reinterpret_cast<uint2*>(smem);                                    // [CH][N_NT][32]
   float* xa = reinterpret_cast<float*>(smem + size_t(CH) * N_NT * 32 * 8);        // [CH*16][XA]
-  __shared__ double red2[GS_MAXW][kMaxK + 2];
-  __shared__ double tot[kMaxK + 2];
+  __shared__ double red2[GS_MAXW][kRedCols];
+  __shared__ double tot[kRedCols];
   __shared__ int am_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gid = lane >> 2, tig = lane & 3;
   const int64_t ltiles = (L + 15) / 16;
   const int64_t lt = blockIdx.x % ltiles, r = blockIdx.x / ltiles;
   const int64_t l0 = lt * 16;
-  const int nt0 = blockIdx.y * N_NT;
-  const int nnt = min(N_NT, nt_total - nt0);
-  const float* Xb = X + L * I * r;
+  const int nb = blockIdx.y;
+  const int nt0 = nb * N_NT;
+  const bool bulk_in = in_blocked && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  if (tid == 0) mbar_init(&bar);
+  __syncthreads();
   float acc[N_NT][4];
 #pragma unroll
   for (int a = 0; a < N_NT; ++a)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
-  const bool vec = (L % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  bool ok = true;
+  uint32_t phase = 0;
   for (int kc0 = 0; kc0 < kt_total; kc0 += CH) {
     const int nk = min(CH, kt_total - kc0);
-    for (int idx = tid; idx < nk * N_NT * 32; idx += TC_THREADS) {
-      const int kk = idx / (N_NT * 32), rem = idx - kk * N_NT * 32, nt = rem >> 5, ln = rem & 31;
-      if (nt < nnt)
-        cp_async8(&fB[idx], &fragB[(static_cast<int64_t>(kc0 + kk) * nt_total + nt0 + nt) * 32 + ln]);
-      else
-        fB[idx] = make_uint2(0u, 0u);
-    }
     const int64_t i0 = static_cast<int64_t>(kc0) * 16;
-    const int rows = nk * 16;
-    if (vec) {
-      for (int idx = tid; idx < rows * 4; idx += TC_THREADS) {
-        const int k = idx >> 2, part = idx & 3;
-        const int64_t i = i0 + k, l = l0 + part * 4;
-        float* dst = &xa[k * XA + part * 4];
-        if (i < I && l + 3 < L) {
-          cp_async16(dst, Xb + l + L * i);
-        } else {
+    const int rows = static_cast<int>((static_cast<int64_t>(nk) * 16 < I - i0) ? static_cast<int64_t>(nk) * 16 : I - i0);
+    if (tid == 0) {
+      const uint32_t fbytes = static_cast<uint32_t>(nk) * N_NT * 32 * 8;
+      const uint32_t xbytes = bulk_in ? static_cast<uint32_t>(rows) * XA * 4 : 0u;
+      mbar_expect(&bar, fbytes + xbytes);
+      bulk_g2s(fB, fragB + (static_cast<int64_t>(nb) * kt_total + kc0) * N_NT * 32, fbytes, &bar);
+      if (bulk_in) bulk_g2s(xa, X + ((r * ltiles + lt) * I + i0) * XA, static_cast<uint32_t>(rows) * XA * 4, &bar);
+    }
+    // rows past I are zero; without bulk input, load the natural layout
+    if (!bulk_in || rows < nk * 16)
+    for (int idx = tid; idx < nk * 16 * 16; idx += TC_THREADS) {
+      const int k = idx >> 4, ll = idx & 15;
+      if (k < rows && bulk_in) continue;
+      float v = 0.f;
+      if (k < rows) {
+        if (in_blocked) v = X[((r * ltiles + lt) * I + i0 + k) * XA + ll];
+        else if (l0 + ll < L) v = X[l0 + ll + L * (i0 + k) + L * I * r];
+      }
+      xa[k * XA + ll] = v;
+    }
+    if (!mbar_wait(&bar, phase)) ok = false;
+    phase ^= 1u;
+    __syncthreads();
+    if (ok) {
+      for (int kk = warp; kk < nk; kk += 8) {
+        uint32_t A[3][4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) dst[u] = (i < I && l + u < L) ? Xb[l + u + L * i] : 0.f;
+        for (int h = 0; h < 4; ++h) {
+          const int l = gid + ((h & 1) ? 8 : 0);
+          const int k = kk * 16 + tig * 2 + ((h & 2) ? 8 : 0);
+          uint32_t lim[3];
+          split_pair(xa[k * XA + l], xa[(k + 1) * XA + l], lim);
+          A[0][h] = lim[0];
+          A[1][h] = lim[1];
+          A[2][h] = lim[2];
         }
-      }
-    } else {
-      for (int idx = tid; idx < rows * 16; idx += TC_THREADS) {
-        const int k = idx >> 4, ll = idx & 15;
-        const int64_t i = i0 + k, l = l0 + ll;
-        const bool v = i < I && l < L;
-        cp_async4(&xa[k * XA + ll], v ? static_cast<const void*>(Xb + l + L * i) : static_cast<const void*>(X), v);
-      }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    for (int kk = warp; kk < nk; kk += 8) {
-      uint32_t A[3][4];
+        uint2 Bv[N_NT];
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int l = gid + ((h & 1) ? 8 : 0);
-        const int k = kk * 16 + tig * 2 + ((h & 2) ? 8 : 0);
-        uint32_t lim[3];
-        split_pair(xa[k * XA + l], xa[(k + 1) * XA + l], lim);
-        A[0][h] = lim[0];
-        A[1][h] = lim[1];
-        A[2][h] = lim[2];
-      }
+        for (int nt = 0; nt < N_NT; ++nt) Bv[nt] = fB[(kk * N_NT + nt) * 32 + lane];
 #pragma unroll
-      for (int nt = 0; nt < N_NT; ++nt) {
-        if (nt >= nnt) break;
-        const uint2 bv = fB[(kk * N_NT + nt) * 32 + lane];
+        for (int l = 0; l < 3; ++l)
 #pragma unroll
-        for (int l = 0; l < 3; ++l) mma_bf16(acc[nt], A[l], bv.x, bv.y);
+          for (int nt = 0; nt < N_NT; ++nt) mma_bf16(acc[nt], A[l], Bv[nt].x, Bv[nt].y);
       }
     }
     __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0 && status != nullptr) atomicExch(status, RTG_ERR_TIMEOUT);
+    return;
   }
   float* red = reinterpret_cast<float*>(smem);               // [8][16][N_NT*8]
   constexpr int TW = N_NT * 8;
@@ -498,8 +593,8 @@ k_sk_inner_tc(PtrRef Xr, float* __restrict__ out, int64_t L, int64_t I, int64_t 
   int64_t ix[ITEMS];
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
-    vals[k] = 0.f;   // entries outside the tensor stay 0 and add nothing below
-    ix[k] = 0;
+    vals[k] = 0.f;   // entries outside the tensor are marked invalid (index -1)
+    ix[k] = -1;
     const int e = tid + k * TC_THREADS;
     if (e >= 16 * TW) continue;
     const int l = e & 15, q = e >> 4;
@@ -509,17 +604,20 @@ k_sk_inner_tc(PtrRef Xr, float* __restrict__ out, int64_t L, int64_t I, int64_t 
 #pragma unroll
     for (int wv = 0; wv < 8; ++wv) v += red[(wv * 16 + l) * TW + q];
     v *= scale;
-    const int64_t g = gl + L * (gq + s * r);
+    const int64_t g = out_pos(om, gl, gq, r);
     out[g] = v;
     vals[k] = v;
     ix[k] = g;
   }
-  const int cnt = ITEMS;
   if (dots_pass < 0) return;
-  const int ncols = (dots_pass == 0) ? 0 : w.ctl->j + 1;
-  block_partials<float, ITEMS>(w, vals, ix, cnt, ncols, red2);
-  if (!last_block_combine(w, ncols, tot, &am_last)) return;
-  if (tid == 0) gs_finish(w, dots_pass, o, tot, ncols);
+  const int J = (dots_pass == 0) ? -1 : w.ctl->j;
+  block_partials<float, ITEMS>(w, vals, ix, ITEMS, J, red2);
+  if (!last_block_combine(w, gs_ncols(J), tot, &am_last)) return;
+  if (dots_pass == 0) {
+    if (tid == 0) gs_finish_start(w, o, tot);
+  } else {
+    gs_finish_gram(w, o, tot, &red2[0][0]);
+  }
 }
 
 // ------------------------------------------------------------------ CUDA-core chain (FP64)
@@ -588,6 +686,17 @@ static cudaError_t sketch_f64(const SketchPlan& sp, const SketchScratch& sc, Ptr
   return cudaSuccess;
 }
 
+static OutMap stage_out_map(const SketchPlan& sp, int t) {
+  OutMap om{};
+  om.L = sp.stage_L[t];
+  om.s = sp.stage_s[t];
+  om.blocked = (t + 1 < sp.nstage) ? sp.stage_in_blocked[t + 1] : 0;
+  om.M = om.blocked ? sp.next_M[t] : 1;
+  om.I2 = om.blocked ? sp.next_I[t] : 1;
+  om.LT2 = om.blocked ? sp.next_LT[t] : 1;
+  return om;
+}
+
 static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, float* out,
                               const SketchDots* dots, const int* stop, cudaStream_t s) {
   PtrRef src = X;
@@ -597,6 +706,8 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
     const float scale = last ? static_cast<float>(sp.scale) : 1.f;
     const int kt = sp.stage_kt[t];
     const uint32_t* fr = sc.frags + sp.frag_off[t];
+    const OutMap om = stage_out_map(sp, t);
+    int* status = (dots != nullptr) ? &dots->w->ctl->status : sc.status;
     cudaError_t e = cudaSuccess;
     if (sp.stage_first[t]) {
       dim3 grid(static_cast<unsigned>((sp.stage_R[t] + F_COLS - 1) / F_COLS),
@@ -607,14 +718,14 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
         if (e != cudaSuccess) return e;
         k_sk_first_tc<32><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_I[t], sp.stage_R[t], sp.stage_s[t],
                                                        kt, reinterpret_cast<const uint4*>(fr),
-                                                       sp.stage_ntile[t], scale, stop);
+                                                       sp.stage_ntile[t], scale, om, status, stop);
       } else {
         constexpr size_t sm = first_smem<16>();
         e = cudaFuncSetAttribute(k_sk_first_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         if (e != cudaSuccess) return e;
         k_sk_first_tc<16><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_I[t], sp.stage_R[t], sp.stage_s[t],
                                                        kt, reinterpret_cast<const uint4*>(fr),
-                                                       sp.stage_ntile[t], scale, stop);
+                                                       sp.stage_ntile[t], scale, om, status, stop);
       }
     } else {
       const int64_t ltiles = (sp.stage_L[t] + 15) / 16;
@@ -623,20 +734,23 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
       const int dpass = (last && dots != nullptr) ? dots->pass : -1;
       const Work wk = (dots != nullptr) ? *dots->w : Work{};
       const StepOpts so = (dots != nullptr) ? dots->o : StepOpts{};
+      const int inb = sp.stage_in_blocked[t];
       if (kt > 16) {
         constexpr size_t sm = inner_smem<32>();
         e = cudaFuncSetAttribute(k_sk_inner_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         if (e != cudaSuccess) return e;
-        k_sk_inner_tc<32><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_L[t], sp.stage_I[t], sp.stage_R[t],
-                                                       sp.stage_s[t], kt, reinterpret_cast<const uint2*>(fr),
-                                                       sp.stage_ntile[t], scale, dpass, wk, so, stop);
+        k_sk_inner_tc<32><<<grid, TC_THREADS, sm, s>>>(src, inb, dst, sp.stage_L[t], sp.stage_I[t],
+                                                       sp.stage_R[t], sp.stage_s[t], kt,
+                                                       reinterpret_cast<const uint2*>(fr), sp.stage_ntile[t],
+                                                       scale, om, dpass, wk, so, status, stop);
       } else {
         constexpr size_t sm = inner_smem<16>();
         e = cudaFuncSetAttribute(k_sk_inner_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         if (e != cudaSuccess) return e;
-        k_sk_inner_tc<16><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_L[t], sp.stage_I[t], sp.stage_R[t],
-                                                       sp.stage_s[t], kt, reinterpret_cast<const uint2*>(fr),
-                                                       sp.stage_ntile[t], scale, dpass, wk, so, stop);
+        k_sk_inner_tc<16><<<grid, TC_THREADS, sm, s>>>(src, inb, dst, sp.stage_L[t], sp.stage_I[t],
+                                                       sp.stage_R[t], sp.stage_s[t], kt,
+                                                       reinterpret_cast<const uint2*>(fr), sp.stage_ntile[t],
+                                                       scale, om, dpass, wk, so, status, stop);
       }
     }
     e = cudaGetLastError();

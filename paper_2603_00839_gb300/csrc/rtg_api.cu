@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -320,7 +321,7 @@ size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, 
   w.tmp0 = sk->tmp0;
   w.tmp1 = sk->tmp1;
   w.Q = c.take<char>(size_t(m + 1) * d * e);
-  w.part = c.take<double>(size_t(G) * (m + 2));
+  w.part = c.take<double>(size_t(G) * (2 * m + 4));
   w.part_rows = static_cast<int>(G);
   w.counter = c.take<unsigned>(8);
   w.ctl = c.take<Ctl>(1);
@@ -329,8 +330,7 @@ size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, 
   w.cs = c.take<double>(m);
   w.sn = c.take<double>(m);
   w.g = c.take<double>(m + 1);
-  w.h1 = c.take<double>(m + 1);
-  w.h2 = c.take<double>(m + 1);
+  w.G = c.take<double>(size_t(m + 1) * (m + 1));
   w.rho_hist = c.take<double>(kMaxK);
   w.y = c.take<double>(m);
   w.gcv = c.take<double>(kMaxMu);
@@ -426,6 +426,37 @@ rtg_status get_op(rtg_context* h, const rtg_factor* A, int nA, const rtg_factor*
   return RTG_OK;
 }
 
+// Opt-in trace of the direct-launch path (environment RTG_TRACE=1): an
+// event is recorded after every phase of the solve and the device time of
+// each phase is printed to stderr after the final synchronisation.
+struct Tracer {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<std::string> name;
+  void mark(const char* nm) {
+    if (!on) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+    name.push_back(nm);
+  }
+  void report() {
+    if (!on || ev.size() < 2) return;
+    cudaEventSynchronize(ev.back());
+    for (size_t i = 1; i < ev.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+      fprintf(stderr, "rtg-trace %-14s %9.2f us\n", name[i].c_str(), ms * 1e3);
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+    ev.clear();
+    name.clear();
+  }
+};
+Tracer g_tracer;
+
 StepOpts solve_step_opts(const SolvePlan& P, int use_cond, cudaGraphConditionalHandle hnd) {
   StepOpts o{};
   o.desc_tol = &P.desc_dev->tol;
@@ -445,7 +476,9 @@ PtrRef desc_ref(const void* const* field) {
 rtg_status enqueue_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s) {
   Work& w = P.w;
   CK(launch_reset(w, 0, s));
+  g_tracer.mark("reset");
   CK(launch_theta(P.sp, P.sk.bits, P.sk.frags, s));
+  g_tracer.mark("theta");
   PtrRef C = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->C));
   PtrRef src = C;
   if (P.has_x0) {   // R_0 = C - Phi(X_0) into the V_0 slot
@@ -456,7 +489,9 @@ rtg_status enqueue_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s) {
   const bool fused = P.sp.fused_dots != 0;
   SketchDots dots{&w, 0, so};
   CK(launch_sketch(P.sp, P.sk, src, fused ? w.S : w.Spart, fused ? &dots : nullptr, nullptr, s));
+  g_tracer.mark("sketch0");
   CK(launch_start(w, src, so, fused, s));
+  g_tracer.mark("start");
   return RTG_OK;
 }
 
@@ -469,12 +504,15 @@ rtg_status enqueue_step(const OpHolder& op, const SketchPlan& sp, const Work& w,
   vj.stride = w.n;
   const int* stop = &w.ctl->stop;
   CK(launch_apply(op.op, dtype, vj, ref(w.W), 1.0, 0.0, PtrRef{}, tA, tB, stop, s));
+  g_tracer.mark("apply");
   const bool fused = sp.fused_dots != 0;
   SketchDots dots{&w, 1, so};
   CK(launch_sketch(sp, sk, ref(w.W), fused ? w.S : w.Spart, fused ? &dots : nullptr, stop, s));
-  if (!fused) CK(launch_pass1(w, s));
-  CK(launch_pass2(w, so, s));
+  g_tracer.mark("sketch+dots");
+  if (!fused) CK(launch_pass1(w, so, s));
+  g_tracer.mark("gs");
   CK(launch_update(w, so, s));
+  g_tracer.mark("update");
   return RTG_OK;
 }
 
@@ -484,10 +522,13 @@ rtg_status enqueue_epilogue(SolvePlan& P, cudaStream_t s) {
   f.n_mu = P.n_mu;
   f.mode = P.mode;
   CK(launch_tikhonov(P.w, f, s));
+  g_tracer.mark("tikhonov");
   PtrRef X0 = P.has_x0 ? desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X0)) : PtrRef{};
   PtrRef X = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X));
   CK(launch_assemble(P.w, X0, X, s));
+  g_tracer.mark("assemble");
   CK(launch_finalize(P.w, P.info_dev, s));
+  g_tracer.mark("finalize");
   return RTG_OK;
 }
 
@@ -868,7 +909,7 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
       const int gs = sp.fused_dots ? 0 : 1;
       P->launches_pro = 1 + (nsk > 0 ? (dtype == RTG_F32 ? 2 : 1) : 0) +
                         (has_x0 ? apply_launches(P->op.op, true) : 0) + sketch_launches(sp) + gs + 1;
-      P->launches_step = apply_launches(P->op.op, false) + sketch_launches(sp) + gs + 2;
+      P->launches_step = apply_launches(P->op.op, false) + sketch_launches(sp) + gs + 1;
       P->launches_epi = 3;
     }
     if (use_graph) RK(build_graph(*P));
@@ -910,6 +951,10 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
     CK(cudaGraphLaunch(P->exec, s));
   } else {
     const StepOpts so = solve_step_opts(*P, 0, 0);
+    const char* tr = getenv("RTG_TRACE");
+    g_tracer.on = tr != nullptr && tr[0] == '1';
+    g_tracer.s = s;
+    g_tracer.mark("begin");
     RK(enqueue_prologue(*P, so, s));
     for (int j = 0; j < m; ++j) RK(enqueue_step(P->op, P->sp, P->w, dtype, P->tA, P->tB, P->sk, so, s));
     RK(enqueue_epilogue(*P, s));
@@ -918,6 +963,10 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
   if (!X_dev) CK(cudaMemcpyAsync(X, P->Xst.p, bytes_t, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(P->info_host, P->info_dev, sizeof(InfoDev), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (!use_graph) {
+    g_tracer.report();
+    g_tracer.on = false;
+  }
   const InfoDev& I = *P->info_host;
   if (info) {
     info->iters = I.iters;

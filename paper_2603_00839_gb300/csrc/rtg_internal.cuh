@@ -101,7 +101,7 @@ struct Work {
   void* tmp0;                  // sketch chain intermediates
   void* tmp1;
   void* Q;                     // (m+1) * d sketched basis
-  double* part;                // partial sums: gridDim x (m+2)
+  double* part;                // partial sums: blocks x (2m+4)
   unsigned* counter;           // last-block counters (several)
   Ctl* ctl;
   double* H;                   // (m+1) x m Hessenberg, column-major
@@ -109,8 +109,7 @@ struct Work {
   double* cs;                  // Givens cosines (m)
   double* sn;                  // Givens sines (m)
   double* g;                   // rotated right-hand side (m+1)
-  double* h1;                  // first-pass coefficients (m+1)
-  double* h2;                  // second-pass coefficients (m+1)
+  double* G;                   // (m+1) x (m+1) Gram matrix of the stored sketched basis
   double* rho_hist;            // (m) per cycle
   double* y;                   // solution coefficients (m)
   double* gcv;                 // GCV values (kMaxMu)
@@ -144,6 +143,16 @@ struct SketchPlan {
   int stage_ntile[kMaxOrder];  // m16 (first) or n8 (later) tiles of the sketch size
   int64_t stage_L[kMaxOrder], stage_I[kMaxOrder], stage_R[kMaxOrder], stage_s[kMaxOrder];
   int64_t stage_out[kMaxOrder];   // elements of one stage output
+  // FP32 chain layouts: an inner stage reads its input either in the
+  // natural (column-major) order or blocked for it: block (r, l/16) holds
+  // I rows of 20 floats (16 values of l, 4 pad).  A stage that is not last
+  // writes its output blocked for the next stage, whose view of the
+  // tensor is (L', I', R') with M = product of the unsketched dims between
+  // the two modes: (l, q, r) -> l' = l + L q + L s (r % M), i' = (r / M) % I',
+  // r' = r / (M I').
+  int stage_in_blocked[kMaxOrder];
+  int64_t next_M[kMaxOrder], next_L[kMaxOrder], next_I[kMaxOrder], next_LT[kMaxOrder];
+  int64_t stage_out_alloc[kMaxOrder];   // floats the stage output buffer needs
   int64_t frag_off[kMaxOrder];    // uint32 offset of the stage's Theta fragments
   int64_t frag_words;
   int64_t part_elems;             // elements of each scratch tensor
@@ -158,6 +167,7 @@ struct SketchScratch {
   uint32_t* frags = nullptr;
   void* tmp0 = nullptr;
   void* tmp1 = nullptr;
+  int* status = nullptr;      // device word: a bounded wait gave up (RTG_ERR_TIMEOUT)
 };
 
 // Fills sp; returns an error message or nullptr (k_sketch.cu).
@@ -220,9 +230,9 @@ int sketch_launches(const SketchPlan& sp);
 
 // k_arnoldi.cu: the sketched Arnoldi process on a Work.
 //   start:  beta = ||S||, V_0 = src / beta, Q_0 = S / beta  (src = R_0)
-//   pass1:  h1 = Q^T S, pre = ||S||^2
-//   pass2:  S <- S - Q h1; h2 = Q^T S; h = h1 + h2; h_{j+1,j}; Givens; stop rule
-//   update: V_{j+1} = (W - V h)/h_{j+1,j}, Q_{j+1} = (S - Q h2)/h_{j+1,j}
+//   pass1:  one reduction (Q^T S, ||S||^2, Gram row), then h (CGS2 through
+//           the Gram matrix), h_{j+1,j}, Givens and the stop rule
+//   update: V_{j+1} = (W - V h)/h_{j+1,j}, Q_{j+1} = (S - Q h)/h_{j+1,j}
 struct StepOpts {
   double tol;            // rho stop level (read from desc when desc_tol is set)
   double bd_tol;
@@ -239,9 +249,8 @@ struct SketchDots {
 };
 // pass 0 on w.Spart (unless the sketch already ran it) and the scaling V_0, Q_0
 cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fused, cudaStream_t s);
-cudaError_t launch_pass1(const Work& w, cudaStream_t s);
+cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s);
 int gs_grid(int64_t d);
-cudaError_t launch_pass2(const Work& w, const StepOpts& o, cudaStream_t s);
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s);
 cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s);
 
