@@ -98,11 +98,33 @@ typedef struct rtg_opts {
     double breakdown_tol;            /* breakdown if h_{j+1,j} <= breakdown_tol * ||S(Phi V_j)||;
                                         0 selects 1e-12 (F64) / 1e-6 (F32) */
     int32_t flags;                   /* RTG_FLAG_* */
-    int32_t reserved;
+    int32_t slot;                    /* workspace slot, 0..RTG_MAX_SLOTS-1: solves that may be
+                                        in flight at the same time on different streams must use
+                                        different slots (each slot owns its own basis, sketch and
+                                        graph); calls on one slot are ordered by their stream */
 } rtg_opts;
+
+#define RTG_MAX_SLOTS 64
 
 #define RTG_FLAG_NO_GRAPH      1     /* launch kernels directly instead of a CUDA graph */
 #define RTG_FLAG_TRUE_RESIDUAL 2     /* also compute ||C - Phi(X)||_F / ||C||_F into info */
+#define RTG_FLAG_PHASE_TIMES   4     /* time every kernel group with CUDA events into
+                                        info->phase_ms (implies RTG_FLAG_NO_GRAPH); see below */
+
+/* Kernel groups of one solve, the index of rtg_info.phase_ms / phase_launches.
+ *   SETUP     workspace reset and the sketch signs / Theta fragments (Section 2, Theta_k)
+ *   INIT      R_0 = C - Phi(X_0), S(R_0), beta, V_1 and its sketch (Algorithm 2 start)
+ *   APPLY     W = Phi(V_j)                                  (Eq. 57 operator)
+ *   SKETCH    S(W) and, where fused, the sketched dots and Gram-Schmidt finish
+ *   GS        sketched dots and Gram-Schmidt finish when not fused into SKETCH
+ *   UPDATE    V_{j+1} = (W - sum_i h_ij V_i) / h_{j+1,j}, sketched basis column
+ *   TIKHONOV  projected Tikhonov / GCV (Eq. 13)
+ *   ASSEMBLE  X = X_0 + sum_j y_j V_j and the info record
+ * Steps after the stop are not counted. */
+enum {
+    RTG_PHASE_SETUP = 0, RTG_PHASE_INIT, RTG_PHASE_APPLY, RTG_PHASE_SKETCH, RTG_PHASE_GS,
+    RTG_PHASE_UPDATE, RTG_PHASE_TIKHONOV, RTG_PHASE_ASSEMBLE, RTG_PHASE_COUNT
+};
 
 typedef struct rtg_info {
     int32_t iters;                   /* Arnoldi steps taken, all cycles */
@@ -118,6 +140,14 @@ typedef struct rtg_info {
     double elapsed_ms;               /* device time of the solve (CUDA events) */
     int32_t device_status;           /* rtg_status seen on the device (NONFINITE, ...) */
     int32_t launches;                /* kernels this library launched for the solve */
+    int32_t reserved;
+    /* With RTG_FLAG_PHASE_TIMES: device time (ms) and kernel launches of each
+     * RTG_PHASE_* group, summed over the solve.  Each group is bracketed by
+     * CUDA events on the solve's stream, and the GPU is held at a gate until
+     * the host has queued the whole group, so no host launch latency falls
+     * between the events.  Zero without the flag. */
+    double phase_ms[RTG_PHASE_COUNT];
+    int32_t phase_launches[RTG_PHASE_COUNT];
 } rtg_info;
 
 typedef struct rtg_context* rtg_handle;
@@ -232,11 +262,12 @@ rtg_status rtg_krylov_query(rtg_handle handle, rtg_krylov krylov, rtg_krylov_vie
  *     lambda > 0: mu = lambda;  lambda == 0: mu = 0 (Eq. 11S);
  *     lambda < 0: mu = argmin GCV(mu) over opts->mu_grid (ties: larger mu);
  *   X = X_0 + sum_j y_j V_j (Eq. 10S).
- * With opts->max_restarts > 0, a cycle that ends at j = m without reaching
- * tol restarts from its least-squares iterate.
+ * Restarted cycles (opts->max_restarts > 0) are not implemented on the
+ * GPU: the call returns RTG_ERR_UNSUPPORTED.
  * C, X0 (may be NULL), X: device or host arrays of prod(dims) elements of
  * dtype (F64 or F32); X may alias X0.  info may be NULL.  The call
- * synchronises `stream` once at the end.
+ * synchronises `stream` once at the end; it equals rtg_gmres_submit
+ * followed by rtg_gmres_wait on opts->slot.
  * Errors: INVALID_ARG, UNSUPPORTED, ALLOC, CUDA; numeric trouble is
  * reported in info->device_status (RTG_ERR_NONFINITE) with RTG_OK returned.
  */
@@ -247,6 +278,28 @@ rtg_status rtg_gmres_solve(rtg_handle handle,
                            const void* C, int32_t m, const int64_t* sketch_dims,
                            uint64_t seed, double lambda, const void* X0, void* X,
                            const rtg_opts* opts, rtg_info* info, rtg_stream stream);
+
+/*
+ * The same solve in two halves, so that one host thread can keep several
+ * independent solves in flight on different streams (each on its own
+ * workspace slot, opts->slot).  rtg_gmres_submit validates the arguments
+ * and queues the whole solve on `stream` (staging copies, the solve's CUDA
+ * graph, the copy-back of X when X is a host array) and returns without
+ * waiting; host arrays C, X0 and X must stay valid until the matching
+ * rtg_gmres_wait.  rtg_gmres_wait(slot) synchronises the stream of the last
+ * solve submitted on `slot` and fills `info` (may be NULL).  A slot holds
+ * one submitted solve at a time: submitting on a slot that was not waited
+ * for returns RTG_ERR_INVALID_ARG.  Phase timing (RTG_FLAG_PHASE_TIMES)
+ * uses one timer per handle, so at most one such solve may be pending.
+ */
+rtg_status rtg_gmres_submit(rtg_handle handle,
+                            const rtg_factor* A_factors, int32_t nA,
+                            const rtg_factor* B_factors, int32_t nB,
+                            rtg_shape shape, rtg_dtype dtype,
+                            const void* C, int32_t m, const int64_t* sketch_dims,
+                            uint64_t seed, double lambda, const void* X0, void* X,
+                            const rtg_opts* opts, rtg_stream stream);
+rtg_status rtg_gmres_wait(rtg_handle handle, int32_t slot, rtg_info* info);
 
 /*
  * rtg_sketch_noalloc -- the paper has no counterpart; this is a service of

@@ -15,6 +15,7 @@ MAX_ORDER = 4
 MAX_RADIUS = 32
 MAX_KRYLOV = 256
 MAX_MU = 32
+MAX_SLOTS = 64
 
 # rtg_status
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_ALLOC, ERR_TIMEOUT, ERR_NONFINITE = range(7)
@@ -22,7 +23,9 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_ALLOC, ERR_TIMEOUT, ERR_NONF
 F64, F32, BF16 = 0, 1, 2
 # rtg_factor_kind
 FACTOR_IDENTITY, FACTOR_BANDED_TOEPLITZ, FACTOR_DENSE = 0, 1, 2
-FLAG_NO_GRAPH, FLAG_TRUE_RESIDUAL = 1, 2
+FLAG_NO_GRAPH, FLAG_TRUE_RESIDUAL, FLAG_PHASE_TIMES = 1, 2, 4
+PHASES = ("setup", "init", "apply", "sketch", "gs", "update", "tikhonov", "assemble")
+PHASE_COUNT = len(PHASES)
 
 
 class Shape(C.Structure):
@@ -37,7 +40,7 @@ class Factor(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("mu_grid", C.POINTER(C.c_double)), ("n_mu", C.c_int32),
                 ("max_restarts", C.c_int32), ("breakdown_tol", C.c_double), ("flags", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("slot", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -45,7 +48,9 @@ class Info(C.Structure):
                 ("converged", C.c_int32), ("beta", C.c_double), ("mu", C.c_double),
                 ("rho_final", C.c_double), ("rho_hist", C.POINTER(C.c_double)),
                 ("gcv", C.POINTER(C.c_double)), ("true_rel_resid", C.c_double),
-                ("elapsed_ms", C.c_double), ("device_status", C.c_int32), ("launches", C.c_int32)]
+                ("elapsed_ms", C.c_double), ("device_status", C.c_int32), ("launches", C.c_int32),
+                ("reserved", C.c_int32), ("phase_ms", C.c_double * PHASE_COUNT),
+                ("phase_launches", C.c_int32 * PHASE_COUNT)]
 
 
 class KrylovView(C.Structure):
@@ -79,6 +84,11 @@ _SIGS = {
                                   C.c_int32, Shape, C.c_int, C.c_void_p, C.c_int32,
                                   C.POINTER(C.c_int64), C.c_uint64, C.c_double, C.c_void_p,
                                   C.c_void_p, C.POINTER(Opts), C.POINTER(Info), C.c_void_p]),
+    "rtg_gmres_submit": (C.c_int, [C.c_void_p, C.POINTER(Factor), C.c_int32, C.POINTER(Factor),
+                                   C.c_int32, Shape, C.c_int, C.c_void_p, C.c_int32,
+                                   C.POINTER(C.c_int64), C.c_uint64, C.c_double, C.c_void_p,
+                                   C.c_void_p, C.POINTER(Opts), C.c_void_p]),
+    "rtg_gmres_wait": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Info)]),
     "rtg_sketch_noalloc": (C.c_int, [Shape, C.c_int, C.POINTER(C.c_int64), C.c_uint64, C.c_uint64,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
 }

@@ -148,6 +148,8 @@ class SolveResult:
     elapsed_ms: float
     device_status: int
     launches: int
+    phase_ms: Optional[dict] = None        # group -> device ms (phase_times=True)
+    phase_launches: Optional[dict] = None  # group -> kernel launches (phase_times=True)
 
 
 class Handle:
@@ -215,8 +217,26 @@ class Handle:
     def gmres_solve(self, C_obs, m: int, sketch_dims: Sequence[int], seed: int, lam: float,
                     A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (),
                     X0=None, X=None, tol: float = 0.0, mu_grid=None, max_restarts: int = 0,
-                    breakdown_tol: float = 0.0, use_graph: bool = True, stream=None):
-        """RTG-GMRES; C_obs, X0, X may be device tensors or host numpy arrays (Fortran order)."""
+                    breakdown_tol: float = 0.0, use_graph: bool = True, phase_times: bool = False,
+                    slot: int = 0, stream=None):
+        """RTG-GMRES; C_obs, X0, X may be device tensors or host numpy arrays (Fortran order).
+
+        phase_times=True launches directly and times each kernel group with
+        CUDA events (result.phase_ms / result.phase_launches).  Returns (X, SolveResult)."""
+        pend = self.gmres_submit(C_obs, m, sketch_dims, seed, lam, A_factors, B_factors, X0=X0, X=X,
+                                 tol=tol, mu_grid=mu_grid, max_restarts=max_restarts,
+                                 breakdown_tol=breakdown_tol, use_graph=use_graph,
+                                 phase_times=phase_times, slot=slot, stream=stream)
+        return self.gmres_wait(pend)
+
+    def gmres_submit(self, C_obs, m: int, sketch_dims: Sequence[int], seed: int, lam: float,
+                     A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (),
+                     X0=None, X=None, tol: float = 0.0, mu_grid=None, max_restarts: int = 0,
+                     breakdown_tol: float = 0.0, use_graph: bool = True, phase_times: bool = False,
+                     slot: int = 0, stream=None) -> "PendingSolve":
+        """Queue a solve on `stream` without waiting (rtg_gmres_submit).  Solves
+        in flight at once on different streams need different workspace slots;
+        gmres_wait(pending) returns (X, SolveResult)."""
         dims = tuple(C_obs.shape)
         host = isinstance(C_obs, np.ndarray)
         if host:
@@ -242,20 +262,45 @@ class Handle:
             opts.n_mu = len(grid)
         opts.max_restarts = int(max_restarts)
         opts.breakdown_tol = float(breakdown_tol)
-        opts.flags = 0 if use_graph else L.FLAG_NO_GRAPH
+        opts.flags = (0 if use_graph else L.FLAG_NO_GRAPH) | (L.FLAG_PHASE_TIMES if phase_times else 0)
+        opts.slot = int(slot)
+        L.check(self.lib.rtg_gmres_submit(self._h, a, na, b, nb, _shape(dims), dt, _ptr(C_obs), int(m),
+                                          sk, C.c_uint64(seed), float(lam), _ptr(X0), _ptr(X),
+                                          C.byref(opts), _stream(stream)))
+        # the host arrays (C, X0, X) and factor arrays stay referenced until the wait
+        return PendingSolve(int(slot), X, m, max_restarts, grid, lam, phase_times,
+                            (C_obs, X0, a, b, ka, kb, sk))
+
+    def gmres_wait(self, pend: "PendingSolve"):
+        """Wait for a submitted solve (rtg_gmres_wait); returns (X, SolveResult)."""
         info = L.Info()
-        rho = np.zeros(m * (max_restarts + 1) + 1)
+        rho = np.zeros(pend.m * (pend.max_restarts + 1) + 1)
         info.rho_hist = rho.ctypes.data_as(C.POINTER(C.c_double))
         gcv = np.zeros(L.MAX_MU)
         info.gcv = gcv.ctypes.data_as(C.POINTER(C.c_double))
-        L.check(self.lib.rtg_gmres_solve(self._h, a, na, b, nb, _shape(dims), dt, _ptr(C_obs), int(m),
-                                         sk, C.c_uint64(seed), float(lam), _ptr(X0), _ptr(X),
-                                         C.byref(opts), C.byref(info), _stream(stream)))
+        L.check(self.lib.rtg_gmres_wait(self._h, pend.slot, C.byref(info)))
+        grid = pend.grid
         res = SolveResult(info.iters, info.restarts, bool(info.breakdown), bool(info.converged),
                           info.beta, info.mu, info.rho_final, rho[:info.iters].copy(),
-                          gcv[:len(grid)].copy() if (grid is not None and lam < 0) else None,
+                          gcv[:len(grid)].copy() if (grid is not None and pend.lam < 0) else None,
                           info.elapsed_ms, info.device_status, info.launches)
-        return X, res
+        if pend.phase_times:
+            res.phase_ms = {k: info.phase_ms[i] for i, k in enumerate(L.PHASES)}
+            res.phase_launches = {k: info.phase_launches[i] for i, k in enumerate(L.PHASES)}
+        return pend.X, res
+
+
+@dataclasses.dataclass
+class PendingSolve:
+    """A solve queued by Handle.gmres_submit and not yet waited for."""
+    slot: int
+    X: object
+    m: int
+    max_restarts: int
+    grid: Optional[np.ndarray]
+    lam: float
+    phase_times: bool
+    keep: tuple
 
 
 class Krylov:

@@ -180,7 +180,9 @@ __device__ inline void gs_finish_start(const Work& w, const StepOpts& o, const d
   Ctl* ctl = w.ctl;
   const double tol = o.desc_tol ? *o.desc_tol : o.tol;
   const double beta = sqrt(tot[0]);
-  if (!isfinite(beta)) {
+  if (ctl->status != 0) {
+    ctl->stop = 1;
+  } else if (!isfinite(beta)) {
     ctl->status = RTG_ERR_NONFINITE;
     ctl->stop = 1;
   } else if (beta == 0.0) {
@@ -309,7 +311,8 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
     if (breakdown) ctl->breakdown = 1;
     const bool conv = finite && rho <= tol;
     if (conv || breakdown) ctl->converged = 1;
-    const bool stop = !finite || breakdown || conv || (J + 1 >= w.m);
+    // a nonzero status (a bounded wait that gave up upstream) ends the solve
+    const bool stop = !finite || breakdown || conv || (J + 1 >= w.m) || ctl->status != 0;
     ctl->stop = stop ? 1 : 0;
     ctl->skip_update = (!finite || breakdown || (o.solve_mode && stop)) ? 1 : 0;
     set_cond(o, !stop);

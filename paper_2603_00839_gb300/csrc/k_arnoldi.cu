@@ -122,6 +122,13 @@ __global__ void k_update(Work w, StepOpts o) {
   }
   if (ctl->skip_update || ctl->j == 0) return;
   const int jj = ctl->j;
+  if (jj > w.m) {   // V holds m+1 tensors: never write past V_m
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctl->status = RTG_ERR_INVALID_ARG;
+      ctl->stop = 1;
+    }
+    return;
+  }
   __shared__ T hs[kMaxK + 1];
   __shared__ double hd[kMaxK + 1];
   const int ld = w.m + 1;
@@ -207,7 +214,10 @@ __global__ void k_update(Work w, StepOpts o) {
   }
 }
 
-__global__ void k_reset(Ctl* ctl, int new_cycle) {
+__global__ void k_reset(Ctl* ctl, unsigned* counter, int new_cycle) {
+  // last-block counters wrap to zero by themselves; clearing them here also
+  // recovers from a solve that ended inside a kernel
+  for (int i = 0; i < 8; ++i) counter[i] = 0u;
   ctl->j = 0;
   ctl->stop = 0;
   ctl->breakdown = 0;
@@ -236,7 +246,7 @@ static unsigned ew_grid(int64_t n) {
 }
 
 cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s) {
-  k_reset<<<1, 1, 0, s>>>(w.ctl, new_cycle);
+  k_reset<<<1, 1, 0, s>>>(w.ctl, w.counter, new_cycle);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ struct ThetaArgs {
   int wpr[kMaxOrder];
   int64_t total_words;
   uint64_t seed, pid;
+  const uint64_t* key;          // if set: (seed, pid) read from device memory at run time
 };
 
 // One thread per packed 32-bit word: bit b of word (q, w) of mode k holds
@@ -50,15 +51,16 @@ __global__ void k_theta_bits(ThetaArgs a, uint32_t* bits) {
   int64_t wi = local % a.wpr[k];
   int64_t i0 = wi * 32;
   int64_t e0 = a.bit_off[k] + q * a.I[k] + i0;
+  const uint64_t seed = a.key ? a.key[0] : a.seed, pid = a.key ? a.key[1] : a.pid;
   // the 32 signs span at most two 64-bit stream words
   int64_t w0 = e0 / 64;
   uint64_t r[4];
-  philox4x64_10(static_cast<uint64_t>(w0 / 4) + 1, 0, 0, 0, a.seed, a.pid, r);
+  philox4x64_10(static_cast<uint64_t>(w0 / 4) + 1, 0, 0, 0, seed, pid, r);
   uint64_t word0 = r[w0 % 4];
   uint64_t word1 = word0;
   int64_t w1 = (e0 + 31) / 64;
   if (w1 != w0) {
-    if (w1 / 4 != w0 / 4) philox4x64_10(static_cast<uint64_t>(w1 / 4) + 1, 0, 0, 0, a.seed, a.pid, r);
+    if (w1 / 4 != w0 / 4) philox4x64_10(static_cast<uint64_t>(w1 / 4) + 1, 0, 0, 0, seed, pid, r);
     word1 = r[w1 % 4];
   }
   uint32_t out = 0;
@@ -71,8 +73,10 @@ __global__ void k_theta_bits(ThetaArgs a, uint32_t* bits) {
   bits[t] = out;
 }
 
-cudaError_t launch_theta_bits(const SketchPlan& sp, uint32_t* bits, cudaStream_t s) {
+cudaError_t launch_theta_bits(const SketchPlan& sp, uint32_t* bits, cudaStream_t s,
+                              const uint64_t* key_dev) {
   ThetaArgs a{};
+  a.key = key_dev;
   int k = 0;
   for (int m = 0; m < sp.order; ++m) {
     if (!sp.sketched[m]) continue;

@@ -233,8 +233,9 @@ __global__ void k_theta_frags(FragArgs a, const uint32_t* __restrict__ bits, uin
   }
 }
 
-cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, cudaStream_t s) {
-  cudaError_t e = launch_theta_bits(sp, bits, s);
+cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, cudaStream_t s,
+                         const uint64_t* key_dev) {
+  cudaError_t e = launch_theta_bits(sp, bits, s, key_dev);
   if (e != cudaSuccess || sp.dtype != RTG_F32 || sp.nstage == 0) return e;
   FragArgs a{};
   a.nstage = sp.nstage;
@@ -341,6 +342,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// Called by every thread after issuing a chunk's copies.  True if a copy
+// did not land within the bounded wait (agreed across the CTA): thread 0
+// then waits once more, bounded, for the copies still in flight, and the
+// timeout is recorded in *status.  The caller stops issuing copies.
+__device__ __forceinline__ bool tc_wait_failed(uint64_t* bar, uint32_t phase, int* status) {
+  const bool landed = mbar_wait(bar, phase);
+  if (!__syncthreads_or(!landed)) return false;
+  if (threadIdx.x == 0) {
+    mbar_wait(bar, phase);
+    if (status != nullptr) atomicExch(status, RTG_ERR_TIMEOUT);
+  }
+  __syncthreads();
+  return true;
+}
+
 template <int CH>
 constexpr size_t first_smem() {
   return size_t(CH) * F_MT * 32 * 16 + size_t(F_COLS) * (CH * 16 + 8) * 4 >
@@ -420,10 +436,12 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
         xs[col * XS + k] = (col < ncol && k < rows) ? X[(c0 + col) * I + i0 + k] : 0.f;
       }
     }
-    if (!mbar_wait(&bar, phase)) ok = false;
+    if (tc_wait_failed(&bar, phase, status)) {
+      ok = false;
+      break;
+    }
     phase ^= 1u;
-    __syncthreads();
-    if (ok) {
+    {
       for (int kk = warp; kk < nk; kk += 8) {
         uint32_t B[2][2][3];
 #pragma unroll
@@ -453,10 +471,15 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
     }
     __syncthreads();
   }
-  if (!ok) {
-    if (tid == 0 && status != nullptr) atomicExch(status, RTG_ERR_TIMEOUT);
-    return;
+  if (!ok) {   // timed out: this CTA contributes zeros
+#pragma unroll
+    for (int a = 0; a < F_MT; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
   }
+  __syncthreads();
   constexpr int ROWS = F_MT * 16;
   float* red = reinterpret_cast<float*>(smem);                // [8][ROWS][F_RED]
 #pragma unroll
@@ -546,10 +569,12 @@ k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int
       }
       xa[k * XA + ll] = v;
     }
-    if (!mbar_wait(&bar, phase)) ok = false;
+    if (tc_wait_failed(&bar, phase, status)) {
+      ok = false;
+      break;
+    }
     phase ^= 1u;
-    __syncthreads();
-    if (ok) {
+    {
       for (int kk = warp; kk < nk; kk += 8) {
         uint32_t A[3][4];
 #pragma unroll
@@ -573,10 +598,13 @@ k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int
     }
     __syncthreads();
   }
-  if (!ok) {
-    if (tid == 0 && status != nullptr) atomicExch(status, RTG_ERR_TIMEOUT);
-    return;
+  if (!ok) {   // timed out: this CTA contributes zeros and still takes part in the dots
+#pragma unroll
+    for (int nt = 0; nt < N_NT; ++nt)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[nt][c] = 0.f;
   }
+  __syncthreads();
   float* red = reinterpret_cast<float*>(smem);               // [8][16][N_NT*8]
   constexpr int TW = N_NT * 8;
 #pragma unroll

@@ -202,6 +202,29 @@ __global__ void k_finalize(Work w, InfoDev* info) {
   for (int i = t; i < kMaxMu; i += blockDim.x) info->gcv[i] = w.gcv[i];
 }
 
+// Holds the stream until the host has queued a whole kernel group (phase
+// timing): one thread polls a flag in mapped host memory.  The wait is
+// bounded (2 s of globaltimer); on expiry the kernel records
+// RTG_ERR_TIMEOUT in *status and returns, so the stream never stalls.
+__global__ void k_gate(const volatile unsigned* flag, unsigned want, volatile unsigned* status) {
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (*flag < want) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 2000000000ull) {
+      *status = RTG_ERR_TIMEOUT;
+      return;
+    }
+    __nanosleep(500);
+  }
+}
+
+cudaError_t launch_gate(const unsigned* flag, unsigned want, unsigned* status, cudaStream_t s) {
+  k_gate<<<1, 1, 0, s>>>(flag, want, status);
+  return cudaGetLastError();
+}
+
 static unsigned ew_grid(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;

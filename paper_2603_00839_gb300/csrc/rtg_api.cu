@@ -373,6 +373,9 @@ struct SolvePlan {
   bool true_resid = false;
   int dtype = RTG_F32;
   int launches_pro = 0, launches_step = 0, launches_epi = 0;   // kernels per phase
+  int launches_setup = 0;                                         // reset + Theta, part of the prologue
+  int direct_steps = 0;                                           // steps launched by the last direct solve
+  int* stop_host = nullptr;                                       // pinned: ctl->stop read back per direct step
   ~SolvePlan() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -380,6 +383,93 @@ struct SolvePlan {
     if (ev1) cudaEventDestroy(ev1);
     if (desc_host) cudaFreeHost(desc_host);
     if (info_host) cudaFreeHost(info_host);
+    if (stop_host) cudaFreeHost(stop_host);
+  }
+};
+
+// Phase timing (RTG_FLAG_PHASE_TIMES): on the direct-launch path every
+// kernel group is bracketed by CUDA events on the solve's stream.  Each
+// group is preceded by a gate kernel that holds the stream until the host
+// has queued the group, so host launch latency never lands between two
+// events; the device then runs the group back to back as it would in the
+// graph.  A group belongs to a step; groups of steps at or after the stop
+// (whose kernels return at once) are dropped when the results are read.
+struct PhaseTimer {
+  cudaStream_t s = nullptr;
+  unsigned* host = nullptr;      // [0] flag written by the host, [1] gate status
+  unsigned* dev = nullptr;
+  unsigned gen = 0;
+  struct Rec {
+    cudaEvent_t a, b;
+    int phase, step, launches;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  cudaEvent_t a_open = nullptr;
+
+  ~PhaseTimer() {
+    for (auto e : pool) cudaEventDestroy(e);
+    if (host) cudaFreeHost(host);
+  }
+  cudaError_t init() {
+    if (host) return cudaSuccess;
+    void* p = nullptr;
+    cudaError_t e = cudaHostAlloc(&p, 2 * sizeof(unsigned), cudaHostAllocMapped);
+    if (e != cudaSuccess) return e;
+    host = static_cast<unsigned*>(p);
+    host[0] = 0;
+    host[1] = 0;
+    return cudaHostGetDevicePointer(reinterpret_cast<void**>(&dev), host, 0);
+  }
+  cudaEvent_t next_event() {
+    if (used == pool.size()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void reset(cudaStream_t st) {
+    s = st;
+    recs.clear();
+    used = 0;
+    host[1] = 0;
+  }
+  cudaError_t hold() { return launch_gate(dev, ++gen, dev + 1, s); }
+  void release() { __atomic_store_n(host, gen, __ATOMIC_RELEASE); }
+  void begin() {
+    a_open = next_event();
+    if (a_open) cudaEventRecord(a_open, s);
+  }
+  void end(int phase, int step, int launches) {
+    cudaEvent_t b = next_event();
+    if (!a_open || !b) return;
+    cudaEventRecord(b, s);
+    recs.push_back(Rec{a_open, b, phase, step, launches});
+    a_open = nullptr;
+  }
+  // after the stream has been synchronised
+  void collect(int iters, rtg_info* info) {
+    for (const Rec& r : recs) {
+      if (r.step >= iters) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) continue;
+      info->phase_ms[r.phase] += ms;
+      info->phase_launches[r.phase] += r.launches;
+    }
+  }
+};
+
+// Brackets one kernel group when a timer is given.
+struct PhaseScope {
+  PhaseTimer* t;
+  int phase, step, launches;
+  PhaseScope(PhaseTimer* t_, int ph, int st, int l) : t(t_), phase(ph), step(st), launches(l) {
+    if (t) t->begin();
+  }
+  ~PhaseScope() {
+    if (t) t->end(phase, step, launches);
   }
 };
 
@@ -388,7 +478,16 @@ struct rtg_context {
   std::map<std::string, std::unique_ptr<OpHolder>> ops;
   std::map<std::string, std::unique_ptr<DevBuf>> sketches;   // signs, fragments and scratch per sketch
   DevBuf tA, tB;
-  std::map<std::string, std::unique_ptr<SolvePlan>> plans;
+  std::map<std::string, std::shared_ptr<SolvePlan>> plans;
+  std::unique_ptr<PhaseTimer> timer;
+  // per workspace slot: the plan and call state of the last submitted solve
+  struct Pending {
+    std::shared_ptr<SolvePlan> plan;
+    cudaStream_t stream = nullptr;
+    int m = 0, n_mu = 0, mode = 0;
+    bool use_graph = true, phase_times = false, active = false;
+  };
+  Pending pending[RTG_MAX_SLOTS];
 };
 
 struct rtg_krylov_state {
@@ -426,36 +525,7 @@ rtg_status get_op(rtg_context* h, const rtg_factor* A, int nA, const rtg_factor*
   return RTG_OK;
 }
 
-// Opt-in trace of the direct-launch path (environment RTG_TRACE=1): an
-// event is recorded after every phase of the solve and the device time of
-// each phase is printed to stderr after the final synchronisation.
-struct Tracer {
-  bool on = false;
-  cudaStream_t s = nullptr;
-  std::vector<cudaEvent_t> ev;
-  std::vector<std::string> name;
-  void mark(const char* nm) {
-    if (!on) return;
-    cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) return;
-    cudaEventRecord(e, s);
-    ev.push_back(e);
-    name.push_back(nm);
-  }
-  void report() {
-    if (!on || ev.size() < 2) return;
-    cudaEventSynchronize(ev.back());
-    for (size_t i = 1; i < ev.size(); ++i) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
-      fprintf(stderr, "rtg-trace %-14s %9.2f us\n", name[i].c_str(), ms * 1e3);
-    }
-    for (auto e : ev) cudaEventDestroy(e);
-    ev.clear();
-    name.clear();
-  }
-};
-Tracer g_tracer;
+
 
 StepOpts solve_step_opts(const SolvePlan& P, int use_cond, cudaGraphConditionalHandle hnd) {
   StepOpts o{};
@@ -473,12 +543,15 @@ PtrRef desc_ref(const void* const* field) {
   return r;
 }
 
-rtg_status enqueue_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s) {
+rtg_status enqueue_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s,
+                            PhaseTimer* pt = nullptr) {
   Work& w = P.w;
-  CK(launch_reset(w, 0, s));
-  g_tracer.mark("reset");
-  CK(launch_theta(P.sp, P.sk.bits, P.sk.frags, s));
-  g_tracer.mark("theta");
+  {
+    PhaseScope ps(pt, RTG_PHASE_SETUP, -1, P.launches_setup);
+    CK(launch_reset(w, 0, s));
+    CK(launch_theta(P.sp, P.sk.bits, P.sk.frags, s, P.desc_dev->key));
+  }
+  PhaseScope ps(pt, RTG_PHASE_INIT, -1, P.launches_pro - P.launches_setup);
   PtrRef C = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->C));
   PtrRef src = C;
   if (P.has_x0) {   // R_0 = C - Phi(X_0) into the V_0 slot
@@ -489,46 +562,51 @@ rtg_status enqueue_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s) {
   const bool fused = P.sp.fused_dots != 0;
   SketchDots dots{&w, 0, so};
   CK(launch_sketch(P.sp, P.sk, src, fused ? w.S : w.Spart, fused ? &dots : nullptr, nullptr, s));
-  g_tracer.mark("sketch0");
   CK(launch_start(w, src, so, fused, s));
-  g_tracer.mark("start");
   return RTG_OK;
 }
 
 rtg_status enqueue_step(const OpHolder& op, const SketchPlan& sp, const Work& w, int dtype,
                         void* tA, void* tB, const SketchScratch& sk, const StepOpts& so,
-                        cudaStream_t s) {
+                        cudaStream_t s, PhaseTimer* pt = nullptr, int step = 0) {
   PtrRef vj;
   vj.base = w.V;
   vj.jidx = &w.ctl->j;
   vj.stride = w.n;
   const int* stop = &w.ctl->stop;
-  CK(launch_apply(op.op, dtype, vj, ref(w.W), 1.0, 0.0, PtrRef{}, tA, tB, stop, s));
-  g_tracer.mark("apply");
+  {
+    PhaseScope ps(pt, RTG_PHASE_APPLY, step, apply_launches(op.op, false));
+    CK(launch_apply(op.op, dtype, vj, ref(w.W), 1.0, 0.0, PtrRef{}, tA, tB, stop, s));
+  }
   const bool fused = sp.fused_dots != 0;
-  SketchDots dots{&w, 1, so};
-  CK(launch_sketch(sp, sk, ref(w.W), fused ? w.S : w.Spart, fused ? &dots : nullptr, stop, s));
-  g_tracer.mark("sketch+dots");
-  if (!fused) CK(launch_pass1(w, so, s));
-  g_tracer.mark("gs");
+  {
+    PhaseScope ps(pt, RTG_PHASE_SKETCH, step, sketch_launches(sp));
+    SketchDots dots{&w, 1, so};
+    CK(launch_sketch(sp, sk, ref(w.W), fused ? w.S : w.Spart, fused ? &dots : nullptr, stop, s));
+  }
+  if (!fused) {
+    PhaseScope ps(pt, RTG_PHASE_GS, step, 1);
+    CK(launch_pass1(w, so, s));
+  }
+  PhaseScope ps(pt, RTG_PHASE_UPDATE, step, 1);
   CK(launch_update(w, so, s));
-  g_tracer.mark("update");
   return RTG_OK;
 }
 
-rtg_status enqueue_epilogue(SolvePlan& P, cudaStream_t s) {
+rtg_status enqueue_epilogue(SolvePlan& P, cudaStream_t s, PhaseTimer* pt = nullptr) {
   FinishOpts f{};
   f.desc = P.desc_dev;
   f.n_mu = P.n_mu;
   f.mode = P.mode;
-  CK(launch_tikhonov(P.w, f, s));
-  g_tracer.mark("tikhonov");
+  {
+    PhaseScope ps(pt, RTG_PHASE_TIKHONOV, -1, 1);
+    CK(launch_tikhonov(P.w, f, s));
+  }
+  PhaseScope ps(pt, RTG_PHASE_ASSEMBLE, -1, 2);
   PtrRef X0 = P.has_x0 ? desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X0)) : PtrRef{};
   PtrRef X = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X));
   CK(launch_assemble(P.w, X0, X, s));
-  g_tracer.mark("assemble");
   CK(launch_finalize(P.w, P.info_dev, s));
-  g_tracer.mark("finalize");
   return RTG_OK;
 }
 
@@ -696,7 +774,6 @@ rtg_status rtg_sketch(rtg_handle h, rtg_shape shape, rtg_dtype dtype, const int6
   append_bytes(key, &sp.order, sizeof sp.order);
   append_bytes(key, sp.dims, sizeof sp.dims);
   append_bytes(key, sp.sdims, sizeof sp.sdims);
-  append_bytes(key, &seed, sizeof seed);
   append_bytes(key, &pid, sizeof pid);
   append_bytes(key, &sp.dtype, sizeof sp.dtype);
   auto it = h->sketches.find(key);
@@ -821,10 +898,10 @@ rtg_status rtg_krylov_query(rtg_handle h, rtg_krylov K, rtg_krylov_view* view, d
   return RTG_OK;
 }
 
-rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
-                           int32_t nB, rtg_shape shape, rtg_dtype dtype, const void* C, int32_t m,
-                           const int64_t* sketch_dims, uint64_t seed, double lambda, const void* X0,
-                           void* X, const rtg_opts* opts_in, rtg_info* info, rtg_stream stream) {
+rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
+                            int32_t nB, rtg_shape shape, rtg_dtype dtype, const void* C, int32_t m,
+                            const int64_t* sketch_dims, uint64_t seed, double lambda, const void* X0,
+                            void* X, const rtg_opts* opts_in, rtg_stream stream) {
   if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
   int64_t n = 0;
   RK(check_shape(shape, &n));
@@ -839,6 +916,7 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
   if (!(opts.tol >= 0.0) || !std::isfinite(opts.tol)) return fail(RTG_ERR_INVALID_ARG, "opts.tol must be finite and >= 0");
   if (opts.max_restarts != 0) return fail(RTG_ERR_UNSUPPORTED, "restarts are not supported on the GPU path (max_restarts=%d)", opts.max_restarts);
   if (!(opts.breakdown_tol >= 0.0)) return fail(RTG_ERR_INVALID_ARG, "opts.breakdown_tol must be >= 0");
+  if (opts.slot < 0 || opts.slot >= RTG_MAX_SLOTS) return fail(RTG_ERR_INVALID_ARG, "opts.slot=%d not in 0..%d", opts.slot, RTG_MAX_SLOTS - 1);
   const int mode = lambda > 0 ? 1 : (lambda == 0 ? 0 : 2);
   if (mode == 2) {
     if (opts.n_mu < 1 || opts.n_mu > kMaxMu || opts.mu_grid == nullptr)
@@ -856,27 +934,41 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
 
   SketchPlan sp;
   RK(build_sketch(shape, sketch_dims, seed, 0, dtype, sp));
-  const bool use_graph = !(opts.flags & RTG_FLAG_NO_GRAPH);
+  const bool phase_times = (opts.flags & RTG_FLAG_PHASE_TIMES) != 0;
+  const bool use_graph = !(opts.flags & RTG_FLAG_NO_GRAPH) && !phase_times;
   std::string key = op_key(A, nA, B, nB, shape);
   append_bytes(key, &dtype, sizeof dtype);
   append_bytes(key, &m, sizeof m);
   append_bytes(key, sp.sdims, sizeof sp.sdims);
-  append_bytes(key, &seed, sizeof seed);
   const int nmu_key = mode == 2 ? opts.n_mu : 0;
   append_bytes(key, &mode, sizeof mode);
   append_bytes(key, &nmu_key, sizeof nmu_key);
   const bool has_x0 = X0 != nullptr;
   key.push_back(has_x0 ? '1' : '0');
   key.push_back(use_graph ? 'g' : 'd');
+  append_bytes(key, &opts.slot, sizeof opts.slot);
 
+  rtg_context::Pending& pend = h->pending[opts.slot];
+  if (pend.active) return fail(RTG_ERR_INVALID_ARG, "slot %d has a submitted solve that was not waited for", opts.slot);
+  if (phase_times)
+    for (const auto& q : h->pending)
+      if (q.active && q.phase_times) return fail(RTG_ERR_INVALID_ARG, "another phase-timed solve is pending");
   auto it = h->plans.find(key);
   SolvePlan* P = nullptr;
+  std::shared_ptr<SolvePlan> hold;
   if (it == h->plans.end()) {
-    if (h->plans.size() >= 8) {
+    if (h->plans.size() >= 8 + RTG_MAX_SLOTS) {
+      // plans of other slots may still run on their streams: wait for the device
       cudaDeviceSynchronize();
+      for (auto& q : h->pending)
+        if (!q.active) q.plan.reset();
       h->plans.clear();
     }
-    auto np = std::make_unique<SolvePlan>();
+    // Building a plan allocates memory and instantiates a CUDA graph; it
+    // does so only while no other solve of this handle is in flight.
+    for (const auto& q : h->pending)
+      if (q.active) CK(cudaStreamSynchronize(q.stream));
+    auto np = std::make_shared<SolvePlan>();
     P = np.get();
     P->dtype = dtype;
     P->mode = mode;
@@ -899,6 +991,7 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
     P->info_dev = reinterpret_cast<InfoDev*>(static_cast<char*>(P->small.p) + ((sizeof(SolveDesc) + 255) & ~size_t(255)));
     CK(cudaMallocHost(&P->desc_host, sizeof(SolveDesc)));
     CK(cudaMallocHost(&P->info_host, sizeof(InfoDev)));
+    CK(cudaMallocHost(&P->stop_host, sizeof(int)));
     std::memset(P->desc_host, 0, sizeof(SolveDesc));
     CK(cudaMemset(P->small.p, 0, P->small.bytes));
     CK(cudaEventCreate(&P->ev0));
@@ -907,15 +1000,18 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
       int nsk = 0;
       for (int k = 0; k < sp.order; ++k) nsk += sp.sketched[k];
       const int gs = sp.fused_dots ? 0 : 1;
-      P->launches_pro = 1 + (nsk > 0 ? (dtype == RTG_F32 ? 2 : 1) : 0) +
+      P->launches_setup = 1 + (nsk > 0 ? (dtype == RTG_F32 ? 2 : 1) : 0);
+      P->launches_pro = P->launches_setup +
                         (has_x0 ? apply_launches(P->op.op, true) : 0) + sketch_launches(sp) + gs + 1;
       P->launches_step = apply_launches(P->op.op, false) + sketch_launches(sp) + gs + 1;
       P->launches_epi = 3;
     }
     if (use_graph) RK(build_graph(*P));
-    h->plans[key] = std::move(np);
+    h->plans[key] = np;
+    hold = np;
   } else {
-    P = it->second.get();
+    hold = it->second;
+    P = hold.get();
   }
   // per-call descriptor (host arrays are staged through plan buffers)
   SolveDesc& D = *P->desc_host;
@@ -940,6 +1036,8 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
       CK(cudaMemcpyAsync(P->Xst.p, X0, bytes_t, cudaMemcpyHostToDevice, s));
     }
   }
+  D.key[0] = seed;
+  D.key[1] = 0;
   D.tol = opts.tol;
   D.bd_tol = opts.breakdown_tol > 0 ? opts.breakdown_tol : (dtype == RTG_F64 ? 1e-12 : 1e-6);
   D.lambda = lambda;
@@ -951,22 +1049,63 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
     CK(cudaGraphLaunch(P->exec, s));
   } else {
     const StepOpts so = solve_step_opts(*P, 0, 0);
-    const char* tr = getenv("RTG_TRACE");
-    g_tracer.on = tr != nullptr && tr[0] == '1';
-    g_tracer.s = s;
-    g_tracer.mark("begin");
-    RK(enqueue_prologue(*P, so, s));
-    for (int j = 0; j < m; ++j) RK(enqueue_step(P->op, P->sp, P->w, dtype, P->tA, P->tB, P->sk, so, s));
-    RK(enqueue_epilogue(*P, s));
+    PhaseTimer* pt = nullptr;
+    if (phase_times) {
+      if (!h->timer) h->timer = std::make_unique<PhaseTimer>();
+      CK(h->timer->init());
+      pt = h->timer.get();
+      pt->reset(s);
+    }
+    // each group is queued behind a gate that the host opens once the group is queued
+    auto group = [&](auto&& body) -> rtg_status {
+      if (pt) CK(pt->hold());
+      rtg_status st = body();
+      if (pt) pt->release();
+      return st;
+    };
+    // The host waits for each step and stops launching once the device has
+    // stopped the solve, so the launch sequence is the one the graph runs.
+    auto stopped = [&]() -> rtg_status {
+      CK(cudaMemcpyAsync(P->stop_host, &P->w.ctl->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      return RTG_OK;
+    };
+    RK(group([&] { return enqueue_prologue(*P, so, s, pt); }));
+    RK(stopped());
+    int steps = 0;
+    while (steps < m && *P->stop_host == 0) {
+      const int j = steps++;
+      RK(group([&] { return enqueue_step(P->op, P->sp, P->w, dtype, P->tA, P->tB, P->sk, so, s, pt, j); }));
+      RK(stopped());
+    }
+    P->direct_steps = steps;
+    RK(group([&] { return enqueue_epilogue(*P, s, pt); }));
   }
   CK(cudaEventRecord(P->ev1, s));
   if (!X_dev) CK(cudaMemcpyAsync(X, P->Xst.p, bytes_t, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(P->info_host, P->info_dev, sizeof(InfoDev), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (!use_graph) {
-    g_tracer.report();
-    g_tracer.on = false;
-  }
+  pend.plan = hold;
+  pend.stream = s;
+  pend.m = m;
+  pend.n_mu = mode == 2 ? opts.n_mu : 0;
+  pend.mode = mode;
+  pend.use_graph = use_graph;
+  pend.phase_times = phase_times;
+  pend.active = true;
+  return RTG_OK;
+}
+
+rtg_status rtg_gmres_wait(rtg_handle h, int32_t slot, rtg_info* info) {
+  if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
+  if (slot < 0 || slot >= RTG_MAX_SLOTS) return fail(RTG_ERR_INVALID_ARG, "slot=%d not in 0..%d", slot, RTG_MAX_SLOTS - 1);
+  rtg_context::Pending& pend = h->pending[slot];
+  if (!pend.active) return fail(RTG_ERR_INVALID_ARG, "slot %d has no submitted solve", slot);
+  pend.active = false;
+  DeviceGuard dg(h->device);
+  SolvePlan* P = pend.plan.get();
+  const int m = pend.m, mode = pend.mode;
+  const bool use_graph = pend.use_graph, phase_times = pend.phase_times;
+  CK(cudaStreamSynchronize(pend.stream));
   const InfoDev& I = *P->info_host;
   if (info) {
     info->iters = I.iters;
@@ -979,16 +1118,33 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
     if (info->rho_hist)
       for (int i = 0; i < I.iters && i < kMaxK; ++i) info->rho_hist[i] = I.rho_hist[i];
     if (info->gcv && mode == 2)
-      for (int i = 0; i < opts.n_mu; ++i) info->gcv[i] = I.gcv[i];
+      for (int i = 0; i < pend.n_mu; ++i) info->gcv[i] = I.gcv[i];
     info->true_rel_resid = -1.0;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, P->ev0, P->ev1);
     info->elapsed_ms = ms;
     info->device_status = I.status;
     info->launches = P->launches_pro + P->launches_epi +
-                     (use_graph ? I.iters : m) * P->launches_step;
+                     (use_graph ? I.iters : P->direct_steps) * P->launches_step;
+    for (int k = 0; k < RTG_PHASE_COUNT; ++k) {
+      info->phase_ms[k] = 0.0;
+      info->phase_launches[k] = 0;
+    }
+    if (phase_times) h->timer->collect(I.iters, info);
+  }
+  if (phase_times && h->timer->host[1] != 0) {
+    return fail(RTG_ERR_TIMEOUT, "phase timing: a gate waited 2 s for the host to queue its group");
   }
   return RTG_OK;
+}
+
+rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
+                           int32_t nB, rtg_shape shape, rtg_dtype dtype, const void* C, int32_t m,
+                           const int64_t* sketch_dims, uint64_t seed, double lambda, const void* X0,
+                           void* X, const rtg_opts* opts_in, rtg_info* info, rtg_stream stream) {
+  RK(rtg_gmres_submit(h, A, nA, B, nB, shape, dtype, C, m, sketch_dims, seed, lambda, X0, X,
+                      opts_in, stream));
+  return rtg_gmres_wait(h, opts_in ? opts_in->slot : 0, info);
 }
 
 }  // extern "C"

@@ -77,6 +77,7 @@ struct SolveDesc {
   int n_mu;
   int pad;
   double mu_grid[kMaxMu];
+  uint64_t key[2];  // Philox seed and problem id of the sketch signs
 };
 
 // Host-visible summary written at the end of a solve (one D2H copy).
@@ -204,9 +205,13 @@ void record_error(const char* msg);
 // k_philox.cu
 cudaError_t launch_philox_words(uint64_t seed, uint64_t pid, int64_t n_words, uint64_t* out,
                                 cudaStream_t s);
-cudaError_t launch_theta_bits(const SketchPlan& sp, uint32_t* bits, cudaStream_t s);
+// key_dev (optional): device array {seed, problem_id} read when the kernel runs,
+// so one captured graph serves every seed; otherwise sp.seed / sp.pid.
+cudaError_t launch_theta_bits(const SketchPlan& sp, uint32_t* bits, cudaStream_t s,
+                              const uint64_t* key_dev = nullptr);
 // signs, then (FP32 chain) the Theta fragments of every stage
-cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, cudaStream_t s);
+cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, cudaStream_t s,
+                         const uint64_t* key_dev = nullptr);
 
 // k_apply.cu: Y = alpha * Phi(X) + beta * Z (Z may be null when beta == 0).
 // tmp: scratch of n elements for the unfused path (may be null if unused).
@@ -263,4 +268,6 @@ struct FinishOpts {
 cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s);
 cudaError_t launch_assemble(const Work& w, PtrRef X0, PtrRef X, cudaStream_t s);
 cudaError_t launch_finalize(const Work& w, InfoDev* info, cudaStream_t s);
+// Phase timing: bounded wait of the stream on a host-written flag.
+cudaError_t launch_gate(const unsigned* flag, unsigned want, unsigned* status, cudaStream_t s);
 }  // namespace rtg

@@ -94,3 +94,31 @@ int main() {
         ref = [int(v) for v in np.random.Philox(key=seed + (pid << 64)).random_raw(20)]
         assert got == ref
         assert got == oracle.philox_words(seed, pid, 20)
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Sizes and field offsets of the binding's ctypes mirrors equal those a
+    C compiler gives the structs of include/rtg.h."""
+    from paper_2603_00839_gb300 import _lib as L
+    structs = {"rtg_shape": L.Shape, "rtg_factor": L.Factor, "rtg_opts": L.Opts,
+               "rtg_info": L.Info, "rtg_krylov_view": L.KrylovView}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rtg.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append(f'  printf("phases %d\\n", (int)RTG_PHASE_COUNT);')
+    lines.append('  return 0; }')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    want = []
+    for cname, py in structs.items():
+        want.append(f"{cname} size {ctypes.sizeof(py)}")
+        for fname, _ in py._fields_:
+            want.append(f"{cname} {fname} {getattr(py, fname).offset}")
+    want.append(f"phases {L.PHASE_COUNT}")
+    assert got[:-1] == want

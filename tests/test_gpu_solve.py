@@ -175,6 +175,90 @@ def test_solve_graph_and_direct_launch_agree(h):
     assert np.array_equal(Xg.cpu().numpy(), Xd.cpu().numpy())
 
 
+def test_phase_timed_solve_equals_graph_solve(h):
+    """The phase-timed (gated, event-bracketed) launch path computes the same
+    solve, counts the kernel groups of the active steps, and its group times
+    fit inside the solve's own device time."""
+    p = w.image_config(2)
+    api = _api()
+    A, B = _api_factors(p)
+    mats, C, nu_c, th = _setup(p)
+    Cd = api.to_device(C, torch.float32)
+    Xg, ig = h.gmres_solve(Cd, p.m, p.sketch_dims, p.seed, p.lam, A, B, tol=1e-2, mu_grid=p.mu_grid)
+    Xt, it = h.gmres_solve(Cd, p.m, p.sketch_dims, p.seed, p.lam, A, B, tol=1e-2, mu_grid=p.mu_grid,
+                           phase_times=True)
+    assert it.iters == ig.iters and it.device_status == 0
+    assert np.array_equal(Xg.cpu().numpy(), Xt.cpu().numpy())
+    k = it.iters
+    assert it.phase_launches["apply"] == k
+    assert it.phase_launches["update"] == k
+    assert it.phase_launches["tikhonov"] == 1 and it.phase_launches["assemble"] == 2
+    assert all(v >= 0.0 for v in it.phase_ms.values())
+    assert it.phase_ms["apply"] > 0 and it.phase_ms["update"] > 0 and it.phase_ms["sketch"] > 0
+    assert sum(it.phase_ms.values()) <= it.elapsed_ms * 1.001
+
+
+def test_concurrent_solves_on_streams_equal_single_solves(h):
+    """Four solves submitted on four streams and workspace slots before any
+    wait give the same iterates as the same solves run one by one."""
+    api = _api()
+    probs = []
+    for seed in range(4):
+        p = w.image_config(2, seed=seed)
+        mats, C, nu_c, th = _setup(p)
+        A, B = _api_factors(p)
+        probs.append((p, A, B, api.to_device(C, torch.float32)))
+    ref = [h.gmres_solve(Cd, p.m, p.sketch_dims, p.seed, p.lam, A, B, tol=1e-2, mu_grid=p.mu_grid)
+           for p, A, B, Cd in probs]
+    streams = [torch.cuda.Stream() for _ in probs]
+    torch.cuda.synchronize()
+    pend = [h.gmres_submit(Cd, p.m, p.sketch_dims, p.seed, p.lam, A, B, tol=1e-2, mu_grid=p.mu_grid,
+                           slot=1 + i, stream=streams[i])
+            for i, (p, A, B, Cd) in enumerate(probs)]
+    got = [h.gmres_wait(q) for q in pend]
+    for (Xr, ir), (Xg, ig) in zip(ref, got):
+        assert ig.iters == ir.iters and ig.mu == ir.mu
+        assert np.array_equal(Xg.cpu().numpy(), Xr.cpu().numpy())
+
+
+def test_one_plan_serves_every_seed(h):
+    """The sketch seed is read from the solve's descriptor when the graph runs:
+    a solve with seed 5 after one with seed 0 on the same handle and slot
+    equals a solve with seed 5 on a fresh handle, and differs from seed 0."""
+    api = _api()
+    p = w.image_config(1)
+    mats, C, nu_c, th = _setup(p)
+    A, B = _api_factors(p)
+    Cd = api.to_device(C, torch.float64)
+    X0, _ = h.gmres_solve(Cd, p.m, p.sketch_dims, 0, 1e-3, A, B, tol=0.0, slot=3)
+    X5, i5 = h.gmres_solve(Cd, p.m, p.sketch_dims, 5, 1e-3, A, B, tol=0.0, slot=3)
+    h2 = api.Handle(0)
+    X5f, i5f = h2.gmres_solve(Cd, p.m, p.sketch_dims, 5, 1e-3, A, B, tol=0.0, slot=3)
+    assert np.array_equal(X5.cpu().numpy(), X5f.cpu().numpy())
+    assert not np.array_equal(X5.cpu().numpy(), X0.cpu().numpy())
+    th5 = oracle.sketch_matrices(p.dims, p.sketch_dims, 5, 0)
+    ref = oracle.rtg_gmres(mats, C, p.m, th5, tol=0.0, lam=1e-3)
+    assert _relnorm(X5.cpu().numpy(), ref["X"]) < 1e-10
+
+
+def test_submit_and_wait_misuse_is_rejected(h):
+    from paper_2603_00839_gb300 import _lib as L
+    api = _api()
+    p = w.image_config(1)
+    mats, C, nu_c, th = _setup(p)
+    A, B = _api_factors(p)
+    Cd = api.to_device(C, torch.float64)
+    with pytest.raises(L.RtgError, match="no submitted solve"):
+        h.gmres_wait(api.PendingSolve(7, None, p.m, 0, None, p.lam, False, ()))
+    q = h.gmres_submit(Cd, p.m, p.sketch_dims, p.seed, p.lam, A, B, tol=1e-3, slot=7)
+    with pytest.raises(L.RtgError, match="not waited"):
+        h.gmres_submit(Cd, p.m, p.sketch_dims, p.seed, p.lam, A, B, tol=1e-3, slot=7)
+    X, info = h.gmres_wait(q)
+    assert info.converged
+    with pytest.raises(L.RtgError, match="slot"):
+        h.gmres_submit(Cd, p.m, p.sketch_dims, p.seed, p.lam, A, B, tol=1e-3, slot=L.MAX_SLOTS)
+
+
 @pytest.mark.parametrize("lam", [0.0, 1e-2])
 def test_solve_with_initial_guess(h, lam):
     p = w.image_config(1)
