@@ -83,6 +83,40 @@ struct DotAcc<double> {
 // Gram matrix G = Q^T Q).  The start of a process (J = -1) has only s . s.
 __device__ __forceinline__ int gs_ncols(int J) { return J < 0 ? 1 : 2 * J + 3; }
 
+// Reduce-scatter of 32 float-float values across a warp: in five halving
+// rounds each lane keeps one half of its values and hands the other half
+// to its partner, adding what it receives; afterwards v[0] of lane l is the
+// warp total of value l.  31 exchanges per lane instead of 32 x 5 for 32
+// separate warp sums, and the adds of a round are independent.  The tree
+// is fixed, so the sums are deterministic.
+__device__ __forceinline__ void ff_reduce_scatter32(FF (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const int half = 16 >> r;          // also the partner's lane offset
+    const bool up = (lane & half) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const FF give = up ? v[k] : v[k + half];
+      const FF keep = up ? v[k + half] : v[k];
+      FF got;
+      got.hi = __shfl_xor_sync(0xffffffffu, give.hi, half);
+      got.lo = __shfl_xor_sync(0xffffffffu, give.lo, half);
+      v[k] = ff_add(keep, got);
+    }
+  }
+}
+
+// Sum of the per-warp values of one column in a fixed order.
+__device__ __forceinline__ double warps_total(const double (*red)[kRedCols], int nw, int i) {
+  if (nw == 8)
+    return ((red[0][i] + red[1][i]) + (red[2][i] + red[3][i])) +
+           ((red[4][i] + red[5][i]) + (red[6][i] + red[7][i]));
+  double acc = 0.0;
+  for (int u = 0; u < nw; ++u) acc += red[u][i];
+  return acc;
+}
+
 // Per-block partial sums of the columns above: products of the stored
 // values accumulated in double-float (FP32 data) or FP64 (FP64 data).
 // Each thread passes up to ITEMS entries (vals at sketch indices idx);
@@ -110,46 +144,77 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
     const double t = a.warp_total();
     if (lane == 0) red[warp][J + 1] = t;
   }
-  // columns of Q in groups of 8: all loads of a group go out before any use
-  constexpr int GRP = 8;
-  for (int i0 = 0; i0 <= J; i0 += GRP) {
-    T qv[GRP][ITEMS];
+  if constexpr (sizeof(T) == 4) {
+    // 16 columns of Q at a time: s . Q_i and Q_J . Q_i for each, 32 values
+    // per thread, reduced across the warp in one reduce-scatter
+    for (int i0 = 0; i0 <= J; i0 += 16) {
+      float qv[16][ITEMS];
 #pragma unroll
-    for (int g = 0; g < GRP; ++g)
+      for (int g = 0; g < 16; ++g)
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k) {
-        const bool ok = k < cnt && idx[k] >= 0 && i0 + g <= J;
-        qv[g][k] = ok ? Q[static_cast<int64_t>(i0 + g) * d + idx[k]] : static_cast<T>(0);
+        for (int k = 0; k < ITEMS; ++k) {
+          const bool ok = k < cnt && idx[k] >= 0 && i0 + g <= J;
+          qv[g][k] = ok ? Q[static_cast<int64_t>(i0 + g) * d + idx[k]] : 0.f;
+        }
+      FF v[32];
+#pragma unroll
+      for (int g = 0; g < 16; ++g) {
+        FF p{0.f, 0.f}, q{0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+          p = ff_add(p, ff_prod(sv[k], qv[g][k]));
+          q = ff_add(q, ff_prod(qJ[k], qv[g][k]));
+        }
+        v[g] = p;
+        v[16 + g] = q;
       }
+      ff_reduce_scatter32(v);
+      const int g = lane & 15;
+      if (i0 + g <= J) red[warp][lane < 16 ? i0 + g : J + 2 + i0 + g] = ff_to_double(v[0]);
+    }
+  } else {
+    // columns of Q in groups of 8: all loads of a group go out before any use
+    constexpr int GRP = 8;
+    for (int i0 = 0; i0 <= J; i0 += GRP) {
+      T qv[GRP][ITEMS];
 #pragma unroll
-    for (int g = 0; g < GRP; ++g) {
-      if (i0 + g > J) break;
-      DotAcc<T> p, q;
+      for (int g = 0; g < GRP; ++g)
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k) {
-        p.add(sv[k], qv[g][k]);
-        q.add(qJ[k], qv[g][k]);
-      }
-      const double tp = p.warp_total(), tq = q.warp_total();
-      if (lane == 0) {
-        red[warp][i0 + g] = tp;
-        red[warp][J + 2 + i0 + g] = tq;
+        for (int k = 0; k < ITEMS; ++k) {
+          const bool ok = k < cnt && idx[k] >= 0 && i0 + g <= J;
+          qv[g][k] = ok ? Q[static_cast<int64_t>(i0 + g) * d + idx[k]] : static_cast<T>(0);
+        }
+#pragma unroll
+      for (int g = 0; g < GRP; ++g) {
+        if (i0 + g > J) break;
+        DotAcc<T> p, q;
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+          p.add(sv[k], qv[g][k]);
+          q.add(qJ[k], qv[g][k]);
+        }
+        const double tp = p.warp_total(), tq = q.warp_total();
+        if (lane == 0) {
+          red[warp][i0 + g] = tp;
+          red[warp][J + 2 + i0 + g] = tq;
+        }
       }
     }
   }
   __syncthreads();
   const int rowlen = 2 * w.m + 4;
-  for (int i = threadIdx.x; i < ncols; i += blockDim.x) {
-    double acc = 0.0;
-    for (int u = 0; u < nw; ++u) acc += red[u][i];
-    w.part[static_cast<int64_t>(blockIdx.x + gridDim.x * blockIdx.y) * rowlen + i] = acc;
-  }
+  for (int i = threadIdx.x; i < ncols; i += blockDim.x)
+    w.part[static_cast<int64_t>(blockIdx.x + gridDim.x * blockIdx.y) * rowlen + i] = warps_total(red, nw, i);
 }
 
 // Ticket: returns true in every thread of the last block to finish, after
-// tot[0..ncols) holds the sum of all blocks' rows (one warp per column,
-// lanes striding over rows).  The counter wraps back to zero by itself.
-__device__ inline bool last_block_combine(const Work& w, int ncols, double* tot, int* am_last) {
+// tot[0..ncols) holds the sum of all blocks' rows.  The rows are summed in
+// one round of loads: thread t takes column t % nc and every G-th row
+// starting at t / nc (four accumulators), then one thread per column adds
+// the G group sums.  The order is fixed, so the result is deterministic.
+// The counter wraps back to zero by itself.  scratch: >= blockDim doubles.
+__device__ inline bool last_block_combine(const Work& w, int ncols, double* tot, int* am_last,
+                                          double* scratch) {
   __threadfence();
   __syncthreads();
   const unsigned nblk = gridDim.x * gridDim.y;
@@ -157,21 +222,42 @@ __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot,
   __syncthreads();
   if (!*am_last) return false;
   __threadfence();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
   const int rowlen = 2 * w.m + 4;
-  for (int i = warp; i < ncols; i += nw) {
-    double a0 = 0.0, a1 = 0.0;
-    unsigned b = lane;
-    for (; b + 32 < nblk; b += 64) {
-      a0 += __ldcg(w.part + static_cast<int64_t>(b) * rowlen + i);
-      a1 += __ldcg(w.part + static_cast<int64_t>(b + 32) * rowlen + i);
+  const int nt = blockDim.x;
+  for (int c0 = 0; c0 < ncols; c0 += nt) {
+    const int nc = (ncols - c0 < nt) ? ncols - c0 : nt;
+    int G = nt / nc;
+    if (G > 32) G = 32;
+    const int t = threadIdx.x;
+    const int c = t % nc, g = t / nc;
+    if (g < G) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      const double* p = w.part + c0 + c;
+      unsigned b = g;
+      for (; b + 3 * G < nblk; b += 4 * G) {
+        a0 += __ldcg(p + static_cast<int64_t>(b) * rowlen);
+        a1 += __ldcg(p + static_cast<int64_t>(b + G) * rowlen);
+        a2 += __ldcg(p + static_cast<int64_t>(b + 2 * G) * rowlen);
+        a3 += __ldcg(p + static_cast<int64_t>(b + 3 * G) * rowlen);
+      }
+      for (; b < nblk; b += G) a0 += __ldcg(p + static_cast<int64_t>(b) * rowlen);
+      scratch[g * nc + c] = (a0 + a1) + (a2 + a3);
     }
-    if (b < nblk) a0 += __ldcg(w.part + static_cast<int64_t>(b) * rowlen + i);
-    a0 = warp_sum(a0 + a1);
-    if (lane == 0) tot[i] = a0;
+    __syncthreads();
+    if (t < nc) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int u = 0;
+      for (; u + 3 < G; u += 4) {
+        a0 += scratch[u * nc + t];
+        a1 += scratch[(u + 1) * nc + t];
+        a2 += scratch[(u + 2) * nc + t];
+        a3 += scratch[(u + 3) * nc + t];
+      }
+      for (; u < G; ++u) a0 += scratch[u * nc + t];
+      tot[c0 + t] = (a0 + a1) + (a2 + a3);
+    }
+    __syncthreads();
   }
-  __syncthreads();
   return true;
 }
 
@@ -207,8 +293,12 @@ __device__ inline void gs_finish_start(const Work& w, const StepOpts& o, const d
 // the Gram matrix G = Q^T Q of the stored sketched basis so that a single
 // pass over Q suffices: h1 = Q^T s, h2 = Q^T (s - Q h1) = h1 - G h1,
 // h = h1 + h2 and h_{j+1,j}^2 = ||s - Q h||^2 = s.s - 2 h.h1 + h.(G h), all
-// in FP64.  Then the Hessenberg column, breakdown test, Givens update
-// (Eq. 11S) and stop rule.  sh: shared scratch of >= 5 (kMaxK + 2) doubles.
+// in FP64.  Writes the Hessenberg column, h_{j+1,j} (0 on breakdown), the
+// breakdown and non-finite flags, and advances j.  The Givens update of
+// Eq. 11S, rho_j and the stop rule follow in givens_step, off this
+// kernel's critical path.  For J < 32 one warp does the arithmetic with
+// the Gram matrix in shared memory (lane i owns row i); larger J use one
+// warp per row.  sh: shared scratch of >= (kMaxK + 6) + 32 * 33 doubles.
 __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const double* tot, double* sh) {
   Ctl* ctl = w.ctl;
   const int J = ctl->j;
@@ -216,85 +306,136 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
   const double* h1 = tot;
   const double s2 = tot[J + 1];
   const double* grow = tot + J + 2;
-  double* col = sh;                    // h, then the rotated column
-  double* cs = col + (kMaxK + 2);
-  double* sn = cs + (kMaxK + 2);
-  double* red = sn + (kMaxK + 2);      // scalars, then one value per row
+  double* col = sh;                    // h
+  double* red = col + (kMaxK + 2);     // a = h.h1, b = h.(G h)
   double* G = w.G;
-  // new row/column of G
-  for (int i = threadIdx.x; i <= J; i += blockDim.x) {
-    G[i + static_cast<int64_t>(ld) * J] = grow[i];
-    G[J + static_cast<int64_t>(ld) * i] = grow[i];
-  }
-  for (int i = threadIdx.x; i < J; i += blockDim.x) {
-    cs[i] = w.cs[i];
-    sn[i] = w.sn[i];
-  }
-  __syncthreads();
-  // h = h1 + (h1 - G h1): one warp per row, lanes across the columns
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i <= J; i += nw) {
-    double gh = 0.0;
-    for (int k = lane; k <= J; k += 32) gh += G[i + static_cast<int64_t>(ld) * k] * h1[k];
-    gh = warp_sum(gh);
-    if (lane == 0) col[i] = 2.0 * h1[i] - gh;
-  }
-  __syncthreads();
-  // h.h1 and h.(G h)
-  double* hgh_row = red + 32;          // (G h)_i * h_i per row
-  for (int i = warp; i <= J; i += nw) {
-    double gh = 0.0;
-    for (int k = lane; k <= J; k += 32) gh += G[i + static_cast<int64_t>(ld) * k] * col[k];
-    gh = warp_sum(gh);
-    if (lane == 0) hgh_row[i] = gh * col[i];
-  }
-  __syncthreads();
-  double a = 0.0, b = 0.0;
-  if (warp == 0) {
-    for (int i = lane; i <= J; i += 32) {
-      a += col[i] * h1[i];
-      b += hgh_row[i];
+  if (J < 32) {
+    double* Gs = red + 4;              // [32][33]
+    for (int e = threadIdx.x; e < (J + 1) * (J + 1); e += blockDim.x) {
+      const int i = e % (J + 1), k = e / (J + 1);
+      Gs[i * 33 + k] = (i == J) ? grow[k] : (k == J ? grow[i] : G[i + static_cast<int64_t>(ld) * k]);
     }
-    a = warp_sum(a);
-    b = warp_sum(b);
-    if (lane == 0) {
-      red[0] = a;
-      red[1] = b;
+    for (int i = threadIdx.x; i <= J; i += blockDim.x) {   // new row/column, for later steps
+      G[i + static_cast<int64_t>(ld) * J] = grow[i];
+      G[J + static_cast<int64_t>(ld) * i] = grow[i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double h1i = 0.0, hi = 0.0, ghi = 0.0;
+      if (lane <= J) {
+        h1i = h1[lane];
+        double u = 0.0;
+        for (int k = 0; k <= J; ++k) u = fma(Gs[lane * 33 + k], h1[k], u);
+        hi = 2.0 * h1i - u;
+        col[lane] = hi;
+      }
+      __syncwarp();
+      if (lane <= J) {
+        double g = 0.0;
+        for (int k = 0; k <= J; ++k) g = fma(Gs[lane * 33 + k], col[k], g);
+        ghi = g;
+      }
+      double a = hi * h1i, b = hi * ghi;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
+      }
+      if (lane == 0) {
+        red[0] = a;
+        red[1] = b;
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i <= J; i += blockDim.x) {
+      G[i + static_cast<int64_t>(ld) * J] = grow[i];
+      G[J + static_cast<int64_t>(ld) * i] = grow[i];
+    }
+    __syncthreads();
+    // h = 2 h1 - G h1: one warp per row, lanes across the columns
+    for (int i = warp; i <= J; i += nw) {
+      double gh = 0.0;
+      for (int k = lane; k <= J; k += 32) gh += G[i + static_cast<int64_t>(ld) * k] * h1[k];
+      gh = warp_sum(gh);
+      if (lane == 0) col[i] = 2.0 * h1[i] - gh;
+    }
+    __syncthreads();
+    double* hgh_row = red + 4;         // (G h)_i * h_i per row
+    for (int i = warp; i <= J; i += nw) {
+      double gh = 0.0;
+      for (int k = lane; k <= J; k += 32) gh += G[i + static_cast<int64_t>(ld) * k] * col[k];
+      gh = warp_sum(gh);
+      if (lane == 0) hgh_row[i] = gh * col[i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double a = 0.0, b = 0.0;
+      for (int i = lane; i <= J; i += 32) {
+        a += col[i] * h1[i];
+        b += hgh_row[i];
+      }
+      a = warp_sum(a);
+      b = warp_sum(b);
+      if (lane == 0) {
+        red[0] = a;
+        red[1] = b;
+      }
     }
   }
   __syncthreads();
-  const double hh1 = red[0];
-  const double hgh = red[1];
   double* Hc = w.H + static_cast<int64_t>(ld) * J;
   for (int i = threadIdx.x; i <= J; i += blockDim.x) Hc[i] = col[i];
   for (int i = J + 2 + threadIdx.x; i < ld; i += blockDim.x) Hc[i] = 0.0;
-  __syncthreads();
   if (threadIdx.x == 0) {
-    const double tol = o.desc_tol ? *o.desc_tol : o.tol;
     const double bd_tol = o.desc_bd_tol ? *o.desc_bd_tol : o.bd_tol;
+    const double hh1 = red[0], hgh = red[1];
     bool finite = isfinite(s2) && isfinite(hh1) && isfinite(hgh);
     for (int i = 0; i <= J; ++i) finite = finite && isfinite(col[i]);
     const double hn2 = s2 - 2.0 * hh1 + hgh;
     const double hn = sqrt(hn2 > 0.0 ? hn2 : 0.0);
     const bool breakdown = finite && (hn <= bd_tol * sqrt(s2));
-    col[J + 1] = breakdown ? 0.0 : hn;
-    Hc[J + 1] = col[J + 1];
+    Hc[J + 1] = breakdown ? 0.0 : hn;
+    ctl->pre2 = s2;
+    ctl->hnext = hn;
+    ctl->j = J + 1;
+    if (!finite) ctl->status = RTG_ERR_NONFINITE;
+    if (breakdown) ctl->breakdown = 1;
+    ctl->skip_update = (!finite || breakdown) ? 1 : 0;
+    ctl->givens = 1;
+  }
+}
+
+// Givens update of Eq. 11S for the Hessenberg column the last finish wrote
+// (column J = j - 1), rho_j = |g_{J+1}| / beta_0, the stop rule and the
+// condition of the device-side loop, which never runs more than m + 1
+// bodies.  One thread; runs beside the basis update, which does not depend
+// on it.
+__device__ inline void givens_step(const Work& w, const StepOpts& o) {
+  Ctl* ctl = w.ctl;
+  if (ctl->givens) {
+    ctl->givens = 0;
+    const int J = ctl->j - 1;
+    const int ld = w.m + 1;
+    const double tol = o.desc_tol ? *o.desc_tol : o.tol;
+    const double* Hc = w.H + static_cast<int64_t>(ld) * J;
+    double* Rc = w.R + static_cast<int64_t>(ld) * J;
     // rotations 0..J-1 on the new column, then the new rotation
-    double x = col[0];
+    double x = Hc[0];
     for (int i = 0; i < J; ++i) {
-      const double y = col[i + 1];
-      col[i] = cs[i] * x + sn[i] * y;
-      x = -sn[i] * x + cs[i] * y;
+      const double y = Hc[i + 1], c = w.cs[i], sv = w.sn[i];
+      Rc[i] = c * x + sv * y;
+      x = -sv * x + c * y;
     }
-    const double y = col[J + 1];
+    const double y = Hc[J + 1];
     const double den = hypot(x, y);
     double c = 1.0, sv = 0.0;
     if (den != 0.0) {
       c = x / den;
       sv = y / den;
     }
-    col[J] = den;
-    col[J + 1] = 0.0;
+    Rc[J] = den;
+    Rc[J + 1] = 0.0;
     w.cs[J] = c;
     w.sn[J] = sv;
     const double gJ = w.g[J];
@@ -302,24 +443,22 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
     w.g[J] = c * gJ;
     const double rho = fabs(sv * gJ) / ctl->beta0;
     ctl->rho = rho;
-    ctl->pre2 = s2;
     w.rho_hist[ctl->iters_total] = rho;
     ctl->iters_total += 1;
-    ctl->hnext = hn;
-    ctl->j = J + 1;
-    if (!finite) ctl->status = RTG_ERR_NONFINITE;
-    if (breakdown) ctl->breakdown = 1;
+    const bool finite = ctl->status != RTG_ERR_NONFINITE && isfinite(rho);
+    if (!finite && ctl->status == 0) ctl->status = RTG_ERR_NONFINITE;
+    const bool breakdown = ctl->breakdown != 0;
     const bool conv = finite && rho <= tol;
     if (conv || breakdown) ctl->converged = 1;
     // a nonzero status (a bounded wait that gave up upstream) ends the solve
-    const bool stop = !finite || breakdown || conv || (J + 1 >= w.m) || ctl->status != 0;
-    ctl->stop = stop ? 1 : 0;
-    ctl->skip_update = (!finite || breakdown || (o.solve_mode && stop)) ? 1 : 0;
-    set_cond(o, !stop);
+    if (!finite || breakdown || conv || J + 1 >= w.m || ctl->status != 0) ctl->stop = 1;
   }
-  __syncthreads();
-  double* Rc = w.R + static_cast<int64_t>(ld) * J;
-  for (int i = threadIdx.x; i <= J + 1; i += blockDim.x) Rc[i] = col[i];
+  const int loops = ++ctl->loops;
+  if (loops > w.m) {
+    ctl->stop = 1;
+    if (o.use_cond && loops > w.m + 1 && ctl->status == 0) ctl->status = RTG_ERR_TIMEOUT;
+  }
+  set_cond(o, !ctl->stop);
 }
 
 }  // namespace rtg

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(Work w, int pass, StepOp
     }
   }
   block_partials<T, GS_ITEMS>(w, sv, ix, cnt, J, red);
-  if (!last_block_combine(w, gs_ncols(J), tot, &am_last)) return;
+  if (!last_block_combine(w, gs_ncols(J), tot, &am_last, &red[0][0])) return;
   if (pass == 0) {
     if (threadIdx.x == 0) gs_finish_start(w, o, tot);
   } else {
@@ -108,17 +108,14 @@ __global__ void k_start_scale(Work w, PtrRef srcr) {
 
 // V_{j} = (W - sum_{i<j} h_i V_i) / h_{j,j-1};  Q_{j} = (S - sum_{i<j} h2_i Q_i) / h_{j,j-1}
 // FP32 tensors move as float4; four basis vectors are in flight per iteration.
+// The last block of the grid runs givens_step (Eq. 11S, rho_j, the stop
+// rule) beside the update; the others share the update.
 template <typename T>
 __global__ void k_update(Work w, StepOpts o) {
   Ctl* ctl = w.ctl;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    // hard cap on the device-controlled loop: never more than m+1 bodies
-    const int loops = ++ctl->loops;
-    if (loops > w.m) {
-      ctl->stop = 1;
-      if (o.use_cond && loops > w.m + 1 && ctl->status == 0) ctl->status = RTG_ERR_TIMEOUT;
-      set_cond(o, 0);
-    }
+  if (blockIdx.x == gridDim.x - 1) {
+    if (threadIdx.x == 0) givens_step(w, o);
+    return;
   }
   if (ctl->skip_update || ctl->j == 0) return;
   const int jj = ctl->j;
@@ -142,7 +139,7 @@ __global__ void k_update(Work w, StepOpts o) {
   const T* W = static_cast<const T*>(w.W);
   const T* S = static_cast<const T*>(w.S);
   const int64_t n = w.n, d = w.d;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (sizeof(T) == 4 && (n % 4) == 0) {
     const int64_t n4 = n / 4;
@@ -226,6 +223,7 @@ __global__ void k_reset(Ctl* ctl, unsigned* counter, int new_cycle) {
   ctl->pre2 = 0.0;
   ctl->hnext = 0.0;
   ctl->loops = 0;
+  ctl->givens = 0;
   if (new_cycle) {
     ctl->cycle += 1;
   } else {
@@ -272,8 +270,9 @@ cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s) {
 
 
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s) {
-  if (w.dtype == RTG_F64) k_update<double><<<ew_grid(w.n), 256, 0, s>>>(w, o);
-  else k_update<float><<<ew_grid(w.n / 4 + 1), 256, 0, s>>>(w, o);
+  // one block more than the update needs: it runs the Givens step
+  if (w.dtype == RTG_F64) k_update<double><<<ew_grid(w.n) + 1, 256, 0, s>>>(w, o);
+  else k_update<float><<<ew_grid(w.n / 4 + 1) + 1, 256, 0, s>>>(w, o);
   return cudaGetLastError();
 }
 

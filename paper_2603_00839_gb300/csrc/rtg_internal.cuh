@@ -57,6 +57,7 @@ struct Ctl {
   int iters_total;  // steps over all cycles
   int cycle;
   int loops;        // executions of the step body since the reset (hard cap m+1)
+  int givens;       // a finished Hessenberg column awaits its Givens update
   double beta;      // ||R_0||_Theta of this cycle
   double beta0;     // of the first cycle (scale of rho)
   double rho;       // last rho_j
