@@ -57,7 +57,8 @@ typedef enum rtg_status {
 typedef enum rtg_dtype {
     RTG_F64 = 0,               /* double data, double arithmetic */
     RTG_F32 = 1,               /* float data, float arithmetic with FP64 small solves */
-    RTG_BF16 = 2               /* reserved */
+    RTG_BF16 = 2               /* bfloat16 storage, FP32 arithmetic (apply, sketch; the
+                                  solve's basis with RTG_FLAG_BF16_BASIS) */
 } rtg_dtype;
 
 typedef enum rtg_factor_kind {
@@ -110,6 +111,15 @@ typedef struct rtg_opts {
 #define RTG_FLAG_TRUE_RESIDUAL 2     /* also compute ||C - Phi(X)||_F / ||C||_F into info */
 #define RTG_FLAG_PHASE_TIMES   4     /* time every kernel group with CUDA events into
                                         info->phase_ms (implies RTG_FLAG_NO_GRAPH); see below */
+#define RTG_FLAG_BF16_BASIS    8     /* precision form (dtype RTG_F32 only): the basis V_i and
+                                        W = Phi(V_j) are stored in BF16, half the bytes of the
+                                        basis update; every sum is accumulated in FP32, the
+                                        sketches S(W) and Q in FP32, the Gram-Schmidt
+                                        coefficients, Givens and Tikhonov in FP64.  Needs the
+                                        spatio-temporal operator form (banded modes 1-2 of
+                                        radius <= 9, a mode-3 mix of 1 or 3 channels, a mode-4
+                                        band of radius <= 2), dims[0] % 8 == 0, mode 1
+                                        sketched, and C / X0 16-byte aligned. */
 
 /* Kernel groups of one solve, the index of rtg_info.phase_ms / phase_launches.
  *   SETUP     workspace reset and the sketch signs / Theta fragments (Section 2, Theta_k)
@@ -168,10 +178,15 @@ int32_t rtg_version(void);
  * Y = Phi(X): the Einstein-product operator of Section 1 with separable
  * factors (Eq. 56-57, zero boundary conditions).  Modes without a factor
  * are untouched.  Several factors on one mode compose (right factors after
- * left ones).  X and Y: device arrays of prod(dims) elements of `dtype`
- * (F64 or F32); Y must not overlap X.
- * Errors: INVALID_ARG (shape, factor mode/size/radius, NULL), UNSUPPORTED
- * (BF16), CUDA.
+ * left ones).  X and Y: device arrays of prod(dims) elements of `dtype`;
+ * Y must not overlap X.  F64 / F32: any factors.  BF16: X and Y in BF16,
+ * FP32 arithmetic, one rounding of each output; needs the spatio-temporal
+ * form (banded modes 1-2 of radius <= 9, a mode-3 mix of 1 or 3 channels,
+ * a mode-4 band of radius <= 2), dims[0] % 8 == 0 and X 16-byte aligned.
+ * The video operator (order 4 with a mode-4 band) also runs as one pass
+ * in F32, with X 16-byte aligned.
+ * Errors: INVALID_ARG (shape, factor mode/size/radius, NULL, alignment),
+ * UNSUPPORTED (BF16 with another operator form), CUDA.
  */
 rtg_status rtg_operator_apply(rtg_handle handle,
                               const rtg_factor* A_factors, int32_t nA,
@@ -187,8 +202,11 @@ rtg_status rtg_operator_apply(rtg_handle handle,
  * increasing mode order, each Theta_k row-major, sign e = bit e%64 of
  * output word e/64 (set bit = -1), output word w from counter (w/4+1,0,0,0).
  * A mode with s_k >= I_k is not sketched (Theta_k = I, s'_k = I_k).
- * SX: device array of prod(s'_k) elements of `dtype`, column-major.
- * Errors: INVALID_ARG (s_k < 1, shape), UNSUPPORTED (BF16), CUDA.
+ * SX: device array of prod(s'_k) elements of `dtype`, column-major; for
+ * dtype BF16 (X in BF16, exact in one tensor-core limb) SX is FP32, and
+ * mode 1 must be sketched.
+ * Errors: INVALID_ARG (s_k < 1, shape), UNSUPPORTED (BF16 with mode 1 not
+ * sketched), CUDA.
  */
 rtg_status rtg_sketch(rtg_handle handle, rtg_shape shape, rtg_dtype dtype,
                       const int64_t* sketch_dims, uint64_t seed, uint64_t problem_id,

@@ -23,7 +23,7 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_ALLOC, ERR_TIMEOUT, ERR_NONF
 F64, F32, BF16 = 0, 1, 2
 # rtg_factor_kind
 FACTOR_IDENTITY, FACTOR_BANDED_TOEPLITZ, FACTOR_DENSE = 0, 1, 2
-FLAG_NO_GRAPH, FLAG_TRUE_RESIDUAL, FLAG_PHASE_TIMES = 1, 2, 4
+FLAG_NO_GRAPH, FLAG_TRUE_RESIDUAL, FLAG_PHASE_TIMES, FLAG_BF16_BASIS = 1, 2, 4, 8
 PHASES = ("setup", "init", "apply", "sketch", "gs", "update", "tikhonov", "assemble")
 PHASE_COUNT = len(PHASES)
 

@@ -56,6 +56,8 @@ def _dtype_code(t) -> int:
         return L.F64
     if t.dtype == torch.float32:
         return L.F32
+    if t.dtype == torch.bfloat16:
+        return L.BF16
     raise TypeError(f"unsupported dtype {t.dtype}")
 
 
@@ -204,8 +206,8 @@ class Handle:
         dims = tuple(X.shape)
         _check_tensor(X, dims, "X")
         sd = tuple(int(min(s, d)) for s, d in zip(sketch_dims, dims))
-        if SX is None:
-            SX = empty(sd, X.dtype, X.device)
+        if SX is None:   # a BF16 input gives an FP32 sketch
+            SX = empty(sd, _torch().float32 if X.dtype == _torch().bfloat16 else X.dtype, X.device)
         _check_tensor(SX, sd, "SX")
         sk = (C.c_int64 * len(dims))(*[int(s) for s in sketch_dims])
         L.check(self.lib.rtg_sketch(self._h, _shape(dims), _dtype_code(X), sk, C.c_uint64(seed),
@@ -218,22 +220,24 @@ class Handle:
                     A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (),
                     X0=None, X=None, tol: float = 0.0, mu_grid=None, max_restarts: int = 0,
                     breakdown_tol: float = 0.0, use_graph: bool = True, phase_times: bool = False,
-                    slot: int = 0, stream=None):
+                    slot: int = 0, bf16_basis: bool = False, stream=None):
         """RTG-GMRES; C_obs, X0, X may be device tensors or host numpy arrays (Fortran order).
 
         phase_times=True launches directly and times each kernel group with
-        CUDA events (result.phase_ms / result.phase_launches).  Returns (X, SolveResult)."""
+        CUDA events (result.phase_ms / result.phase_launches).  bf16_basis=True
+        stores the Krylov basis in BF16 (the precision form).  Returns (X, SolveResult)."""
         pend = self.gmres_submit(C_obs, m, sketch_dims, seed, lam, A_factors, B_factors, X0=X0, X=X,
                                  tol=tol, mu_grid=mu_grid, max_restarts=max_restarts,
                                  breakdown_tol=breakdown_tol, use_graph=use_graph,
-                                 phase_times=phase_times, slot=slot, stream=stream)
+                                 phase_times=phase_times, slot=slot, bf16_basis=bf16_basis,
+                                 stream=stream)
         return self.gmres_wait(pend)
 
     def gmres_submit(self, C_obs, m: int, sketch_dims: Sequence[int], seed: int, lam: float,
                      A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (),
                      X0=None, X=None, tol: float = 0.0, mu_grid=None, max_restarts: int = 0,
                      breakdown_tol: float = 0.0, use_graph: bool = True, phase_times: bool = False,
-                     slot: int = 0, stream=None) -> "PendingSolve":
+                     slot: int = 0, bf16_basis: bool = False, stream=None) -> "PendingSolve":
         """Queue a solve on `stream` without waiting (rtg_gmres_submit).  Solves
         in flight at once on different streams need different workspace slots;
         gmres_wait(pending) returns (X, SolveResult)."""
@@ -262,7 +266,8 @@ class Handle:
             opts.n_mu = len(grid)
         opts.max_restarts = int(max_restarts)
         opts.breakdown_tol = float(breakdown_tol)
-        opts.flags = (0 if use_graph else L.FLAG_NO_GRAPH) | (L.FLAG_PHASE_TIMES if phase_times else 0)
+        opts.flags = ((0 if use_graph else L.FLAG_NO_GRAPH) | (L.FLAG_PHASE_TIMES if phase_times else 0)
+                      | (L.FLAG_BF16_BASIS if bf16_basis else 0))
         opts.slot = int(slot)
         L.check(self.lib.rtg_gmres_submit(self._h, a, na, b, nb, _shape(dims), dt, _ptr(C_obs), int(m),
                                           sk, C.c_uint64(seed), float(lam), _ptr(X0), _ptr(X),

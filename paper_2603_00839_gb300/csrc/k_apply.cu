@@ -9,6 +9,8 @@
 // along mode 2 into registers; the mode-3 matrix mixes the channels in
 // registers before the single store.  Unfused path: one kernel per mode
 // product, ping-ponging through scratch tensors.
+#include <cuda_bf16.h>
+
 #include "rtg_internal.cuh"
 
 namespace rtg {
@@ -259,6 +261,230 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- spatio-temporal path
+// One HBM pass for the video operator (order 4: blur on modes 1-2, channel
+// mix on mode 3, banded temporal filter of radius <= 2 on mode 4) and for
+// any image operator whose tensors are stored in BF16.  A CTA owns a
+// 64 x 16 tile of modes 1-2, all NC channels of one channel group and a
+// chunk of output frames.  It walks the input frames in order: each frame's
+// halo tile is loaded into registers (16-byte loads, BF16 or FP32) while
+// the previous frame is being filtered, converted to FP32 in shared memory,
+// filtered along modes 1 and 2 as in the image kernel, and added into a
+// ring of five partial output frames held in registers; the oldest ring
+// entry is complete after each input frame, is mixed across the channels
+// and stored.  Arithmetic is FP32 in every storage format.
+constexpr int STX = 64, STY = 16, ST_THREADS = 256, ST_RING = 5, ST_SEG = 8, ST_VSEG = 4;
+
+struct StArgs {
+  int64_t I1, I2, I3, nF;   // mode sizes; nF = 1 for order 3
+  int F;                    // output frames per CTA
+  int nchunk;               // frame chunks
+  int rt;                   // temporal radius (0..2)
+  float t1[kMaxTaps], t2[kMaxTaps];   // spatial taps zero-padded to the compiled radius
+  float t4[ST_RING];                  // temporal taps zero-padded to radius 2: t4[2 + s]
+  float M[kMaxMix * kMaxMix];         // channel mix M[p + nc * c]
+  float alpha, beta;
+};
+
+template <typename TI>
+struct StVec {   // elements of TI in one 16-byte load
+  static constexpr int V = 16 / static_cast<int>(sizeof(TI));
+};
+
+template <int RR, typename TI>
+struct StGeom {
+  static constexpr int V = StVec<TI>::V;
+  static constexpr int RA = ((RR + V - 1) / V) * V;   // halo widened to whole 16-byte loads
+  static constexpr int OFF = RA - RR;
+  static constexpr int Wd = STX + 2 * RA;
+  static constexpr int Ht = STY + 2 * RR;
+};
+
+__device__ __forceinline__ void st_to_float(const uint4& q, float* dst, float) {
+  dst[0] = __uint_as_float(q.x);
+  dst[1] = __uint_as_float(q.y);
+  dst[2] = __uint_as_float(q.z);
+  dst[3] = __uint_as_float(q.w);
+}
+__device__ __forceinline__ void st_to_float(const uint4& q, float* dst, __nv_bfloat16) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    dst[2 * i] = __uint_as_float(w[i] << 16);
+    dst[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+__device__ __forceinline__ void st_store(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+template <typename TI, typename TO, int NC, int RR>
+__global__ void __launch_bounds__(ST_THREADS, 2)
+k_apply_st(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, StArgs a) {
+  if (stop != nullptr && *stop) return;
+  const TI* __restrict__ X = Xr.get<const TI>();
+  TO* __restrict__ Y = Yr.get<TO>();
+  const float* __restrict__ Z = Zr.get<const float>();
+  using G = StGeom<RR, TI>;
+  constexpr int V = G::V, Wd = G::Wd, Ht = G::Ht, RA = G::RA, OFF = G::OFF;
+  constexpr int NT = 2 * RR + 1;
+  constexpr int NCH = NC * Ht * (Wd / V);                    // 16-byte loads per frame
+  constexpr int NPT = (NCH + ST_THREADS - 1) / ST_THREADS;   // per thread
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* in_s = reinterpret_cast<float*>(smem_raw);   // NC x Ht x Wd
+  float* tmp = in_s + NC * Ht * Wd;                   // Ht x STX
+  const int x0 = blockIdx.x * STX, y0 = blockIdx.y * STY;
+  const int I1 = static_cast<int>(a.I1), I2 = static_cast<int>(a.I2);
+  const int64_t plane = a.I1 * a.I2;
+  const int group = static_cast<int>(blockIdx.z / a.nchunk);
+  const int chunk = static_cast<int>(blockIdx.z % a.nchunk);
+  const int64_t f0 = static_cast<int64_t>(chunk) * a.F;
+  const int64_t f1 = (f0 + a.F < a.nF) ? f0 + a.F : a.nF;
+  const int rt = a.rt;
+  const int vx = threadIdx.x & (STX - 1);
+  const int vy = (threadIdx.x / STX) * ST_VSEG;
+  uint4 pre[NPT];
+  auto load_frame = [&](int64_t u) {
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+      pre[q] = make_uint4(0u, 0u, 0u, 0u);
+      const int idx = threadIdx.x + q * ST_THREADS;
+      if (idx >= NCH) continue;
+      const int row = idx / (Wd / V), f = idx - row * (Wd / V);
+      const int c = row / Ht, yy = row - c * Ht;
+      const int gy = y0 - RR + yy, gx = x0 - RA + V * f;
+      if (gy < 0 || gy >= I2 || gx < 0 || gx >= I1) continue;
+      const int64_t pl = (static_cast<int64_t>(group) * NC + c) + a.I3 * u;
+      pre[q] = __ldg(reinterpret_cast<const uint4*>(X + pl * plane + static_cast<int64_t>(gy) * I1 + gx));
+    }
+  };
+  auto store_frame = [&]() {
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+      const int idx = threadIdx.x + q * ST_THREADS;
+      if (idx >= NCH) continue;
+      const int row = idx / (Wd / V), f = idx - row * (Wd / V);
+      float v[V];
+      st_to_float(pre[q], v, TI());
+      float4* d = reinterpret_cast<float4*>(in_s + row * Wd + V * f);
+#pragma unroll
+      for (int h = 0; h < V / 4; ++h) d[h] = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+    }
+  };
+  float ring[ST_RING][NC][ST_VSEG];
+#pragma unroll
+  for (int k = 0; k < ST_RING; ++k)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int o = 0; o < ST_VSEG; ++o) ring[k][c][o] = 0.f;
+  const int64_t u0 = f0 - rt, u1 = f1 + rt;
+  {   // the first frame inside the tensor; each frame then prefetches the next
+    const int64_t uf = u0 > 0 ? u0 : 0;
+    if (uf < u1 && uf < a.nF) load_frame(uf);
+  }
+  for (int64_t u = u0; u < u1; ++u) {
+    const bool have = u >= 0 && u < a.nF;
+    float P[NC][ST_VSEG];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int o = 0; o < ST_VSEG; ++o) P[c][o] = 0.f;
+    if (have) {
+      __syncthreads();              // the previous frame's filters are done with in_s
+      store_frame();
+      __syncthreads();
+      if (u + 1 < u1 && u + 1 < a.nF) load_frame(u + 1);   // in flight during the filters
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float* ins = in_s + c * Ht * Wd;
+        for (int task = threadIdx.x; task < Ht * (STX / ST_SEG); task += ST_THREADS) {
+          const int yy = task / (STX / ST_SEG);
+          const int xs = (task - yy * (STX / ST_SEG)) * ST_SEG;
+          constexpr int A0 = OFF & ~3, SH = OFF & 3;
+          constexpr int NV = (SH + ST_SEG + 2 * RR + 3) / 4;
+          const float4* rp = reinterpret_cast<const float4*>(ins + yy * Wd + xs + A0);
+          float buf[NV * 4];
+#pragma unroll
+          for (int v4 = 0; v4 < NV; ++v4) {
+            const float4 q = rp[v4];
+            buf[4 * v4] = q.x;
+            buf[4 * v4 + 1] = q.y;
+            buf[4 * v4 + 2] = q.z;
+            buf[4 * v4 + 3] = q.w;
+          }
+#pragma unroll
+          for (int o = 0; o < ST_SEG; ++o) {
+            float sacc = 0.f;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) sacc = fmaf(a.t1[t], buf[SH + o + t], sacc);
+            tmp[yy * STX + xs + o] = sacc;
+          }
+        }
+        __syncthreads();
+        float win[ST_VSEG + 2 * RR];
+#pragma unroll
+        for (int w2 = 0; w2 < ST_VSEG + 2 * RR; ++w2) win[w2] = tmp[(vy + w2) * STX + vx];
+#pragma unroll
+        for (int o = 0; o < ST_VSEG; ++o) {
+          float sacc = 0.f;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) sacc = fmaf(a.t2[t], win[o + t], sacc);
+          P[c][o] = sacc;
+        }
+        if (c + 1 < NC) __syncthreads();
+      }
+    }
+    // ring[k] is output frame u - rt + k; frame u enters with tap t4[2 + rt - k]
+#pragma unroll
+    for (int k = 0; k < ST_RING; ++k) {
+      if (k > 2 * rt) break;
+      const float tk = a.t4[2 + rt - k];
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int o = 0; o < ST_VSEG; ++o) ring[k][c][o] = fmaf(tk, P[c][o], ring[k][c][o]);
+    }
+    const int64_t t = u - rt;
+    const int gx = x0 + vx;
+    if (t >= f0 && t < f1 && gx < I1) {
+#pragma unroll
+      for (int o = 0; o < ST_VSEG; ++o) {
+        const int gy = y0 + vy + o;
+        if (gy >= I2) break;
+#pragma unroll
+        for (int p = 0; p < NC; ++p) {
+          float v = 0.f;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v = fmaf(a.M[p + NC * c], ring[0][c][o], v);
+          const int64_t idx = ((static_cast<int64_t>(group) * NC + p) + a.I3 * t) * plane +
+                              static_cast<int64_t>(gy) * I1 + gx;
+          float out = a.alpha * v;
+          if (Z != nullptr) out = fmaf(a.beta, Z[idx], out);
+          st_store(Y + idx, out);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k + 1 < ST_RING; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int o = 0; o < ST_VSEG; ++o) ring[k][c][o] = ring[k + 1][c][o];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int o = 0; o < ST_VSEG; ++o) ring[ST_RING - 1][c][o] = 0.f;
+  }
+}
+
+// Spatial radius bucket of the spatio-temporal kernel (0 when none holds r).
+int st_bucket(int r) {
+  const int b[] = {3, 5, 7, 9};
+  for (int v : b)
+    if (r <= v) return v;
+  return 0;
+}
+
 // Smallest compiled radius bucket that holds r (0 when none does).
 static int reg_bucket(int r) {
   const int b[] = {3, 5, 7, 9, 12, 16};
@@ -347,8 +573,15 @@ int64_t apply_scratch_elems(const OpPlan& op) {
   return n;
 }
 
-int apply_launches(const OpPlan& op, bool combine) {
-  if (op.fused || op.npass == 0) return 1;
+bool apply_uses_st(const OpPlan& op, int dtype, int tin, int tout) {
+  if (tin < 0) tin = dtype;
+  if (tout < 0) tout = dtype;
+  const bool want = tin == RTG_BF16 || tout == RTG_BF16 || (dtype == RTG_F32 && op.st && op.r4 > 0);
+  return want && st_supported(op, tin);
+}
+
+int apply_launches(const OpPlan& op, bool combine, int dtype, int tin, int tout) {
+  if (op.fused || op.npass == 0 || apply_uses_st(op, dtype, tin, tout)) return 1;
   return op.npass + (combine ? 1 : 0);
 }
 
@@ -456,9 +689,83 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
   return cudaGetLastError();
 }
 
+// Frame chunking of the spatio-temporal kernel: about two CTAs per SM.
+static void st_chunks(int64_t tiles, int64_t nF, int* F, int* nchunk) {
+  int64_t want = (304 + tiles - 1) / tiles;
+  if (want < 1) want = 1;
+  if (want > nF) want = nF;
+  int64_t f = (nF + want - 1) / want;
+  *F = static_cast<int>(f);
+  *nchunk = static_cast<int>((nF + f - 1) / f);
+}
+
+bool st_supported(const OpPlan& op, int tin) {
+  if (!op.st) return false;
+  const int64_t V = (tin == RTG_BF16) ? 8 : 4;
+  return op.dims[0] % V == 0 && st_bucket(op.r1 > op.r2 ? op.r1 : op.r2) > 0;
+}
+
+template <typename TI, typename TO>
+static cudaError_t apply_st_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, double beta,
+                              PtrRef Z, const int* stop, cudaStream_t s) {
+  StArgs a{};
+  a.I1 = op.dims[0];
+  a.I2 = op.order > 1 ? op.dims[1] : 1;
+  a.I3 = op.order > 2 ? op.dims[2] : 1;
+  a.nF = op.order > 3 ? op.dims[3] : 1;
+  const int nc = op.st_nc;
+  const int rr = st_bucket(op.r1 > op.r2 ? op.r1 : op.r2);
+  for (int t = 0; t <= 2 * rr; ++t) {
+    const int u1 = t - (rr - op.r1), u2 = t - (rr - op.r2);
+    a.t1[t] = (u1 >= 0 && u1 <= 2 * op.r1) ? static_cast<float>(op.t1[u1]) : 0.f;
+    a.t2[t] = (u2 >= 0 && u2 <= 2 * op.r2) ? static_cast<float>(op.t2[u2]) : 0.f;
+  }
+  a.rt = op.r4;
+  for (int k = 0; k < ST_RING; ++k) {
+    const int sft = k - 2;
+    a.t4[k] = (sft >= -op.r4 && sft <= op.r4) ? static_cast<float>(op.t4[sft + op.r4]) : 0.f;
+  }
+  for (int i = 0; i < nc * nc; ++i) a.M[i] = static_cast<float>(op.st_M[i]);
+  a.alpha = static_cast<float>(alpha);
+  a.beta = has_ptr(Z) ? static_cast<float>(beta) : 0.f;
+  const int64_t gx = (a.I1 + STX - 1) / STX, gy = (a.I2 + STY - 1) / STY, groups = a.I3 / nc;
+  st_chunks(gx * gy * groups, a.nF, &a.F, &a.nchunk);
+  dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy), static_cast<unsigned>(groups * a.nchunk));
+#define RTG_ST_CASE(NC, RR)                                                                         \
+  if (nc == NC && rr == RR) {                                                                       \
+    using Gm = StGeom<RR, TI>;                                                                      \
+    const size_t smem = static_cast<size_t>(NC * Gm::Ht * Gm::Wd + Gm::Ht * STX) * sizeof(float);   \
+    cudaError_t e = cudaFuncSetAttribute(k_apply_st<TI, TO, NC, RR>,                                \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                         static_cast<int>(smem));                                  \
+    if (e != cudaSuccess) return e;                                                                 \
+    k_apply_st<TI, TO, NC, RR><<<grid, ST_THREADS, smem, s>>>(X, Y, Z, stop, a);                    \
+    return cudaGetLastError();                                                                      \
+  }
+  RTG_ST_CASE(1, 3) RTG_ST_CASE(1, 5) RTG_ST_CASE(1, 7) RTG_ST_CASE(1, 9)
+  RTG_ST_CASE(3, 3) RTG_ST_CASE(3, 5) RTG_ST_CASE(3, 7) RTG_ST_CASE(3, 9)
+#undef RTG_ST_CASE
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_apply(const OpPlan& op, int dtype, PtrRef X, PtrRef Y, double alpha,
                          double beta, PtrRef Z, void* tmp, void* tmp2, const int* stop,
-                         cudaStream_t s) {
+                         cudaStream_t s, int tin, int tout) {
+  if (tin < 0) tin = dtype;
+  if (tout < 0) tout = dtype;
+  if (tin == RTG_BF16 || tout == RTG_BF16 || (dtype == RTG_F32 && op.st && op.r4 > 0)) {
+    if (!apply_uses_st(op, dtype, tin, tout)) {
+      if (tin == RTG_BF16 || tout == RTG_BF16) return cudaErrorInvalidValue;
+    } else if (tin == RTG_BF16 && tout == RTG_BF16) {
+      return apply_st_t<__nv_bfloat16, __nv_bfloat16>(op, X, Y, alpha, beta, Z, stop, s);
+    } else if (tin == RTG_F32 && tout == RTG_BF16) {
+      return apply_st_t<float, __nv_bfloat16>(op, X, Y, alpha, beta, Z, stop, s);
+    } else if (tin == RTG_F32 && tout == RTG_F32) {
+      return apply_st_t<float, float>(op, X, Y, alpha, beta, Z, stop, s);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   if (dtype == RTG_F64)
     return apply_t<double>(op, X, Y, alpha, beta, Z, static_cast<double*>(tmp),
                            static_cast<double*>(tmp2), stop, s);

@@ -19,6 +19,8 @@
 // shuffles, FP64 across warps) into a row of `part`; the last CTA to finish
 // (atomic ticket) sums the rows in FP64 and runs the scalar epilogue.
 // Nothing waits on another CTA.
+#include <cuda_bf16.h>
+
 #include "gs_common.cuh"
 
 namespace rtg {
@@ -248,8 +250,140 @@ cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fused, cudaStream_t s) {
+// BF16 basis: V_0 = src / beta with src in FP32 (C) or BF16 (the V_0 slot).
+// Eight values per 16-byte load (n is a multiple of 8).
+__device__ __forceinline__ void bf8_to_f(const uint4& q, float* f) {
+  const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f[2 * i] = __uint_as_float(w4[i] << 16);
+    f[2 * i + 1] = __uint_as_float(w4[i] & 0xffff0000u);
+  }
+}
+__device__ __forceinline__ uint4 f_to_bf8(const float* f) {
+  uint32_t w4[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+    w4[i] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+  return make_uint4(w4[0], w4[1], w4[2], w4[3]);
+}
+
+template <bool SRC_BF16>
+__global__ void k_start_scale_bf16(Work w, PtrRef srcr) {
+  const Ctl* ctl = w.ctl;
+  if (ctl->stop) return;
+  const float fi = static_cast<float>(1.0 / ctl->beta);
+  uint4* V8 = static_cast<uint4*>(w.V);
+  const int64_t n8 = w.n / 8;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t o = t0; o < n8; o += stride) {
+    float f[8];
+    if (SRC_BF16) {
+      bf8_to_f(srcr.get<const uint4>()[o], f);
+    } else {
+      const float4* s4 = srcr.get<const float4>();
+      const float4 a = s4[2 * o], b = s4[2 * o + 1];
+      f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) f[i] *= fi;
+    V8[o] = f_to_bf8(f);
+  }
+  float* Q = static_cast<float*>(w.Q);
+  const float* S = static_cast<const float*>(w.S);
+  const float inv = static_cast<float>(1.0 / ctl->beta);
+  for (int64_t o = t0; o < w.d; o += stride) Q[o] = S[o] * inv;
+}
+
+// BF16 basis: V_{j+1} = (W - sum_i h_i V_i) / h_{j+1,j} with FP32 arithmetic;
+// Q_{j+1} as in k_update.  The last block runs givens_step.
+__global__ void k_update_bf16(Work w, StepOpts o) {
+  Ctl* ctl = w.ctl;
+  if (blockIdx.x == gridDim.x - 1) {
+    if (threadIdx.x == 0) givens_step(w, o);
+    return;
+  }
+  if (ctl->skip_update || ctl->j == 0) return;
+  const int jj = ctl->j;
+  if (jj > w.m) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctl->status = RTG_ERR_INVALID_ARG;
+      ctl->stop = 1;
+    }
+    return;
+  }
+  __shared__ float hs[kMaxK + 1];
+  __shared__ double hd[kMaxK + 1];
+  const int ld = w.m + 1;
+  for (int i = threadIdx.x; i < jj; i += blockDim.x) {
+    const double h = w.H[static_cast<int64_t>(ld) * (jj - 1) + i];
+    hs[i] = static_cast<float>(h);
+    hd[i] = h;
+  }
+  __syncthreads();
+  const uint4* W8 = static_cast<const uint4*>(w.W);
+  const uint4* V8 = static_cast<const uint4*>(w.V);
+  const int64_t n8 = w.n / 8;
+  uint4* out = static_cast<uint4*>(w.V) + static_cast<int64_t>(jj) * n8;
+  const float fi = static_cast<float>(1.0 / ctl->hnext);
+  const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t e = t0; e < n8; e += stride) {
+    float acc[8];
+    bf8_to_f(W8[e], acc);
+    int i = 0;
+    for (; i + 4 <= jj; i += 4) {
+      const uint4 q0 = V8[static_cast<int64_t>(i) * n8 + e];
+      const uint4 q1 = V8[static_cast<int64_t>(i + 1) * n8 + e];
+      const uint4 q2 = V8[static_cast<int64_t>(i + 2) * n8 + e];
+      const uint4 q3 = V8[static_cast<int64_t>(i + 3) * n8 + e];
+      float f[8];
+      bf8_to_f(q0, f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] = fmaf(-hs[i], f[k], acc[k]);
+      bf8_to_f(q1, f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] = fmaf(-hs[i + 1], f[k], acc[k]);
+      bf8_to_f(q2, f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] = fmaf(-hs[i + 2], f[k], acc[k]);
+      bf8_to_f(q3, f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] = fmaf(-hs[i + 3], f[k], acc[k]);
+    }
+    for (; i < jj; ++i) {
+      float f[8];
+      bf8_to_f(V8[static_cast<int64_t>(i) * n8 + e], f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] = fmaf(-hs[i], f[k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] *= fi;
+    out[e] = f_to_bf8(acc);
+  }
+  float* Q = static_cast<float*>(w.Q);
+  const float* S = static_cast<const float*>(w.S);
+  const double invd = 1.0 / ctl->hnext;
+  for (int64_t e = t0; e < w.d; e += stride) {
+    double v = static_cast<double>(S[e]);
+    for (int i = 0; i < jj; ++i) v -= hd[i] * static_cast<double>(Q[static_cast<int64_t>(i) * w.d + e]);
+    Q[static_cast<int64_t>(jj) * w.d + e] = static_cast<float>(v * invd);
+  }
+}
+
+cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fused, cudaStream_t s,
+                         int sdtype) {
   const int g = gs_grid(w.d);
+  if (sdtype < 0) sdtype = w.dtype;
+  if (w.vdtype == RTG_BF16) {
+    if (!fused) k_gs_pass<float><<<g, GS_THREADS, 0, s>>>(w, 0, o);
+    if (sdtype == RTG_BF16) k_start_scale_bf16<true><<<ew_grid(w.n / 8 + 1), 256, 0, s>>>(w, src);
+    else k_start_scale_bf16<false><<<ew_grid(w.n / 8 + 1), 256, 0, s>>>(w, src);
+    return cudaGetLastError();
+  }
   if (w.dtype == RTG_F64) {
     if (!fused) k_gs_pass<double><<<g, GS_THREADS, 0, s>>>(w, 0, o);
     k_start_scale<double><<<ew_grid(w.n), 256, 0, s>>>(w, src);
@@ -271,7 +405,8 @@ cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s) {
 
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s) {
   // one block more than the update needs: it runs the Givens step
-  if (w.dtype == RTG_F64) k_update<double><<<ew_grid(w.n) + 1, 256, 0, s>>>(w, o);
+  if (w.vdtype == RTG_BF16) k_update_bf16<<<ew_grid(w.n / 8 + 1) + 1, 256, 0, s>>>(w, o);
+  else if (w.dtype == RTG_F64) k_update<double><<<ew_grid(w.n) + 1, 256, 0, s>>>(w, o);
   else k_update<float><<<ew_grid(w.n / 4 + 1) + 1, 256, 0, s>>>(w, o);
   return cudaGetLastError();
 }

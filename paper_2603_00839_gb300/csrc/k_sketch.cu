@@ -386,23 +386,26 @@ __device__ __forceinline__ int64_t out_pos(const OutMap& om, int64_t l, int64_t 
 // by TMA bulk copies: one for the Theta fragments, one per column of X.
 // Warp w takes the K tiles w, w+8, ...; the 8 partial tiles are summed in
 // shared memory.
-template <int CH>
+template <int CH, typename TI>
 __global__ void __launch_bounds__(TC_THREADS)
 k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t s, int kt_total,
               const uint4* __restrict__ fragA, int mt_total, float scale, OutMap om,
               int* status, const int* stop) {
   if (stop != nullptr && *stop) return;
-  const float* __restrict__ X = Xr.get<const float>();
+  // BF16 data are exact in one limb; FP32 data take three (see split3)
+  constexpr int LIMBS = sizeof(TI) == 4 ? 3 : 1;
+  constexpr int EV = 16 / static_cast<int>(sizeof(TI));   // elements per 16 bytes
+  const TI* __restrict__ X = Xr.get<const TI>();
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   constexpr int XS = CH * 16 + 8;
   uint4* fA = reinterpret_cast<uint4*>(smem);                                   // [CH][F_MT][32]
-  float* xs = reinterpret_cast<float*>(smem + size_t(CH) * F_MT * 32 * 16);       // [F_COLS][XS]
+  TI* xs = reinterpret_cast<TI*>(smem + size_t(CH) * F_MT * 32 * 16);             // [F_COLS][XS]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gid = lane >> 2, tig = lane & 3;
   const int64_t c0 = static_cast<int64_t>(blockIdx.x) * F_COLS;
   const int mb = blockIdx.y;
   const int nmt = min(F_MT, mt_total - mb * F_MT);
-  const bool bulk = (I % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  const bool bulk = (I % EV == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
   if (tid == 0) mbar_init(&bar);
   __syncthreads();
   float acc[F_MT][2][4];
@@ -421,19 +424,19 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
     const int ncol = static_cast<int>((static_cast<int64_t>(F_COLS) < R - c0) ? static_cast<int64_t>(F_COLS) : R - c0);
     if (tid == 0) {
       const uint32_t fbytes = static_cast<uint32_t>(nk) * F_MT * 32 * 16;
-      const uint32_t xbytes = bulk ? static_cast<uint32_t>(ncol) * rows * 4 : 0u;
+      const uint32_t xbytes = bulk ? static_cast<uint32_t>(ncol) * rows * sizeof(TI) : 0u;
       mbar_expect(&bar, fbytes + xbytes);
       bulk_g2s(fA, fragA + (static_cast<int64_t>(mb) * kt_total + kc0) * F_MT * 32, fbytes, &bar);
       if (bulk)
         for (int col = 0; col < ncol; ++col)
-          bulk_g2s(&xs[col * XS], X + (c0 + col) * I + i0, static_cast<uint32_t>(rows) * 4, &bar);
+          bulk_g2s(&xs[col * XS], X + (c0 + col) * I + i0, static_cast<uint32_t>(rows * sizeof(TI)), &bar);
     }
     // zero the rows and columns the copies do not cover; without bulk, plain loads
     if (!bulk || ncol < F_COLS || rows < nk * 16) {
       for (int idx = tid; idx < F_COLS * nk * 16; idx += TC_THREADS) {
         const int col = idx / (nk * 16), k = idx - col * (nk * 16);
         if (bulk && col < ncol && k < rows) continue;
-        xs[col * XS + k] = (col < ncol && k < rows) ? X[(c0 + col) * I + i0 + k] : 0.f;
+        xs[col * XS + k] = (col < ncol && k < rows) ? X[(c0 + col) * I + i0 + k] : static_cast<TI>(0.f);
       }
     }
     if (tc_wait_failed(&bar, phase, status)) {
@@ -448,8 +451,13 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const float2 v = *reinterpret_cast<const float2*>(&xs[(nt * 8 + gid) * XS + kk * 16 + tig * 2 + h * 8]);
-            split_pair(v.x, v.y, B[nt][h]);
+            const TI* xp = &xs[(nt * 8 + gid) * XS + kk * 16 + tig * 2 + h * 8];
+            if constexpr (sizeof(TI) == 4) {
+              const float2 v = *reinterpret_cast<const float2*>(xp);
+              split_pair(v.x, v.y, B[nt][h]);
+            } else {
+              B[nt][h][0] = *reinterpret_cast<const uint32_t*>(xp);   // two BF16 values, k and k+1
+            }
           }
         uint32_t A[F_MT][4];
 #pragma unroll
@@ -462,7 +470,7 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
         }
         // limb-outer order: consecutive MMAs update independent accumulators
 #pragma unroll
-        for (int l = 0; l < 3; ++l)
+        for (int l = 0; l < LIMBS; ++l)
 #pragma unroll
           for (int mt = 0; mt < F_MT; ++mt)
 #pragma unroll
@@ -725,8 +733,21 @@ static OutMap stage_out_map(const SketchPlan& sp, int t) {
   return om;
 }
 
+template <int CH, typename TI>
+static cudaError_t launch_first(dim3 grid, PtrRef src, float* dst, const SketchPlan& sp, int t, int kt,
+                                const uint32_t* fr, float scale, OutMap om, int* status, const int* stop,
+                                cudaStream_t s) {
+  constexpr size_t sm = first_smem<CH>();
+  cudaError_t e = cudaFuncSetAttribute(k_sk_first_tc<CH, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  if (e != cudaSuccess) return e;
+  k_sk_first_tc<CH, TI><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_I[t], sp.stage_R[t], sp.stage_s[t], kt,
+                                                     reinterpret_cast<const uint4*>(fr), sp.stage_ntile[t],
+                                                     scale, om, status, stop);
+  return cudaGetLastError();
+}
+
 static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, float* out,
-                              const SketchDots* dots, const int* stop, cudaStream_t s) {
+                              const SketchDots* dots, const int* stop, cudaStream_t s, int xdtype) {
   PtrRef src = X;
   for (int t = 0; t < sp.nstage; ++t) {
     const bool last = (t == sp.nstage - 1);
@@ -740,21 +761,13 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
     if (sp.stage_first[t]) {
       dim3 grid(static_cast<unsigned>((sp.stage_R[t] + F_COLS - 1) / F_COLS),
                 static_cast<unsigned>((sp.stage_ntile[t] + F_MT - 1) / F_MT));
-      if (kt > 16) {
-        constexpr size_t sm = first_smem<32>();
-        e = cudaFuncSetAttribute(k_sk_first_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-        if (e != cudaSuccess) return e;
-        k_sk_first_tc<32><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_I[t], sp.stage_R[t], sp.stage_s[t],
-                                                       kt, reinterpret_cast<const uint4*>(fr),
-                                                       sp.stage_ntile[t], scale, om, status, stop);
-      } else {
-        constexpr size_t sm = first_smem<16>();
-        e = cudaFuncSetAttribute(k_sk_first_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-        if (e != cudaSuccess) return e;
-        k_sk_first_tc<16><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_I[t], sp.stage_R[t], sp.stage_s[t],
-                                                       kt, reinterpret_cast<const uint4*>(fr),
-                                                       sp.stage_ntile[t], scale, om, status, stop);
-      }
+      const bool bf = (t == 0 && xdtype == RTG_BF16);
+      if (kt > 16)
+        e = bf ? launch_first<32, __nv_bfloat16>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s)
+               : launch_first<32, float>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s);
+      else
+        e = bf ? launch_first<16, __nv_bfloat16>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s)
+               : launch_first<16, float>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s);
     } else {
       const int64_t ltiles = (sp.stage_L[t] + 15) / 16;
       dim3 grid(static_cast<unsigned>(ltiles * sp.stage_R[t]),
@@ -789,7 +802,11 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
 }
 
 cudaError_t launch_sketch(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, void* out,
-                          const SketchDots* dots, const int* stop, cudaStream_t s) {
+                          const SketchDots* dots, const int* stop, cudaStream_t s, int xdtype) {
+  if (xdtype < 0) xdtype = sp.dtype;
+  // BF16 input is read only by a first stage on mode 1 (FP32 plans)
+  if (xdtype == RTG_BF16 && (sp.dtype != RTG_F32 || sp.nstage == 0 || !sp.stage_first[0]))
+    return cudaErrorInvalidValue;
   int64_t n = 1;
   for (int k = 0; k < sp.order; ++k) n *= sp.dims[k];
   if (sp.nstage == 0) {     // no sketched mode: S = identity
@@ -798,7 +815,7 @@ cudaError_t launch_sketch(const SketchPlan& sp, const SketchScratch& sc, PtrRef 
     return cudaGetLastError();
   }
   if (sp.dtype == RTG_F64) return sketch_f64(sp, sc, X, static_cast<double*>(out), stop, s);
-  return sketch_f32(sp, sc, X, static_cast<float*>(out), sp.fused_dots ? dots : nullptr, stop, s);
+  return sketch_f32(sp, sc, X, static_cast<float*>(out), sp.fused_dots ? dots : nullptr, stop, s, xdtype);
 }
 
 }  // namespace rtg

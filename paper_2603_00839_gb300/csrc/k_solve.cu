@@ -237,7 +237,40 @@ cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s) 
   return cudaGetLastError();
 }
 
+// X = X0 + sum_{i<k} y_i V_i with V in BF16 (FP32 arithmetic, 8 values per load)
+__global__ void k_assemble_bf16(Work w, PtrRef X0r, PtrRef Xr) {
+  const int k = w.ctl->j;
+  __shared__ float ys[kMaxK];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = static_cast<float>(w.y[i]);
+  __syncthreads();
+  const float* X0 = X0r.get<const float>();
+  float* X = Xr.get<float>();
+  const uint4* V8 = static_cast<const uint4*>(w.V);
+  const int64_t n8 = w.n / 8;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n8;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = (X0 != nullptr) ? X0[8 * o + q] : 0.f;
+    for (int i = 0; i < k; ++i) {
+      const uint4 v = V8[static_cast<int64_t>(i) * n8 + o];
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[2 * q] = fmaf(ys[i], __uint_as_float(w4[q] << 16), acc[2 * q]);
+        acc[2 * q + 1] = fmaf(ys[i], __uint_as_float(w4[q] & 0xffff0000u), acc[2 * q + 1]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) X[8 * o + q] = acc[q];
+  }
+}
+
 cudaError_t launch_assemble(const Work& w, PtrRef X0, PtrRef X, cudaStream_t s) {
+  if (w.vdtype == RTG_BF16) {
+    k_assemble_bf16<<<ew_grid(w.n / 8 + 1), 256, 0, s>>>(w, X0, X);
+    return cudaGetLastError();
+  }
   if (w.dtype == RTG_F64) k_assemble<double><<<ew_grid(w.n), 256, 0, s>>>(w, X0, X);
   else k_assemble<float><<<ew_grid(w.n), 256, 0, s>>>(w, X0, X);
   return cudaGetLastError();

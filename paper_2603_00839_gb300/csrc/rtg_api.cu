@@ -92,7 +92,7 @@ struct DeviceGuard {
   }
 };
 
-size_t elt_size(int dtype) { return dtype == RTG_F64 ? 8 : 4; }
+size_t elt_size(int dtype) { return dtype == RTG_F64 ? 8 : (dtype == RTG_BF16 ? 2 : 4); }
 
 // ------------------------------------------------------------------ operator plans
 
@@ -113,9 +113,12 @@ rtg_status check_shape(const rtg_shape& sh, int64_t* n_out) {
   return RTG_OK;
 }
 
-rtg_status check_dtype(rtg_dtype dt) {
+rtg_status check_dtype(rtg_dtype dt, bool bf16_ok = false) {
   if (dt == RTG_F64 || dt == RTG_F32) return RTG_OK;
-  if (dt == RTG_BF16) return fail(RTG_ERR_UNSUPPORTED, "dtype RTG_BF16 is not supported by this call");
+  if (dt == RTG_BF16) {
+    if (bf16_ok) return RTG_OK;
+    return fail(RTG_ERR_UNSUPPORTED, "dtype RTG_BF16 is not supported by this call");
+  }
   return fail(RTG_ERR_INVALID_ARG, "unknown dtype %d", (int)dt);
 }
 
@@ -254,6 +257,64 @@ rtg_status build_op(const rtg_factor* A, int nA, const rtg_factor* B, int nB, co
     }
   }
   (void)nslab;
+  // spatio-temporal pattern: banded modes 1-2 (<= 1 pass each), <= 1 pass on
+  // mode 3 mixing 1 or 3 channels, <= 1 banded pass of radius <= 2 on mode 4
+  {
+    bool st = op.order <= 4;
+    int c4[kMaxOrder] = {0, 0, 0, 0};
+    op.st_nc = 1;
+    op.r4 = 0;
+    op.t4[0] = 1.0;
+    op.st_M[0] = 1.0;
+    for (int p = 0; p < op.npass && st; ++p) {
+      const Pass& ps = op.pass[p];
+      if (++c4[ps.mode] > 1) st = false;
+      if (ps.mode <= 1 && ps.kind != PK_BAND) st = false;
+      if (ps.mode == 2) {
+        if (ps.n != 1 && ps.n != 3) {
+          st = false;
+        } else {
+          const int nn = ps.n;
+          op.st_nc = nn;
+          for (int pp = 0; pp < nn; ++pp)
+            for (int c = 0; c < nn; ++c) {
+              if (ps.kind == PK_BAND) {
+                const int t = c - pp;
+                op.st_M[pp + nn * c] = (t >= -ps.radius && t <= ps.radius) ? ps.taps[ps.radius + t] : 0.0;
+              } else {
+                op.st_M[pp + nn * c] = op.M3[pp + nn * c];
+              }
+            }
+        }
+      }
+      if (ps.mode == 3) {
+        if (ps.kind != PK_BAND || ps.radius > 2) {
+          st = false;
+        } else {
+          op.r4 = ps.radius;
+          for (int t = 0; t <= 2 * ps.radius; ++t) op.t4[t] = ps.taps[t];
+        }
+      }
+    }
+    if (op.order >= 2 && op.dims[1] > 65535LL * 16) st = false;
+    if (op.order >= 1 && op.dims[0] > 65535LL * 64) st = false;
+    // the fused image kernel's fields carry the spatial taps
+    if (st && !op.fused) {
+      op.r1 = op.r2 = 0;
+      op.t1[0] = op.t2[0] = 1.0;
+      for (int p = 0; p < op.npass; ++p) {
+        const Pass& ps = op.pass[p];
+        if (ps.mode == 0) {
+          op.r1 = ps.radius;
+          for (int t = 0; t <= 2 * ps.radius; ++t) op.t1[t] = ps.taps[t];
+        } else if (ps.mode == 1) {
+          op.r2 = ps.radius;
+          for (int t = 0; t <= 2 * ps.radius; ++t) op.t2[t] = ps.taps[t];
+        }
+      }
+    }
+    op.st = st;
+  }
   return RTG_OK;
 }
 
@@ -300,19 +361,23 @@ struct Carver {
 
 // Lays out (and, with mem != null, points) every buffer of an Arnoldi workspace.
 size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, int tk_blocks,
-                  int64_t apply_elems, Work& w, void** tA, void** tB, SketchScratch* sk) {
+                  int64_t apply_elems, Work& w, void** tA, void** tB, SketchScratch* sk,
+                  int vdtype = -1) {
   Carver c(mem);
   const size_t e = elt_size(dtype);
+  if (vdtype < 0) vdtype = dtype;
+  const size_t ev = elt_size(vdtype);
   const int64_t d = sp.d;
   w = Work{};
   w.dtype = dtype;
+  w.vdtype = vdtype;
   w.n = n;
   w.d = static_cast<int>(d);
   w.m = m;
   int64_t G = gs_grid(d);
   if (sp.dots_blocks > G) G = sp.dots_blocks;
-  w.V = c.take<char>(size_t(m + 1) * n * e);
-  w.W = c.take<char>(size_t(n) * e);
+  w.V = c.take<char>(size_t(m + 1) * n * ev);
+  w.W = c.take<char>(size_t(n) * ev);
   w.S = c.take<char>(size_t(d) * e);
   w.Spart = c.take<char>(size_t(d) * e);
   w.nparts = 1;
@@ -372,6 +437,7 @@ struct SolvePlan {
   bool use_graph = true;
   bool true_resid = false;
   int dtype = RTG_F32;
+  int vdtype = RTG_F32;                                           // storage of V and W
   int launches_pro = 0, launches_step = 0, launches_epi = 0;   // kernels per phase
   int launches_setup = 0;                                         // reset + Theta, part of the prologue
   int direct_steps = 0;                                           // steps launched by the last direct solve
@@ -554,15 +620,17 @@ rtg_status enqueue_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s,
   PhaseScope ps(pt, RTG_PHASE_INIT, -1, P.launches_pro - P.launches_setup);
   PtrRef C = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->C));
   PtrRef src = C;
+  int sdt = P.dtype;
   if (P.has_x0) {   // R_0 = C - Phi(X_0) into the V_0 slot
     PtrRef X0 = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X0));
-    CK(launch_apply(P.op.op, P.dtype, X0, ref(w.V), -1.0, 1.0, C, P.tA, P.tB, nullptr, s));
+    CK(launch_apply(P.op.op, P.dtype, X0, ref(w.V), -1.0, 1.0, C, P.tA, P.tB, nullptr, s, P.dtype, P.vdtype));
     src = ref(w.V);
+    sdt = P.vdtype;
   }
   const bool fused = P.sp.fused_dots != 0;
   SketchDots dots{&w, 0, so};
-  CK(launch_sketch(P.sp, P.sk, src, fused ? w.S : w.Spart, fused ? &dots : nullptr, nullptr, s));
-  CK(launch_start(w, src, so, fused, s));
+  CK(launch_sketch(P.sp, P.sk, src, fused ? w.S : w.Spart, fused ? &dots : nullptr, nullptr, s, sdt));
+  CK(launch_start(w, src, so, fused, s, sdt));
   return RTG_OK;
 }
 
@@ -575,14 +643,14 @@ rtg_status enqueue_step(const OpHolder& op, const SketchPlan& sp, const Work& w,
   vj.stride = w.n;
   const int* stop = &w.ctl->stop;
   {
-    PhaseScope ps(pt, RTG_PHASE_APPLY, step, apply_launches(op.op, false));
-    CK(launch_apply(op.op, dtype, vj, ref(w.W), 1.0, 0.0, PtrRef{}, tA, tB, stop, s));
+    PhaseScope ps(pt, RTG_PHASE_APPLY, step, apply_launches(op.op, false, dtype, w.vdtype, w.vdtype));
+    CK(launch_apply(op.op, dtype, vj, ref(w.W), 1.0, 0.0, PtrRef{}, tA, tB, stop, s, w.vdtype, w.vdtype));
   }
   const bool fused = sp.fused_dots != 0;
   {
     PhaseScope ps(pt, RTG_PHASE_SKETCH, step, sketch_launches(sp));
     SketchDots dots{&w, 1, so};
-    CK(launch_sketch(sp, sk, ref(w.W), fused ? w.S : w.Spart, fused ? &dots : nullptr, stop, s));
+    CK(launch_sketch(sp, sk, ref(w.W), fused ? w.S : w.Spart, fused ? &dots : nullptr, stop, s, w.vdtype));
   }
   if (!fused) {
     PhaseScope ps(pt, RTG_PHASE_GS, step, 1);
@@ -741,7 +809,7 @@ rtg_status rtg_operator_apply(rtg_handle h, const rtg_factor* A, int32_t nA, con
   if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
   int64_t n = 0;
   RK(check_shape(shape, &n));
-  RK(check_dtype(dtype));
+  RK(check_dtype(dtype, true));
   RK(check_factors(A, nA, shape, "A_factors"));
   RK(check_factors(B, nB, shape, "B_factors"));
   DeviceGuard dg(h->device);
@@ -749,6 +817,17 @@ rtg_status rtg_operator_apply(rtg_handle h, const rtg_factor* A, int32_t nA, con
   if (overlaps(X, Y, size_t(n) * elt_size(dtype))) return fail(RTG_ERR_INVALID_ARG, "Y overlaps X");
   OpHolder* op = nullptr;
   RK(get_op(h, A, nA, B, nB, shape, &op));
+  if (dtype == RTG_BF16) {
+    if (!st_supported(op->op, RTG_BF16))
+      return fail(RTG_ERR_UNSUPPORTED, "BF16 apply needs banded modes 1-2 (radius <= 9), a mode-3 mix of 1 or 3 "
+                                       "channels, a mode-4 band of radius <= 2 and dims[0] %% 8 == 0");
+    if (reinterpret_cast<uintptr_t>(X) % 16 != 0) return fail(RTG_ERR_INVALID_ARG, "BF16 X must be 16-byte aligned");
+    CK(launch_apply(op->op, RTG_F32, ref(X), ref(Y), 1.0, 0.0, PtrRef{}, nullptr, nullptr, nullptr,
+                    reinterpret_cast<cudaStream_t>(stream), RTG_BF16, RTG_BF16));
+    return RTG_OK;
+  }
+  if (apply_uses_st(op->op, dtype, dtype, dtype) && reinterpret_cast<uintptr_t>(X) % 16 != 0)
+    return fail(RTG_ERR_INVALID_ARG, "X must be 16-byte aligned for this operator");
   const int64_t sc = apply_scratch_elems(op->op);
   RK(h->tA.ensure(size_t(sc) * elt_size(dtype)));
   RK(h->tB.ensure(size_t(sc) * elt_size(dtype)));
@@ -762,12 +841,15 @@ rtg_status rtg_sketch(rtg_handle h, rtg_shape shape, rtg_dtype dtype, const int6
   if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
   int64_t n = 0;
   RK(check_shape(shape, &n));
-  RK(check_dtype(dtype));
+  RK(check_dtype(dtype, true));
+  const rtg_dtype pdt = dtype == RTG_BF16 ? RTG_F32 : dtype;   // BF16 input: FP32 plan and output
   SketchPlan sp;
-  RK(build_sketch(shape, sketch_dims, seed, pid, dtype, sp));
+  RK(build_sketch(shape, sketch_dims, seed, pid, pdt, sp));
+  if (dtype == RTG_BF16 && (sp.nstage == 0 || !sp.stage_first[0]))
+    return fail(RTG_ERR_UNSUPPORTED, "a BF16 sketch needs mode 1 sketched (sketch_dims[0] < dims[0])");
   DeviceGuard dg(h->device);
   if (!is_device_ptr(X) || !is_device_ptr(SX)) return fail(RTG_ERR_INVALID_ARG, "X and SX must be device pointers");
-  if (overlaps(X, SX, size_t(std::min<int64_t>(n, sp.d)) * elt_size(dtype)))
+  if (overlaps(X, SX, size_t(std::min<int64_t>(n, sp.d)) * elt_size(pdt)))
     return fail(RTG_ERR_INVALID_ARG, "SX must not overlap X");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::string key;
@@ -794,7 +876,7 @@ rtg_status rtg_sketch(rtg_handle h, rtg_shape shape, rtg_dtype dtype, const int6
   }
   const SketchScratch sc = carve_sketch_scratch(sp, buf->p);
   if (fresh) CK(launch_theta(sp, sc.bits, sc.frags, s));
-  CK(launch_sketch(sp, sc, ref(X), SX, nullptr, nullptr, s));
+  CK(launch_sketch(sp, sc, ref(X), SX, nullptr, nullptr, s, dtype));
   return RTG_OK;
 }
 
@@ -935,6 +1017,12 @@ rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const
   SketchPlan sp;
   RK(build_sketch(shape, sketch_dims, seed, 0, dtype, sp));
   const bool phase_times = (opts.flags & RTG_FLAG_PHASE_TIMES) != 0;
+  const int vdtype = (opts.flags & RTG_FLAG_BF16_BASIS) ? RTG_BF16 : dtype;
+  if (vdtype == RTG_BF16) {
+    if (dtype != RTG_F32) return fail(RTG_ERR_UNSUPPORTED, "RTG_FLAG_BF16_BASIS needs dtype RTG_F32");
+    if (sp.nstage == 0 || !sp.stage_first[0])
+      return fail(RTG_ERR_UNSUPPORTED, "RTG_FLAG_BF16_BASIS needs mode 1 sketched (sketch_dims[0] < dims[0])");
+  }
   const bool use_graph = !(opts.flags & RTG_FLAG_NO_GRAPH) && !phase_times;
   std::string key = op_key(A, nA, B, nB, shape);
   append_bytes(key, &dtype, sizeof dtype);
@@ -947,6 +1035,7 @@ rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const
   key.push_back(has_x0 ? '1' : '0');
   key.push_back(use_graph ? 'g' : 'd');
   append_bytes(key, &opts.slot, sizeof opts.slot);
+  append_bytes(key, &vdtype, sizeof vdtype);
 
   rtg_context::Pending& pend = h->pending[opts.slot];
   if (pend.active) return fail(RTG_ERR_INVALID_ARG, "slot %d has a submitted solve that was not waited for", opts.slot);
@@ -977,15 +1066,19 @@ rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const
     P->use_graph = use_graph;
     P->sp = sp;
     RK(build_op(A, nA, B, nB, shape, P->op));
+    P->vdtype = vdtype;
+    if (vdtype == RTG_BF16 && !st_supported(P->op.op, RTG_BF16))
+      return fail(RTG_ERR_UNSUPPORTED, "RTG_FLAG_BF16_BASIS needs banded modes 1-2 (radius <= 9), a mode-3 mix "
+                                       "of 1 or 3 channels, a mode-4 band of radius <= 2 and dims[0] %% 8 == 0");
     const int64_t ae = apply_scratch_elems(P->op.op);
     const int tkb = mode == 2 ? opts.n_mu : 1;
     Work tmpw;
     void *ta, *tb;
     SketchScratch tsk;
-    const size_t bytes = carve_work(nullptr, dtype, n, sp, m, tkb, ae, tmpw, &ta, &tb, &tsk);
+    const size_t bytes = carve_work(nullptr, dtype, n, sp, m, tkb, ae, tmpw, &ta, &tb, &tsk, vdtype);
     RK(P->mem.ensure(bytes));
     CK(cudaMemset(P->mem.p, 0, bytes));
-    carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk);
+    carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk, vdtype);
     RK(P->small.ensure(sizeof(SolveDesc) + sizeof(InfoDev) + 512));
     P->desc_dev = static_cast<SolveDesc*>(P->small.p);
     P->info_dev = reinterpret_cast<InfoDev*>(static_cast<char*>(P->small.p) + ((sizeof(SolveDesc) + 255) & ~size_t(255)));
@@ -1002,8 +1095,9 @@ rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const
       const int gs = sp.fused_dots ? 0 : 1;
       P->launches_setup = 1 + (nsk > 0 ? (dtype == RTG_F32 ? 2 : 1) : 0);
       P->launches_pro = P->launches_setup +
-                        (has_x0 ? apply_launches(P->op.op, true) : 0) + sketch_launches(sp) + gs + 1;
-      P->launches_step = apply_launches(P->op.op, false) + sketch_launches(sp) + gs + 1;
+                        (has_x0 ? apply_launches(P->op.op, true, dtype, dtype, vdtype) : 0) +
+                        sketch_launches(sp) + gs + 1;
+      P->launches_step = apply_launches(P->op.op, false, dtype, vdtype, vdtype) + sketch_launches(sp) + gs + 1;
       P->launches_epi = 3;
     }
     if (use_graph) RK(build_graph(*P));
@@ -1035,6 +1129,13 @@ rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const
     if (has_x0 && X0 == X && !X0_dev) {
       CK(cudaMemcpyAsync(P->Xst.p, X0, bytes_t, cudaMemcpyHostToDevice, s));
     }
+  }
+  {   // the 16-byte loads of the spatio-temporal apply and of the BF16 start kernel
+    const bool x0_st = has_x0 && apply_uses_st(P->op.op, dtype, dtype, P->vdtype);
+    if (x0_st && reinterpret_cast<uintptr_t>(D.X0) % 16 != 0)
+      return fail(RTG_ERR_INVALID_ARG, "X0 must be 16-byte aligned for this operator");
+    if (P->vdtype == RTG_BF16 && reinterpret_cast<uintptr_t>(D.C) % 16 != 0)
+      return fail(RTG_ERR_INVALID_ARG, "C must be 16-byte aligned with RTG_FLAG_BF16_BASIS");
   }
   D.key[0] = seed;
   D.key[1] = 0;

@@ -44,6 +44,13 @@ struct OpPlan {
   double t1[kMaxTaps], t2[kMaxTaps];
   int mix;                   // fused: 0 = no channel mixing, else mix size (= dims[2])
   double M3[kMaxMix * kMaxMix];   // fused: mode-3 matrix, M3[p + mix*c] = M(p, c)
+  // spatio-temporal path: banded modes 1-2, mode-3 mix of st_nc (1 or 3)
+  // channels, banded mode 4 of radius r4 <= 2 (t4: 2 r4 + 1 taps)
+  bool st;
+  int st_nc;
+  double st_M[kMaxMix * kMaxMix];
+  int r4;
+  double t4[5];
 };
 
 // Control block of one sketched Arnoldi process (device resident).
@@ -91,7 +98,8 @@ struct InfoDev {
 
 // Workspace of one Arnoldi process.  T is the data type (double / float).
 struct Work {
-  int dtype;                   // RTG_F64 / RTG_F32
+  int dtype;                   // RTG_F64 / RTG_F32: C, X, S, Q and the arithmetic
+  int vdtype;                  // storage of V and W: dtype, or RTG_BF16 for an FP32 solve
   int64_t n;                   // elements per tensor
   int d;                       // sketch size prod(s'_k)
   int m;                       // Krylov dimension
@@ -216,13 +224,20 @@ cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, 
 
 // k_apply.cu: Y = alpha * Phi(X) + beta * Z (Z may be null when beta == 0).
 // tmp: scratch of n elements for the unfused path (may be null if unused).
+// tin / tout: storage type of X and Y when they differ from dtype (RTG_BF16
+// runs the spatio-temporal kernel, FP32 arithmetic); Z has type dtype.
 cudaError_t launch_apply(const OpPlan& op, int dtype, PtrRef X, PtrRef Y, double alpha,
                          double beta, PtrRef Z, void* tmp, void* tmp2, const int* stop,
-                         cudaStream_t s);
+                         cudaStream_t s, int tin = -1, int tout = -1);
+// The spatio-temporal kernel can apply op to X stored as tin.
+bool st_supported(const OpPlan& op, int tin);
+int st_bucket(int r);
 // Scratch elements the unfused path needs (0 when fused).
 int64_t apply_scratch_elems(const OpPlan& op);
 // Kernels one launch_apply issues (combine: alpha != 1 or a Z term).
-int apply_launches(const OpPlan& op, bool combine);
+int apply_launches(const OpPlan& op, bool combine, int dtype = RTG_F32, int tin = -1, int tout = -1);
+// launch_apply takes the spatio-temporal kernel for these types.
+bool apply_uses_st(const OpPlan& op, int dtype, int tin, int tout);
 
 // k_sketch.cu: S(X) into `out` (d elements).  With dots != null and
 // sp.fused_dots, the last contraction also runs Gram-Schmidt pass
@@ -230,8 +245,10 @@ int apply_launches(const OpPlan& op, bool combine);
 struct Work;
 struct StepOpts;
 struct SketchDots;
+// xdtype: storage type of X (default sp.dtype); RTG_BF16 needs an FP32 plan whose
+// first stage contracts mode 1.
 cudaError_t launch_sketch(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, void* out,
-                          const SketchDots* dots, const int* stop, cudaStream_t s);
+                          const SketchDots* dots, const int* stop, cudaStream_t s, int xdtype = -1);
 int sketch_launches(const SketchPlan& sp);
 
 // k_arnoldi.cu: the sketched Arnoldi process on a Work.
@@ -254,7 +271,9 @@ struct SketchDots {
   StepOpts o;
 };
 // pass 0 on w.Spart (unless the sketch already ran it) and the scaling V_0, Q_0
-cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fused, cudaStream_t s);
+// src has type sdtype (dtype, or vdtype when it is the V_0 slot).
+cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fused, cudaStream_t s,
+                         int sdtype = -1);
 cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s);
 int gs_grid(int64_t d);
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s);
