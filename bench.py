@@ -41,7 +41,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--problems", type=int, default=4, help="distinct seeded problems cycled")
+    ap.add_argument("--problems", type=int, default=16,
+                    help="distinct seeded problems (the plain form cycles them, the batched form solves "
+                         "them together)")
+    ap.add_argument("--batch", type=int, default=16, help="problems per batched launch (chosen form)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--direct", action="store_true",
@@ -344,15 +347,45 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    # warm-up (builds the plan and its CUDA graph)
+    grid = workloads.mu_grid()
+
+    def batch_of(k):
+        return [dict(C=probs[(k * B + i) % len(probs)]["C"], A=probs[(k * B + i) % len(probs)]["A"],
+                     B=probs[(k * B + i) % len(probs)]["B"], m=probs[0]["p"].m,
+                     sketch_dims=probs[0]["p"].sketch_dims, seed=probs[(k * B + i) % len(probs)]["p"].seed,
+                     lam=probs[0]["p"].lam, tol=probs[(k * B + i) % len(probs)]["tol"], X=Xb[i])
+                for i in range(B)]
+
+    B = args.batch
+    Xb = [api.empty(probs[0]["p"].dims, torch.float32) for _ in range(B)]
+    nb = max(1, len(probs) // B)
+
+    # ---- plain FP32 form: one solve per step, device-timed, L2 flushed between steps
     for s in range(args.warmup):
         solve(h, probs[s % len(probs)], X)
     torch.cuda.synchronize()
-
-    # device-timed steps; L2 flushed between steps (outside the events)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
-    iters, launches = [], 0
+    iters, conv_plain = [], []
+    for s in range(args.steps):
+        flush.zero_()
+        evs[s][0].record(stream)
+        _, info = solve(h, probs[s % len(probs)], X)
+        evs[s][1].record(stream)
+        iters.append(info.iters)
+        conv_plain.append(bool(info.converged))
+        if info.device_status != 0:
+            raise RuntimeError(f"solve failed: device status {info.device_status}")
+    torch.cuda.synchronize()
+    plain_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+
+    # ---- chosen form: batched (B problems per CUDA-graph launch), one batch per step
+    for s in range(args.warmup):
+        h.gmres_solve_batched(batch_of(s % nb), mu_grid=grid)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    iters_b, conv_b, launches = [], [], 0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -360,42 +393,58 @@ def run_ours(args):
         for s in range(args.steps):
             flush.zero_()
             evs[s][0].record(stream)
-            _, info = solve(h, probs[s % len(probs)], X)
+            _, res = h.gmres_solve_batched(batch_of(s % nb), mu_grid=grid)
             evs[s][1].record(stream)
-            iters.append(info.iters)
-            launches += info.launches
-            if info.device_status != 0 or not info.converged:
-                raise RuntimeError(f"solve failed: status {info.device_status} converged {info.converged}")
+            for r in res:
+                iters_b.append(r.iters)
+                conv_b.append(bool(r.converged))
+                launches += r.launches
+                if r.device_status != 0:
+                    raise RuntimeError(f"batched solve failed: device status {r.device_status}")
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    ms_t = torch.tensor([ms], device="cuda")
+    ms_t = torch.tensor([ms, plain_ms], device="cuda")
     if world > 1:
         torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * 1e3 / ms_max
+    ms_max, plain_max = float(ms_t[0].item()), float(ms_t[1].item())
+    value = world * B * 1e3 / ms_max
+    plain_value = world * 1e3 / plain_max
 
-    # end-to-end through the C ABI with pinned host buffers (H2D of C, D2H of X and the summary)
+    # ---- end to end through the C ABI with pinned host buffers, every step:
+    # H2D of the batch's observations, the batched solve, D2H of the solutions
     n = int(np.prod(probs[0]["p"].dims))
     for pr in probs:
         ch = torch.empty(tuple(reversed(pr["p"].dims)), dtype=torch.float32, pin_memory=True)
         ch = ch.permute(2, 1, 0)
         ch.copy_(pr["C"].cpu())
         pr["C_host"] = ch
-    Xh = torch.empty(tuple(reversed(probs[0]["p"].dims)), dtype=torch.float32,
-                     pin_memory=True).permute(2, 1, 0)
+    Cdev = [api.empty(probs[0]["p"].dims, torch.float32) for _ in range(B)]
+    Xh = [torch.empty(tuple(reversed(probs[0]["p"].dims)), dtype=torch.float32,
+                      pin_memory=True).permute(2, 1, 0) for _ in range(B)]
+
+    def e2e_step(k):
+        bt = batch_of(k)
+        for i in range(B):
+            Cdev[i].copy_(probs[(k * B + i) % len(probs)]["C_host"], non_blocking=True)
+            bt[i]["C"] = Cdev[i]
+        _, res = h.gmres_solve_batched(bt, mu_grid=grid)
+        for i in range(B):
+            Xh[i].copy_(Xb[i], non_blocking=True)
+        torch.cuda.synchronize()
+        return res
+
     for s in range(2):
-        solve(h, probs[s % len(probs)], Xh, host=True)
-    torch.cuda.synchronize()
+        e2e_step(s % nb)
     t0 = time.perf_counter()
     for s in range(args.steps):
-        solve(h, probs[s % len(probs)], Xh, host=True)
+        e2e_step(s % nb)
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_t = torch.tensor([e2e_s], device="cuda")
     if world > 1:
         torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-    e2e_val = world / float(e2e_t.item())
+    e2e_val = world * B / float(e2e_t.item())
 
     # phase timing holds the stream at gates the host opens; a profiler that
     # serialises every launch would wait on them, so --direct (the profiler
@@ -412,13 +461,21 @@ def run_ours(args):
                "data": "synthetic",
                "config": {"workload": WORKLOAD, "dims": [512, 512, 3], "m": 50,
                           "sketch": [128, 128, 3], "blur": "gaussian sigma 2.5 radius 7 + 3x3 mix",
-                          "noise": 1e-2, "gcv_grid": 8, "mean_iters": float(np.mean(iters)),
-                          "stop": "rho <= max(1e-3, 1.01*nu_C)", "problems": args.problems,
+                          "noise": 1e-2, "gcv_grid": 8, "mean_iters": float(np.mean(iters_b)),
+                          "stop": "rho <= max(1e-3, 1.01*nu_C), else m steps",
+                          "reached_stop_level": f"{sum(conv_b)}/{len(conv_b)}", "problems": len(probs),
                           "l2": "flushed (256 MB write) between timed steps",
-                          "form": "plain fp32",
-                          "launch": "direct" if args.direct else "cuda graph (device-side WHILE loop)"},
+                          "form": f"batched: {B} problems per CUDA-graph launch (one step = one batch)",
+                          "launch": "cuda graph (one branch per problem, device-side WHILE loops)"},
+               "forms": {"batched_fp32": {"value": round(value, 2), "ms_per_batch": round(ms_max, 4),
+                                          "batch": B},
+                         "plain_fp32": {"value": round(plain_value, 2), "ms_per_solve": round(plain_max, 4),
+                                        "mean_iters": float(np.mean(iters)),
+                                        "launch": "direct" if args.direct else "cuda graph"}},
                "e2e": {"value": round(e2e_val, 2), "unit": "solves/s",
-                       "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n + 2368},
+                       # per problem: C and X, plus the 512-byte descriptor and 2560-byte info
+                       # record slots of the batch call
+                       "h2d_bytes_per_step": (4 * n + 512) * B, "d2h_bytes_per_step": (4 * n + 2560) * B},
                "gpu_launches": launches,
                "roofline": roof, "kernels": phases, "cpu_baseline": cpu, "clocks": clk.summary()}
         print(json.dumps(out), flush=True)

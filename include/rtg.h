@@ -319,6 +319,45 @@ rtg_status rtg_gmres_submit(rtg_handle handle,
                             const rtg_opts* opts, rtg_stream stream);
 rtg_status rtg_gmres_wait(rtg_handle handle, int32_t slot, rtg_info* info);
 
+/* One problem of a batched solve: the arguments of rtg_gmres_solve. */
+typedef struct rtg_problem {
+    const rtg_factor* A_factors;
+    int32_t nA;
+    const rtg_factor* B_factors;
+    int32_t nB;
+    rtg_shape shape;
+    const void* C;                   /* device, prod(dims) elements of the batch dtype */
+    const void* X0;                  /* device or NULL */
+    void* X;                         /* device; may alias X0 */
+    int32_t m;
+    int32_t pad;
+    int64_t sketch_dims[RTG_MAX_ORDER];
+    uint64_t seed;
+    double lam;                      /* lambda: > 0 fixed, 0 least squares, < 0 GCV over opts->mu_grid */
+    double tol;                      /* stop level of rho_j */
+} rtg_problem;
+
+#define RTG_MAX_BATCH 1024
+
+/*
+ * Batched form: nprob independent RTG-GMRES solves, of any mix of shapes,
+ * operators, Krylov dimensions and sketch sizes, launched as one CUDA
+ * graph in which every problem is an independent branch (its own
+ * prologue, device-side loop over Arnoldi steps with its own stop
+ * decision, and epilogue), so the GPU runs the problems' kernels side by
+ * side.  The graph is built on the first call for a given list of problem
+ * shapes and replayed afterwards; descriptors go up in one copy and the
+ * info records come back in one copy.  opts (may be NULL) is shared: GCV
+ * grid, breakdown level and RTG_FLAG_BF16_BASIS; slot, NO_GRAPH and
+ * PHASE_TIMES do not apply.  infos: NULL or nprob records (elapsed_ms is
+ * the whole batch's).  The call synchronises `stream` once.
+ * Errors: as rtg_gmres_solve, per problem (the message names it); host
+ * pointers are INVALID_ARG.
+ */
+rtg_status rtg_gmres_solve_batched(rtg_handle handle, int32_t nprob, const rtg_problem* probs,
+                                   rtg_dtype dtype, const rtg_opts* opts, rtg_info* infos,
+                                   rtg_stream stream);
+
 /*
  * rtg_sketch_noalloc -- the paper has no counterpart; this is a service of
  * the library.  Same result as rtg_sketch (same kernels, same Philox

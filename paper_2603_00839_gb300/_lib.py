@@ -16,6 +16,7 @@ MAX_RADIUS = 32
 MAX_KRYLOV = 256
 MAX_MU = 32
 MAX_SLOTS = 64
+MAX_BATCH = 1024
 
 # rtg_status
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_ALLOC, ERR_TIMEOUT, ERR_NONFINITE = range(7)
@@ -41,6 +42,14 @@ class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("mu_grid", C.POINTER(C.c_double)), ("n_mu", C.c_int32),
                 ("max_restarts", C.c_int32), ("breakdown_tol", C.c_double), ("flags", C.c_int32),
                 ("slot", C.c_int32)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("A_factors", C.POINTER(Factor)), ("nA", C.c_int32), ("B_factors", C.POINTER(Factor)),
+                ("nB", C.c_int32), ("shape", Shape), ("C", C.c_void_p), ("X0", C.c_void_p),
+                ("X", C.c_void_p), ("m", C.c_int32), ("pad", C.c_int32),
+                ("sketch_dims", C.c_int64 * MAX_ORDER), ("seed", C.c_uint64), ("lam", C.c_double),
+                ("tol", C.c_double)]
 
 
 class Info(C.Structure):
@@ -89,6 +98,8 @@ _SIGS = {
                                    C.POINTER(C.c_int64), C.c_uint64, C.c_double, C.c_void_p,
                                    C.c_void_p, C.POINTER(Opts), C.c_void_p]),
     "rtg_gmres_wait": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Info)]),
+    "rtg_gmres_solve_batched": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Problem), C.c_int,
+                                          C.POINTER(Opts), C.POINTER(Info), C.c_void_p]),
     "rtg_sketch_noalloc": (C.c_int, [Shape, C.c_int, C.POINTER(C.c_int64), C.c_uint64, C.c_uint64,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
 }

@@ -276,6 +276,64 @@ class Handle:
         return PendingSolve(int(slot), X, m, max_restarts, grid, lam, phase_times,
                             (C_obs, X0, a, b, ka, kb, sk))
 
+    def gmres_solve_batched(self, problems: Sequence[dict], mu_grid=None, breakdown_tol: float = 0.0,
+                            bf16_basis: bool = False, stream=None):
+        """Batched form (rtg_gmres_solve_batched): every problem is a dict with
+        C (device tensor), m, sketch_dims, seed, lam, and optionally A, B
+        (factor lists), tol, X0, X.  All problems share C's dtype; each may
+        have its own shape.  Returns ([X], [SolveResult])."""
+        if not problems:
+            raise ValueError("no problems")
+        arr = (L.Problem * len(problems))()
+        keep = []
+        Xs = []
+        dt = _dtype_code(problems[0]["C"])
+        for i, q in enumerate(problems):
+            Cq = q["C"]
+            dims = tuple(Cq.shape)
+            _check_tensor(Cq, dims, "C")
+            if _dtype_code(Cq) != dt:
+                raise ValueError("all problems of a batch share one dtype")
+            X = q.get("X")
+            if X is None:
+                X = empty(dims, Cq.dtype, Cq.device)
+            _check_tensor(X, dims, "X")
+            a, na, ka = _factor_array(q.get("A", ()))
+            b, nb, kb = _factor_array(q.get("B", ()))
+            keep.append((a, b, ka, kb, q.get("X0")))
+            pr = arr[i]
+            pr.A_factors, pr.nA, pr.B_factors, pr.nB = a, na, b, nb
+            pr.shape = _shape(dims)
+            pr.C, pr.X0, pr.X = _ptr(Cq), _ptr(q.get("X0")), _ptr(X)
+            pr.m = int(q["m"])
+            for k, sdim in enumerate(q["sketch_dims"]):
+                pr.sketch_dims[k] = int(sdim)
+            pr.seed = int(q["seed"])
+            pr.lam = float(q["lam"])
+            pr.tol = float(q.get("tol", 0.0))
+            Xs.append(X)
+        opts = L.Opts()
+        grid = None
+        if mu_grid is not None:
+            grid = np.ascontiguousarray(mu_grid, dtype=np.float64)
+            opts.mu_grid = grid.ctypes.data_as(C.POINTER(C.c_double))
+            opts.n_mu = len(grid)
+        opts.breakdown_tol = float(breakdown_tol)
+        opts.flags = L.FLAG_BF16_BASIS if bf16_basis else 0
+        infos = (L.Info * len(problems))()
+        bufs = []
+        for i, q in enumerate(problems):
+            rho = np.zeros(int(q["m"]) + 1)
+            gcv = np.zeros(L.MAX_MU)
+            infos[i].rho_hist = rho.ctypes.data_as(C.POINTER(C.c_double))
+            infos[i].gcv = gcv.ctypes.data_as(C.POINTER(C.c_double))
+            bufs.append((rho, gcv))
+        L.check(self.lib.rtg_gmres_solve_batched(self._h, len(problems), arr, dt, C.byref(opts), infos,
+                                                 _stream(stream)))
+        res = [_solve_result(infos[i], bufs[i][0], bufs[i][1], grid, float(q["lam"]))
+               for i, q in enumerate(problems)]
+        return Xs, res
+
     def gmres_wait(self, pend: "PendingSolve"):
         """Wait for a submitted solve (rtg_gmres_wait); returns (X, SolveResult)."""
         info = L.Info()
@@ -293,6 +351,13 @@ class Handle:
             res.phase_ms = {k: info.phase_ms[i] for i, k in enumerate(L.PHASES)}
             res.phase_launches = {k: info.phase_launches[i] for i, k in enumerate(L.PHASES)}
         return pend.X, res
+
+
+def _solve_result(info, rho, gcv, grid, lam):
+    return SolveResult(info.iters, info.restarts, bool(info.breakdown), bool(info.converged),
+                       info.beta, info.mu, info.rho_final, rho[:info.iters].copy(),
+                       gcv[:len(grid)].copy() if (grid is not None and lam < 0) else None,
+                       info.elapsed_ms, info.device_status, info.launches)
 
 
 @dataclasses.dataclass

@@ -442,14 +442,36 @@ struct SolvePlan {
   int launches_setup = 0;                                         // reset + Theta, part of the prologue
   int direct_steps = 0;                                           // steps launched by the last direct solve
   int* stop_host = nullptr;                                       // pinned: ctl->stop read back per direct step
+  bool ext_desc = false;  // desc/info live in a batch's buffers (not owned)
   ~SolvePlan() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
-    if (desc_host) cudaFreeHost(desc_host);
-    if (info_host) cudaFreeHost(info_host);
+    if (desc_host && !ext_desc) cudaFreeHost(desc_host);
+    if (info_host && !ext_desc) cudaFreeHost(info_host);
     if (stop_host) cudaFreeHost(stop_host);
+  }
+};
+
+// A batch of independent solves replayed as one CUDA graph: one branch per
+// problem (its prologue, device-side loop and epilogue), descriptors and
+// info records contiguous so that one copy each way serves the batch.
+struct BatchPlan {
+  std::vector<std::shared_ptr<SolvePlan>> plans;
+  DevBuf small;
+  char* desc_host = nullptr;     // pinned, nprob descriptors then nprob info records
+  size_t desc_stride = 0, info_stride = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  ~BatchPlan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    plans.clear();
+    if (desc_host) cudaFreeHost(desc_host);
   }
 };
 
@@ -545,6 +567,7 @@ struct rtg_context {
   std::map<std::string, std::unique_ptr<DevBuf>> sketches;   // signs, fragments and scratch per sketch
   DevBuf tA, tB;
   std::map<std::string, std::shared_ptr<SolvePlan>> plans;
+  std::map<std::string, std::unique_ptr<BatchPlan>> batches;
   std::unique_ptr<PhaseTimer> timer;
   // per workspace slot: the plan and call state of the last submitted solve
   struct Pending {
@@ -678,7 +701,9 @@ rtg_status enqueue_epilogue(SolvePlan& P, cudaStream_t s, PhaseTimer* pt = nullp
   return RTG_OK;
 }
 
-rtg_status build_graph(SolvePlan& P) {
+// Captures P's solve (prologue, a WHILE node over one Arnoldi step, epilogue)
+// into g as a branch with no dependencies on the rest of g.
+rtg_status build_branch(SolvePlan& P, cudaGraph_t g) {
   cudaStream_t cs = nullptr, cs2 = nullptr;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   CK(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
@@ -689,8 +714,6 @@ rtg_status build_graph(SolvePlan& P) {
       cudaStreamDestroy(b);
     }
   } sg{cs, cs2};
-  cudaGraph_t g = nullptr;
-  CK(cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle hnd;
   CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
   const StepOpts so = solve_step_opts(P, 1, hnd);
@@ -733,9 +756,16 @@ rtg_status build_graph(SolvePlan& P) {
   cudaGraph_t gout = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &gout);
   if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture");
+  if (st != RTG_OK) cudaGetLastError();
+  return st;
+}
+
+rtg_status build_graph(SolvePlan& P) {
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  const rtg_status st = build_branch(P, g);
   if (st != RTG_OK) {
     cudaGraphDestroy(g);
-    cudaGetLastError();
     return st;
   }
   P.graph = g;
@@ -746,6 +776,129 @@ rtg_status build_graph(SolvePlan& P) {
 }  // namespace
 
 // ================================================================== C ABI
+
+// Everything a solve plan is built from.
+struct PlanSpec {
+  const rtg_factor* A;
+  int nA;
+  const rtg_factor* B;
+  int nB;
+  rtg_shape shape;
+  int dtype, vdtype;
+  int64_t n;
+  int m;
+  SketchPlan sp;
+  int mode, n_mu;
+  bool has_x0, use_graph;
+};
+
+// Builds a plan: operator, workspace, descriptor / info record (in the
+// given batch buffers, or its own), launch counts and, for a stand-alone
+// graph solve, its CUDA graph.  Builds only while nothing of the handle runs.
+rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDesc* dhost, InfoDev* ihost,
+                     std::shared_ptr<SolvePlan>* out) {
+  const rtg_factor* A = ps.A;
+  const rtg_factor* B = ps.B;
+  const int nA = ps.nA, nB = ps.nB, dtype = ps.dtype, vdtype = ps.vdtype, m = ps.m, mode = ps.mode;
+  const int n_mu = ps.n_mu;
+  const bool has_x0 = ps.has_x0, use_graph = ps.use_graph;
+  const rtg_shape& shape = ps.shape;
+  const int64_t n = ps.n;
+  const SketchPlan& sp = ps.sp;
+  auto np = std::make_shared<SolvePlan>();
+  SolvePlan* P = np.get();
+  P->dtype = dtype;
+  P->mode = mode;
+  P->n_mu = n_mu;
+  P->has_x0 = has_x0;
+  P->use_graph = use_graph;
+  P->sp = sp;
+  RK(build_op(A, nA, B, nB, shape, P->op));
+  P->vdtype = vdtype;
+  if (vdtype == RTG_BF16 && !st_supported(P->op.op, RTG_BF16))
+    return fail(RTG_ERR_UNSUPPORTED, "RTG_FLAG_BF16_BASIS needs banded modes 1-2 (radius <= 9), a mode-3 mix "
+                                     "of 1 or 3 channels, a mode-4 band of radius <= 2 and dims[0] %% 8 == 0");
+  const int64_t ae = apply_scratch_elems(P->op.op);
+  const int tkb = mode == 2 ? n_mu : 1;
+  Work tmpw;
+  void *ta, *tb;
+  SketchScratch tsk;
+  const size_t bytes = carve_work(nullptr, dtype, n, sp, m, tkb, ae, tmpw, &ta, &tb, &tsk, vdtype);
+  RK(P->mem.ensure(bytes));
+  CK(cudaMemset(P->mem.p, 0, bytes));
+  carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk, vdtype);
+  if (ddev != nullptr) {   // descriptor and info record in a batch's buffers
+    P->ext_desc = true;
+    P->desc_dev = ddev;
+    P->info_dev = idev;
+    P->desc_host = dhost;
+    P->info_host = ihost;
+  } else {
+    RK(P->small.ensure(sizeof(SolveDesc) + sizeof(InfoDev) + 512));
+    P->desc_dev = static_cast<SolveDesc*>(P->small.p);
+    P->info_dev = reinterpret_cast<InfoDev*>(static_cast<char*>(P->small.p) + ((sizeof(SolveDesc) + 255) & ~size_t(255)));
+    CK(cudaMallocHost(&P->desc_host, sizeof(SolveDesc)));
+    CK(cudaMallocHost(&P->info_host, sizeof(InfoDev)));
+    std::memset(P->desc_host, 0, sizeof(SolveDesc));
+    CK(cudaMemset(P->small.p, 0, P->small.bytes));
+  }
+  CK(cudaMallocHost(&P->stop_host, sizeof(int)));
+  CK(cudaEventCreate(&P->ev0));
+  CK(cudaEventCreate(&P->ev1));
+  {
+    int nsk = 0;
+    for (int k = 0; k < sp.order; ++k) nsk += sp.sketched[k];
+    const int gs = sp.fused_dots ? 0 : 1;
+    P->launches_setup = 1 + (nsk > 0 ? (dtype == RTG_F32 ? 2 : 1) : 0);
+    P->launches_pro = P->launches_setup +
+                      (has_x0 ? apply_launches(P->op.op, true, dtype, dtype, vdtype) : 0) +
+                      sketch_launches(sp) + gs + 1;
+    P->launches_step = apply_launches(P->op.op, false, dtype, vdtype, vdtype) + sketch_launches(sp) + gs + 1;
+    P->launches_epi = 3;
+  }
+  if (use_graph && ddev == nullptr) RK(build_graph(*P));
+  *out = std::move(np);
+  return RTG_OK;
+}
+
+// Host summary of a finished solve from its info record.
+void fill_info(const SolvePlan& P, const InfoDev& I, int mode, int n_mu, bool use_graph, float ms,
+               rtg_info* info) {
+  info->iters = I.iters;
+  info->restarts = I.restarts;
+  info->breakdown = I.breakdown;
+  info->converged = I.converged;
+  info->beta = I.beta;
+  info->mu = I.mu;
+  info->rho_final = I.rho_final;
+  if (info->rho_hist)
+    for (int i = 0; i < I.iters && i < kMaxK; ++i) info->rho_hist[i] = I.rho_hist[i];
+  if (info->gcv && mode == 2)
+    for (int i = 0; i < n_mu; ++i) info->gcv[i] = I.gcv[i];
+  info->true_rel_resid = -1.0;
+  info->elapsed_ms = ms;
+  info->device_status = I.status;
+  info->launches = P.launches_pro + P.launches_epi + (use_graph ? I.iters : P.direct_steps) * P.launches_step;
+  for (int k = 0; k < RTG_PHASE_COUNT; ++k) {
+    info->phase_ms[k] = 0.0;
+    info->phase_launches[k] = 0;
+  }
+}
+
+// Per-call descriptor of a solve.
+void fill_desc(SolveDesc& D, const void* C, const void* X0, void* X, uint64_t seed, double tol,
+               double bd_tol, int dtype, double lambda, int n_mu, const double* mu_grid) {
+  D.C = C;
+  D.X0 = X0;
+  D.X = X;
+  D.key[0] = seed;
+  D.key[1] = 0;
+  D.tol = tol;
+  D.bd_tol = bd_tol > 0 ? bd_tol : (dtype == RTG_F64 ? 1e-12 : 1e-6);
+  D.lambda = lambda;
+  D.n_mu = n_mu;
+  for (int i = 0; i < n_mu; ++i) D.mu_grid[i] = mu_grid[i];
+}
 
 extern "C" {
 
@@ -1057,50 +1210,10 @@ rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const
     // does so only while no other solve of this handle is in flight.
     for (const auto& q : h->pending)
       if (q.active) CK(cudaStreamSynchronize(q.stream));
-    auto np = std::make_shared<SolvePlan>();
+    PlanSpec ps{A, nA, B, nB, shape, dtype, vdtype, n, m, sp, mode, nmu_key, has_x0, use_graph};
+    std::shared_ptr<SolvePlan> np;
+    RK(make_plan(ps, nullptr, nullptr, nullptr, nullptr, &np));
     P = np.get();
-    P->dtype = dtype;
-    P->mode = mode;
-    P->n_mu = nmu_key;
-    P->has_x0 = has_x0;
-    P->use_graph = use_graph;
-    P->sp = sp;
-    RK(build_op(A, nA, B, nB, shape, P->op));
-    P->vdtype = vdtype;
-    if (vdtype == RTG_BF16 && !st_supported(P->op.op, RTG_BF16))
-      return fail(RTG_ERR_UNSUPPORTED, "RTG_FLAG_BF16_BASIS needs banded modes 1-2 (radius <= 9), a mode-3 mix "
-                                       "of 1 or 3 channels, a mode-4 band of radius <= 2 and dims[0] %% 8 == 0");
-    const int64_t ae = apply_scratch_elems(P->op.op);
-    const int tkb = mode == 2 ? opts.n_mu : 1;
-    Work tmpw;
-    void *ta, *tb;
-    SketchScratch tsk;
-    const size_t bytes = carve_work(nullptr, dtype, n, sp, m, tkb, ae, tmpw, &ta, &tb, &tsk, vdtype);
-    RK(P->mem.ensure(bytes));
-    CK(cudaMemset(P->mem.p, 0, bytes));
-    carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk, vdtype);
-    RK(P->small.ensure(sizeof(SolveDesc) + sizeof(InfoDev) + 512));
-    P->desc_dev = static_cast<SolveDesc*>(P->small.p);
-    P->info_dev = reinterpret_cast<InfoDev*>(static_cast<char*>(P->small.p) + ((sizeof(SolveDesc) + 255) & ~size_t(255)));
-    CK(cudaMallocHost(&P->desc_host, sizeof(SolveDesc)));
-    CK(cudaMallocHost(&P->info_host, sizeof(InfoDev)));
-    CK(cudaMallocHost(&P->stop_host, sizeof(int)));
-    std::memset(P->desc_host, 0, sizeof(SolveDesc));
-    CK(cudaMemset(P->small.p, 0, P->small.bytes));
-    CK(cudaEventCreate(&P->ev0));
-    CK(cudaEventCreate(&P->ev1));
-    {
-      int nsk = 0;
-      for (int k = 0; k < sp.order; ++k) nsk += sp.sketched[k];
-      const int gs = sp.fused_dots ? 0 : 1;
-      P->launches_setup = 1 + (nsk > 0 ? (dtype == RTG_F32 ? 2 : 1) : 0);
-      P->launches_pro = P->launches_setup +
-                        (has_x0 ? apply_launches(P->op.op, true, dtype, dtype, vdtype) : 0) +
-                        sketch_launches(sp) + gs + 1;
-      P->launches_step = apply_launches(P->op.op, false, dtype, vdtype, vdtype) + sketch_launches(sp) + gs + 1;
-      P->launches_epi = 3;
-    }
-    if (use_graph) RK(build_graph(*P));
     h->plans[key] = np;
     hold = np;
   } else {
@@ -1204,38 +1317,145 @@ rtg_status rtg_gmres_wait(rtg_handle h, int32_t slot, rtg_info* info) {
   pend.active = false;
   DeviceGuard dg(h->device);
   SolvePlan* P = pend.plan.get();
-  const int m = pend.m, mode = pend.mode;
+  const int mode = pend.mode;
   const bool use_graph = pend.use_graph, phase_times = pend.phase_times;
   CK(cudaStreamSynchronize(pend.stream));
   const InfoDev& I = *P->info_host;
   if (info) {
-    info->iters = I.iters;
-    info->restarts = I.restarts;
-    info->breakdown = I.breakdown;
-    info->converged = I.converged;
-    info->beta = I.beta;
-    info->mu = I.mu;
-    info->rho_final = I.rho_final;
-    if (info->rho_hist)
-      for (int i = 0; i < I.iters && i < kMaxK; ++i) info->rho_hist[i] = I.rho_hist[i];
-    if (info->gcv && mode == 2)
-      for (int i = 0; i < pend.n_mu; ++i) info->gcv[i] = I.gcv[i];
-    info->true_rel_resid = -1.0;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, P->ev0, P->ev1);
-    info->elapsed_ms = ms;
-    info->device_status = I.status;
-    info->launches = P->launches_pro + P->launches_epi +
-                     (use_graph ? I.iters : P->direct_steps) * P->launches_step;
-    for (int k = 0; k < RTG_PHASE_COUNT; ++k) {
-      info->phase_ms[k] = 0.0;
-      info->phase_launches[k] = 0;
-    }
+    fill_info(*P, I, mode, pend.n_mu, use_graph, ms, info);
     if (phase_times) h->timer->collect(I.iters, info);
   }
   if (phase_times && h->timer->host[1] != 0) {
     return fail(RTG_ERR_TIMEOUT, "phase timing: a gate waited 2 s for the host to queue its group");
   }
+  return RTG_OK;
+}
+
+rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_problem* probs,
+                                   rtg_dtype dtype, const rtg_opts* opts_in, rtg_info* infos,
+                                   rtg_stream stream) {
+  if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
+  if (nprob < 1 || nprob > RTG_MAX_BATCH) return fail(RTG_ERR_INVALID_ARG, "nprob=%d not in 1..%d", nprob, RTG_MAX_BATCH);
+  if (probs == nullptr) return fail(RTG_ERR_INVALID_ARG, "probs is NULL");
+  RK(check_dtype(dtype));
+  rtg_opts opts{};
+  if (opts_in) opts = *opts_in;
+  if (opts.max_restarts != 0) return fail(RTG_ERR_UNSUPPORTED, "restarts are not supported on the GPU path");
+  if (opts.flags & (RTG_FLAG_NO_GRAPH | RTG_FLAG_PHASE_TIMES))
+    return fail(RTG_ERR_UNSUPPORTED, "batched solves run as one CUDA graph (no direct or phase-timed launch)");
+  if (!(opts.breakdown_tol >= 0.0)) return fail(RTG_ERR_INVALID_ARG, "opts.breakdown_tol must be >= 0");
+  const int vdtype = (opts.flags & RTG_FLAG_BF16_BASIS) ? RTG_BF16 : dtype;
+  if (vdtype == RTG_BF16 && dtype != RTG_F32) return fail(RTG_ERR_UNSUPPORTED, "RTG_FLAG_BF16_BASIS needs dtype RTG_F32");
+  DeviceGuard dg(h->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // validate every problem and form its plan key (problem index included:
+  // each branch owns its workspace)
+  std::vector<PlanSpec> specs(nprob);
+  std::string bkey;
+  append_bytes(bkey, &dtype, sizeof dtype);
+  append_bytes(bkey, &vdtype, sizeof vdtype);
+  for (int i = 0; i < nprob; ++i) {
+    const rtg_problem& q = probs[i];
+    int64_t n = 0;
+    RK(check_shape(q.shape, &n));
+    RK(check_factors(q.A_factors, q.nA, q.shape, "A_factors"));
+    RK(check_factors(q.B_factors, q.nB, q.shape, "B_factors"));
+    if (q.m < 1 || q.m > kMaxK) return fail(RTG_ERR_INVALID_ARG, "problem %d: m=%d not in 1..%d", i, q.m, kMaxK);
+    if (q.C == nullptr || q.X == nullptr) return fail(RTG_ERR_INVALID_ARG, "problem %d: C and X must not be NULL", i);
+    if (!is_device_ptr(q.C) || !is_device_ptr(q.X) || (q.X0 && !is_device_ptr(q.X0)))
+      return fail(RTG_ERR_INVALID_ARG, "problem %d: batched solves take device pointers", i);
+    const size_t bytes_t = size_t(n) * elt_size(dtype);
+    if (q.X0 != nullptr && q.X0 != q.X && overlaps(q.X0, q.X, bytes_t)) return fail(RTG_ERR_INVALID_ARG, "problem %d: X partially overlaps X0", i);
+    if (overlaps(q.C, q.X, bytes_t)) return fail(RTG_ERR_INVALID_ARG, "problem %d: X overlaps C", i);
+    if (!std::isfinite(q.lam) || !(q.tol >= 0.0) || !std::isfinite(q.tol))
+      return fail(RTG_ERR_INVALID_ARG, "problem %d: lambda and tol must be finite, tol >= 0", i);
+    const int mode = q.lam > 0 ? 1 : (q.lam == 0 ? 0 : 2);
+    if (mode == 2) {
+      if (opts.n_mu < 1 || opts.n_mu > kMaxMu || opts.mu_grid == nullptr)
+        return fail(RTG_ERR_INVALID_ARG, "lambda < 0 needs opts.mu_grid with 1..%d values", kMaxMu);
+      for (int k = 0; k < opts.n_mu; ++k)
+        if (!(opts.mu_grid[k] > 0.0) || !std::isfinite(opts.mu_grid[k])) return fail(RTG_ERR_INVALID_ARG, "mu_grid[%d] must be finite and > 0", k);
+    }
+    SketchPlan sp;
+    RK(build_sketch(q.shape, q.sketch_dims, q.seed, 0, dtype, sp));
+    if (vdtype == RTG_BF16 && (sp.nstage == 0 || !sp.stage_first[0]))
+      return fail(RTG_ERR_UNSUPPORTED, "problem %d: RTG_FLAG_BF16_BASIS needs mode 1 sketched", i);
+    const int nmu = mode == 2 ? opts.n_mu : 0;
+    specs[i] = PlanSpec{q.A_factors, q.nA, q.B_factors, q.nB, q.shape, dtype, vdtype, n, q.m, sp, mode, nmu,
+                        q.X0 != nullptr, true};
+    std::string key = op_key(q.A_factors, q.nA, q.B_factors, q.nB, q.shape);
+    append_bytes(key, &q.m, sizeof q.m);
+    append_bytes(key, sp.sdims, sizeof sp.sdims);
+    append_bytes(key, &mode, sizeof mode);
+    append_bytes(key, &nmu, sizeof nmu);
+    key.push_back(q.X0 ? '1' : '0');
+    const uint32_t len = static_cast<uint32_t>(key.size());
+    append_bytes(bkey, &len, sizeof len);
+    bkey += key;
+  }
+  auto it = h->batches.find(bkey);
+  BatchPlan* BP = nullptr;
+  if (it == h->batches.end()) {
+    // building allocates and instantiates: nothing of this handle may run
+    CK(cudaDeviceSynchronize());
+    if (h->batches.size() >= 4) h->batches.clear();
+    auto nb = std::make_unique<BatchPlan>();
+    BP = nb.get();
+    BP->desc_stride = (sizeof(SolveDesc) + 255) & ~size_t(255);
+    BP->info_stride = (sizeof(InfoDev) + 255) & ~size_t(255);
+    const size_t total = size_t(nprob) * (BP->desc_stride + BP->info_stride);
+    RK(BP->small.ensure(total));
+    CK(cudaMemset(BP->small.p, 0, total));
+    CK(cudaMallocHost(&BP->desc_host, total));
+    std::memset(BP->desc_host, 0, total);
+    char* dd = static_cast<char*>(BP->small.p);
+    char* dh = BP->desc_host;
+    const size_t info0 = size_t(nprob) * BP->desc_stride;
+    CK(cudaGraphCreate(&BP->graph, 0));
+    for (int i = 0; i < nprob; ++i) {
+      std::shared_ptr<SolvePlan> pl;
+      RK(make_plan(specs[i], reinterpret_cast<SolveDesc*>(dd + i * BP->desc_stride),
+                   reinterpret_cast<InfoDev*>(dd + info0 + i * BP->info_stride),
+                   reinterpret_cast<SolveDesc*>(dh + i * BP->desc_stride),
+                   reinterpret_cast<InfoDev*>(dh + info0 + i * BP->info_stride), &pl));
+      RK(build_branch(*pl, BP->graph));
+      BP->plans.push_back(std::move(pl));
+    }
+    CK(cudaGraphInstantiate(&BP->exec, BP->graph, 0));
+    CK(cudaEventCreate(&BP->ev0));
+    CK(cudaEventCreate(&BP->ev1));
+    h->batches[bkey] = std::move(nb);
+  } else {
+    BP = it->second.get();
+  }
+  for (int i = 0; i < nprob; ++i) {
+    const rtg_problem& q = probs[i];
+    SolvePlan& P = *BP->plans[i];
+    if (q.X0 && apply_uses_st(P.op.op, dtype, dtype, vdtype) && reinterpret_cast<uintptr_t>(q.X0) % 16 != 0)
+      return fail(RTG_ERR_INVALID_ARG, "problem %d: X0 must be 16-byte aligned for this operator", i);
+    if (vdtype == RTG_BF16 && reinterpret_cast<uintptr_t>(q.C) % 16 != 0)
+      return fail(RTG_ERR_INVALID_ARG, "problem %d: C must be 16-byte aligned with RTG_FLAG_BF16_BASIS", i);
+    fill_desc(*P.desc_host, q.C, q.X0, q.X, q.seed, q.tol, opts.breakdown_tol, dtype, q.lam,
+              P.mode == 2 ? opts.n_mu : 0, opts.mu_grid);
+  }
+  const size_t dbytes = size_t(nprob) * BP->desc_stride;
+  const size_t ibytes = size_t(nprob) * BP->info_stride;
+  CK(cudaMemcpyAsync(BP->small.p, BP->desc_host, dbytes, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(BP->ev0, s));
+  CK(cudaGraphLaunch(BP->exec, s));
+  CK(cudaEventRecord(BP->ev1, s));
+  CK(cudaMemcpyAsync(BP->desc_host + dbytes, static_cast<char*>(BP->small.p) + dbytes, ibytes,
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, BP->ev0, BP->ev1);
+  if (infos)
+    for (int i = 0; i < nprob; ++i) {
+      const SolvePlan& P = *BP->plans[i];
+      fill_info(P, *P.info_host, P.mode, P.n_mu, true, ms, &infos[i]);
+    }
   return RTG_OK;
 }
 

@@ -101,7 +101,7 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
     C compiler gives the structs of include/rtg.h."""
     from paper_2603_00839_gb300 import _lib as L
     structs = {"rtg_shape": L.Shape, "rtg_factor": L.Factor, "rtg_opts": L.Opts,
-               "rtg_info": L.Info, "rtg_krylov_view": L.KrylovView}
+               "rtg_info": L.Info, "rtg_krylov_view": L.KrylovView, "rtg_problem": L.Problem}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rtg.h"', 'int main(void) {']
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
