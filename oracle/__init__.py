@@ -31,5 +31,6 @@ from .krylov import (sketched_arnoldi, frobenius_arnoldi, rtg_gmres, tg_gmres,
 from .tikhonov import (tikhonov_stacked, tikhonov_normal, tikhonov_svd, gcv_value,
                        gcv_choose)
 from .metrics import make_observation, relative_error, psnr, rho_star
+from .golub_kahan import transpose_mats, sketched_golub_kahan, sketched_gk_solve
 
 __all__ = [n for n in dir() if not n.startswith("_")]
