@@ -319,6 +319,29 @@ rtg_status rtg_gmres_submit(rtg_handle handle,
                             const rtg_opts* opts, rtg_stream stream);
 rtg_status rtg_gmres_wait(rtg_handle handle, int32_t slot, rtg_info* info);
 
+/*
+ * Sketched Golub-Kahan (Algorithm 4, "Block Golub-Kahan via Sketched
+ * Einstein Product") for the same problem and with the same arguments as
+ * rtg_gmres_solve: R_0 = C - Phi(X_0), beta_1 = ||R_0||_Theta,
+ * U_1 = R_0 / beta_1, alpha_1 V_1 = Phi^T(U_1); for k = 1, 2, ...:
+ * beta_{k+1} U_{k+1} = Phi(V_k) - alpha_k U_k,
+ * alpha_{k+1} V_{k+1} = Phi^T(U_{k+1}) - beta_{k+1} V_k, with Theta-norms
+ * (only norms are sketched; short recurrences, no re-orthogonalisation).
+ * Phi^T is the adjoint of Phi (every mode matrix transposed).  The lower
+ * bidiagonal Btilde_k takes the place of Hbar_k: rho_k, the stop rule, the
+ * projected Tikhonov / GCV solve (Eq. 13) and X = X_0 + sum y_k V_k are as
+ * for RTG-GMRES.  Stops also when alpha_{k+1} falls to the breakdown level.
+ * Memory: m+1 tensors V plus two U.  RTG_FLAG_BF16_BASIS is not available.
+ * Errors: as rtg_gmres_solve.
+ */
+rtg_status rtg_gk_solve(rtg_handle handle,
+                        const rtg_factor* A_factors, int32_t nA,
+                        const rtg_factor* B_factors, int32_t nB,
+                        rtg_shape shape, rtg_dtype dtype,
+                        const void* C, int32_t m, const int64_t* sketch_dims,
+                        uint64_t seed, double lambda, const void* X0, void* X,
+                        const rtg_opts* opts, rtg_info* info, rtg_stream stream);
+
 /* One problem of a batched solve: the arguments of rtg_gmres_solve. */
 typedef struct rtg_problem {
     const rtg_factor* A_factors;

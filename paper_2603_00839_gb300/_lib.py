@@ -98,6 +98,10 @@ _SIGS = {
                                    C.POINTER(C.c_int64), C.c_uint64, C.c_double, C.c_void_p,
                                    C.c_void_p, C.POINTER(Opts), C.c_void_p]),
     "rtg_gmres_wait": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Info)]),
+    "rtg_gk_solve": (C.c_int, [C.c_void_p, C.POINTER(Factor), C.c_int32, C.POINTER(Factor),
+                               C.c_int32, Shape, C.c_int, C.c_void_p, C.c_int32,
+                               C.POINTER(C.c_int64), C.c_uint64, C.c_double, C.c_void_p,
+                               C.c_void_p, C.POINTER(Opts), C.POINTER(Info), C.c_void_p]),
     "rtg_gmres_solve_batched": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Problem), C.c_int,
                                           C.POINTER(Opts), C.POINTER(Info), C.c_void_p]),
     "rtg_sketch_noalloc": (C.c_int, [Shape, C.c_int, C.POINTER(C.c_int64), C.c_uint64, C.c_uint64,

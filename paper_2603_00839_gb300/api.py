@@ -233,6 +233,43 @@ class Handle:
                                  stream=stream)
         return self.gmres_wait(pend)
 
+    def gk_solve(self, C_obs, m: int, sketch_dims: Sequence[int], seed: int, lam: float,
+                 A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (),
+                 X0=None, X=None, tol: float = 0.0, mu_grid=None, breakdown_tol: float = 0.0,
+                 use_graph: bool = True, phase_times: bool = False, slot: int = 0, stream=None):
+        """Sketched Golub-Kahan (rtg_gk_solve): same problem and arguments as
+        gmres_solve (device tensors).  Returns (X, SolveResult)."""
+        dims = tuple(C_obs.shape)
+        _check_tensor(C_obs, dims, "C")
+        if X is None:
+            X = empty(dims, C_obs.dtype, C_obs.device)
+        a, na, ka = _factor_array(A_factors)
+        b, nb, kb = _factor_array(B_factors)
+        sk = (C.c_int64 * len(dims))(*[int(s) for s in sketch_dims])
+        opts = L.Opts()
+        opts.tol = float(tol)
+        grid = None
+        if mu_grid is not None:
+            grid = np.ascontiguousarray(mu_grid, dtype=np.float64)
+            opts.mu_grid = grid.ctypes.data_as(C.POINTER(C.c_double))
+            opts.n_mu = len(grid)
+        opts.breakdown_tol = float(breakdown_tol)
+        opts.flags = (0 if use_graph else L.FLAG_NO_GRAPH) | (L.FLAG_PHASE_TIMES if phase_times else 0)
+        opts.slot = int(slot)
+        info = L.Info()
+        rho = np.zeros(m + 1)
+        info.rho_hist = rho.ctypes.data_as(C.POINTER(C.c_double))
+        gcv = np.zeros(L.MAX_MU)
+        info.gcv = gcv.ctypes.data_as(C.POINTER(C.c_double))
+        L.check(self.lib.rtg_gk_solve(self._h, a, na, b, nb, _shape(dims), _dtype_code(C_obs), _ptr(C_obs),
+                                      int(m), sk, C.c_uint64(seed), float(lam), _ptr(X0), _ptr(X),
+                                      C.byref(opts), C.byref(info), _stream(stream)))
+        res = _solve_result(info, rho, gcv, grid, lam)
+        if phase_times:
+            res.phase_ms = {k: info.phase_ms[i] for i, k in enumerate(L.PHASES)}
+            res.phase_launches = {k: info.phase_launches[i] for i, k in enumerate(L.PHASES)}
+        return X, res
+
     def gmres_submit(self, C_obs, m: int, sketch_dims: Sequence[int], seed: int, lam: float,
                      A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (),
                      X0=None, X=None, tol: float = 0.0, mu_grid=None, max_restarts: int = 0,

@@ -362,7 +362,7 @@ struct Carver {
 // Lays out (and, with mem != null, points) every buffer of an Arnoldi workspace.
 size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, int tk_blocks,
                   int64_t apply_elems, Work& w, void** tA, void** tB, SketchScratch* sk,
-                  int vdtype = -1) {
+                  int vdtype = -1, int nU = 0) {
   Carver c(mem);
   const size_t e = elt_size(dtype);
   if (vdtype < 0) vdtype = dtype;
@@ -376,8 +376,10 @@ size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, 
   w.m = m;
   int64_t G = gs_grid(d);
   if (sp.dots_blocks > G) G = sp.dots_blocks;
+  if (nU > 0 && G < 1024) G = 1024;   // Golub-Kahan norm reductions
   w.V = c.take<char>(size_t(m + 1) * n * ev);
   w.W = c.take<char>(size_t(n) * ev);
+  w.U = nU > 0 ? c.take<char>(size_t(nU) * n * ev) : nullptr;
   w.S = c.take<char>(size_t(d) * e);
   w.Spart = c.take<char>(size_t(d) * e);
   w.nparts = 1;
@@ -416,6 +418,8 @@ struct rtg_context;
 
 struct SolvePlan {
   OpHolder op;
+  OpHolder opT;           // Golub-Kahan: the adjoint operator
+  int method = 0;         // 0 RTG-GMRES, 1 sketched Golub-Kahan
   SketchPlan sp{};
   DevBuf mem;
   Work w{};
@@ -684,6 +688,82 @@ rtg_status enqueue_step(const OpHolder& op, const SketchPlan& sp, const Work& w,
   return RTG_OK;
 }
 
+// Sketched Golub-Kahan (Algorithm 4): prologue U_0, alpha_0, V_0 and one step
+// (forward half: beta_{j+1}, U_{j+1}, Givens; backward half: alpha_{j+1}, V_{j+1}).
+rtg_status enqueue_gk_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s, PhaseTimer* pt = nullptr) {
+  Work& w = P.w;
+  {
+    PhaseScope ps(pt, RTG_PHASE_SETUP, -1, P.launches_setup);
+    CK(launch_reset(w, 0, s));
+    CK(launch_theta(P.sp, P.sk.bits, P.sk.frags, s, P.desc_dev->key));
+  }
+  PhaseScope ps(pt, RTG_PHASE_INIT, -1, P.launches_pro - P.launches_setup);
+  PtrRef C = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->C));
+  PtrRef src = C;
+  if (P.has_x0) {   // R_0 = C - Phi(X_0) into W
+    PtrRef X0 = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X0));
+    CK(launch_apply(P.op.op, P.dtype, X0, ref(w.W), -1.0, 1.0, C, P.tA, P.tB, nullptr, s));
+    src = ref(w.W);
+  }
+  CK(launch_sketch(P.sp, P.sk, src, w.S, nullptr, nullptr, s));
+  CK(launch_gk_norm(w, 0, so, s));
+  CK(launch_gk_update(w, 0, src, so, s));
+  const int* stop = &w.ctl->stop;
+  CK(launch_apply(P.opT.op, P.dtype, ref(w.U), ref(w.W), 1.0, 0.0, PtrRef{}, P.tA, P.tB, stop, s));
+  CK(launch_sketch(P.sp, P.sk, ref(w.W), w.S, nullptr, stop, s));
+  CK(launch_gk_norm(w, 1, so, s));
+  CK(launch_gk_update(w, 1, PtrRef{}, so, s));
+  return RTG_OK;
+}
+
+rtg_status enqueue_gk_step(SolvePlan& P, const StepOpts& so, cudaStream_t s, PhaseTimer* pt = nullptr,
+                           int step = 0) {
+  Work& w = P.w;
+  const int* stop = &w.ctl->stop;
+  PtrRef vj;   // V_j, j = ctl->j
+  vj.base = w.V;
+  vj.jidx = &w.ctl->j;
+  vj.stride = w.n;
+  PtrRef uj;   // U_{j+1} after the forward half advanced j: ring slot j % 2
+  uj.base = w.U;
+  uj.jidx = &w.ctl->j;
+  uj.stride = w.n;
+  uj.mod = 2;
+  const int al = apply_launches(P.op.op, false, P.dtype, P.dtype, P.dtype);
+  const int alT = apply_launches(P.opT.op, false, P.dtype, P.dtype, P.dtype);
+  {
+    PhaseScope ps(pt, RTG_PHASE_APPLY, step, al);
+    CK(launch_apply(P.op.op, P.dtype, vj, ref(w.W), 1.0, 0.0, PtrRef{}, P.tA, P.tB, stop, s));
+  }
+  {
+    PhaseScope ps(pt, RTG_PHASE_SKETCH, step, sketch_launches(P.sp));
+    CK(launch_sketch(P.sp, P.sk, ref(w.W), w.S, nullptr, stop, s));
+  }
+  {
+    PhaseScope ps(pt, RTG_PHASE_GS, step, 1);
+    CK(launch_gk_norm(w, 2, so, s));
+  }
+  {
+    PhaseScope ps(pt, RTG_PHASE_UPDATE, step, 1);
+    CK(launch_gk_update(w, 2, PtrRef{}, so, s));
+  }
+  {
+    PhaseScope ps(pt, RTG_PHASE_APPLY, step, alT);
+    CK(launch_apply(P.opT.op, P.dtype, uj, ref(w.W), 1.0, 0.0, PtrRef{}, P.tA, P.tB, stop, s));
+  }
+  {
+    PhaseScope ps(pt, RTG_PHASE_SKETCH, step, sketch_launches(P.sp));
+    CK(launch_sketch(P.sp, P.sk, ref(w.W), w.S, nullptr, stop, s));
+  }
+  {
+    PhaseScope ps(pt, RTG_PHASE_GS, step, 1);
+    CK(launch_gk_norm(w, 3, so, s));
+  }
+  PhaseScope ps(pt, RTG_PHASE_UPDATE, step, 1);
+  CK(launch_gk_update(w, 3, PtrRef{}, so, s));
+  return RTG_OK;
+}
+
 rtg_status enqueue_epilogue(SolvePlan& P, cudaStream_t s, PhaseTimer* pt = nullptr) {
   FinishOpts f{};
   f.desc = P.desc_dev;
@@ -718,7 +798,7 @@ rtg_status build_branch(SolvePlan& P, cudaGraph_t g) {
   CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
   const StepOpts so = solve_step_opts(P, 1, hnd);
   CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  rtg_status st = enqueue_prologue(P, so, cs);
+  rtg_status st = P.method == 1 ? enqueue_gk_prologue(P, so, cs) : enqueue_prologue(P, so, cs);
   cudaStreamCaptureStatus cst;
   cudaGraph_t gcap = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -746,7 +826,8 @@ rtg_status build_branch(SolvePlan& P, cudaGraph_t g) {
     cudaError_t e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCaptureToGraph(body)");
     if (st == RTG_OK) {
-      st = enqueue_step(P.op, P.sp, P.w, P.dtype, P.tA, P.tB, P.sk, so, cs2);
+      st = P.method == 1 ? enqueue_gk_step(P, so, cs2)
+                         : enqueue_step(P.op, P.sp, P.w, P.dtype, P.tA, P.tB, P.sk, so, cs2);
       cudaGraph_t bodyout = nullptr;
       e = cudaStreamEndCapture(cs2, &bodyout);
       if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture(body)");
@@ -790,6 +871,31 @@ struct PlanSpec {
   SketchPlan sp;
   int mode, n_mu;
   bool has_x0, use_graph;
+  int method = 0;   // 0 RTG-GMRES, 1 sketched Golub-Kahan
+};
+
+// Factors of the adjoint operator: every mode matrix transposed (banded:
+// taps reversed; dense: the matrix transposed).
+struct TransposedFactors {
+  std::vector<rtg_factor> f;
+  std::vector<std::vector<double>> data;
+  TransposedFactors(const rtg_factor* in, int nf) {
+    f.assign(in, in + nf);
+    data.resize(nf);
+    for (int i = 0; i < nf; ++i) {
+      const rtg_factor& x = in[i];
+      if (x.kind == RTG_FACTOR_BANDED_TOEPLITZ) {
+        data[i].assign(x.taps, x.taps + 2 * x.radius + 1);
+        std::reverse(data[i].begin(), data[i].end());
+        f[i].taps = data[i].data();
+      } else if (x.kind == RTG_FACTOR_DENSE) {
+        data[i].resize(size_t(x.n) * x.n);
+        for (int a = 0; a < x.n; ++a)
+          for (int b = 0; b < x.n; ++b) data[i][a + size_t(x.n) * b] = x.dense[b + size_t(x.n) * a];
+        f[i].dense = data[i].data();
+      }
+    }
+  }
 };
 
 // Builds a plan: operator, workspace, descriptor / info record (in the
@@ -813,20 +919,27 @@ rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDe
   P->has_x0 = has_x0;
   P->use_graph = use_graph;
   P->sp = sp;
+  P->method = ps.method;
   RK(build_op(A, nA, B, nB, shape, P->op));
+  if (ps.method == 1) {
+    TransposedFactors tA(A, nA), tB(B, nB);
+    RK(build_op(tA.f.data(), nA, tB.f.data(), nB, shape, P->opT));
+  }
   P->vdtype = vdtype;
   if (vdtype == RTG_BF16 && !st_supported(P->op.op, RTG_BF16))
     return fail(RTG_ERR_UNSUPPORTED, "RTG_FLAG_BF16_BASIS needs banded modes 1-2 (radius <= 9), a mode-3 mix "
                                      "of 1 or 3 channels, a mode-4 band of radius <= 2 and dims[0] %% 8 == 0");
-  const int64_t ae = apply_scratch_elems(P->op.op);
+  int64_t ae = apply_scratch_elems(P->op.op);
+  if (ps.method == 1 && apply_scratch_elems(P->opT.op) > ae) ae = apply_scratch_elems(P->opT.op);
   const int tkb = mode == 2 ? n_mu : 1;
+  const int nU = ps.method == 1 ? 2 : 0;
   Work tmpw;
   void *ta, *tb;
   SketchScratch tsk;
-  const size_t bytes = carve_work(nullptr, dtype, n, sp, m, tkb, ae, tmpw, &ta, &tb, &tsk, vdtype);
+  const size_t bytes = carve_work(nullptr, dtype, n, sp, m, tkb, ae, tmpw, &ta, &tb, &tsk, vdtype, nU);
   RK(P->mem.ensure(bytes));
   CK(cudaMemset(P->mem.p, 0, bytes));
-  carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk, vdtype);
+  carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk, vdtype, nU);
   if (ddev != nullptr) {   // descriptor and info record in a batch's buffers
     P->ext_desc = true;
     P->desc_dev = ddev;
@@ -855,6 +968,13 @@ rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDe
                       sketch_launches(sp) + gs + 1;
     P->launches_step = apply_launches(P->op.op, false, dtype, vdtype, vdtype) + sketch_launches(sp) + gs + 1;
     P->launches_epi = 3;
+    if (ps.method == 1) {
+      const int al = apply_launches(P->op.op, false, dtype, dtype, dtype);
+      const int alT = apply_launches(P->opT.op, false, dtype, dtype, dtype);
+      P->launches_pro = P->launches_setup + (has_x0 ? apply_launches(P->op.op, true, dtype, dtype, dtype) : 0) +
+                        2 * sketch_launches(sp) + alT + 4;
+      P->launches_step = al + alT + 2 * sketch_launches(sp) + 4;
+    }
   }
   if (use_graph && ddev == nullptr) RK(build_graph(*P));
   *out = std::move(np);
@@ -1133,10 +1253,13 @@ rtg_status rtg_krylov_query(rtg_handle h, rtg_krylov K, rtg_krylov_view* view, d
   return RTG_OK;
 }
 
-rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
-                            int32_t nB, rtg_shape shape, rtg_dtype dtype, const void* C, int32_t m,
-                            const int64_t* sketch_dims, uint64_t seed, double lambda, const void* X0,
-                            void* X, const rtg_opts* opts_in, rtg_stream stream) {
+}  // extern "C"
+
+// method 0: RTG-GMRES; 1: sketched Golub-Kahan.
+static rtg_status submit_impl(int method, rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
+                              int32_t nB, rtg_shape shape, rtg_dtype dtype, const void* C, int32_t m,
+                              const int64_t* sketch_dims, uint64_t seed, double lambda, const void* X0,
+                              void* X, const rtg_opts* opts_in, rtg_stream stream) {
   if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
   int64_t n = 0;
   RK(check_shape(shape, &n));
@@ -1171,6 +1294,8 @@ rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const
   RK(build_sketch(shape, sketch_dims, seed, 0, dtype, sp));
   const bool phase_times = (opts.flags & RTG_FLAG_PHASE_TIMES) != 0;
   const int vdtype = (opts.flags & RTG_FLAG_BF16_BASIS) ? RTG_BF16 : dtype;
+  if (vdtype == RTG_BF16 && method == 1)
+    return fail(RTG_ERR_UNSUPPORTED, "RTG_FLAG_BF16_BASIS is for rtg_gmres_solve");
   if (vdtype == RTG_BF16) {
     if (dtype != RTG_F32) return fail(RTG_ERR_UNSUPPORTED, "RTG_FLAG_BF16_BASIS needs dtype RTG_F32");
     if (sp.nstage == 0 || !sp.stage_first[0])
@@ -1189,6 +1314,7 @@ rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const
   key.push_back(use_graph ? 'g' : 'd');
   append_bytes(key, &opts.slot, sizeof opts.slot);
   append_bytes(key, &vdtype, sizeof vdtype);
+  append_bytes(key, &method, sizeof method);
 
   rtg_context::Pending& pend = h->pending[opts.slot];
   if (pend.active) return fail(RTG_ERR_INVALID_ARG, "slot %d has a submitted solve that was not waited for", opts.slot);
@@ -1210,7 +1336,7 @@ rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const
     // does so only while no other solve of this handle is in flight.
     for (const auto& q : h->pending)
       if (q.active) CK(cudaStreamSynchronize(q.stream));
-    PlanSpec ps{A, nA, B, nB, shape, dtype, vdtype, n, m, sp, mode, nmu_key, has_x0, use_graph};
+    PlanSpec ps{A, nA, B, nB, shape, dtype, vdtype, n, m, sp, mode, nmu_key, has_x0, use_graph, method};
     std::shared_ptr<SolvePlan> np;
     RK(make_plan(ps, nullptr, nullptr, nullptr, nullptr, &np));
     P = np.get();
@@ -1284,12 +1410,15 @@ rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const
       CK(cudaStreamSynchronize(s));
       return RTG_OK;
     };
-    RK(group([&] { return enqueue_prologue(*P, so, s, pt); }));
+    RK(group([&] { return P->method == 1 ? enqueue_gk_prologue(*P, so, s, pt) : enqueue_prologue(*P, so, s, pt); }));
     RK(stopped());
     int steps = 0;
     while (steps < m && *P->stop_host == 0) {
       const int j = steps++;
-      RK(group([&] { return enqueue_step(P->op, P->sp, P->w, dtype, P->tA, P->tB, P->sk, so, s, pt, j); }));
+      RK(group([&] {
+        return P->method == 1 ? enqueue_gk_step(*P, so, s, pt, j)
+                              : enqueue_step(P->op, P->sp, P->w, dtype, P->tA, P->tB, P->sk, so, s, pt, j);
+      }));
       RK(stopped());
     }
     P->direct_steps = steps;
@@ -1307,6 +1436,23 @@ rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const
   pend.phase_times = phase_times;
   pend.active = true;
   return RTG_OK;
+}
+
+extern "C" {
+
+rtg_status rtg_gmres_submit(rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
+                            int32_t nB, rtg_shape shape, rtg_dtype dtype, const void* C, int32_t m,
+                            const int64_t* sketch_dims, uint64_t seed, double lambda, const void* X0,
+                            void* X, const rtg_opts* opts_in, rtg_stream stream) {
+  return submit_impl(0, h, A, nA, B, nB, shape, dtype, C, m, sketch_dims, seed, lambda, X0, X, opts_in, stream);
+}
+
+rtg_status rtg_gk_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
+                        int32_t nB, rtg_shape shape, rtg_dtype dtype, const void* C, int32_t m,
+                        const int64_t* sketch_dims, uint64_t seed, double lambda, const void* X0,
+                        void* X, const rtg_opts* opts_in, rtg_info* info, rtg_stream stream) {
+  RK(submit_impl(1, h, A, nA, B, nB, shape, dtype, C, m, sketch_dims, seed, lambda, X0, X, opts_in, stream));
+  return rtg_gmres_wait(h, opts_in ? opts_in->slot : 0, info);
 }
 
 rtg_status rtg_gmres_wait(rtg_handle h, int32_t slot, rtg_info* info) {

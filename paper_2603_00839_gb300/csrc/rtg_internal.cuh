@@ -72,6 +72,7 @@ struct Ctl {
   double hnext;     // h_{j+1,j}
   double mu;        // chosen regularisation
   double gcv_best;
+  double gk_scale;  // Golub-Kahan: the norm the next update divides by
 };
 
 // Per-call parameters of a solve, read by the graph's kernels.
@@ -105,6 +106,7 @@ struct Work {
   int m;                       // Krylov dimension
   void* V;                     // (m+1) * n
   void* W;                     // n
+  void* U;                     // Golub-Kahan: ring of 2 left-basis tensors (else null)
   void* S;                     // d   (sketch of W, then s after the first GS pass)
   void* Spart;                 // nparts * d partial sketches written by the chain
   int nparts;
@@ -195,12 +197,16 @@ struct PtrRef {
   const int* jidx = nullptr;
   int64_t stride = 0;
   int joff = 0;
+  int mod = 0;      // > 0: slot (*jidx + joff) % mod of a ring
 #ifdef __CUDACC__
   template <typename T>
   __device__ __forceinline__ T* get() const {
     const void* b = ind ? *ind : base;
     T* p = static_cast<T*>(const_cast<void*>(b));
-    if (jidx) p += static_cast<int64_t>(*jidx + joff) * stride;
+    if (jidx) {
+      const int slot = mod > 0 ? (*jidx + joff) % mod : *jidx + joff;
+      p += static_cast<int64_t>(slot) * stride;
+    }
     return p;
   }
 #endif
@@ -288,6 +294,16 @@ struct FinishOpts {
 cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s);
 cudaError_t launch_assemble(const Work& w, PtrRef X0, PtrRef X, cudaStream_t s);
 cudaError_t launch_finalize(const Work& w, InfoDev* info, cudaStream_t s);
+// k_gk.cu: sketched Golub-Kahan (Algorithm 4).  phase 0: beta_0 = ||S(R_0)||;
+// 1: alpha_0 = ||S(Phi^T U_0)||; 2: beta_{j+1} = ||S(Phi V_j) - alpha_j S(U_j)||;
+// 3: alpha_{j+1} = ||S(Phi^T U_{j+1}) - beta_{j+1} S(V_j)||.  The sketch of the
+// product is in w.S, S(U_j) in Q slot 0, S(V_j) in Q slot 1.
+cudaError_t launch_gk_norm(const Work& w, int phase, const StepOpts& o, cudaStream_t s);
+// phase 0: U_0 = src / beta_0; 1: V_0 = W / alpha_0; 2: U_{j+1} = (W - alpha_j U_j) / beta_{j+1}
+// (and the Givens step of column j beside it); 3: V_{j+1} = (W - beta_{j+1} V_j) / alpha_{j+1};
+// the sketched vectors follow the same recurrences.
+cudaError_t launch_gk_update(const Work& w, int phase, PtrRef src, const StepOpts& o, cudaStream_t s);
+
 // Phase timing: bounded wait of the stream on a host-written flag.
 cudaError_t launch_gate(const unsigned* flag, unsigned want, unsigned* status, cudaStream_t s);
 }  // namespace rtg
