@@ -379,6 +379,27 @@ def run_ours(args):
     torch.cuda.synchronize()
     plain_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
 
+    # ---- sketched Golub-Kahan (Algorithm 4) on the same problems, one solve per step
+    def gk(pr):
+        p = pr["p"]
+        return h.gk_solve(pr["C"], p.m, p.sketch_dims, p.seed, p.lam, pr["A"], pr["B"], X=X,
+                          tol=pr["tol"], mu_grid=p.mu_grid)
+    for s in range(args.warmup):
+        gk(probs[s % len(probs)])
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    iters_gk, conv_gk = [], []
+    for s in range(args.steps):
+        flush.zero_()
+        evs[s][0].record(stream)
+        _, info = gk(probs[s % len(probs)])
+        evs[s][1].record(stream)
+        iters_gk.append(info.iters)
+        conv_gk.append(bool(info.converged))
+    torch.cuda.synchronize()
+    gk_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+
     # ---- chosen form: batched (B problems per CUDA-graph launch), one batch per step
     for s in range(args.warmup):
         h.gmres_solve_batched(batch_of(s % nb), mu_grid=grid)
@@ -471,7 +492,12 @@ def run_ours(args):
                                           "batch": B},
                          "plain_fp32": {"value": round(plain_value, 2), "ms_per_solve": round(plain_max, 4),
                                         "mean_iters": float(np.mean(iters)),
-                                        "launch": "direct" if args.direct else "cuda graph"}},
+                                        "reached_stop_level": f"{sum(conv_plain)}/{len(conv_plain)}",
+                                        "launch": "direct" if args.direct else "cuda graph"},
+                         "golub_kahan_fp32": {"value": round(1e3 / gk_ms, 2), "ms_per_solve": round(gk_ms, 4),
+                                              "mean_iters": float(np.mean(iters_gk)),
+                                              "reached_stop_level": f"{sum(conv_gk)}/{len(conv_gk)}",
+                                              "method": "sketched Golub-Kahan (Algorithm 4)"}},
                "e2e": {"value": round(e2e_val, 2), "unit": "solves/s",
                        # per problem: C and X, plus the 512-byte descriptor and 2560-byte info
                        # record slots of the batch call
