@@ -32,5 +32,6 @@ from .tikhonov import (tikhonov_stacked, tikhonov_normal, tikhonov_svd, gcv_valu
                        gcv_choose)
 from .metrics import make_observation, relative_error, psnr, rho_star
 from .golub_kahan import transpose_mats, sketched_golub_kahan, sketched_gk_solve
+from . import warmstart
 
 __all__ = [n for n in dir() if not n.startswith("_")]
