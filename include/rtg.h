@@ -342,6 +342,55 @@ rtg_status rtg_gk_solve(rtg_handle handle,
                         uint64_t seed, double lambda, const void* X0, void* X,
                         const rtg_opts* opts, rtg_info* info, rtg_stream stream);
 
+/*
+ * Learned warm start (no paper counterpart: the form this library adds).
+ * A convolutional encoder-decoder with base width c (four levels: c, 2c,
+ * 4c, 4c channels; 3x3 convolutions, stride-2 down-sampling, nearest x2
+ * up-sampling with additive skips) maps an observation C to
+ * X_0 = C + net(C) and log(lambda) = w . mean_pixels(bottleneck) + b.
+ * Images are I1 x I2 x 3 in the solver's layout (mode 1 fastest), I1 and
+ * I2 multiples of 8; a batch is n_img such images back to back.  BF16
+ * tensor-core products with FP32 accumulation; FP32 master parameters.
+ * Flat parameter order: per layer e1, e2, e3, e4, d3, d2, d1, out the
+ * weights (c_out, 3, 3, c_in) then the biases, then the head's 4c weights
+ * and its bias (rtg_ws_num_params entries).
+ */
+typedef struct rtg_warmstart* rtg_ws;
+/* params: host array of the initial parameters (rtg_ws_num_params of a
+ * network of this base; the caller draws them). */
+rtg_status rtg_ws_create(int32_t device, int32_t base, const float* params, rtg_ws* ws);
+rtg_status rtg_ws_destroy(rtg_ws ws);
+int64_t rtg_ws_num_params(rtg_ws ws);
+/* Copies the parameters and / or the gradients of the last training step
+ * to host arrays (either may be NULL). */
+rtg_status rtg_ws_get(rtg_ws ws, float* params, float* grads);
+/* X0 (device, same layout as C) and loglam (device, n_img floats). */
+rtg_status rtg_ws_predict(rtg_ws ws, int32_t n_img, int32_t I1, int32_t I2, const float* C, float* X0,
+                          float* loglam, rtg_stream stream);
+/* One training step on a batch: forward, loss
+ *   mean over images of ||X_0 - X*||^2 / ||X*||^2 + (log lambda - log mu*)^2,
+ * backward, and (lr > 0) one Adam step (beta 0.9 / 0.999, eps 1e-8).
+ * Xstar, logmu: device targets (solver solutions and log regularisation);
+ * X0_scratch: device array like C; loss_out: host (may be NULL; when given
+ * the call synchronises the stream). */
+rtg_status rtg_ws_train_step(rtg_ws ws, int32_t n_img, int32_t I1, int32_t I2, const float* C,
+                             const float* Xstar, const float* logmu, float lr, float* X0_scratch,
+                             double* loss_out, rtg_stream stream);
+
+/*
+ * One 3x3 convolution layer of the warm-start network with the same
+ * kernels (zero padding 1, stride 1 or 2, channels-last FP32 activations
+ * x (N, H, W, cin), weights w (cout, 3, 3, cin) FP32 rounded to BF16 for
+ * the tensor-core product, FP32 accumulation).  Forward: y = conv(x) + b
+ * (y: N, H/stride, W/stride, cout).  Backward (dy given): dx, dw, db (each
+ * may be NULL); dy is rounded to BF16 for the products, db sums dy in FP32.
+ * All pointers are device arrays; workspace is allocated per call and the
+ * stream is synchronised before returning.
+ */
+rtg_status rtg_nn_conv3x3(int32_t device, int32_t N, int32_t H, int32_t W, int32_t cin, int32_t cout,
+                          int32_t stride, const float* x, const float* w, const float* b, float* y,
+                          const float* dy, float* dx, float* dw, float* db, rtg_stream stream);
+
 /* One problem of a batched solve: the arguments of rtg_gmres_solve. */
 typedef struct rtg_problem {
     const rtg_factor* A_factors;

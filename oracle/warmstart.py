@@ -28,29 +28,16 @@ from typing import Dict, List
 
 import numpy as np
 
-LAYERS = [  # name, c_in factor, c_out factor, stride (c = base channels; 0 -> 3 channels)
-    ("e1", 0, 1, 1), ("e2", 1, 2, 2), ("e3", 2, 4, 2), ("e4", 4, 4, 2),
-    ("d3", 4, 4, 1), ("d2", 4, 2, 1), ("d1", 2, 1, 1), ("out", 1, 0, 1),
-]
-
-
 def layer_shapes(base: int):
-    ch = lambda f: 3 if f == 0 else f * base
-    return [(name, ch(ci), ch(co), s) for name, ci, co, s in LAYERS]
+    """(name, c_in, c_out, stride) per convolution, from the shared generator module."""
+    import workloads
+    return workloads.warmstart_layer_shapes(base)
 
 
 def init_params(base: int, seed: int) -> Dict[str, np.ndarray]:
-    """He-normal weights (out, 3, 3, in), zero biases; the output layer and the
-    lambda head start at zero, so the untrained network returns X_0 = C."""
-    rng = np.random.default_rng(seed)
-    P = {}
-    for name, cin, cout, _ in layer_shapes(base):
-        std = np.sqrt(2.0 / (9 * cin)) if name != "out" else 0.0
-        P[name + ".w"] = rng.standard_normal((cout, 3, 3, cin)) * std
-        P[name + ".b"] = np.zeros(cout)
-    P["lam.w"] = np.zeros(4 * base)
-    P["lam.b"] = np.zeros(1)
-    return P
+    """The seeded initial parameters the GPU network also starts from."""
+    import workloads
+    return workloads.warmstart_params(base, seed)
 
 
 def conv(x: np.ndarray, w: np.ndarray, b: np.ndarray, stride: int) -> np.ndarray:

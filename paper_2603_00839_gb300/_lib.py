@@ -104,6 +104,15 @@ _SIGS = {
                                C.c_void_p, C.POINTER(Opts), C.POINTER(Info), C.c_void_p]),
     "rtg_gmres_solve_batched": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Problem), C.c_int,
                                           C.POINTER(Opts), C.POINTER(Info), C.c_void_p]),
+    "rtg_ws_create": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_void_p)]),
+    "rtg_ws_destroy": (C.c_int, [C.c_void_p]),
+    "rtg_ws_num_params": (C.c_int64, [C.c_void_p]),
+    "rtg_ws_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "rtg_ws_predict": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]),
+    "rtg_ws_train_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_float, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "rtg_nn_conv3x3": (C.c_int, [C.c_int32] * 7 + [C.c_void_p] * 8 + [C.c_void_p]),
     "rtg_sketch_noalloc": (C.c_int, [Shape, C.c_int, C.POINTER(C.c_int64), C.c_uint64, C.c_uint64,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
 }

@@ -487,3 +487,92 @@ def _wrap(ptr: int, dims, dtype, device):
     typestr = "<f8" if dtype == torch.float64 else "<f4"
     flat = torch.as_tensor(_DeviceRange(ptr, n, typestr), device=f"cuda:{device}").clone()
     return flat.reshape(tuple(reversed(dims))).permute(*reversed(range(len(dims))))
+
+
+class WarmStart:
+    """The learned warm start (rtg_ws_*): X_0 = C + net(C) and log(lambda).
+
+    params: flat initial parameters in the library's order (e.g. from
+    workloads.warmstart_params).  Batches are device tensors of shape
+    (n, I1, I2, 3)... given as a list-free contiguous float32 buffer of
+    n images in the solver layout: use stack_images / unstack_images."""
+
+    def __init__(self, base: int, params: np.ndarray, device: int = 0):
+        self.lib = L.load()
+        flat = np.ascontiguousarray(params, dtype=np.float32)
+        h = C.c_void_p()
+        L.check(self.lib.rtg_ws_create(int(device), int(base), flat.ctypes.data_as(C.POINTER(C.c_float)),
+                                       C.byref(h)))
+        self._h = h
+        self.base = base
+        self.n = int(self.lib.rtg_ws_num_params(h))
+        if self.n != flat.size:
+            raise ValueError(f"expected {self.n} parameters, got {flat.size}")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.rtg_ws_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self):
+        p = np.zeros(self.n, dtype=np.float32)
+        g = np.zeros(self.n, dtype=np.float32)
+        L.check(self.lib.rtg_ws_get(self._h, p.ctypes.data_as(C.POINTER(C.c_float)),
+                                    g.ctypes.data_as(C.POINTER(C.c_float))))
+        return p, g
+
+    def predict(self, Cb, I1: int, I2: int, stream=None):
+        """Cb: device float32 buffer of n images (solver layout, back to back)."""
+        torch = _torch()
+        n = Cb.numel() // (I1 * I2 * 3)
+        X0 = torch.empty_like(Cb)
+        ll = torch.empty(n, dtype=torch.float32, device=Cb.device)
+        L.check(self.lib.rtg_ws_predict(self._h, n, I1, I2, Cb.data_ptr(), X0.data_ptr(), ll.data_ptr(),
+                                        _stream(stream)))
+        return X0, ll
+
+    def train_step(self, Cb, Xs, logmu, I1: int, I2: int, lr: float, stream=None):
+        torch = _torch()
+        n = Cb.numel() // (I1 * I2 * 3)
+        X0 = torch.empty_like(Cb)
+        loss = C.c_double()
+        L.check(self.lib.rtg_ws_train_step(self._h, n, I1, I2, Cb.data_ptr(), Xs.data_ptr(), logmu.data_ptr(),
+                                           float(lr), X0.data_ptr(), C.byref(loss), _stream(stream)))
+        return float(loss.value)
+
+
+def stack_images(images) -> "object":
+    """Column-major (I1, I2, 3) device tensors -> one contiguous buffer in the solver layout."""
+    torch = _torch()
+    return torch.cat([im.permute(2, 1, 0).reshape(-1) for im in images])
+
+
+def unstack_images(buf, n: int, I1: int, I2: int):
+    return [buf[i * I1 * I2 * 3:(i + 1) * I1 * I2 * 3].view(3, I2, I1).permute(2, 1, 0) for i in range(n)]
+
+
+def conv3x3(x, w, b=None, stride: int = 1, dy=None, device: int = 0):
+    """One warm-start convolution layer (rtg_nn_conv3x3) on channels-last device tensors.
+    Forward (dy None): returns y.  Backward: returns (dx, dw, db)."""
+    torch = _torch()
+    lib = L.load()
+    N, H, W, cin = x.shape
+    cout = w.shape[0]
+    p = lambda t: 0 if t is None else t.data_ptr()
+    if dy is None:
+        y = torch.empty((N, H // stride, W // stride, cout), dtype=torch.float32, device=x.device)
+        L.check(lib.rtg_nn_conv3x3(device, N, H, W, cin, cout, stride, x.data_ptr(), w.data_ptr(), p(b),
+                                   y.data_ptr(), 0, 0, 0, 0, _stream(None)))
+        return y
+    dx = torch.empty_like(x)
+    dw = torch.empty_like(w)
+    db = torch.empty(cout, dtype=torch.float32, device=x.device)
+    L.check(lib.rtg_nn_conv3x3(device, N, H, W, cin, cout, stride, x.data_ptr(), w.data_ptr(), 0, 0,
+                               dy.data_ptr(), dx.data_ptr(), dw.data_ptr(), db.data_ptr(), _stream(None)))
+    return dx, dw, db

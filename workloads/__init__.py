@@ -214,3 +214,30 @@ CONFIGS = {
     "image512_f32": lambda seed=0: image_config(2, seed),
     "video256x64": lambda seed=0: video_config(seed),
 }
+
+
+def warmstart_layer_shapes(base: int):
+    """(name, c_in, c_out, stride) of the warm-start network's 3x3 convolutions."""
+    c = base
+    return [("e1", 3, c, 1), ("e2", c, 2 * c, 2), ("e3", 2 * c, 4 * c, 2), ("e4", 4 * c, 4 * c, 2),
+            ("d3", 4 * c, 4 * c, 1), ("d2", 4 * c, 2 * c, 1), ("d1", 2 * c, c, 1), ("out", c, 3, 1)]
+
+
+def warmstart_params(base: int, seed: int) -> dict:
+    """Seeded initial parameters of the warm-start network: He-normal
+    convolution weights (c_out, 3, 3, c_in), zero biases, and a zero output
+    layer and lambda head (so the untrained network returns X_0 = C,
+    log lambda = 0).  Ordered as the flat parameter array."""
+    rng = _rng(seed, 5)
+    P = {}
+    for name, cin, cout, _ in warmstart_layer_shapes(base):
+        std = math.sqrt(2.0 / (9 * cin)) if name != "out" else 0.0
+        P[name + ".w"] = rng.standard_normal((cout, 3, 3, cin)) * std
+        P[name + ".b"] = np.zeros(cout)
+    P["lam.w"] = np.zeros(4 * base)
+    P["lam.b"] = np.zeros(1)
+    return P
+
+
+def flatten_params(P: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(v, dtype=np.float64).ravel() for v in P.values()])
