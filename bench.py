@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=16, help="problems per batched launch (chosen form)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start form")
     ap.add_argument("--direct", action="store_true",
                     help="launch every solve's kernels directly instead of replaying its CUDA graph "
                          "(for profilers that do not see kernels inside conditional graph nodes); "
@@ -251,6 +252,105 @@ def phase_report(h, probs, X, peaks, workload: str):
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)",
             "mean_iters": float(np.mean(iters))}
     return roof, table
+
+
+# ----------------------------------------------------------------------------- warm start
+
+def warm_start_form(h, api, torch, probs, train_n=512, steps=400, I=128, base=32):
+    """Learned warm start: trained here on solver-labelled 128x128x3 pairs of the
+    workload's operator family (sigma U[0.5, 3], radius ceil(3 sigma), the 3x3
+    channel mix, noise 2e-3..2e-2), then the benchmark's problems solved cold
+    and warm to the same stop level ||S(C - Phi X)|| <= rho* ||S(C)||, warm
+    falling back to X_0 = 0 when its residual is not below the cold one.
+    Wall-clock per solve, inference and the fallback test included."""
+    rng = np.random.default_rng(123)
+    grid = workloads.mu_grid()
+    sk = (64, 64, 3)
+    train, Xs, mus = [], [], []
+    t0 = time.perf_counter()
+    for i in range(train_n):
+        x = workloads.piecewise_image(I, I, 3, 70000 + i)
+        sig = float(rng.uniform(0.5, 3.0))
+        taps = workloads.gaussian_taps(sig, int(np.ceil(3 * sig)))
+        A = [api.banded(1, I, taps), api.banded(2, I, taps)]
+        B = [api.dense(3, workloads.channel_mix())]
+        X = api.to_device(x, torch.float32)
+        Ch = h.operator_apply(X, A, B)
+        E = api.to_device(workloads.noise_draw(x.shape, 70000 + i), torch.float32)
+        nu = float(10 ** rng.uniform(np.log10(2e-3), np.log10(2e-2)))
+        C = api.empty(x.shape, torch.float32)
+        C.copy_(Ch + E * (nu * torch.linalg.vector_norm(Ch) / torch.linalg.vector_norm(E)))
+        train.append(dict(C=C, A=A, B=B, m=30, sketch_dims=sk, seed=5, lam=-1.0, tol=max(1e-3, 1.01 * nu)))
+    for k in range(0, train_n, 64):
+        X, res = h.gmres_solve_batched(train[k:k + 64], mu_grid=grid)
+        Xs += X
+        mus += [r.mu for r in res]
+    label_s = time.perf_counter() - t0
+    net = api.WarmStart(base, workloads.flatten_params(workloads.warmstart_params(base, 11)))
+    t0 = time.perf_counter()
+    losses = []
+    for step in range(steps):
+        idx = rng.choice(train_n, 16, replace=False)
+        Cb = api.stack_images([train[i]["C"] for i in idx])
+        Xb = api.stack_images([Xs[i] for i in idx])
+        lm = torch.tensor(np.log([mus[i] for i in idx]), dtype=torch.float32, device="cuda")
+        losses.append(net.train_step(Cb, Xb, lm, I, I, lr=2e-3 if step < steps * 3 // 4 else 5e-4))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    def cold(pr):
+        p = pr["p"]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, info = h.gmres_solve(pr["C"], p.m, p.sketch_dims, p.seed, p.lam, pr["A"], pr["B"], tol=pr["tol"],
+                                mu_grid=p.mu_grid)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, info.iters
+
+    def warm(pr):
+        p = pr["p"]
+        I1, I2, _ = p.dims
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        X0b, ll = net.predict(api.stack_images([pr["C"]]), I1, I2)
+        X0 = api.empty(p.dims, torch.float32)
+        X0.copy_(api.unstack_images(X0b, 1, I1, I2)[0])
+        R0 = api.empty(p.dims, torch.float32)
+        R0.copy_(pr["C"] - h.operator_apply(X0, pr["A"], pr["B"]))
+        sC = float(torch.linalg.vector_norm(h.sketch(pr["C"], p.sketch_dims, p.seed)))
+        sR = float(torch.linalg.vector_norm(h.sketch(R0, p.sketch_dims, p.seed)))
+        fell_back = sR >= sC
+        if fell_back:
+            _, info = h.gmres_solve(pr["C"], p.m, p.sketch_dims, p.seed, p.lam, pr["A"], pr["B"], tol=pr["tol"],
+                                    mu_grid=p.mu_grid)
+        elif pr["tol"] * sC / sR >= 1.0:
+            info = None
+        else:
+            _, info = h.gmres_solve(pr["C"], p.m, p.sketch_dims, p.seed, float(np.exp(ll.item())), pr["A"],
+                                    pr["B"], X0=X0, tol=pr["tol"] * sC / sR)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, (0 if info is None else info.iters), fell_back
+
+    for pr in probs[:2]:
+        cold(pr)
+        warm(pr)
+    tc, ic, tw, iw, fb = [], [], [], [], 0
+    for pr in probs:
+        a, b = cold(pr)
+        tc.append(a)
+        ic.append(b)
+        a, b, f = warm(pr)
+        tw.append(a)
+        iw.append(b)
+        fb += int(f)
+    return {"value": round(len(probs) / sum(tw), 2), "unit": "solves/s (wall clock, one at a time)",
+            "cold_value": round(len(probs) / sum(tc), 2), "mean_iters_warm": float(np.mean(iw)),
+            "mean_iters_cold": float(np.mean(ic)), "fallbacks": f"{fb}/{len(probs)}",
+            "training": {"pairs": train_n, "image": [I, I, 3], "steps": steps, "batch": 16,
+                         "loss_first": round(float(np.mean(losses[:5])), 4),
+                         "loss_last": round(float(np.mean(losses[-20:])), 4),
+                         "label_s": round(label_s, 2), "train_s": round(train_s, 2)},
+            "network": f"4-level conv encoder-decoder, base {base}, BF16 tensor-core kernels"}
 
 
 # ----------------------------------------------------------------------------- CPU baseline
@@ -467,6 +567,10 @@ def run_ours(args):
         torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
     e2e_val = world * B / float(e2e_t.item())
 
+    ws_form = None
+    if rank == 0 and not args.no_warm_start:
+        ws_form = warm_start_form(h, api, torch, probs)
+
     # phase timing holds the stream at gates the host opens; a profiler that
     # serialises every launch would wait on them, so --direct (the profiler
     # mode) leaves it out
@@ -497,7 +601,8 @@ def run_ours(args):
                          "golub_kahan_fp32": {"value": round(1e3 / gk_ms, 2), "ms_per_solve": round(gk_ms, 4),
                                               "mean_iters": float(np.mean(iters_gk)),
                                               "reached_stop_level": f"{sum(conv_gk)}/{len(conv_gk)}",
-                                              "method": "sketched Golub-Kahan (Algorithm 4)"}},
+                                              "method": "sketched Golub-Kahan (Algorithm 4)"},
+                         "warm_start_fp32": ws_form},
                "e2e": {"value": round(e2e_val, 2), "unit": "solves/s",
                        # per problem: C and X, plus the 512-byte descriptor and 2560-byte info
                        # record slots of the batch call
