@@ -1,9 +1,10 @@
 // Kernels of the learned warm start (a convolutional encoder-decoder that
 // predicts X_0 and log(lambda) from C).  Activations are FP32 and channels
-// last (N, H, W, C); 3x3 convolutions with zero padding 1 run as
-// im2col + a BF16 tensor-core GEMM with FP32 accumulation, forward and
-// backward (data gradient through the transposed product, weight gradient
-// as a split-K product over the pixels).  Everything else (ReLU masks,
+// last (N, H, W, C); 3x3 convolutions with zero padding 1 run on BF16
+// tensor cores with FP32 accumulation: forward as an implicit GEMM that
+// gathers its patches from the activations, backward as im2col + GEMM
+// (data gradient through the transposed product, weight gradient as a
+// split-K product over the pixels).  Everything else (ReLU masks,
 // nearest up-sampling, skip sums, pooling, the lambda head, the loss and
 // Adam) is elementwise or a small reduction.
 #include <cuda_bf16.h>
@@ -145,6 +146,172 @@ cudaError_t gemm(bool a_cm, bool b_t, const __nv_bfloat16* A, const __nv_bfloat1
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   k_sum_slices<<<grid_of(int64_t(M) * N), 256, 0, s>>>(part, C, int64_t(M) * N, splits);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ implicit-GEMM convolution
+// Forward 3x3 convolution without a materialised im2col: the A tile (128
+// output pixels x 32 of the 9 c_in patch entries) is gathered from the
+// channels-last input while the previous tile is multiplied.  When
+// c_in % 32 == 0 a 32-wide K slice is one tap and 32 consecutive channels,
+// i.e. 8 float4 per pixel; otherwise (the 3-channel input layer) entries are
+// gathered one by one.  Weights (c_out x K, BF16) come in 16-byte pieces
+// when K % 8 == 0.  The epilogue adds the bias, applies the ReLU and the skip
+// sum and stores FP32: r = act(acc + b) (optional), out = r + skip.
+// Eight warps; warp w owns output rows 16w..16w+15 and all BN channels.
+constexpr int CBM = 128, CBK = 32, CPAD = 8;
+
+template <int BN>
+__global__ void __launch_bounds__(256)
+k_conv_fwd(const float* __restrict__ x, const __nv_bfloat16* __restrict__ wt, const float* __restrict__ bias,
+           float* __restrict__ rout, const float* __restrict__ skip, float* __restrict__ out, int N, int H, int W,
+           int C, int stride, int cout, int relu) {
+  __shared__ __align__(16) __nv_bfloat16 As[2][CBM][CBK + CPAD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[2][BN][CBK + CPAD];
+  constexpr int NB = (BN * 4 + 255) / 256;   // 16-byte weight pieces per thread
+  const int Ho = H / stride, Wo = W / stride;
+  const int M = N * Ho * Wo, K = 9 * C;
+  const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * BN;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gid = lane >> 2, tig = lane & 3;
+  const bool fastA = (C % 32) == 0;
+  const bool fastB = (K % 8) == 0;
+  float4 ra[4];
+  float rs[16];
+  uint4 rb[NB];
+  auto load_tiles = [&](int k0) {
+    if (fastA) {
+      const int tap = k0 / C, c0 = k0 - tap * C, ky = tap / 3, kx = tap - ky * 3;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + q * 256, row = e >> 3, piece = e & 7;
+        const int m = m0 + row;
+        ra[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m < M) {
+          const int j = m % Wo, i = (m / Wo) % Ho, n = m / (Wo * Ho);
+          const int yy = stride * i + ky - 1, xx = stride * j + kx - 1;
+          if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+            ra[q] = *reinterpret_cast<const float4*>(x + ((static_cast<int64_t>(n) * H + yy) * W + xx) * C + c0 + piece * 4);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int e = tid + q * 256, row = e >> 5, kk = e & 31;
+        const int m = m0 + row, k = k0 + kk;
+        rs[q] = 0.f;
+        if (m < M && k < K) {
+          const int c = k % C, t = k / C, kx = t % 3, ky = t / 3;
+          const int j = m % Wo, i = (m / Wo) % Ho, n = m / (Wo * Ho);
+          const int yy = stride * i + ky - 1, xx = stride * j + kx - 1;
+          if (yy >= 0 && yy < H && xx >= 0 && xx < W) rs[q] = x[((static_cast<int64_t>(n) * H + yy) * W + xx) * C + c];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + q * 256, row = e >> 2, piece = e & 3;
+      rb[q] = make_uint4(0u, 0u, 0u, 0u);
+      if (row < BN && n0 + row < cout) {
+        const int k = k0 + piece * 8;
+        if (fastB && k + 8 <= K) {
+          rb[q] = *reinterpret_cast<const uint4*>(wt + static_cast<int64_t>(n0 + row) * K + k);
+        } else {
+          __nv_bfloat16 t8[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            t8[u] = (k + u < K) ? wt[static_cast<int64_t>(n0 + row) * K + k + u] : __float2bfloat16(0.f);
+          rb[q] = *reinterpret_cast<const uint4*>(t8);
+        }
+      }
+    }
+  };
+  auto store_tiles = [&](int buf) {
+    if (fastA) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + q * 256, row = e >> 3, piece = e & 7;
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(ra[q].x, ra[q].y);
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(ra[q].z, ra[q].w);
+        uint2 v;
+        v.x = *reinterpret_cast<uint32_t*>(&h0);
+        v.y = *reinterpret_cast<uint32_t*>(&h1);
+        *reinterpret_cast<uint2*>(&As[buf][row][piece * 4]) = v;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int e = tid + q * 256, row = e >> 5, kk = e & 31;
+        As[buf][row][kk] = __float2bfloat16(rs[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + q * 256, row = e >> 2, piece = e & 3;
+      if (row < BN) *reinterpret_cast<uint4*>(&Bs[buf][row][piece * 8]) = rb[q];
+    }
+  };
+  float acc[BN / 8][4];
+#pragma unroll
+  for (int a = 0; a < BN / 8; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+  load_tiles(0);
+  store_tiles(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += CBK) {
+    const bool more = k0 + CBK < K;
+    if (more) load_tiles(k0 + CBK);   // in flight during the products
+#pragma unroll
+    for (int kk = 0; kk < CBK; kk += 16) {
+      uint32_t af[4];
+      const int r = warp * 16 + gid;
+      af[0] = *reinterpret_cast<const uint32_t*>(&As[buf][r][kk + tig * 2]);
+      af[1] = *reinterpret_cast<const uint32_t*>(&As[buf][r + 8][kk + tig * 2]);
+      af[2] = *reinterpret_cast<const uint32_t*>(&As[buf][r][kk + tig * 2 + 8]);
+      af[3] = *reinterpret_cast<const uint32_t*>(&As[buf][r + 8][kk + tig * 2 + 8]);
+#pragma unroll
+      for (int nt = 0; nt < BN / 8; ++nt) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Bs[buf][nt * 8 + gid][kk + tig * 2]);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Bs[buf][nt * 8 + gid][kk + tig * 2 + 8]);
+        mma16816(acc[nt], af, b0, b1);
+      }
+    }
+    if (more) {
+      store_tiles(buf ^ 1);   // the other buffer: nobody reads it during this step
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int nt = 0; nt < BN / 8; ++nt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = m0 + warp * 16 + gid + h * 8;
+      if (m >= M) continue;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int c = n0 + nt * 8 + tig * 2 + q;
+        if (c >= cout) continue;
+        float v = acc[nt][2 * h + q] + (bias ? bias[c] : 0.f);
+        if (relu) v = fmaxf(v, 0.f);
+        const int64_t o = static_cast<int64_t>(m) * cout + c;
+        if (rout != nullptr) rout[o] = v;
+        if (out != nullptr) out[o] = skip ? v + skip[o] : v;
+      }
+    }
+}
+
+cudaError_t conv_fwd(const float* x, const __nv_bfloat16* w, const float* bias, float* r, const float* skip,
+                     float* out, int N, int H, int W, int C, int stride, int cout, bool relu, cudaStream_t s) {
+  const int M = N * (H / stride) * (W / stride);
+  const int bn = cout <= 8 ? 8 : (cout <= 32 ? 32 : (cout <= 64 ? 64 : 128));
+  dim3 grid((M + CBM - 1) / CBM, (cout + bn - 1) / bn);
+  const int rl = relu ? 1 : 0;
+  if (bn == 8) k_conv_fwd<8><<<grid, 256, 0, s>>>(x, w, bias, r, skip, out, N, H, W, C, stride, cout, rl);
+  else if (bn == 32) k_conv_fwd<32><<<grid, 256, 0, s>>>(x, w, bias, r, skip, out, N, H, W, C, stride, cout, rl);
+  else if (bn == 64) k_conv_fwd<64><<<grid, 256, 0, s>>>(x, w, bias, r, skip, out, N, H, W, C, stride, cout, rl);
+  else k_conv_fwd<128><<<grid, 256, 0, s>>>(x, w, bias, r, skip, out, N, H, W, C, stride, cout, rl);
   return cudaGetLastError();
 }
 
@@ -309,26 +476,41 @@ __global__ void k_from_nhwc_add(const float* __restrict__ src, const float* __re
   }
 }
 
-// g[n, c] = mean over pixels of e[n, ., ., c]; loglam[n] = w . g[n] + b (one block per image)
-__global__ void k_pool_head(const float* __restrict__ e, const float* __restrict__ w, const float* __restrict__ b,
-                            float* __restrict__ g, float* __restrict__ loglam, int HW, int C) {
-  const int n = blockIdx.x;
-  __shared__ float part[256];
+// g[n, c] = mean over pixels of e[n, ., ., c] in two fixed-order stages:
+// block (n, b) sums the pixels of slice b for every channel (consecutive
+// threads read consecutive channels), then one block per image adds the
+// slices and applies the head loglam[n] = w . g[n] + b.
+constexpr int POOL_SLICES = 32;
+__global__ void k_pool_part(const float* __restrict__ e, float* __restrict__ part, int HW, int C) {
+  const int n = blockIdx.x, b = blockIdx.y;
+  const int p0 = static_cast<int>((static_cast<int64_t>(HW) * b) / POOL_SLICES);
+  const int p1 = static_cast<int>((static_cast<int64_t>(HW) * (b + 1)) / POOL_SLICES);
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
     float v = 0.f;
-    for (int p = 0; p < HW; ++p) v += e[(static_cast<int64_t>(n) * HW + p) * C + c];
+    for (int p = p0; p < p1; ++p) v += e[(static_cast<int64_t>(n) * HW + p) * C + c];
+    part[(static_cast<int64_t>(n) * POOL_SLICES + b) * C + c] = v;
+  }
+}
+
+__global__ void k_pool_head(const float* __restrict__ part, const float* __restrict__ w, const float* __restrict__ b,
+                            float* __restrict__ g, float* __restrict__ loglam, int HW, int C) {
+  const int n = blockIdx.x;
+  __shared__ float red[256];
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    float v = 0.f;
+    for (int s2 = 0; s2 < POOL_SLICES; ++s2) v += part[(static_cast<int64_t>(n) * POOL_SLICES + s2) * C + c];
     g[static_cast<int64_t>(n) * C + c] = v / HW;
   }
   __syncthreads();
   float v = 0.f;
   for (int c = threadIdx.x; c < C; c += blockDim.x) v += w[c] * g[static_cast<int64_t>(n) * C + c];
-  part[threadIdx.x] = v;
+  red[threadIdx.x] = v;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) loglam[n] = part[0] + b[0];
+  if (threadIdx.x == 0) loglam[n] = red[0] + b[0];
 }
 
 // Loss of the batch (one block, fixed order) and the output gradients:
@@ -462,9 +644,10 @@ cudaError_t from_nhwc_add(const float* src, const float* base, float* dst, int N
                           cudaStream_t s) {
   NN_EW(k_from_nhwc_add, int64_t(N) * H * W * C, src, base, dst, N, H, W, C);
 }
-cudaError_t pool_head(const float* e, const float* w, const float* b, float* g, float* loglam, int N, int HW,
-                      int C, cudaStream_t s) {
-  k_pool_head<<<N, 256, 0, s>>>(e, w, b, g, loglam, HW, C);
+cudaError_t pool_head(const float* e, const float* w, const float* b, float* g, float* loglam, float* part, int N,
+                      int HW, int C, cudaStream_t s) {
+  k_pool_part<<<dim3(N, POOL_SLICES), 128, 0, s>>>(e, part, HW, C);
+  k_pool_head<<<N, 256, 0, s>>>(part, w, b, g, loglam, HW, C);
   return cudaGetLastError();
 }
 cudaError_t loss(const float* X0, const float* Xs, const float* loglam, const float* logmu, float* dout,

@@ -160,6 +160,7 @@ rtg_status shape_buffers(rtg_warmstart* ws, int N, int H, int W) {
     mk = std::max<int64_t>(mk, M * 9 * ws->L[l].cin);
     mn = std::max<int64_t>(mn, M * ws->L[l].cout);
   }
+  mk = std::max<int64_t>(mk, int64_t(N) * 32 * 4 * c);   // dA also holds the pooling partial sums
   NRK(ws->col.ensure(size_t(mk) * 2));
   NRK(ws->dA.ensure(size_t(mk) * 4));
   NRK(ws->z.ensure(size_t(mn) * 4));
@@ -177,16 +178,6 @@ rtg_status shape_buffers(rtg_warmstart* ws, int N, int H, int W) {
 const float* Wf(const rtg_warmstart* ws, int l) { return ws->P.as<float>() + ws->L[l].w; }
 const float* Bf(const rtg_warmstart* ws, int l) { return ws->P.as<float>() + ws->L[l].b; }
 const __nv_bfloat16* Wb(const rtg_warmstart* ws, int l) { return ws->Pb.as<__nv_bfloat16>() + ws->L[l].w; }
-
-// z = conv(x; layer l) for input (N, h, w, cin)
-rtg_status conv_fwd(rtg_warmstart* ws, int l, const float* x, int h, int w, float* z, cudaStream_t s) {
-  const Layer& L = ws->L[l];
-  const int ho = h / L.stride, wo = w / L.stride;
-  const int M = ws->N * ho * wo, K = 9 * L.cin;
-  NCK(nn::im2col(x, ws->col.as<__nv_bfloat16>(), ws->N, h, w, L.cin, L.stride, s));
-  NCK(nn::gemm(false, true, ws->col.as<__nv_bfloat16>(), Wb(ws, l), z, Bf(ws, l), M, L.cout, K, K, K, 1, nullptr, s));
-  return RTG_OK;
-}
 
 // Backward of layer l: dy is the gradient of its output (after the ReLU when
 // mask != null); x its input (N, h, w, cin).  Writes the parameter gradients
@@ -213,32 +204,33 @@ rtg_status conv_bwd(rtg_warmstart* ws, int l, const float* x, int h, int w, cons
   return RTG_OK;
 }
 
+// One forward layer through the implicit-GEMM kernel: r = relu(conv(x) + b)
+// (when r), out = r + skip (skip may be null); the output layer has no ReLU.
+rtg_status layer_fwd(rtg_warmstart* ws, int l, const float* x, int h, int w, float* r, const float* skip,
+                     float* out, cudaStream_t s) {
+  const Layer& L = ws->L[l];
+  NCK(nn::conv_fwd(x, Wb(ws, l), Bf(ws, l), r, skip, out, ws->N, h, w, L.cin, L.stride, L.cout, l != OUT, s));
+  return RTG_OK;
+}
+
 rtg_status forward(rtg_warmstart* ws, const float* C, float* X0, float* loglam_out, cudaStream_t s) {
   const int N = ws->N, H = ws->H, W = ws->W, c = ws->base;
-  float* z = ws->z.as<float>();
-  const int64_t p1 = int64_t(N) * H * W, p2 = p1 / 4, p4 = p1 / 16;
   NCK(nn::to_nhwc(C, ws->x0, N, H, W, 3, s));
-  NRK(conv_fwd(ws, E1, ws->x0, H, W, z, s));
-  NCK(nn::relu_skip(z, nullptr, nullptr, ws->e1, p1 * c, s));
-  NRK(conv_fwd(ws, E2, ws->e1, H, W, z, s));
-  NCK(nn::relu_skip(z, nullptr, nullptr, ws->e2, p2 * 2 * c, s));
-  NRK(conv_fwd(ws, E3, ws->e2, H / 2, W / 2, z, s));
-  NCK(nn::relu_skip(z, nullptr, nullptr, ws->e3, p4 * 4 * c, s));
-  NRK(conv_fwd(ws, E4, ws->e3, H / 4, W / 4, z, s));
-  NCK(nn::relu_skip(z, nullptr, nullptr, ws->e4, p1 / 64 * 4 * c, s));
+  NRK(layer_fwd(ws, E1, ws->x0, H, W, nullptr, nullptr, ws->e1, s));
+  NRK(layer_fwd(ws, E2, ws->e1, H, W, nullptr, nullptr, ws->e2, s));
+  NRK(layer_fwd(ws, E3, ws->e2, H / 2, W / 2, nullptr, nullptr, ws->e3, s));
+  NRK(layer_fwd(ws, E4, ws->e3, H / 4, W / 4, nullptr, nullptr, ws->e4, s));
   NCK(nn::up2(ws->e4, ws->u4, N, H / 8, W / 8, 4 * c, s));
-  NRK(conv_fwd(ws, D3, ws->u4, H / 4, W / 4, z, s));
-  NCK(nn::relu_skip(z, ws->r3, ws->e3, ws->d3, p4 * 4 * c, s));
+  NRK(layer_fwd(ws, D3, ws->u4, H / 4, W / 4, ws->r3, ws->e3, ws->d3, s));
   NCK(nn::up2(ws->d3, ws->u3, N, H / 4, W / 4, 4 * c, s));
-  NRK(conv_fwd(ws, D2, ws->u3, H / 2, W / 2, z, s));
-  NCK(nn::relu_skip(z, ws->r2, ws->e2, ws->d2, p2 * 2 * c, s));
+  NRK(layer_fwd(ws, D2, ws->u3, H / 2, W / 2, ws->r2, ws->e2, ws->d2, s));
   NCK(nn::up2(ws->d2, ws->u2, N, H / 2, W / 2, 2 * c, s));
-  NRK(conv_fwd(ws, D1, ws->u2, H, W, z, s));
-  NCK(nn::relu_skip(z, ws->r1, ws->e1, ws->d1, p1 * c, s));
-  NRK(conv_fwd(ws, OUT, ws->d1, H, W, ws->zo, s));
+  NRK(layer_fwd(ws, D1, ws->u2, H, W, ws->r1, ws->e1, ws->d1, s));
+  NRK(layer_fwd(ws, OUT, ws->d1, H, W, nullptr, nullptr, ws->zo, s));
   NCK(nn::from_nhwc_add(ws->zo, C, X0, N, H, W, 3, s));
   const float* Pf = ws->P.as<float>();
-  NCK(nn::pool_head(ws->e4, Pf + ws->head_w, Pf + ws->head_b, ws->g, loglam_out, N, (H / 8) * (W / 8), 4 * c, s));
+  NCK(nn::pool_head(ws->e4, Pf + ws->head_w, Pf + ws->head_b, ws->g, loglam_out, ws->dA.as<float>(), N,
+                    (H / 8) * (W / 8), 4 * c, s));
   return RTG_OK;
 }
 
@@ -395,7 +387,7 @@ rtg_status rtg_nn_conv3x3(int32_t device, int32_t N, int32_t H, int32_t W, int32
   NCK(nn::to_bf16(w, wb.as<__nv_bfloat16>(), int64_t(cout) * K, s));
   NCK(nn::im2col(x, col.as<__nv_bfloat16>(), N, H, W, cin, stride, s));
   if (y != nullptr)
-    NCK(nn::gemm(false, true, col.as<__nv_bfloat16>(), wb.as<__nv_bfloat16>(), y, b, M, cout, K, K, K, 1, nullptr, s));
+    NCK(nn::conv_fwd(x, wb.as<__nv_bfloat16>(), b, nullptr, nullptr, y, N, H, W, cin, stride, cout, false, s));
   if (dy != nullptr) {
     NRK(zf.ensure(size_t(M) * cout * 4));
     NRK(zb.ensure(size_t(M) * cout * 2));

@@ -24,8 +24,13 @@ cudaError_t add(const float* a, const float* b, float* out, int64_t n, cudaStrea
 cudaError_t to_nhwc(const float* src, float* dst, int N, int H, int W, int C, cudaStream_t s);
 cudaError_t from_nhwc_add(const float* src, const float* base, float* dst, int N, int H, int W, int C,
                           cudaStream_t s);
-cudaError_t pool_head(const float* e, const float* w, const float* b, float* g, float* loglam, int N, int HW,
-                      int C, cudaStream_t s);
+// part: N * 32 * C floats of scratch
+cudaError_t pool_head(const float* e, const float* w, const float* b, float* g, float* loglam, float* part, int N,
+                      int HW, int C, cudaStream_t s);
+// Implicit-GEMM 3x3 convolution forward with fused bias, ReLU and skip:
+// r = act(conv(x) + b) (if r), out = r + skip (if out; skip may be null).
+cudaError_t conv_fwd(const float* x, const __nv_bfloat16* w, const float* bias, float* r, const float* skip,
+                     float* out, int N, int H, int W, int C, int stride, int cout, bool relu, cudaStream_t s);
 cudaError_t loss(const float* X0, const float* Xs, const float* loglam, const float* logmu, float* dout,
                  float* dloglam, double* out, int N, int H, int W, int C, cudaStream_t s);
 cudaError_t head_back(const float* g, const float* dll, const float* w, float* dw, float* db, float* de, int N,
