@@ -161,20 +161,27 @@ cudaError_t gemm(bool a_cm, bool b_t, const __nv_bfloat16* A, const __nv_bfloat1
 // Eight warps; warp w owns output rows 16w..16w+15 and all BN channels.
 constexpr int CBM = 128, CBK = 32, CPAD = 8;
 
+// up = 1: x holds the half-resolution tensor (H/2 x W/2) and the layer
+// reads its nearest x2 up-sampling without materialising it.  gridDim.z > 1
+// splits K: slice z writes its raw sums to part + z * M * cout and the
+// epilogue runs in k_conv_split_epilogue.
 template <int BN>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, BN <= 64 ? 3 : 2)
 k_conv_fwd(const float* __restrict__ x, const __nv_bfloat16* __restrict__ wt, const float* __restrict__ bias,
            float* __restrict__ rout, const float* __restrict__ skip, float* __restrict__ out, int N, int H, int W,
-           int C, int stride, int cout, int relu) {
+           int C, int stride, int cout, int relu, int up, int kchunk, float* __restrict__ part) {
   __shared__ __align__(16) __nv_bfloat16 As[2][CBM][CBK + CPAD];
   __shared__ __align__(16) __nv_bfloat16 Bs[2][BN][CBK + CPAD];
   constexpr int NB = (BN * 4 + 255) / 256;   // 16-byte weight pieces per thread
   const int Ho = H / stride, Wo = W / stride;
-  const int M = N * Ho * Wo, K = 9 * C;
+  const int M = N * Ho * Wo, Kfull = 9 * C;
+  const int kbeg = blockIdx.z * kchunk;
+  const int K = min(Kfull, kbeg + kchunk);   // this slice covers [kbeg, K)
+  const int Hs = up ? H / 2 : H, Ws = up ? W / 2 : W, sh = up ? 1 : 0;   // stored input grid
   const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * BN;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gid = lane >> 2, tig = lane & 3;
   const bool fastA = (C % 32) == 0;
-  const bool fastB = (K % 8) == 0;
+  const bool fastB = (Kfull % 8) == 0;
   float4 ra[4];
   float rs[16];
   uint4 rb[NB];
@@ -190,7 +197,8 @@ k_conv_fwd(const float* __restrict__ x, const __nv_bfloat16* __restrict__ wt, co
           const int j = m % Wo, i = (m / Wo) % Ho, n = m / (Wo * Ho);
           const int yy = stride * i + ky - 1, xx = stride * j + kx - 1;
           if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-            ra[q] = *reinterpret_cast<const float4*>(x + ((static_cast<int64_t>(n) * H + yy) * W + xx) * C + c0 + piece * 4);
+            ra[q] = *reinterpret_cast<const float4*>(
+                x + ((static_cast<int64_t>(n) * Hs + (yy >> sh)) * Ws + (xx >> sh)) * C + c0 + piece * 4);
         }
       }
     } else {
@@ -203,7 +211,8 @@ k_conv_fwd(const float* __restrict__ x, const __nv_bfloat16* __restrict__ wt, co
           const int c = k % C, t = k / C, kx = t % 3, ky = t / 3;
           const int j = m % Wo, i = (m / Wo) % Ho, n = m / (Wo * Ho);
           const int yy = stride * i + ky - 1, xx = stride * j + kx - 1;
-          if (yy >= 0 && yy < H && xx >= 0 && xx < W) rs[q] = x[((static_cast<int64_t>(n) * H + yy) * W + xx) * C + c];
+          if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+            rs[q] = x[((static_cast<int64_t>(n) * Hs + (yy >> sh)) * Ws + (xx >> sh)) * C + c];
         }
       }
     }
@@ -214,12 +223,12 @@ k_conv_fwd(const float* __restrict__ x, const __nv_bfloat16* __restrict__ wt, co
       if (row < BN && n0 + row < cout) {
         const int k = k0 + piece * 8;
         if (fastB && k + 8 <= K) {
-          rb[q] = *reinterpret_cast<const uint4*>(wt + static_cast<int64_t>(n0 + row) * K + k);
+          rb[q] = *reinterpret_cast<const uint4*>(wt + static_cast<int64_t>(n0 + row) * Kfull + k);
         } else {
           __nv_bfloat16 t8[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            t8[u] = (k + u < K) ? wt[static_cast<int64_t>(n0 + row) * K + k + u] : __float2bfloat16(0.f);
+            t8[u] = (k + u < K) ? wt[static_cast<int64_t>(n0 + row) * Kfull + k + u] : __float2bfloat16(0.f);
           rb[q] = *reinterpret_cast<const uint4*>(t8);
         }
       }
@@ -255,11 +264,11 @@ k_conv_fwd(const float* __restrict__ x, const __nv_bfloat16* __restrict__ wt, co
   for (int a = 0; a < BN / 8; ++a)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
-  load_tiles(0);
+  load_tiles(kbeg);
   store_tiles(0);
   __syncthreads();
   int buf = 0;
-  for (int k0 = 0; k0 < K; k0 += CBK) {
+  for (int k0 = kbeg; k0 < K; k0 += CBK) {
     const bool more = k0 + CBK < K;
     if (more) load_tiles(k0 + CBK);   // in flight during the products
 #pragma unroll
@@ -293,6 +302,10 @@ k_conv_fwd(const float* __restrict__ x, const __nv_bfloat16* __restrict__ wt, co
       for (int q = 0; q < 2; ++q) {
         const int c = n0 + nt * 8 + tig * 2 + q;
         if (c >= cout) continue;
+        if (gridDim.z > 1) {
+          part[(static_cast<int64_t>(blockIdx.z) * M + m) * cout + c] = acc[nt][2 * h + q];
+          continue;
+        }
         float v = acc[nt][2 * h + q] + (bias ? bias[c] : 0.f);
         if (relu) v = fmaxf(v, 0.f);
         const int64_t o = static_cast<int64_t>(m) * cout + c;
@@ -302,16 +315,51 @@ k_conv_fwd(const float* __restrict__ x, const __nv_bfloat16* __restrict__ wt, co
     }
 }
 
+// Epilogue of a K-split convolution: sum the slices in order, then bias,
+// activation and skip as in k_conv_fwd.
+__global__ void k_conv_split_epilogue(const float* __restrict__ part, const float* __restrict__ bias,
+                                      float* __restrict__ rout, const float* __restrict__ skip,
+                                      float* __restrict__ out, int64_t MC, int cout, int nz, int relu) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < MC;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float v = 0.f;
+    for (int z = 0; z < nz; ++z) v += part[static_cast<int64_t>(z) * MC + i];
+    v += bias ? bias[i % cout] : 0.f;
+    if (relu) v = fmaxf(v, 0.f);
+    if (rout != nullptr) rout[i] = v;
+    if (out != nullptr) out[i] = skip ? v + skip[i] : v;
+  }
+}
+
 cudaError_t conv_fwd(const float* x, const __nv_bfloat16* w, const float* bias, float* r, const float* skip,
-                     float* out, int N, int H, int W, int C, int stride, int cout, bool relu, cudaStream_t s) {
+                     float* out, int N, int H, int W, int C, int stride, int cout, bool relu, bool up,
+                     float* part, int64_t part_floats, cudaStream_t s) {
   const int M = N * (H / stride) * (W / stride);
+  const int K = 9 * C;
   const int bn = cout <= 8 ? 8 : (cout <= 32 ? 32 : (cout <= 64 ? 64 : 128));
-  dim3 grid((M + CBM - 1) / CBM, (cout + bn - 1) / bn);
-  const int rl = relu ? 1 : 0;
-  if (bn == 8) k_conv_fwd<8><<<grid, 256, 0, s>>>(x, w, bias, r, skip, out, N, H, W, C, stride, cout, rl);
-  else if (bn == 32) k_conv_fwd<32><<<grid, 256, 0, s>>>(x, w, bias, r, skip, out, N, H, W, C, stride, cout, rl);
-  else if (bn == 64) k_conv_fwd<64><<<grid, 256, 0, s>>>(x, w, bias, r, skip, out, N, H, W, C, stride, cout, rl);
-  else k_conv_fwd<128><<<grid, 256, 0, s>>>(x, w, bias, r, skip, out, N, H, W, C, stride, cout, rl);
+  const int mtiles = (M + CBM - 1) / CBM, ntiles = (cout + bn - 1) / bn;
+  // split K (in whole 32-wide steps) when the tiles alone leave SMs idle
+  int splits = 1;
+  if (part != nullptr && mtiles * ntiles < 152) {
+    splits = (304 + mtiles * ntiles - 1) / (mtiles * ntiles);
+    const int ksteps = (K + CBK - 1) / CBK;
+    if (splits > ksteps / 2) splits = ksteps / 2 > 1 ? ksteps / 2 : 1;
+    while (splits > 1 && int64_t(splits) * M * cout > part_floats) --splits;
+  }
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = ((kchunk + CBK - 1) / CBK) * CBK;
+  splits = (K + kchunk - 1) / kchunk;
+  dim3 grid(mtiles, ntiles, splits);
+  const int rl = relu ? 1 : 0, u = up ? 1 : 0;
+#define RTG_CONV_CASE(B_)                                                                                   \
+  if (bn == B_)                                                                                             \
+    k_conv_fwd<B_><<<grid, 256, 0, s>>>(x, w, bias, r, skip, out, N, H, W, C, stride, cout, rl, u, kchunk, part);
+  RTG_CONV_CASE(8) RTG_CONV_CASE(32) RTG_CONV_CASE(64) RTG_CONV_CASE(128)
+#undef RTG_CONV_CASE
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  const int64_t MC = int64_t(M) * cout;
+  k_conv_split_epilogue<<<grid_of(MC), 256, 0, s>>>(part, bias, r, skip, out, MC, cout, splits, rl);
   return cudaGetLastError();
 }
 

@@ -206,27 +206,37 @@ rtg_status conv_bwd(rtg_warmstart* ws, int l, const float* x, int h, int w, cons
 
 // One forward layer through the implicit-GEMM kernel: r = relu(conv(x) + b)
 // (when r), out = r + skip (skip may be null); the output layer has no ReLU.
-rtg_status layer_fwd(rtg_warmstart* ws, int l, const float* x, int h, int w, float* r, const float* skip,
+// up: x is the half-resolution tensor, read through its x2 up-sampling.
+rtg_status layer_fwd(rtg_warmstart* ws, int l, const float* x, int h, int w, bool up, float* r, const float* skip,
                      float* out, cudaStream_t s) {
   const Layer& L = ws->L[l];
-  NCK(nn::conv_fwd(x, Wb(ws, l), Bf(ws, l), r, skip, out, ws->N, h, w, L.cin, L.stride, L.cout, l != OUT, s));
+  NCK(nn::conv_fwd(x, Wb(ws, l), Bf(ws, l), r, skip, out, ws->N, h, w, L.cin, L.stride, L.cout, l != OUT, up,
+                   ws->dA.as<float>(), int64_t(ws->dA.bytes / 4), s));
   return RTG_OK;
 }
 
-rtg_status forward(rtg_warmstart* ws, const float* C, float* X0, float* loglam_out, cudaStream_t s) {
+// training: the up-sampled decoder inputs are materialised (the backward
+// pass reads them); inference reads them through the convolution's gather.
+rtg_status forward(rtg_warmstart* ws, const float* C, float* X0, float* loglam_out, bool training, cudaStream_t s) {
   const int N = ws->N, H = ws->H, W = ws->W, c = ws->base;
   NCK(nn::to_nhwc(C, ws->x0, N, H, W, 3, s));
-  NRK(layer_fwd(ws, E1, ws->x0, H, W, nullptr, nullptr, ws->e1, s));
-  NRK(layer_fwd(ws, E2, ws->e1, H, W, nullptr, nullptr, ws->e2, s));
-  NRK(layer_fwd(ws, E3, ws->e2, H / 2, W / 2, nullptr, nullptr, ws->e3, s));
-  NRK(layer_fwd(ws, E4, ws->e3, H / 4, W / 4, nullptr, nullptr, ws->e4, s));
-  NCK(nn::up2(ws->e4, ws->u4, N, H / 8, W / 8, 4 * c, s));
-  NRK(layer_fwd(ws, D3, ws->u4, H / 4, W / 4, ws->r3, ws->e3, ws->d3, s));
-  NCK(nn::up2(ws->d3, ws->u3, N, H / 4, W / 4, 4 * c, s));
-  NRK(layer_fwd(ws, D2, ws->u3, H / 2, W / 2, ws->r2, ws->e2, ws->d2, s));
-  NCK(nn::up2(ws->d2, ws->u2, N, H / 2, W / 2, 2 * c, s));
-  NRK(layer_fwd(ws, D1, ws->u2, H, W, ws->r1, ws->e1, ws->d1, s));
-  NRK(layer_fwd(ws, OUT, ws->d1, H, W, nullptr, nullptr, ws->zo, s));
+  NRK(layer_fwd(ws, E1, ws->x0, H, W, false, nullptr, nullptr, ws->e1, s));
+  NRK(layer_fwd(ws, E2, ws->e1, H, W, false, nullptr, nullptr, ws->e2, s));
+  NRK(layer_fwd(ws, E3, ws->e2, H / 2, W / 2, false, nullptr, nullptr, ws->e3, s));
+  NRK(layer_fwd(ws, E4, ws->e3, H / 4, W / 4, false, nullptr, nullptr, ws->e4, s));
+  if (training) {
+    NCK(nn::up2(ws->e4, ws->u4, N, H / 8, W / 8, 4 * c, s));
+    NRK(layer_fwd(ws, D3, ws->u4, H / 4, W / 4, false, ws->r3, ws->e3, ws->d3, s));
+    NCK(nn::up2(ws->d3, ws->u3, N, H / 4, W / 4, 4 * c, s));
+    NRK(layer_fwd(ws, D2, ws->u3, H / 2, W / 2, false, ws->r2, ws->e2, ws->d2, s));
+    NCK(nn::up2(ws->d2, ws->u2, N, H / 2, W / 2, 2 * c, s));
+    NRK(layer_fwd(ws, D1, ws->u2, H, W, false, ws->r1, ws->e1, ws->d1, s));
+  } else {
+    NRK(layer_fwd(ws, D3, ws->e4, H / 4, W / 4, true, nullptr, ws->e3, ws->d3, s));
+    NRK(layer_fwd(ws, D2, ws->d3, H / 2, W / 2, true, nullptr, ws->e2, ws->d2, s));
+    NRK(layer_fwd(ws, D1, ws->d2, H, W, true, nullptr, ws->e1, ws->d1, s));
+  }
+  NRK(layer_fwd(ws, OUT, ws->d1, H, W, false, nullptr, nullptr, ws->zo, s));
   NCK(nn::from_nhwc_add(ws->zo, C, X0, N, H, W, 3, s));
   const float* Pf = ws->P.as<float>();
   NCK(nn::pool_head(ws->e4, Pf + ws->head_w, Pf + ws->head_b, ws->g, loglam_out, ws->dA.as<float>(), N,
@@ -341,7 +351,7 @@ rtg_status rtg_ws_predict(rtg_ws ws, int32_t n_img, int32_t I1, int32_t I2, cons
   DevGuard dg(ws->device);
   NRK(check_batch(ws, n_img, I1, I2));
   if (C == nullptr || X0 == nullptr || loglam == nullptr) return nfail(RTG_ERR_INVALID_ARG, "NULL argument");
-  return forward(ws, C, X0, loglam, reinterpret_cast<cudaStream_t>(stream));
+  return forward(ws, C, X0, loglam, false, reinterpret_cast<cudaStream_t>(stream));
 }
 
 rtg_status rtg_ws_train_step(rtg_ws ws, int32_t n_img, int32_t I1, int32_t I2, const float* C, const float* Xstar,
@@ -353,7 +363,7 @@ rtg_status rtg_ws_train_step(rtg_ws ws, int32_t n_img, int32_t I1, int32_t I2, c
   if (C == nullptr || Xstar == nullptr || logmu == nullptr || X0_scratch == nullptr)
     return nfail(RTG_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  NRK(forward(ws, C, X0_scratch, ws->loglam, s));
+  NRK(forward(ws, C, X0_scratch, ws->loglam, true, s));
   NCK(nn::loss(X0_scratch, Xstar, ws->loglam, logmu, ws->dout, ws->dll, ws->loss, ws->N, ws->H, ws->W, 3, s));
   NRK(backward(ws, s));
   if (lr > 0.f) {
@@ -387,7 +397,8 @@ rtg_status rtg_nn_conv3x3(int32_t device, int32_t N, int32_t H, int32_t W, int32
   NCK(nn::to_bf16(w, wb.as<__nv_bfloat16>(), int64_t(cout) * K, s));
   NCK(nn::im2col(x, col.as<__nv_bfloat16>(), N, H, W, cin, stride, s));
   if (y != nullptr)
-    NCK(nn::conv_fwd(x, wb.as<__nv_bfloat16>(), b, nullptr, nullptr, y, N, H, W, cin, stride, cout, false, s));
+    NCK(nn::conv_fwd(x, wb.as<__nv_bfloat16>(), b, nullptr, nullptr, y, N, H, W, cin, stride, cout, false, false,
+                     nullptr, 0, s));
   if (dy != nullptr) {
     NRK(zf.ensure(size_t(M) * cout * 4));
     NRK(zb.ensure(size_t(M) * cout * 2));

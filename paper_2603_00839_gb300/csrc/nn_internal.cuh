@@ -29,8 +29,12 @@ cudaError_t pool_head(const float* e, const float* w, const float* b, float* g, 
                       int HW, int C, cudaStream_t s);
 // Implicit-GEMM 3x3 convolution forward with fused bias, ReLU and skip:
 // r = act(conv(x) + b) (if r), out = r + skip (if out; skip may be null).
+// H x W is the grid the convolution reads; up: x is stored at H/2 x W/2 and
+// read through its nearest x2 up-sampling.  part (part_floats floats, may be
+// null) lets small layers split K across CTAs.
 cudaError_t conv_fwd(const float* x, const __nv_bfloat16* w, const float* bias, float* r, const float* skip,
-                     float* out, int N, int H, int W, int C, int stride, int cout, bool relu, cudaStream_t s);
+                     float* out, int N, int H, int W, int C, int stride, int cout, bool relu, bool up,
+                     float* part, int64_t part_floats, cudaStream_t s);
 cudaError_t loss(const float* X0, const float* Xs, const float* loglam, const float* logmu, float* dout,
                  float* dloglam, double* out, int N, int H, int W, int C, cudaStream_t s);
 cudaError_t head_back(const float* g, const float* dll, const float* w, float* dw, float* db, float* de, int N,
