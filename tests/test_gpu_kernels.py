@@ -155,6 +155,9 @@ SKETCH_CASES = [
     ((97,), (13,), 3),                    # order 1
     ((12, 10, 3), (12, 10, 3), 0),        # nothing sketched: S = I
     ((33, 20, 5), (1, 1, 2), 4),          # sketch size 1
+    ((64, 512, 20), (32, 64, 20), 2),     # >= 608 column tiles: the multi-tile first stage
+    ((36, 300, 35), (20, 50, 35), 6),     # multi-tile, ragged rows and a 4-column last tile
+    ((320, 64, 160), (80, 16, 16), 7),    # multi-tile, 20 K tiles, two row blocks
 ]
 
 
@@ -183,6 +186,21 @@ def test_sketch_full_size_image512_sampled(h):
         a, b, c = rng.integers(0, 128), rng.integers(0, 128), rng.integers(0, 3)
         ref = th[0][a] @ X[:, :, c] @ th[1][b]
         assert abs(SX[a, b, c] - ref) <= 2e-6 * max(1.0, np.abs(X[:, :, c]).sum() / 128)
+
+
+def test_sketch_full_size_video_sampled(h):
+    """256x256x3x64 with sketch (96,96,3,32): sampled entries against the definition."""
+    api = _api()
+    X = np.random.default_rng(4).standard_normal((256, 256, 3, 64))
+    SX = h.sketch(api.to_device(X, torch.float32), (96, 96, 3, 32), seed=5).cpu().double().numpy()
+    th = oracle.sketch_matrices((256, 256, 3, 64), (96, 96, 3, 32), 5)
+    rng = np.random.default_rng(2)
+    for _ in range(48):
+        a, b, c, d = rng.integers(0, 96), rng.integers(0, 96), rng.integers(0, 3), rng.integers(0, 32)
+        ref = np.einsum("i,ijf,j,f->", th[0][a], X[:, :, c, :], th[1][b], th[3][d])
+        mag = np.einsum("i,ijf,j,f->", np.abs(th[0][a]), np.abs(X[:, :, c, :]), np.abs(th[1][b]),
+                        np.abs(th[3][d]))
+        assert abs(SX[a, b, c, d] - ref) <= 1e-6 * mag
 
 
 def test_sketch_problem_id_changes_signs(h):
