@@ -103,6 +103,9 @@ typedef struct rtg_opts {
                                         in flight at the same time on different streams must use
                                         different slots (each slot owns its own basis, sketch and
                                         graph); calls on one slot are ordered by their stream */
+    int32_t group_max;               /* batched solves: most problems in one lock-step group;
+                                        0 or 1: every problem its own graph branch */
+    int32_t pad;
 } rtg_opts;
 
 #define RTG_MAX_SLOTS 64
@@ -413,16 +416,25 @@ typedef struct rtg_problem {
 
 /*
  * Batched form: nprob independent RTG-GMRES solves, of any mix of shapes,
- * operators, Krylov dimensions and sketch sizes, launched as one CUDA
- * graph in which every problem is an independent branch (its own
- * prologue, device-side loop over Arnoldi steps with its own stop
- * decision, and epilogue), so the GPU runs the problems' kernels side by
- * side.  The graph is built on the first call for a given list of problem
- * shapes and replayed afterwards; descriptors go up in one copy and the
- * info records come back in one copy.  opts (may be NULL) is shared: GCV
- * grid, breakdown level and RTG_FLAG_BF16_BASIS; slot, NO_GRAPH and
- * PHASE_TIMES do not apply.  infos: NULL or nprob records (elapsed_ms is
- * the whole batch's).  The call synchronises `stream` once.
+ * operators, Krylov dimensions and sketch sizes.  By default every problem
+ * is its own group.  With opts->group_max = g > 1, problems of the same
+ * structure (shape, factor list and values, m, sketch sizes, kind of
+ * regularisation -- fixed, least squares or GCV -- and whether X0 is given)
+ * form lock-step groups of up to g problems: every kernel launch serves the
+ * whole group, each problem keeps its own stop decision (a stopped
+ * problem's blocks return at once), and the group's device-side loop runs
+ * while any of its problems does.  Lock step pays when single problems are
+ * too small to fill the GPU and converge alike; separate groups pay when
+ * convergence varies.  Each result equals, bit for bit, the same problem
+ * solved alone.  The groups are independent branches of one CUDA graph, built on
+ * the first call for a given list of problem structures and replayed
+ * afterwards; descriptors go up in one strided copy per group and the info
+ * records come back the same way.  opts (may be NULL) is shared: GCV grid,
+ * breakdown level, RTG_FLAG_BF16_BASIS, and RTG_FLAG_NO_GRAPH /
+ * RTG_FLAG_PHASE_TIMES (direct launches, one group after another; with
+ * PHASE_TIMES each problem's phase_ms / phase_launches are those of its
+ * whole group); slot does not apply.  infos: NULL or nprob records
+ * (elapsed_ms is the whole batch's).  The call synchronises `stream`.
  * Errors: as rtg_gmres_solve, per problem (the message names it); host
  * pointers are INVALID_ARG.
  */

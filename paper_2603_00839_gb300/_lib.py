@@ -41,7 +41,7 @@ class Factor(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("mu_grid", C.POINTER(C.c_double)), ("n_mu", C.c_int32),
                 ("max_restarts", C.c_int32), ("breakdown_tol", C.c_double), ("flags", C.c_int32),
-                ("slot", C.c_int32)]
+                ("slot", C.c_int32), ("group_max", C.c_int32), ("pad", C.c_int32)]
 
 
 class Problem(C.Structure):

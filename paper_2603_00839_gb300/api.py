@@ -314,11 +314,16 @@ class Handle:
                             (C_obs, X0, a, b, ka, kb, sk))
 
     def gmres_solve_batched(self, problems: Sequence[dict], mu_grid=None, breakdown_tol: float = 0.0,
-                            bf16_basis: bool = False, stream=None):
+                            bf16_basis: bool = False, use_graph: bool = True, phase_times: bool = False,
+                            group_max: int = 0, stream=None):
         """Batched form (rtg_gmres_solve_batched): every problem is a dict with
         C (device tensor), m, sketch_dims, seed, lam, and optionally A, B
         (factor lists), tol, X0, X.  All problems share C's dtype; each may
-        have its own shape.  Returns ([X], [SolveResult])."""
+        have its own shape; problems of equal structure run in lock step.
+        use_graph=False / phase_times=True launch directly, one group after
+        another (phase_ms: the problem's whole group).  group_max > 1 runs
+        problems of equal structure in lock-step groups of up to that many
+        (default: one graph branch per problem).  Returns ([X], [SolveResult])."""
         if not problems:
             raise ValueError("no problems")
         arr = (L.Problem * len(problems))()
@@ -356,7 +361,9 @@ class Handle:
             opts.mu_grid = grid.ctypes.data_as(C.POINTER(C.c_double))
             opts.n_mu = len(grid)
         opts.breakdown_tol = float(breakdown_tol)
-        opts.flags = L.FLAG_BF16_BASIS if bf16_basis else 0
+        opts.group_max = int(group_max)
+        opts.flags = ((L.FLAG_BF16_BASIS if bf16_basis else 0) | (0 if use_graph else L.FLAG_NO_GRAPH) |
+                      (L.FLAG_PHASE_TIMES if phase_times else 0))
         infos = (L.Info * len(problems))()
         bufs = []
         for i, q in enumerate(problems):
@@ -369,6 +376,10 @@ class Handle:
                                                  _stream(stream)))
         res = [_solve_result(infos[i], bufs[i][0], bufs[i][1], grid, float(q["lam"]))
                for i, q in enumerate(problems)]
+        if phase_times:
+            for i, r in enumerate(res):
+                r.phase_ms = {k: infos[i].phase_ms[j] for j, k in enumerate(L.PHASES)}
+                r.phase_launches = {k: infos[i].phase_launches[j] for j, k in enumerate(L.PHASES)}
         return Xs, res
 
     def gmres_wait(self, pend: "PendingSolve"):

@@ -19,9 +19,19 @@ __device__ __forceinline__ A warp_sum(A v) {
   return v;
 }
 
-__device__ __forceinline__ void set_cond(const StepOpts& o, int keep_going) {
-  if (o.use_cond)
-    cudaGraphSetConditional(static_cast<cudaGraphConditionalHandle>(o.cond), keep_going ? 1u : 0u);
+// Condition of the device-side loop.  A lock-step batch (o.group_left set)
+// keeps looping while any of its problems runs: each problem's stop is
+// counted once, and the count reaching zero ends the loop.
+// (The count is kept on direct launches too: the host reads it per step.)
+__device__ __forceinline__ void set_cond(const StepOpts& o, int keep_going, Ctl* ctl = nullptr) {
+  const cudaGraphConditionalHandle h = static_cast<cudaGraphConditionalHandle>(o.cond);
+  if (o.group_left == nullptr) {
+    if (o.use_cond) cudaGraphSetConditional(h, keep_going ? 1u : 0u);
+    return;
+  }
+  if (!keep_going && ctl != nullptr && atomicExch(&ctl->counted, 1) == 0 && atomicSub(o.group_left, 1u) == 1u &&
+      o.use_cond)
+    cudaGraphSetConditional(h, 0u);
 }
 
 // Double-float ("float-float") accumulation for FP32 data: the FP64 pipe
@@ -285,7 +295,7 @@ __device__ inline void gs_finish_start(const Work& w, const StepOpts& o, const d
     }
     if (w.m == 0) ctl->stop = 1;
   }
-  set_cond(o, !ctl->stop);
+  set_cond(o, !ctl->stop, ctl);
 }
 
 // Step finish from one reduction (every thread of the last block).
@@ -458,7 +468,7 @@ __device__ inline void givens_step(const Work& w, const StepOpts& o) {
     ctl->stop = 1;
     if (o.use_cond && loops > w.m + 1 && ctl->status == 0) ctl->status = RTG_ERR_TIMEOUT;
   }
-  set_cond(o, !ctl->stop);
+  set_cond(o, !ctl->stop, ctl);
 }
 
 }  // namespace rtg

@@ -31,7 +31,12 @@ struct FusedArgs {
 
 template <typename T, int NC>
 __global__ void __launch_bounds__(FTHREADS)
-k_apply_fused(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
+k_apply_fused(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch bt) {
+  const BIdx bi = bidx(bt);
+  Xr = Xr.at(bi.off);
+  Yr = Yr.at(bi.off);
+  Zr = Zr.at(bi.off);
+  stop = bsh(stop, bi.off);
   if (stop != nullptr && *stop) return;
   const T* __restrict__ X = Xr.get<const T>();
   T* __restrict__ Y = Yr.get<T>();
@@ -52,7 +57,7 @@ k_apply_fused(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
   const int ty = threadIdx.x / FTX;          // 0..3, rows ty + 4k
   T acc[NC][FTY / 4];
 
-  for (int64_t slab = blockIdx.z; slab < a.nslab; slab += gridDim.z) {
+  for (int64_t slab = bi.z; slab < a.nslab; slab += bi.nz) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const T* Xc = X + (slab * NC + c) * plane;
@@ -133,8 +138,13 @@ struct RegGeom {
 };
 
 template <typename T, int NC, int RR>
-__global__ void __launch_bounds__(FTHREADS)
-k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
+__global__ void __launch_bounds__(FTHREADS, (RR <= 7 ? 3 : 1))
+k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch bt) {
+  const BIdx bi = bidx(bt);
+  Xr = Xr.at(bi.off);
+  Yr = Yr.at(bi.off);
+  Zr = Zr.at(bi.off);
+  stop = bsh(stop, bi.off);
   if (stop != nullptr && *stop) return;
   const T* __restrict__ X = Xr.get<const T>();
   T* __restrict__ Y = Yr.get<T>();
@@ -158,7 +168,7 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a) {
   const int64_t plane = a.I1 * a.I2;
   const int vx = threadIdx.x & (RTX - 1);        // mode-2 pass: column
   const int vy = (threadIdx.x / RTX) * VSEG;     // mode-2 pass: first of 4 rows
-  for (int64_t slab = blockIdx.z; slab < a.nslab; slab += gridDim.z) {
+  for (int64_t slab = bi.z; slab < a.nslab; slab += bi.nz) {
     __syncthreads();
     const T* Xs = X + slab * NC * plane;
     if (sizeof(T) == 4 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
@@ -319,7 +329,12 @@ __device__ __forceinline__ void st_store(__nv_bfloat16* p, float v) { *p = __flo
 
 template <typename TI, typename TO, int NC, int RR>
 __global__ void __launch_bounds__(ST_THREADS, 2)
-k_apply_st(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, StArgs a) {
+k_apply_st(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, StArgs a, Batch bt) {
+  const BIdx bi = bidx(bt);
+  Xr = Xr.at(bi.off);
+  Yr = Yr.at(bi.off);
+  Zr = Zr.at(bi.off);
+  stop = bsh(stop, bi.off);
   if (stop != nullptr && *stop) return;
   const TI* __restrict__ X = Xr.get<const TI>();
   TO* __restrict__ Y = Yr.get<TO>();
@@ -335,8 +350,8 @@ k_apply_st(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, StArgs a) {
   const int x0 = blockIdx.x * STX, y0 = blockIdx.y * STY;
   const int I1 = static_cast<int>(a.I1), I2 = static_cast<int>(a.I2);
   const int64_t plane = a.I1 * a.I2;
-  const int group = static_cast<int>(blockIdx.z / a.nchunk);
-  const int chunk = static_cast<int>(blockIdx.z % a.nchunk);
+  const int group = static_cast<int>(bi.z / a.nchunk);
+  const int chunk = static_cast<int>(bi.z % a.nchunk);
   const int64_t f0 = static_cast<int64_t>(chunk) * a.F;
   const int64_t f1 = (f0 + a.F < a.nF) ? f0 + a.F : a.nF;
   const int rt = a.rt;
@@ -500,7 +515,11 @@ struct TapArgs {
 // out(l, i, r) = sum_t taps[r+t] X(l, i+t, r), zero outside [0, I)
 template <typename T>
 __global__ void k_pass_band(PtrRef Xr, PtrRef Yr, int64_t L, int64_t I, int64_t R, int rad,
-                            TapArgs taps, const int* stop) {
+                            TapArgs taps, const int* stop, Batch bt) {
+  const int64_t bo = bidx(bt).off;
+  Xr = Xr.at(bo);
+  Yr = Yr.at(bo);
+  stop = bsh(stop, bo);
   if (stop != nullptr && *stop) return;
   const T* __restrict__ X = Xr.get<const T>();
   T* __restrict__ Y = Yr.get<T>();
@@ -522,7 +541,11 @@ __global__ void k_pass_band(PtrRef Xr, PtrRef Yr, int64_t L, int64_t I, int64_t 
 // out(l, p, r) = sum_i M(p, i) X(l, i, r), M column-major on the device
 template <typename T>
 __global__ void k_pass_dense(PtrRef Xr, PtrRef Yr, int64_t L, int64_t I, int64_t R,
-                             const double* __restrict__ M, const int* stop) {
+                             const double* __restrict__ M, const int* stop, Batch bt) {
+  const int64_t bo = bidx(bt).off;
+  Xr = Xr.at(bo);
+  Yr = Yr.at(bo);
+  stop = bsh(stop, bo);
   if (stop != nullptr && *stop) return;
   const T* __restrict__ X = Xr.get<const T>();
   T* __restrict__ Y = Yr.get<T>();
@@ -541,7 +564,12 @@ __global__ void k_pass_dense(PtrRef Xr, PtrRef Yr, int64_t L, int64_t I, int64_t
 // Y = alpha * A + beta * Z (Y may alias A)
 template <typename T>
 __global__ void k_axpby(PtrRef Ar, PtrRef Yr, PtrRef Zr, double alpha, double beta, int64_t n,
-                        const int* stop) {
+                        const int* stop, Batch bt) {
+  const int64_t bo = bidx(bt).off;
+  Ar = Ar.at(bo);
+  Yr = Yr.at(bo);
+  Zr = Zr.at(bo);
+  stop = bsh(stop, bo);
   if (stop != nullptr && *stop) return;
   const T* A = Ar.get<const T>();
   T* Y = Yr.get<T>();
@@ -589,7 +617,7 @@ static bool has_ptr(const PtrRef& r) { return r.base != nullptr || r.ind != null
 
 template <typename T>
 static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, double beta,
-                           PtrRef Z, T* tmp, T* tmp2, const int* stop, cudaStream_t s) {
+                           PtrRef Z, T* tmp, T* tmp2, const int* stop, cudaStream_t s, Batch b) {
   int64_t n = 1;
   for (int k = 0; k < op.order; ++k) n *= op.dims[k];
   if (n == 0) return cudaSuccess;
@@ -620,7 +648,7 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
                       (sizeof(T) == 8 || (a.I1 % 4) == 0);
     if (rr > 0 && fits && (a.nc == 1 || a.nc == 3)) {
       dim3 grid(static_cast<unsigned>((a.I1 + RTX - 1) / RTX), static_cast<unsigned>((a.I2 + RTY - 1) / RTY),
-                static_cast<unsigned>(a.nslab < 65535 ? a.nslab : 65535));
+                batch_z(a.nslab, b));
       cudaError_t e = cudaSuccess;
 #define RTG_REG_CASE(NC, RR)                                                                          \
   if (a.nc == NC && rr == RR) {                                                                       \
@@ -629,7 +657,7 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
     e = cudaFuncSetAttribute(k_apply_reg<T, NC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                              static_cast<int>(smem));                                                  \
     if (e != cudaSuccess) return e;                                                                   \
-    k_apply_reg<T, NC, RR><<<grid, FTHREADS, smem, s>>>(X, Y, Z, stop, a);                            \
+    k_apply_reg<T, NC, RR><<<grid, FTHREADS, smem, s>>>(X, Y, Z, stop, a, b);                            \
     return cudaGetLastError();                                                                        \
   }
       RTG_REG_CASE(1, 3) RTG_REG_CASE(1, 5) RTG_REG_CASE(1, 7) RTG_REG_CASE(1, 9) RTG_REG_CASE(1, 12) RTG_REG_CASE(1, 16)
@@ -639,7 +667,7 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
     const size_t smem = fused_smem(op, sizeof(T));
     dim3 grid(static_cast<unsigned>((a.I1 + FTX - 1) / FTX),
               static_cast<unsigned>((a.I2 + FTY - 1) / FTY),
-              static_cast<unsigned>(a.nslab < 65535 ? a.nslab : 65535));
+              batch_z(a.nslab, b));
     cudaError_t e = cudaSuccess;
     switch (a.nc) {
 #define RTG_FUSED_CASE(NC)                                                                        \
@@ -647,7 +675,7 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
     e = cudaFuncSetAttribute(k_apply_fused<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                              static_cast<int>(smem));                                              \
     if (e != cudaSuccess) return e;                                                               \
-    k_apply_fused<T, NC><<<grid, FTHREADS, smem, s>>>(X, Y, Z, stop, a);                          \
+    k_apply_fused<T, NC><<<grid, FTHREADS, smem, s>>>(X, Y, Z, stop, a, b);                          \
     break;
       RTG_FUSED_CASE(1)
       RTG_FUSED_CASE(2)
@@ -661,7 +689,7 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
   }
   // unfused: one kernel per mode product
   if (op.npass == 0) {
-    k_axpby<T><<<grid_for(n, 256), 256, 0, s>>>(X, Y, Z, alpha, has_ptr(Z) ? beta : 0.0, n, stop);
+    k_axpby<T><<<dim3(grid_for(n, 256), 1, b.n), 256, 0, s>>>(X, Y, Z, alpha, has_ptr(Z) ? beta : 0.0, n, stop, b);
     return cudaGetLastError();
   }
   PtrRef src = X;
@@ -675,16 +703,16 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
     if (ps.kind == PK_BAND) {
       TapArgs ta{};
       for (int t = 0; t <= 2 * ps.radius; ++t) ta.t[t] = ps.taps[t];
-      k_pass_band<T><<<grid_for(n, 256), 256, 0, s>>>(src, dst, L, I, R, ps.radius, ta, stop);
+      k_pass_band<T><<<dim3(grid_for(n, 256), 1, b.n), 256, 0, s>>>(src, dst, L, I, R, ps.radius, ta, stop, b);
     } else {
-      k_pass_dense<T><<<grid_for(n, 256), 256, 0, s>>>(src, dst, L, I, R, ps.dense, stop);
+      k_pass_dense<T><<<dim3(grid_for(n, 256), 1, b.n), 256, 0, s>>>(src, dst, L, I, R, ps.dense, stop, b);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     src = dst;
   }
   if (alpha != 1.0 || has_ptr(Z)) {
-    k_axpby<T><<<grid_for(n, 256), 256, 0, s>>>(Y, Y, Z, alpha, has_ptr(Z) ? beta : 0.0, n, stop);
+    k_axpby<T><<<dim3(grid_for(n, 256), 1, b.n), 256, 0, s>>>(Y, Y, Z, alpha, has_ptr(Z) ? beta : 0.0, n, stop, b);
   }
   return cudaGetLastError();
 }
@@ -707,7 +735,7 @@ bool st_supported(const OpPlan& op, int tin) {
 
 template <typename TI, typename TO>
 static cudaError_t apply_st_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, double beta,
-                              PtrRef Z, const int* stop, cudaStream_t s) {
+                              PtrRef Z, const int* stop, cudaStream_t s, Batch b) {
   StArgs a{};
   a.I1 = op.dims[0];
   a.I2 = op.order > 1 ? op.dims[1] : 1;
@@ -730,7 +758,8 @@ static cudaError_t apply_st_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha
   a.beta = has_ptr(Z) ? static_cast<float>(beta) : 0.f;
   const int64_t gx = (a.I1 + STX - 1) / STX, gy = (a.I2 + STY - 1) / STY, groups = a.I3 / nc;
   st_chunks(gx * gy * groups, a.nF, &a.F, &a.nchunk);
-  dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy), static_cast<unsigned>(groups * a.nchunk));
+  if (groups * a.nchunk * b.n > 65535) return cudaErrorInvalidConfiguration;
+  dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy), static_cast<unsigned>(groups * a.nchunk * b.n));
 #define RTG_ST_CASE(NC, RR)                                                                         \
   if (nc == NC && rr == RR) {                                                                       \
     using Gm = StGeom<RR, TI>;                                                                      \
@@ -739,7 +768,7 @@ static cudaError_t apply_st_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,              \
                                          static_cast<int>(smem));                                  \
     if (e != cudaSuccess) return e;                                                                 \
-    k_apply_st<TI, TO, NC, RR><<<grid, ST_THREADS, smem, s>>>(X, Y, Z, stop, a);                    \
+    k_apply_st<TI, TO, NC, RR><<<grid, ST_THREADS, smem, s>>>(X, Y, Z, stop, a, b);                    \
     return cudaGetLastError();                                                                      \
   }
   RTG_ST_CASE(1, 3) RTG_ST_CASE(1, 5) RTG_ST_CASE(1, 7) RTG_ST_CASE(1, 9)
@@ -750,27 +779,27 @@ static cudaError_t apply_st_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha
 
 cudaError_t launch_apply(const OpPlan& op, int dtype, PtrRef X, PtrRef Y, double alpha,
                          double beta, PtrRef Z, void* tmp, void* tmp2, const int* stop,
-                         cudaStream_t s, int tin, int tout) {
+                         cudaStream_t s, int tin, int tout, Batch b) {
   if (tin < 0) tin = dtype;
   if (tout < 0) tout = dtype;
   if (tin == RTG_BF16 || tout == RTG_BF16 || (dtype == RTG_F32 && op.st && op.r4 > 0)) {
     if (!apply_uses_st(op, dtype, tin, tout)) {
       if (tin == RTG_BF16 || tout == RTG_BF16) return cudaErrorInvalidValue;
     } else if (tin == RTG_BF16 && tout == RTG_BF16) {
-      return apply_st_t<__nv_bfloat16, __nv_bfloat16>(op, X, Y, alpha, beta, Z, stop, s);
+      return apply_st_t<__nv_bfloat16, __nv_bfloat16>(op, X, Y, alpha, beta, Z, stop, s, b);
     } else if (tin == RTG_F32 && tout == RTG_BF16) {
-      return apply_st_t<float, __nv_bfloat16>(op, X, Y, alpha, beta, Z, stop, s);
+      return apply_st_t<float, __nv_bfloat16>(op, X, Y, alpha, beta, Z, stop, s, b);
     } else if (tin == RTG_F32 && tout == RTG_F32) {
-      return apply_st_t<float, float>(op, X, Y, alpha, beta, Z, stop, s);
+      return apply_st_t<float, float>(op, X, Y, alpha, beta, Z, stop, s, b);
     } else {
       return cudaErrorInvalidValue;
     }
   }
   if (dtype == RTG_F64)
     return apply_t<double>(op, X, Y, alpha, beta, Z, static_cast<double*>(tmp),
-                           static_cast<double*>(tmp2), stop, s);
+                           static_cast<double*>(tmp2), stop, s, b);
   return apply_t<float>(op, X, Y, alpha, beta, Z, static_cast<float*>(tmp),
-                        static_cast<float*>(tmp2), stop, s);
+                        static_cast<float*>(tmp2), stop, s, b);
 }
 
 }  // namespace rtg

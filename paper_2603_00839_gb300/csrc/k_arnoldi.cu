@@ -42,7 +42,10 @@ int gs_grid(int64_t d) {
 // chain's partial sketches; pass 1: one Arnoldi step's Gram-Schmidt
 // reduction on S (s . Q_i, s . s and the new Gram row) and its finish.
 template <typename T>
-__global__ void __launch_bounds__(GS_THREADS) k_gs_pass(Work w, int pass, StepOpts o) {
+__global__ void __launch_bounds__(GS_THREADS) k_gs_pass(Work w0, int pass, StepOpts o0) {
+  const int64_t bo = bidx(w0.b).off;
+  const Work w = w0.at(bo);
+  const StepOpts o = o0.at(bo);
   Ctl* ctl = w.ctl;
   if (ctl->stop) return;
   const int J = (pass == 0) ? -1 : ctl->j;
@@ -83,7 +86,10 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(Work w, int pass, StepOp
 
 // V_0 = src / beta, Q_0 = S / beta
 template <typename T>
-__global__ void k_start_scale(Work w, PtrRef srcr) {
+__global__ void k_start_scale(Work w0, PtrRef srcr0) {
+  const int64_t bo = bidx(w0.b).off;
+  const Work w = w0.at(bo);
+  const PtrRef srcr = srcr0.at(bo);
   const Ctl* ctl = w.ctl;
   if (ctl->stop) return;
   const T* src = srcr.get<const T>();
@@ -113,13 +119,18 @@ __global__ void k_start_scale(Work w, PtrRef srcr) {
 // The last block of the grid runs givens_step (Eq. 11S, rho_j, the stop
 // rule) beside the update; the others share the update.
 template <typename T>
-__global__ void k_update(Work w, StepOpts o) {
+__global__ void k_update(Work w0, StepOpts o0) {
+  const int64_t bo = bidx(w0.b).off;
+  const Work w = w0.at(bo);
+  const StepOpts o = o0.at(bo);
   Ctl* ctl = w.ctl;
   if (blockIdx.x == gridDim.x - 1) {
     if (threadIdx.x == 0) givens_step(w, o);
     return;
   }
   if (ctl->skip_update || ctl->j == 0) return;
+  // lock-step batch: a problem that stopped in an earlier body has nothing to update
+  if (o.group_left != nullptr && ctl->stop && !ctl->givens) return;
   const int jj = ctl->j;
   if (jj > w.m) {   // V holds m+1 tensors: never write past V_m
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -213,10 +224,15 @@ __global__ void k_update(Work w, StepOpts o) {
   }
 }
 
-__global__ void k_reset(Ctl* ctl, unsigned* counter, int new_cycle) {
+__global__ void k_reset(Work w0, int new_cycle, unsigned* group_left) {
+  const BIdx bi = bidx(w0.b);
+  Ctl* ctl = bsh(w0.ctl, bi.off);
+  unsigned* counter = bsh(w0.counter, bi.off);
+  if (group_left != nullptr && bi.p == 0) *group_left = static_cast<unsigned>(w0.b.n);
   // last-block counters wrap to zero by themselves; clearing them here also
   // recovers from a solve that ended inside a kernel
   for (int i = 0; i < 8; ++i) counter[i] = 0u;
+  ctl->counted = 0;
   ctl->j = 0;
   ctl->stop = 0;
   ctl->breakdown = 0;
@@ -245,8 +261,8 @@ static unsigned ew_grid(int64_t n) {
   return static_cast<unsigned>(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s) {
-  k_reset<<<1, 1, 0, s>>>(w.ctl, w.counter, new_cycle);
+cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s, unsigned* group_left) {
+  k_reset<<<dim3(1, 1, w.b.n), 1, 0, s>>>(w, new_cycle, group_left);
   return cudaGetLastError();
 }
 
@@ -271,7 +287,10 @@ __device__ __forceinline__ uint4 f_to_bf8(const float* f) {
 }
 
 template <bool SRC_BF16>
-__global__ void k_start_scale_bf16(Work w, PtrRef srcr) {
+__global__ void k_start_scale_bf16(Work w0, PtrRef srcr0) {
+  const int64_t bo = bidx(w0.b).off;
+  const Work w = w0.at(bo);
+  const PtrRef srcr = srcr0.at(bo);
   const Ctl* ctl = w.ctl;
   if (ctl->stop) return;
   const float fi = static_cast<float>(1.0 / ctl->beta);
@@ -300,13 +319,17 @@ __global__ void k_start_scale_bf16(Work w, PtrRef srcr) {
 
 // BF16 basis: V_{j+1} = (W - sum_i h_i V_i) / h_{j+1,j} with FP32 arithmetic;
 // Q_{j+1} as in k_update.  The last block runs givens_step.
-__global__ void k_update_bf16(Work w, StepOpts o) {
+__global__ void k_update_bf16(Work w0, StepOpts o0) {
+  const int64_t bo = bidx(w0.b).off;
+  const Work w = w0.at(bo);
+  const StepOpts o = o0.at(bo);
   Ctl* ctl = w.ctl;
   if (blockIdx.x == gridDim.x - 1) {
     if (threadIdx.x == 0) givens_step(w, o);
     return;
   }
   if (ctl->skip_update || ctl->j == 0) return;
+  if (o.group_left != nullptr && ctl->stop && !ctl->givens) return;
   const int jj = ctl->j;
   if (jj > w.m) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -376,26 +399,26 @@ __global__ void k_update_bf16(Work w, StepOpts o) {
 
 cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fused, cudaStream_t s,
                          int sdtype) {
-  const int g = gs_grid(w.d);
+  const unsigned g = static_cast<unsigned>(gs_grid(w.d)), nb = static_cast<unsigned>(w.b.n);
   if (sdtype < 0) sdtype = w.dtype;
   if (w.vdtype == RTG_BF16) {
-    if (!fused) k_gs_pass<float><<<g, GS_THREADS, 0, s>>>(w, 0, o);
-    if (sdtype == RTG_BF16) k_start_scale_bf16<true><<<ew_grid(w.n / 8 + 1), 256, 0, s>>>(w, src);
-    else k_start_scale_bf16<false><<<ew_grid(w.n / 8 + 1), 256, 0, s>>>(w, src);
+    if (!fused) k_gs_pass<float><<<dim3(g, 1, nb), GS_THREADS, 0, s>>>(w, 0, o);
+    if (sdtype == RTG_BF16) k_start_scale_bf16<true><<<dim3(ew_grid(w.n / 8 + 1), 1, nb), 256, 0, s>>>(w, src);
+    else k_start_scale_bf16<false><<<dim3(ew_grid(w.n / 8 + 1), 1, nb), 256, 0, s>>>(w, src);
     return cudaGetLastError();
   }
   if (w.dtype == RTG_F64) {
-    if (!fused) k_gs_pass<double><<<g, GS_THREADS, 0, s>>>(w, 0, o);
-    k_start_scale<double><<<ew_grid(w.n), 256, 0, s>>>(w, src);
+    if (!fused) k_gs_pass<double><<<dim3(g, 1, nb), GS_THREADS, 0, s>>>(w, 0, o);
+    k_start_scale<double><<<dim3(ew_grid(w.n), 1, nb), 256, 0, s>>>(w, src);
   } else {
-    if (!fused) k_gs_pass<float><<<g, GS_THREADS, 0, s>>>(w, 0, o);
-    k_start_scale<float><<<ew_grid(w.n / 4 + 1), 256, 0, s>>>(w, src);
+    if (!fused) k_gs_pass<float><<<dim3(g, 1, nb), GS_THREADS, 0, s>>>(w, 0, o);
+    k_start_scale<float><<<dim3(ew_grid(w.n / 4 + 1), 1, nb), 256, 0, s>>>(w, src);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s) {
-  const int g = gs_grid(w.d);
+  const dim3 g(static_cast<unsigned>(gs_grid(w.d)), 1, static_cast<unsigned>(w.b.n));
   if (w.dtype == RTG_F64) k_gs_pass<double><<<g, GS_THREADS, 0, s>>>(w, 1, o);
   else k_gs_pass<float><<<g, GS_THREADS, 0, s>>>(w, 1, o);
   return cudaGetLastError();
@@ -405,9 +428,10 @@ cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s) {
 
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s) {
   // one block more than the update needs: it runs the Givens step
-  if (w.vdtype == RTG_BF16) k_update_bf16<<<ew_grid(w.n / 8 + 1) + 1, 256, 0, s>>>(w, o);
-  else if (w.dtype == RTG_F64) k_update<double><<<ew_grid(w.n) + 1, 256, 0, s>>>(w, o);
-  else k_update<float><<<ew_grid(w.n / 4 + 1) + 1, 256, 0, s>>>(w, o);
+  const unsigned nb = static_cast<unsigned>(w.b.n);
+  if (w.vdtype == RTG_BF16) k_update_bf16<<<dim3(ew_grid(w.n / 8 + 1) + 1, 1, nb), 256, 0, s>>>(w, o);
+  else if (w.dtype == RTG_F64) k_update<double><<<dim3(ew_grid(w.n) + 1, 1, nb), 256, 0, s>>>(w, o);
+  else k_update<float><<<dim3(ew_grid(w.n / 4 + 1) + 1, 1, nb), 256, 0, s>>>(w, o);
   return cudaGetLastError();
 }
 

@@ -41,7 +41,10 @@ struct ThetaArgs {
 
 // One thread per packed 32-bit word: bit b of word (q, w) of mode k holds
 // the sign of Theta_k(q, 32 w + b); padding bits past I_k are 0 (+1).
-__global__ void k_theta_bits(ThetaArgs a, uint32_t* bits) {
+__global__ void k_theta_bits(ThetaArgs a, uint32_t* bits0, Batch bt) {
+  const int64_t bo = bidx(bt).off;
+  uint32_t* bits = bsh(bits0, bo);
+  a.key = bsh(a.key, bo);
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= a.total_words) return;
   int k = 0;
@@ -74,7 +77,7 @@ __global__ void k_theta_bits(ThetaArgs a, uint32_t* bits) {
 }
 
 cudaError_t launch_theta_bits(const SketchPlan& sp, uint32_t* bits, cudaStream_t s,
-                              const uint64_t* key_dev) {
+                              const uint64_t* key_dev, Batch b) {
   ThetaArgs a{};
   a.key = key_dev;
   int k = 0;
@@ -92,7 +95,7 @@ cudaError_t launch_theta_bits(const SketchPlan& sp, uint32_t* bits, cudaStream_t
   a.seed = sp.seed;
   a.pid = sp.pid;
   if (k == 0 || sp.total_words == 0) return cudaSuccess;
-  k_theta_bits<<<(unsigned)((sp.total_words + 255) / 256), 256, 0, s>>>(a, bits);
+  k_theta_bits<<<dim3((unsigned)((sp.total_words + 255) / 256), 1, b.n), 256, 0, s>>>(a, bits, b);
   return cudaGetLastError();
 }
 

@@ -186,7 +186,10 @@ struct FragArgs {
 // One thread per (tile, k-tile, lane) of every stage: the fragment
 // registers of mma.m16n8k16 for Theta (A operand, first stage) or
 // Theta^T (B operand, later stages).
-__global__ void k_theta_frags(FragArgs a, const uint32_t* __restrict__ bits, uint32_t* frags) {
+__global__ void k_theta_frags(FragArgs a, const uint32_t* __restrict__ bits0, uint32_t* frags0, Batch bt) {
+  const int64_t bo = bidx(bt).off;
+  const uint32_t* __restrict__ bits = bsh(bits0, bo);
+  uint32_t* frags = bsh(frags0, bo);
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= a.total_lanes) return;
   int t = 0;
@@ -234,8 +237,8 @@ __global__ void k_theta_frags(FragArgs a, const uint32_t* __restrict__ bits, uin
 }
 
 cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, cudaStream_t s,
-                         const uint64_t* key_dev) {
-  cudaError_t e = launch_theta_bits(sp, bits, s, key_dev);
+                         const uint64_t* key_dev, Batch b) {
+  cudaError_t e = launch_theta_bits(sp, bits, s, key_dev, b);
   if (e != cudaSuccess || sp.dtype != RTG_F32 || sp.nstage == 0) return e;
   FragArgs a{};
   a.nstage = sp.nstage;
@@ -256,7 +259,7 @@ cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, 
   }
   a.lane_off[sp.nstage] = lanes;
   a.total_lanes = lanes;
-  k_theta_frags<<<static_cast<unsigned>((lanes + 255) / 256), 256, 0, s>>>(a, bits, frags);
+  k_theta_frags<<<dim3(static_cast<unsigned>((lanes + 255) / 256), 1, b.n), 256, 0, s>>>(a, bits, frags, b);
   return cudaGetLastError();
 }
 
@@ -390,7 +393,15 @@ template <int CH, typename TI>
 __global__ void __launch_bounds__(TC_THREADS)
 k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t s, int kt_total,
               const uint4* __restrict__ fragA, int mt_total, float scale, OutMap om,
-              int* status, const int* stop) {
+              int* status, const int* stop, Batch bt) {
+  {
+    const int64_t bo = bidx(bt).off;
+    Xr = Xr.at(bo);
+    out = bsh(out, bo);
+    fragA = bsh(fragA, bo);
+    status = bsh(status, bo);
+    stop = bsh(stop, bo);
+  }
   if (stop != nullptr && *stop) return;
   // BF16 data are exact in one limb; FP32 data take three (see split3)
   constexpr int LIMBS = sizeof(TI) == 4 ? 3 : 1;
@@ -528,7 +539,17 @@ template <int CH>
 __global__ void __launch_bounds__(TC_THREADS)
 k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int64_t I, int64_t R,
               int64_t s, int kt_total, const uint2* __restrict__ fragB, int nt_total, float scale,
-              OutMap om, int dots_pass, Work w, StepOpts o, int* status, const int* stop) {
+              OutMap om, int dots_pass, Work w, StepOpts o, int* status, const int* stop, Batch bt) {
+  {
+    const int64_t bo = bidx(bt).off;
+    Xr = Xr.at(bo);
+    out = bsh(out, bo);
+    fragB = bsh(fragB, bo);
+    w = w.at(bo);
+    o = o.at(bo);
+    status = bsh(status, bo);
+    stop = bsh(stop, bo);
+  }
   if (stop != nullptr && *stop) return;
   const float* __restrict__ X = Xr.get<const float>();
   extern __shared__ __align__(128) unsigned char smem[];
@@ -662,7 +683,14 @@ k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int
 template <typename T>
 __global__ void k_sketch_mode(PtrRef Xr, T* __restrict__ Y, int64_t L, int64_t I, int64_t R,
                               int64_t s, const uint32_t* __restrict__ bits, int wpr, T scale,
-                              const int* stop) {
+                              const int* stop, Batch bt) {
+  {
+    const int64_t bo = bidx(bt).off;
+    Xr = Xr.at(bo);
+    Y = bsh(Y, bo);
+    bits = bsh(bits, bo);
+    stop = bsh(stop, bo);
+  }
   if (stop != nullptr && *stop) return;
   const T* __restrict__ X = Xr.get<const T>();
   const int64_t total = L * s * R;
@@ -688,7 +716,13 @@ __global__ void k_sketch_mode(PtrRef Xr, T* __restrict__ Y, int64_t L, int64_t I
 }
 
 template <typename T>
-__global__ void k_copy(PtrRef Xr, T* __restrict__ Y, int64_t n, const int* stop) {
+__global__ void k_copy(PtrRef Xr, T* __restrict__ Y, int64_t n, const int* stop, Batch bt) {
+  {
+    const int64_t bo = bidx(bt).off;
+    Xr = Xr.at(bo);
+    Y = bsh(Y, bo);
+    stop = bsh(stop, bo);
+  }
   if (stop != nullptr && *stop) return;
   const T* X = Xr.get<const T>();
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
@@ -705,16 +739,16 @@ static unsigned grid_for(int64_t n) {
 int sketch_launches(const SketchPlan& sp) { return sp.nstage == 0 ? 1 : sp.nstage; }
 
 static cudaError_t sketch_f64(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, double* out,
-                              const int* stop, cudaStream_t s) {
+                              const int* stop, cudaStream_t s, Batch b) {
   PtrRef src = X;
   for (int t = 0; t < sp.nstage; ++t) {
     const int k = sp.stage_mode[t];
     const bool last = (t == sp.nstage - 1);
     double* dst = last ? out : static_cast<double*>((t % 2 == 0) ? sc.tmp0 : sc.tmp1);
     const double scale = last ? sp.scale : 1.0;
-    k_sketch_mode<double><<<grid_for(sp.stage_out[t]), 256, 0, s>>>(
+    k_sketch_mode<double><<<dim3(grid_for(sp.stage_out[t]), 1, b.n), 256, 0, s>>>(
         src, dst, sp.stage_L[t], sp.stage_I[t], sp.stage_R[t], sp.stage_s[t],
-        sc.bits + sp.word_off[k], sp.wpr[k], scale, stop);
+        sc.bits + sp.word_off[k], sp.wpr[k], scale, stop, b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     src = ref(dst);
@@ -736,18 +770,18 @@ static OutMap stage_out_map(const SketchPlan& sp, int t) {
 template <int CH, typename TI>
 static cudaError_t launch_first(dim3 grid, PtrRef src, float* dst, const SketchPlan& sp, int t, int kt,
                                 const uint32_t* fr, float scale, OutMap om, int* status, const int* stop,
-                                cudaStream_t s) {
+                                cudaStream_t s, Batch b) {
   constexpr size_t sm = first_smem<CH>();
   cudaError_t e = cudaFuncSetAttribute(k_sk_first_tc<CH, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   if (e != cudaSuccess) return e;
   k_sk_first_tc<CH, TI><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_I[t], sp.stage_R[t], sp.stage_s[t], kt,
                                                      reinterpret_cast<const uint4*>(fr), sp.stage_ntile[t],
-                                                     scale, om, status, stop);
+                                                     scale, om, status, stop, b);
   return cudaGetLastError();
 }
 
 static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, float* out,
-                              const SketchDots* dots, const int* stop, cudaStream_t s, int xdtype) {
+                              const SketchDots* dots, const int* stop, cudaStream_t s, int xdtype, Batch b) {
   PtrRef src = X;
   for (int t = 0; t < sp.nstage; ++t) {
     const bool last = (t == sp.nstage - 1);
@@ -760,18 +794,18 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
     cudaError_t e = cudaSuccess;
     if (sp.stage_first[t]) {
       dim3 grid(static_cast<unsigned>((sp.stage_R[t] + F_COLS - 1) / F_COLS),
-                static_cast<unsigned>((sp.stage_ntile[t] + F_MT - 1) / F_MT));
+                static_cast<unsigned>((sp.stage_ntile[t] + F_MT - 1) / F_MT), static_cast<unsigned>(b.n));
       const bool bf = (t == 0 && xdtype == RTG_BF16);
       if (kt > 16)
-        e = bf ? launch_first<32, __nv_bfloat16>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s)
-               : launch_first<32, float>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s);
+        e = bf ? launch_first<32, __nv_bfloat16>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s, b)
+               : launch_first<32, float>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s, b);
       else
-        e = bf ? launch_first<16, __nv_bfloat16>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s)
-               : launch_first<16, float>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s);
+        e = bf ? launch_first<16, __nv_bfloat16>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s, b)
+               : launch_first<16, float>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s, b);
     } else {
       const int64_t ltiles = (sp.stage_L[t] + 15) / 16;
       dim3 grid(static_cast<unsigned>(ltiles * sp.stage_R[t]),
-                static_cast<unsigned>((sp.stage_ntile[t] + N_NT - 1) / N_NT));
+                static_cast<unsigned>((sp.stage_ntile[t] + N_NT - 1) / N_NT), static_cast<unsigned>(b.n));
       const int dpass = (last && dots != nullptr) ? dots->pass : -1;
       const Work wk = (dots != nullptr) ? *dots->w : Work{};
       const StepOpts so = (dots != nullptr) ? dots->o : StepOpts{};
@@ -783,7 +817,7 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
         k_sk_inner_tc<32><<<grid, TC_THREADS, sm, s>>>(src, inb, dst, sp.stage_L[t], sp.stage_I[t],
                                                        sp.stage_R[t], sp.stage_s[t], kt,
                                                        reinterpret_cast<const uint2*>(fr), sp.stage_ntile[t],
-                                                       scale, om, dpass, wk, so, status, stop);
+                                                       scale, om, dpass, wk, so, status, stop, b);
       } else {
         constexpr size_t sm = inner_smem<16>();
         e = cudaFuncSetAttribute(k_sk_inner_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
@@ -791,7 +825,7 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
         k_sk_inner_tc<16><<<grid, TC_THREADS, sm, s>>>(src, inb, dst, sp.stage_L[t], sp.stage_I[t],
                                                        sp.stage_R[t], sp.stage_s[t], kt,
                                                        reinterpret_cast<const uint2*>(fr), sp.stage_ntile[t],
-                                                       scale, om, dpass, wk, so, status, stop);
+                                                       scale, om, dpass, wk, so, status, stop, b);
       }
     }
     e = cudaGetLastError();
@@ -802,7 +836,7 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
 }
 
 cudaError_t launch_sketch(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, void* out,
-                          const SketchDots* dots, const int* stop, cudaStream_t s, int xdtype) {
+                          const SketchDots* dots, const int* stop, cudaStream_t s, int xdtype, Batch b) {
   if (xdtype < 0) xdtype = sp.dtype;
   // BF16 input is read only by a first stage on mode 1 (FP32 plans)
   if (xdtype == RTG_BF16 && (sp.dtype != RTG_F32 || sp.nstage == 0 || !sp.stage_first[0]))
@@ -810,12 +844,13 @@ cudaError_t launch_sketch(const SketchPlan& sp, const SketchScratch& sc, PtrRef 
   int64_t n = 1;
   for (int k = 0; k < sp.order; ++k) n *= sp.dims[k];
   if (sp.nstage == 0) {     // no sketched mode: S = identity
-    if (sp.dtype == RTG_F64) k_copy<double><<<grid_for(n), 256, 0, s>>>(X, static_cast<double*>(out), n, stop);
-    else k_copy<float><<<grid_for(n), 256, 0, s>>>(X, static_cast<float*>(out), n, stop);
+    const dim3 g(grid_for(n), 1, static_cast<unsigned>(b.n));
+    if (sp.dtype == RTG_F64) k_copy<double><<<g, 256, 0, s>>>(X, static_cast<double*>(out), n, stop, b);
+    else k_copy<float><<<g, 256, 0, s>>>(X, static_cast<float*>(out), n, stop, b);
     return cudaGetLastError();
   }
-  if (sp.dtype == RTG_F64) return sketch_f64(sp, sc, X, static_cast<double*>(out), stop, s);
-  return sketch_f32(sp, sc, X, static_cast<float*>(out), sp.fused_dots ? dots : nullptr, stop, s, xdtype);
+  if (sp.dtype == RTG_F64) return sketch_f64(sp, sc, X, static_cast<double*>(out), stop, s, b);
+  return sketch_f32(sp, sc, X, static_cast<float*>(out), sp.fused_dots ? dots : nullptr, stop, s, xdtype, b);
 }
 
 }  // namespace rtg

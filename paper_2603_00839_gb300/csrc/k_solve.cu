@@ -45,7 +45,11 @@ __device__ void back_subst(const double* U, int ldu, const double* rinv, double*
 // mode 0: least squares (mu = 0); 1: fixed mu = lambda; 2: GCV over the grid.
 // scratch: per block 2*m*m + 4*m doubles.
 __global__ void __launch_bounds__(TK_THREADS)
-k_tikhonov(Work w, const SolveDesc* desc, int mode, double* scratch) {
+k_tikhonov(Work w0, const SolveDesc* desc0, int mode, double* scratch0) {
+  const int64_t bo = bidx(w0.b).off;
+  const Work w = w0.at(bo);
+  const SolveDesc* desc = bsh(desc0, bo);
+  double* scratch = bsh(scratch0, bo);
   Ctl* ctl = w.ctl;
   const int k = ctl->j;
   const int m = w.m, ld = m + 1;
@@ -167,7 +171,10 @@ k_tikhonov(Work w, const SolveDesc* desc, int mode, double* scratch) {
 
 // X = X0 + sum_{i<k} y_i V_i  (Eq. 10S)
 template <typename T>
-__global__ void k_assemble(Work w, PtrRef X0r, PtrRef Xr) {
+__global__ void k_assemble(Work w0, PtrRef X0r0, PtrRef Xr0) {
+  const int64_t bo = bidx(w0.b).off;
+  const Work w = w0.at(bo);
+  const PtrRef X0r = X0r0.at(bo), Xr = Xr0.at(bo);
   const int k = w.ctl->j;
   __shared__ T ys[kMaxK];
   for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = static_cast<T>(w.y[i]);
@@ -184,7 +191,10 @@ __global__ void k_assemble(Work w, PtrRef X0r, PtrRef Xr) {
   }
 }
 
-__global__ void k_finalize(Work w, InfoDev* info) {
+__global__ void k_finalize(Work w0, InfoDev* info0) {
+  const int64_t bo = bidx(w0.b).off;
+  const Work w = w0.at(bo);
+  InfoDev* info = bsh(info0, bo);
   const Ctl* c = w.ctl;
   const int t = threadIdx.x;
   if (t == 0) {
@@ -204,7 +214,8 @@ __global__ void k_finalize(Work w, InfoDev* info) {
 
 // Holds the stream until the host has queued a whole kernel group (phase
 // timing): one thread polls a flag in mapped host memory.  The wait is
-// bounded (2 s of globaltimer); on expiry the kernel records
+// bounded (10 s of globaltimer, room for the lazy loading of modules on a
+// first launch); on expiry the kernel records
 // RTG_ERR_TIMEOUT in *status and returns, so the stream never stalls.
 __global__ void k_gate(const volatile unsigned* flag, unsigned want, volatile unsigned* status) {
   unsigned long long t0;
@@ -212,7 +223,7 @@ __global__ void k_gate(const volatile unsigned* flag, unsigned want, volatile un
   while (*flag < want) {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > 2000000000ull) {
+    if (t - t0 > 10000000000ull) {
       *status = RTG_ERR_TIMEOUT;
       return;
     }
@@ -233,12 +244,15 @@ static unsigned ew_grid(int64_t n) {
 
 cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s) {
   const unsigned blocks = (f.mode == 2) ? static_cast<unsigned>(f.n_mu) : 1u;
-  k_tikhonov<<<blocks, TK_THREADS, 0, s>>>(w, f.desc, f.mode, w.ysel + kMaxMu * w.m);
+  k_tikhonov<<<dim3(blocks, 1, w.b.n), TK_THREADS, 0, s>>>(w, f.desc, f.mode, w.ysel + kMaxMu * w.m);
   return cudaGetLastError();
 }
 
 // X = X0 + sum_{i<k} y_i V_i with V in BF16 (FP32 arithmetic, 8 values per load)
-__global__ void k_assemble_bf16(Work w, PtrRef X0r, PtrRef Xr) {
+__global__ void k_assemble_bf16(Work w0, PtrRef X0r0, PtrRef Xr0) {
+  const int64_t bo = bidx(w0.b).off;
+  const Work w = w0.at(bo);
+  const PtrRef X0r = X0r0.at(bo), Xr = Xr0.at(bo);
   const int k = w.ctl->j;
   __shared__ float ys[kMaxK];
   for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = static_cast<float>(w.y[i]);
@@ -268,16 +282,16 @@ __global__ void k_assemble_bf16(Work w, PtrRef X0r, PtrRef Xr) {
 
 cudaError_t launch_assemble(const Work& w, PtrRef X0, PtrRef X, cudaStream_t s) {
   if (w.vdtype == RTG_BF16) {
-    k_assemble_bf16<<<ew_grid(w.n / 8 + 1), 256, 0, s>>>(w, X0, X);
+    k_assemble_bf16<<<dim3(ew_grid(w.n / 8 + 1), 1, w.b.n), 256, 0, s>>>(w, X0, X);
     return cudaGetLastError();
   }
-  if (w.dtype == RTG_F64) k_assemble<double><<<ew_grid(w.n), 256, 0, s>>>(w, X0, X);
-  else k_assemble<float><<<ew_grid(w.n), 256, 0, s>>>(w, X0, X);
+  if (w.dtype == RTG_F64) k_assemble<double><<<dim3(ew_grid(w.n), 1, w.b.n), 256, 0, s>>>(w, X0, X);
+  else k_assemble<float><<<dim3(ew_grid(w.n), 1, w.b.n), 256, 0, s>>>(w, X0, X);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const Work& w, InfoDev* info, cudaStream_t s) {
-  k_finalize<<<1, 256, 0, s>>>(w, info);
+  k_finalize<<<dim3(1, 1, w.b.n), 256, 0, s>>>(w, info);
   return cudaGetLastError();
 }
 

@@ -447,6 +447,9 @@ struct SolvePlan {
   int direct_steps = 0;                                           // steps launched by the last direct solve
   int* stop_host = nullptr;                                       // pinned: ctl->stop read back per direct step
   bool ext_desc = false;  // desc/info live in a batch's buffers (not owned)
+  // lock-step batch (w.b.n problems in one launch per kernel): the problems'
+  // blocks of `mem` each start with their descriptor and info record
+  unsigned* group_left = nullptr;   // device counter of problems still running
   ~SolvePlan() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -458,14 +461,17 @@ struct SolvePlan {
   }
 };
 
-// A batch of independent solves replayed as one CUDA graph: one branch per
-// problem (its prologue, device-side loop and epilogue), descriptors and
-// info records contiguous so that one copy each way serves the batch.
+// A batch of independent solves replayed as one CUDA graph.  Problems that
+// share every structural parameter (shape, operator, sketch sizes, m,
+// regularisation mode, X0 or not) form a lock-step group: one plan whose
+// kernels each serve the whole group (problem = slowest part of blockIdx.z)
+// and one device-side loop that runs while any of them does.  Each group is
+// one branch of the graph (its prologue, loop and epilogue).
 struct BatchPlan {
-  std::vector<std::shared_ptr<SolvePlan>> plans;
-  DevBuf small;
-  char* desc_host = nullptr;     // pinned, nprob descriptors then nprob info records
-  size_t desc_stride = 0, info_stride = 0;
+  std::vector<std::shared_ptr<SolvePlan>> plans;   // one per group
+  std::vector<int> group_of, slot_of;              // per problem: its group, its place in the host records
+  std::vector<int> gfirst;                         // per group: first host record
+  char* desc_host = nullptr;     // pinned: nprob descriptors, then nprob info records, in group order
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -627,6 +633,7 @@ StepOpts solve_step_opts(const SolvePlan& P, int use_cond, cudaGraphConditionalH
   o.solve_mode = 1;
   o.use_cond = use_cond;
   o.cond = static_cast<unsigned long long>(hnd);
+  o.group_left = P.group_left;
   return o;
 }
 
@@ -641,8 +648,8 @@ rtg_status enqueue_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s,
   Work& w = P.w;
   {
     PhaseScope ps(pt, RTG_PHASE_SETUP, -1, P.launches_setup);
-    CK(launch_reset(w, 0, s));
-    CK(launch_theta(P.sp, P.sk.bits, P.sk.frags, s, P.desc_dev->key));
+    CK(launch_reset(w, 0, s, P.group_left));
+    CK(launch_theta(P.sp, P.sk.bits, P.sk.frags, s, P.desc_dev->key, w.b));
   }
   PhaseScope ps(pt, RTG_PHASE_INIT, -1, P.launches_pro - P.launches_setup);
   PtrRef C = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->C));
@@ -650,13 +657,13 @@ rtg_status enqueue_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s,
   int sdt = P.dtype;
   if (P.has_x0) {   // R_0 = C - Phi(X_0) into the V_0 slot
     PtrRef X0 = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X0));
-    CK(launch_apply(P.op.op, P.dtype, X0, ref(w.V), -1.0, 1.0, C, P.tA, P.tB, nullptr, s, P.dtype, P.vdtype));
+    CK(launch_apply(P.op.op, P.dtype, X0, ref(w.V), -1.0, 1.0, C, P.tA, P.tB, nullptr, s, P.dtype, P.vdtype, w.b));
     src = ref(w.V);
     sdt = P.vdtype;
   }
   const bool fused = P.sp.fused_dots != 0;
   SketchDots dots{&w, 0, so};
-  CK(launch_sketch(P.sp, P.sk, src, fused ? w.S : w.Spart, fused ? &dots : nullptr, nullptr, s, sdt));
+  CK(launch_sketch(P.sp, P.sk, src, fused ? w.S : w.Spart, fused ? &dots : nullptr, nullptr, s, sdt, w.b));
   CK(launch_start(w, src, so, fused, s, sdt));
   return RTG_OK;
 }
@@ -671,13 +678,13 @@ rtg_status enqueue_step(const OpHolder& op, const SketchPlan& sp, const Work& w,
   const int* stop = &w.ctl->stop;
   {
     PhaseScope ps(pt, RTG_PHASE_APPLY, step, apply_launches(op.op, false, dtype, w.vdtype, w.vdtype));
-    CK(launch_apply(op.op, dtype, vj, ref(w.W), 1.0, 0.0, PtrRef{}, tA, tB, stop, s, w.vdtype, w.vdtype));
+    CK(launch_apply(op.op, dtype, vj, ref(w.W), 1.0, 0.0, PtrRef{}, tA, tB, stop, s, w.vdtype, w.vdtype, w.b));
   }
   const bool fused = sp.fused_dots != 0;
   {
     PhaseScope ps(pt, RTG_PHASE_SKETCH, step, sketch_launches(sp));
     SketchDots dots{&w, 1, so};
-    CK(launch_sketch(sp, sk, ref(w.W), fused ? w.S : w.Spart, fused ? &dots : nullptr, stop, s, w.vdtype));
+    CK(launch_sketch(sp, sk, ref(w.W), fused ? w.S : w.Spart, fused ? &dots : nullptr, stop, s, w.vdtype, w.b));
   }
   if (!fused) {
     PhaseScope ps(pt, RTG_PHASE_GS, step, 1);
@@ -902,7 +909,7 @@ struct TransposedFactors {
 // given batch buffers, or its own), launch counts and, for a stand-alone
 // graph solve, its CUDA graph.  Builds only while nothing of the handle runs.
 rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDesc* dhost, InfoDev* ihost,
-                     std::shared_ptr<SolvePlan>* out) {
+                     std::shared_ptr<SolvePlan>* out, int nbatch = 0) {
   const rtg_factor* A = ps.A;
   const rtg_factor* B = ps.B;
   const int nA = ps.nA, nB = ps.nB, dtype = ps.dtype, vdtype = ps.vdtype, m = ps.m, mode = ps.mode;
@@ -937,10 +944,34 @@ rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDe
   void *ta, *tb;
   SketchScratch tsk;
   const size_t bytes = carve_work(nullptr, dtype, n, sp, m, tkb, ae, tmpw, &ta, &tb, &tsk, vdtype, nU);
-  RK(P->mem.ensure(bytes));
-  CK(cudaMemset(P->mem.p, 0, bytes));
-  carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk, vdtype, nU);
-  if (ddev != nullptr) {   // descriptor and info record in a batch's buffers
+  if (nbatch > 0) {
+    // lock-step batch: one block per problem (descriptor, info record,
+    // workspace), every block laid out alike, `bs` bytes apart; the host
+    // records (dhost, ihost) hold nbatch entries each, contiguous
+    const size_t dsz = (sizeof(SolveDesc) + 255) & ~size_t(255);
+    const size_t isz = (sizeof(InfoDev) + 255) & ~size_t(255);
+    const size_t bs = (dsz + isz + bytes + 255) & ~size_t(255);
+    RK(P->mem.ensure(bs * size_t(nbatch)));
+    CK(cudaMemset(P->mem.p, 0, bs * size_t(nbatch)));
+    char* b0 = static_cast<char*>(P->mem.p);
+    carve_work(b0 + dsz + isz, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk, vdtype, nU);
+    P->w.b.n = nbatch;
+    P->w.b.stride = static_cast<int64_t>(bs);
+    P->ext_desc = true;
+    P->desc_dev = reinterpret_cast<SolveDesc*>(b0);
+    P->info_dev = reinterpret_cast<InfoDev*>(b0 + dsz);
+    P->desc_host = dhost;
+    P->info_host = ihost;
+    RK(P->small.ensure(256));
+    CK(cudaMemset(P->small.p, 0, 256));
+    P->group_left = static_cast<unsigned*>(P->small.p);
+  } else {
+    RK(P->mem.ensure(bytes));
+    CK(cudaMemset(P->mem.p, 0, bytes));
+    carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk, vdtype, nU);
+  }
+  if (nbatch > 0) {
+  } else if (ddev != nullptr) {   // descriptor and info record in a batch's buffers
     P->ext_desc = true;
     P->desc_dev = ddev;
     P->info_dev = idev;
@@ -1474,7 +1505,7 @@ rtg_status rtg_gmres_wait(rtg_handle h, int32_t slot, rtg_info* info) {
     if (phase_times) h->timer->collect(I.iters, info);
   }
   if (phase_times && h->timer->host[1] != 0) {
-    return fail(RTG_ERR_TIMEOUT, "phase timing: a gate waited 2 s for the host to queue its group");
+    return fail(RTG_ERR_TIMEOUT, "phase timing: a gate waited 10 s for the host to queue its group");
   }
   return RTG_OK;
 }
@@ -1489,17 +1520,20 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
   rtg_opts opts{};
   if (opts_in) opts = *opts_in;
   if (opts.max_restarts != 0) return fail(RTG_ERR_UNSUPPORTED, "restarts are not supported on the GPU path");
-  if (opts.flags & (RTG_FLAG_NO_GRAPH | RTG_FLAG_PHASE_TIMES))
-    return fail(RTG_ERR_UNSUPPORTED, "batched solves run as one CUDA graph (no direct or phase-timed launch)");
+  const bool use_graph = !(opts.flags & (RTG_FLAG_NO_GRAPH | RTG_FLAG_PHASE_TIMES));
+  const bool phase_times = (opts.flags & RTG_FLAG_PHASE_TIMES) != 0;
   if (!(opts.breakdown_tol >= 0.0)) return fail(RTG_ERR_INVALID_ARG, "opts.breakdown_tol must be >= 0");
   const int vdtype = (opts.flags & RTG_FLAG_BF16_BASIS) ? RTG_BF16 : dtype;
   if (vdtype == RTG_BF16 && dtype != RTG_F32) return fail(RTG_ERR_UNSUPPORTED, "RTG_FLAG_BF16_BASIS needs dtype RTG_F32");
   DeviceGuard dg(h->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // validate every problem and form its plan key (problem index included:
-  // each branch owns its workspace)
+  // validate every problem and form its structural key (problems with equal
+  // keys run in lock step; the sequence of keys names the batch plan)
   std::vector<PlanSpec> specs(nprob);
+  std::vector<std::string> keys(nprob);
   std::string bkey;
+  if (opts.group_max < 0) return fail(RTG_ERR_INVALID_ARG, "opts.group_max must be >= 0");
+  append_bytes(bkey, &opts.group_max, sizeof opts.group_max);
   append_bytes(bkey, &dtype, sizeof dtype);
   append_bytes(bkey, &vdtype, sizeof vdtype);
   for (int i = 0; i < nprob; ++i) {
@@ -1540,6 +1574,7 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
     const uint32_t len = static_cast<uint32_t>(key.size());
     append_bytes(bkey, &len, sizeof len);
     bkey += key;
+    keys[i] = std::move(key);
   }
   auto it = h->batches.find(bkey);
   BatchPlan* BP = nullptr;
@@ -1549,23 +1584,40 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
     if (h->batches.size() >= 4) h->batches.clear();
     auto nb = std::make_unique<BatchPlan>();
     BP = nb.get();
-    BP->desc_stride = (sizeof(SolveDesc) + 255) & ~size_t(255);
-    BP->info_stride = (sizeof(InfoDev) + 255) & ~size_t(255);
-    const size_t total = size_t(nprob) * (BP->desc_stride + BP->info_stride);
-    RK(BP->small.ensure(total));
-    CK(cudaMemset(BP->small.p, 0, total));
+    // groups in order of first appearance; problems keep their order inside a group
+    std::map<std::string, int> gid;
+    std::vector<std::vector<int>> members;
+    BP->group_of.resize(nprob);
+    for (int i = 0; i < nprob; ++i) {
+      auto g = gid.find(keys[i]);
+      int k = 0;
+      if (g == gid.end() || int(members[g->second].size()) >= (opts.group_max > 1 ? opts.group_max : 1)) {
+        k = static_cast<int>(members.size());
+        gid[keys[i]] = k;
+        members.emplace_back();
+      } else {
+        k = g->second;
+      }
+      members[k].push_back(i);
+      BP->group_of[i] = k;
+    }
+    BP->slot_of.resize(nprob);
+    int pos = 0;
+    for (size_t k = 0; k < members.size(); ++k) {
+      BP->gfirst.push_back(pos);
+      for (int i : members[k]) BP->slot_of[i] = pos++;
+    }
+    const size_t total = size_t(nprob) * (sizeof(SolveDesc) + sizeof(InfoDev));
     CK(cudaMallocHost(&BP->desc_host, total));
     std::memset(BP->desc_host, 0, total);
-    char* dd = static_cast<char*>(BP->small.p);
-    char* dh = BP->desc_host;
-    const size_t info0 = size_t(nprob) * BP->desc_stride;
+    SolveDesc* dh = reinterpret_cast<SolveDesc*>(BP->desc_host);
+    InfoDev* ih = reinterpret_cast<InfoDev*>(BP->desc_host + size_t(nprob) * sizeof(SolveDesc));
     CK(cudaGraphCreate(&BP->graph, 0));
-    for (int i = 0; i < nprob; ++i) {
+    for (size_t k = 0; k < members.size(); ++k) {
       std::shared_ptr<SolvePlan> pl;
-      RK(make_plan(specs[i], reinterpret_cast<SolveDesc*>(dd + i * BP->desc_stride),
-                   reinterpret_cast<InfoDev*>(dd + info0 + i * BP->info_stride),
-                   reinterpret_cast<SolveDesc*>(dh + i * BP->desc_stride),
-                   reinterpret_cast<InfoDev*>(dh + info0 + i * BP->info_stride), &pl));
+      const int first = BP->gfirst[k];
+      RK(make_plan(specs[members[k][0]], nullptr, nullptr, dh + first, ih + first, &pl,
+                   static_cast<int>(members[k].size())));
       RK(build_branch(*pl, BP->graph));
       BP->plans.push_back(std::move(pl));
     }
@@ -1576,31 +1628,93 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
   } else {
     BP = it->second.get();
   }
+  SolveDesc* dh = reinterpret_cast<SolveDesc*>(BP->desc_host);
+  InfoDev* ih = reinterpret_cast<InfoDev*>(BP->desc_host + size_t(nprob) * sizeof(SolveDesc));
   for (int i = 0; i < nprob; ++i) {
     const rtg_problem& q = probs[i];
-    SolvePlan& P = *BP->plans[i];
+    const SolvePlan& P = *BP->plans[BP->group_of[i]];
     if (q.X0 && apply_uses_st(P.op.op, dtype, dtype, vdtype) && reinterpret_cast<uintptr_t>(q.X0) % 16 != 0)
       return fail(RTG_ERR_INVALID_ARG, "problem %d: X0 must be 16-byte aligned for this operator", i);
     if (vdtype == RTG_BF16 && reinterpret_cast<uintptr_t>(q.C) % 16 != 0)
       return fail(RTG_ERR_INVALID_ARG, "problem %d: C must be 16-byte aligned with RTG_FLAG_BF16_BASIS", i);
-    fill_desc(*P.desc_host, q.C, q.X0, q.X, q.seed, q.tol, opts.breakdown_tol, dtype, q.lam,
+    fill_desc(dh[BP->slot_of[i]], q.C, q.X0, q.X, q.seed, q.tol, opts.breakdown_tol, dtype, q.lam,
               P.mode == 2 ? opts.n_mu : 0, opts.mu_grid);
   }
-  const size_t dbytes = size_t(nprob) * BP->desc_stride;
-  const size_t ibytes = size_t(nprob) * BP->info_stride;
-  CK(cudaMemcpyAsync(BP->small.p, BP->desc_host, dbytes, cudaMemcpyHostToDevice, s));
+  // one strided copy per group each way: host records are contiguous, device
+  // records sit at the start of each problem's block
+  for (size_t k = 0; k < BP->plans.size(); ++k) {
+    const SolvePlan& P = *BP->plans[k];
+    CK(cudaMemcpy2DAsync(P.desc_dev, size_t(P.w.b.stride), dh + BP->gfirst[k], sizeof(SolveDesc),
+                         sizeof(SolveDesc), size_t(P.w.b.n), cudaMemcpyHostToDevice, s));
+  }
   CK(cudaEventRecord(BP->ev0, s));
-  CK(cudaGraphLaunch(BP->exec, s));
+  std::vector<rtg_info> gph(BP->plans.size());   // phase times per group (direct launches)
+  if (use_graph) {
+    CK(cudaGraphLaunch(BP->exec, s));
+  } else {
+    // Direct launches, one group after another.  The host reads the group's
+    // count of running problems after each step and stops launching when it
+    // reaches zero, so the launch sequence is the one the graph runs.
+    PhaseTimer* pt = nullptr;
+    if (phase_times) {
+      if (!h->timer) h->timer = std::make_unique<PhaseTimer>();
+      CK(h->timer->init());
+      pt = h->timer.get();
+    }
+    for (size_t k = 0; k < BP->plans.size(); ++k) {
+      SolvePlan& P = *BP->plans[k];
+      if (pt) pt->reset(s);
+      auto group = [&](auto&& body) -> rtg_status {
+        if (pt) CK(pt->hold());
+        rtg_status st = body();
+        if (pt) pt->release();
+        return st;
+      };
+      auto left = [&]() -> rtg_status {
+        CK(cudaMemcpyAsync(P.stop_host, P.group_left, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return RTG_OK;
+      };
+      const StepOpts so = solve_step_opts(P, 0, 0);
+      RK(group([&] { return enqueue_prologue(P, so, s, pt); }));
+      RK(left());
+      int steps = 0;
+      while (steps < P.w.m && *P.stop_host != 0) {
+        const int j = steps++;
+        RK(group([&] { return enqueue_step(P.op, P.sp, P.w, dtype, P.tA, P.tB, P.sk, so, s, pt, j); }));
+        RK(left());
+      }
+      P.direct_steps = steps;
+      RK(group([&] { return enqueue_epilogue(P, s, pt); }));
+      if (pt) {
+        CK(cudaStreamSynchronize(s));
+        rtg_info& gi = gph[k];
+        for (int q = 0; q < RTG_PHASE_COUNT; ++q) {
+          gi.phase_ms[q] = 0.0;
+          gi.phase_launches[q] = 0;
+        }
+        pt->collect(steps, &gi);
+      }
+    }
+  }
   CK(cudaEventRecord(BP->ev1, s));
-  CK(cudaMemcpyAsync(BP->desc_host + dbytes, static_cast<char*>(BP->small.p) + dbytes, ibytes,
-                     cudaMemcpyDeviceToHost, s));
+  for (size_t k = 0; k < BP->plans.size(); ++k) {
+    const SolvePlan& P = *BP->plans[k];
+    CK(cudaMemcpy2DAsync(ih + BP->gfirst[k], sizeof(InfoDev), P.info_dev, size_t(P.w.b.stride),
+                         sizeof(InfoDev), size_t(P.w.b.n), cudaMemcpyDeviceToHost, s));
+  }
   CK(cudaStreamSynchronize(s));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, BP->ev0, BP->ev1);
   if (infos)
     for (int i = 0; i < nprob; ++i) {
-      const SolvePlan& P = *BP->plans[i];
-      fill_info(P, *P.info_host, P.mode, P.n_mu, true, ms, &infos[i]);
+      const SolvePlan& P = *BP->plans[BP->group_of[i]];
+      fill_info(P, ih[BP->slot_of[i]], P.mode, P.n_mu, use_graph, ms, &infos[i]);
+      if (phase_times)   // the phase times of the problem's whole group
+        for (int q = 0; q < RTG_PHASE_COUNT; ++q) {
+          infos[i].phase_ms[q] = gph[BP->group_of[i]].phase_ms[q];
+          infos[i].phase_launches[q] = gph[BP->group_of[i]].phase_launches[q];
+        }
     }
   return RTG_OK;
 }

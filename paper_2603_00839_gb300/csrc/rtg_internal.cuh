@@ -17,6 +17,43 @@ constexpr int kMaxMu = RTG_MAX_MU;
 constexpr int kMaxPasses = 8;
 constexpr int kMaxMix = 4;          // channel-mixing size handled inside the fused blur kernel
 
+// Lock-step batch: one launch serves n problems of identical shape.  Every
+// pointer a kernel receives is problem 0's; problem p's memory (workspace,
+// descriptor, info record, sketch scratch) sits `stride` bytes further per
+// problem.  The problem is the slowest part of blockIdx.z (z = p * nz + local
+// z, nz = gridDim.z / n).  n = 1, stride = 0 for a single solve.
+struct Batch {
+  int n = 1;
+  int64_t stride = 0;
+};
+#ifdef __CUDACC__
+struct BIdx {
+  int p;          // problem
+  unsigned z;     // local blockIdx.z
+  unsigned nz;    // local gridDim.z
+  int64_t off;    // byte offset of the problem's memory
+};
+__device__ __forceinline__ BIdx bidx(const Batch& b) {
+  BIdx r;
+  r.nz = gridDim.z / static_cast<unsigned>(b.n);
+  r.p = static_cast<int>(blockIdx.z / r.nz);
+  r.z = blockIdx.z % r.nz;
+  r.off = static_cast<int64_t>(r.p) * b.stride;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ T* bsh(T* p, int64_t off) {
+  return p == nullptr ? p : reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(p) + off);
+}
+#endif
+// grid z of a batched launch: local z, capped so that n * z fits the limit
+inline unsigned batch_z(int64_t local, const Batch& b) {
+  int64_t cap = 65535 / (b.n > 0 ? b.n : 1);
+  if (local > cap) local = cap;
+  if (local < 1) local = 1;
+  return static_cast<unsigned>(local * b.n);
+}
+
 enum PassKind : int { PK_BAND = 1, PK_DENSE = 2 };
 
 // One mode product of the separable operator Phi (Eq. 56-57): either a
@@ -65,6 +102,7 @@ struct Ctl {
   int cycle;
   int loops;        // executions of the step body since the reset (hard cap m+1)
   int givens;       // a finished Hessenberg column awaits its Givens update
+  int counted;      // lock-step batch: this problem's stop has been counted
   double beta;      // ||R_0||_Theta of this cycle
   double beta0;     // of the first cycle (scale of rho)
   double rho;       // last rho_j
@@ -127,6 +165,35 @@ struct Work {
   double* gcv;                 // GCV values (kMaxMu)
   double* ysel;                // per-mu coefficient candidates (kMaxMu * m)
   int part_rows;               // rows available in part
+  Batch b;                     // lock-step batch of identical workspaces
+#ifdef __CUDACC__
+  // this workspace moved to the problem `off` bytes further
+  __device__ __forceinline__ Work at(int64_t off) const {
+    Work r = *this;
+    r.V = bsh(V, off);
+    r.W = bsh(W, off);
+    r.U = bsh(U, off);
+    r.S = bsh(S, off);
+    r.Spart = bsh(Spart, off);
+    r.tmp0 = bsh(tmp0, off);
+    r.tmp1 = bsh(tmp1, off);
+    r.Q = bsh(Q, off);
+    r.part = bsh(part, off);
+    r.counter = bsh(counter, off);
+    r.ctl = bsh(ctl, off);
+    r.H = bsh(H, off);
+    r.R = bsh(R, off);
+    r.cs = bsh(cs, off);
+    r.sn = bsh(sn, off);
+    r.g = bsh(g, off);
+    r.G = bsh(G, off);
+    r.rho_hist = bsh(rho_hist, off);
+    r.y = bsh(y, off);
+    r.gcv = bsh(gcv, off);
+    r.ysel = bsh(ysel, off);
+    return r;
+  }
+#endif
 };
 
 // Sketch description: modes with s_k < I_k carry Theta_k as packed sign
@@ -199,6 +266,13 @@ struct PtrRef {
   int joff = 0;
   int mod = 0;      // > 0: slot (*jidx + joff) % mod of a ring
 #ifdef __CUDACC__
+  __device__ __forceinline__ PtrRef at(int64_t off) const {
+    PtrRef r = *this;
+    r.base = bsh(base, off);
+    r.ind = bsh(ind, off);
+    r.jidx = bsh(jidx, off);
+    return r;
+  }
   template <typename T>
   __device__ __forceinline__ T* get() const {
     const void* b = ind ? *ind : base;
@@ -223,10 +297,10 @@ cudaError_t launch_philox_words(uint64_t seed, uint64_t pid, int64_t n_words, ui
 // key_dev (optional): device array {seed, problem_id} read when the kernel runs,
 // so one captured graph serves every seed; otherwise sp.seed / sp.pid.
 cudaError_t launch_theta_bits(const SketchPlan& sp, uint32_t* bits, cudaStream_t s,
-                              const uint64_t* key_dev = nullptr);
+                              const uint64_t* key_dev = nullptr, Batch b = Batch{});
 // signs, then (FP32 chain) the Theta fragments of every stage
 cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, cudaStream_t s,
-                         const uint64_t* key_dev = nullptr);
+                         const uint64_t* key_dev = nullptr, Batch b = Batch{});
 
 // k_apply.cu: Y = alpha * Phi(X) + beta * Z (Z may be null when beta == 0).
 // tmp: scratch of n elements for the unfused path (may be null if unused).
@@ -234,7 +308,7 @@ cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, 
 // runs the spatio-temporal kernel, FP32 arithmetic); Z has type dtype.
 cudaError_t launch_apply(const OpPlan& op, int dtype, PtrRef X, PtrRef Y, double alpha,
                          double beta, PtrRef Z, void* tmp, void* tmp2, const int* stop,
-                         cudaStream_t s, int tin = -1, int tout = -1);
+                         cudaStream_t s, int tin = -1, int tout = -1, Batch b = Batch{});
 // The spatio-temporal kernel can apply op to X stored as tin.
 bool st_supported(const OpPlan& op, int tin);
 int st_bucket(int r);
@@ -254,7 +328,8 @@ struct SketchDots;
 // xdtype: storage type of X (default sp.dtype); RTG_BF16 needs an FP32 plan whose
 // first stage contracts mode 1.
 cudaError_t launch_sketch(const SketchPlan& sp, const SketchScratch& sc, PtrRef X, void* out,
-                          const SketchDots* dots, const int* stop, cudaStream_t s, int xdtype = -1);
+                          const SketchDots* dots, const int* stop, cudaStream_t s, int xdtype = -1,
+                          Batch b = Batch{});
 int sketch_launches(const SketchPlan& sp);
 
 // k_arnoldi.cu: the sketched Arnoldi process on a Work.
@@ -270,6 +345,17 @@ struct StepOpts {
   int solve_mode;        // 1: skip V_{j+1} once the solve stops
   int use_cond;
   unsigned long long cond;   // cudaGraphConditionalHandle
+  // lock-step batch: problems still running (the loop ends when it reaches 0);
+  // shared by the batch, not moved with a problem's memory
+  unsigned* group_left;
+#ifdef __CUDACC__
+  __device__ __forceinline__ StepOpts at(int64_t off) const {
+    StepOpts r = *this;
+    r.desc_tol = bsh(desc_tol, off);
+    r.desc_bd_tol = bsh(desc_bd_tol, off);
+    return r;
+  }
+#endif
 };
 struct SketchDots {
   const Work* w;
@@ -283,7 +369,8 @@ cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fuse
 cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s);
 int gs_grid(int64_t d);
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s);
-cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s);
+// group_left (lock-step batch): set to the number of problems
+cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s, unsigned* group_left = nullptr);
 
 // k_solve.cu: projected Tikhonov / GCV, assembly and the info summary.
 struct FinishOpts {

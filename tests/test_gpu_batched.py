@@ -1,9 +1,12 @@
 """Batched form on the GPU: many independent solves in one CUDA graph launch.
 
-Every problem of a batch runs as its own branch of one graph with its own
-device-side stop decision, so each result must equal, bit for bit, the same
-problem solved alone (same kernels, same launch shapes, deterministic
-reductions).  Problems of one batch differ in shape (square and not),
+By default every problem is its own branch of the graph; with group_max > 1
+problems of equal structure (shape, operator, sketch sizes, m,
+regularisation mode, X0 or not) run in lock step: one launch per kernel
+serves the group, each problem keeps its own device-side stop decision, and
+the group's loop runs while any of them does.  Each result must equal, bit
+for bit, the same problem solved alone (same kernels, same per-problem
+launch shapes, deterministic reductions).  Problems of one batch differ in shape (square and not),
 operator, Krylov dimension, sketch sizes, regularisation and stop level, as
 in the batched workload (side lengths 64..1024, sigma 0.5..3, radius
 ceil(3 sigma), m = 30, sketch min(I_k, 128)).
@@ -131,3 +134,105 @@ def test_batched_rejects_bad_arguments(h):
     q64["C"] = api.to_device(q["C"].cpu().double().numpy(), torch.float64)
     with pytest.raises(ValueError, match="one dtype"):
         h.gmres_solve_batched([q, q64])
+
+
+def _same_shape(h, n, dims=(96, 80, 3), m=20, sk=(48, 40, 3), seed0=0, dtype=torch.float32):
+    """n problems of one structure (one lock-step group): own image, noise level, seed, mu, tol."""
+    out = []
+    for k in range(n):
+        cfg = dict(dims=dims, image_seed=seed0 + k, sigma=1.5, radius=5, nu=0.005 * (k + 1), m=m,
+                   sketch_dims=sk, problem_id=seed0 + 7 * k + 1, mu=1e-3 * (k + 1))
+        out.append(_problem(h, cfg, dtype))
+    return out
+
+
+def _assert_same(h, probs, Xs, res, **kw):
+    for q, X, r in zip(probs, Xs, res):
+        Xr, rr = h.gmres_solve(q["C"], q["m"], q["sketch_dims"], q["seed"], q["lam"], q["A"], q["B"],
+                               tol=q["tol"], X0=q.get("X0"), **kw)
+        assert r.device_status == 0 and rr.device_status == 0
+        assert r.iters == rr.iters and r.converged == rr.converged
+        assert np.array_equal(r.rho, rr.rho)
+        assert r.mu == rr.mu
+        assert np.array_equal(X.cpu().numpy(), Xr.cpu().numpy())
+
+
+def test_lockstep_group_equals_single_solves(h):
+    """Five problems of one structure stopping at different steps: one runs all m
+    steps (tol 0), one stops after the first step, the others at rho*."""
+    probs = _same_shape(h, 5)
+    probs[1]["tol"] = 0.0
+    probs[3]["tol"] = 0.9
+    Xs, res = h.gmres_solve_batched(probs, group_max=8)
+    iters = [r.iters for r in res]
+    assert iters[1] == 20 and iters[3] == 1 and len(set(iters)) >= 3
+    _assert_same(h, probs, Xs, res)
+
+
+def test_lockstep_group_gcv(h):
+    grid = w.mu_grid()
+    probs = _same_shape(h, 4, seed0=10)
+    for q in probs:
+        q["lam"] = -1.0
+    Xs, res = h.gmres_solve_batched(probs, mu_grid=grid, group_max=4)
+    _assert_same(h, probs, Xs, res, mu_grid=grid)
+
+
+def test_interleaved_groups(h):
+    """Problems of two structures given alternately: two groups, results in caller order."""
+    a = _same_shape(h, 3, seed0=20)
+    b = _same_shape(h, 2, dims=(64, 72, 3), m=15, sk=(32, 36, 3), seed0=30)
+    probs = [a[0], b[0], a[1], b[1], a[2]]
+    Xs, res = h.gmres_solve_batched(probs, group_max=16)
+    _assert_same(h, probs, Xs, res)
+    # a second call on the same plan with new data
+    for q in probs:
+        q["C"] = _api().to_device(0.25 * q["C"].cpu().numpy(), torch.float32)
+    Xs, res = h.gmres_solve_batched(probs, group_max=16)
+    _assert_same(h, probs, Xs, res)
+    # capped groups: {a0, a1}, {a2}, {b0, b1}
+    Xs, res = h.gmres_solve_batched(probs, group_max=2)
+    _assert_same(h, probs, Xs, res)
+
+
+def test_lockstep_group_with_initial_guesses(h):
+    api = _api()
+    probs = _same_shape(h, 3, seed0=40)
+    rng = np.random.default_rng(0)
+    for q in probs:
+        q["X0"] = api.to_device(0.1 * rng.standard_normal(tuple(q["C"].shape)), torch.float32)
+    Xs, res = h.gmres_solve_batched(probs, group_max=3)
+    _assert_same(h, probs, Xs, res)
+
+
+def test_lockstep_group_fp64(h):
+    probs = _same_shape(h, 3, seed0=50, dtype=torch.float64)
+    Xs, res = h.gmres_solve_batched(probs, group_max=3)
+    _assert_same(h, probs, Xs, res)
+
+
+def test_lockstep_group_bf16_basis(h):
+    probs = _same_shape(h, 3, dims=(96, 80, 3), sk=(48, 40, 3), seed0=60)
+    Xs, res = h.gmres_solve_batched(probs, bf16_basis=True, group_max=3)
+    _assert_same(h, probs, Xs, res, bf16_basis=True)
+
+
+def test_lockstep_direct_and_phase_timed_launches_equal_the_graph(h):
+    """Direct launches (one group after another, host stops at the group's end)
+    and phase-timed launches give the graph's results bit for bit."""
+    probs = _same_shape(h, 3, seed0=70) + _same_shape(h, 2, dims=(64, 72, 3), m=15, sk=(32, 36, 3), seed0=80)
+    probs[0]["tol"] = 0.0
+    with pytest.raises(Exception):
+        h.gmres_solve_batched(probs, group_max=-1)
+    Xg, rg = h.gmres_solve_batched(probs, group_max=8)
+    Xg = [X.cpu().numpy().copy() for X in Xg]
+    for kw in (dict(use_graph=False), dict(phase_times=True)):
+        Xd, rd = h.gmres_solve_batched(probs, group_max=8, **kw)
+        for a, b, ra, rb in zip(Xg, Xd, rg, rd):
+            assert ra.iters == rb.iters and np.array_equal(ra.rho, rb.rho)
+            assert np.array_equal(a, b.cpu().numpy())
+    # phase times: the group's own, shared by its problems; the apply group runs once per step
+    assert rd[0].phase_ms == rd[1].phase_ms and rd[3].phase_ms == rd[4].phase_ms
+    assert rd[0].phase_launches["apply"] == max(r.iters for r in rd[:3])
+    assert rd[3].phase_launches["apply"] == max(r.iters for r in rd[3:])
+    assert all(v >= 0 for v in rd[0].phase_ms.values()) and rd[0].phase_ms["sketch"] > 0
