@@ -11,6 +11,12 @@ namespace rtg {
 
 constexpr int GS_MAXW = 8;   // warps per block of the reducing kernels (256 threads)
 constexpr int kRedCols = 2 * kMaxK + 4;   // columns of one reduction (see gs_ncols)
+// Gram matrices of up to this many rows are staged in shared memory by the
+// step finish (it needs (kMaxK + 6) + r (r + 1) + GS_MAXW r + 4 doubles of scratch)
+constexpr int kGramSmemRows = 56;
+static_assert((kMaxK + 6) + kGramSmemRows * (kGramSmemRows + 1) + GS_MAXW * kGramSmemRows + 4 <=
+                  GS_MAXW * kRedCols,
+              "Gram staging must fit the reduction scratch");
 
 template <typename A>
 __device__ __forceinline__ A warp_sum(A v) {
@@ -218,10 +224,10 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
 }
 
 // Ticket: returns true in every thread of the last block to finish, after
-// tot[0..ncols) holds the sum of all blocks' rows.  The rows are summed in
-// one round of loads: thread t takes column t % nc and every G-th row
-// starting at t / nc (four accumulators), then one thread per column adds
-// the G group sums.  The order is fixed, so the result is deterministic.
+// tot[0..ncols) holds the sum of all blocks' rows.  Thread t takes column
+// t % nc and every G-th row starting at t / nc, sixteen rows per round of
+// loads, then one thread per column adds the G group sums (pairwise trees:
+// FP64 adds have a long dependent latency on this GPU).  The order is fixed, so the result is deterministic.
 // The counter wraps back to zero by itself.  scratch: >= blockDim doubles.
 __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot, int* am_last,
                                           double* scratch) {
@@ -241,30 +247,36 @@ __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot,
     const int t = threadIdx.x;
     const int c = t % nc, g = t / nc;
     if (g < G) {
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      // rows g, g + G, ...: sixteen loads in flight per round (one L2
+      // round trip per sixteen rows), summed in a fixed tree
+      constexpr int U = 16;
+      double acc = 0.0;
       const double* p = w.part + c0 + c;
-      unsigned b = g;
-      for (; b + 3 * G < nblk; b += 4 * G) {
-        a0 += __ldcg(p + static_cast<int64_t>(b) * rowlen);
-        a1 += __ldcg(p + static_cast<int64_t>(b + G) * rowlen);
-        a2 += __ldcg(p + static_cast<int64_t>(b + 2 * G) * rowlen);
-        a3 += __ldcg(p + static_cast<int64_t>(b + 3 * G) * rowlen);
+      for (unsigned b = g; b < nblk; b += U * G) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const unsigned bb = b + u * G;
+          v[u] = bb < nblk ? __ldcg(p + static_cast<int64_t>(bb) * rowlen) : 0.0;
+        }
+#pragma unroll
+        for (int h = U / 2; h > 0; h >>= 1)
+#pragma unroll
+          for (int u = 0; u < h; ++u) v[u] += v[u + h];
+        acc += v[0];
       }
-      for (; b < nblk; b += G) a0 += __ldcg(p + static_cast<int64_t>(b) * rowlen);
-      scratch[g * nc + c] = (a0 + a1) + (a2 + a3);
+      scratch[g * nc + c] = acc;
     }
     __syncthreads();
-    if (t < nc) {
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int u = 0;
-      for (; u + 3 < G; u += 4) {
-        a0 += scratch[u * nc + t];
-        a1 += scratch[(u + 1) * nc + t];
-        a2 += scratch[(u + 2) * nc + t];
-        a3 += scratch[(u + 3) * nc + t];
-      }
-      for (; u < G; ++u) a0 += scratch[u * nc + t];
-      tot[c0 + t] = (a0 + a1) + (a2 + a3);
+    if (t < nc) {   // pairwise tree over the G group sums
+      double v[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) v[u] = u < G ? scratch[u * nc + t] : 0.0;
+#pragma unroll
+      for (int h = 16; h > 0; h >>= 1)
+#pragma unroll
+        for (int u = 0; u < h; ++u) v[u] += v[u + h];
+      tot[c0 + t] = v[0];
     }
     __syncthreads();
   }
@@ -306,9 +318,10 @@ __device__ inline void gs_finish_start(const Work& w, const StepOpts& o, const d
 // in FP64.  Writes the Hessenberg column, h_{j+1,j} (0 on breakdown), the
 // breakdown and non-finite flags, and advances j.  The Givens update of
 // Eq. 11S, rho_j and the stop rule follow in givens_step, off this
-// kernel's critical path.  For J < 32 one warp does the arithmetic with
-// the Gram matrix in shared memory (lane i owns row i); larger J use one
-// warp per row.  sh: shared scratch of >= (kMaxK + 6) + 32 * 33 doubles.
+// kernel's critical path.  Up to kGramSmemRows rows the Gram matrix is
+// staged in shared memory and every warp takes part in the two products
+// with it; beyond, one warp per row reads it from global memory.  sh:
+// shared scratch of GS_MAXW * kRedCols doubles, 256 threads.
 __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const double* tot, double* sh) {
   Ctl* ctl = w.ctl;
   const int J = ctl->j;
@@ -320,42 +333,70 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
   double* red = col + (kMaxK + 2);     // a = h.h1, b = h.(G h)
   double* G = w.G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (J < 32) {
-    double* Gs = red + 4;              // [32][33]
-    for (int e = threadIdx.x; e < (J + 1) * (J + 1); e += blockDim.x) {
-      const int i = e % (J + 1), k = e / (J + 1);
-      Gs[i * 33 + k] = (i == J) ? grow[k] : (k == J ? grow[i] : G[i + static_cast<int64_t>(ld) * k]);
+  const int n = J + 1;
+  if (n <= kGramSmemRows) {
+    // G staged in shared memory (row stride n + 1); each product G x runs
+    // on every warp: warp w takes a slice of the columns, lane the rows
+    // lane and lane + 32, and the warps' partial rows are summed in order
+    const int lg = n + 1;
+    double* Gs = red + 4;              // n x n
+    double* pr = Gs + n * lg;          // [nw][n] partial products
+    double* ab = pr + nw * n;          // [2][2] the two warps' sums of a and b
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e % n, k = e / n;
+      Gs[i * lg + k] = (i == J) ? grow[k] : (k == J ? grow[i] : G[i + static_cast<int64_t>(ld) * k]);
     }
     for (int i = threadIdx.x; i <= J; i += blockDim.x) {   // new row/column, for later steps
       G[i + static_cast<int64_t>(ld) * J] = grow[i];
       G[J + static_cast<int64_t>(ld) * i] = grow[i];
     }
     __syncthreads();
-    if (warp == 0) {
-      double h1i = 0.0, hi = 0.0, ghi = 0.0;
-      if (lane <= J) {
-        h1i = h1[lane];
+    const int ks = (n + nw - 1) / nw;
+    const int k0 = warp * ks, k1 = (k0 + ks < n) ? k0 + ks : n;
+    auto gmul = [&](const double* x) {   // pr[w][i] = sum over the warp's columns of G(i, k) x_k
+      for (int i = lane; i < n; i += 32) {
         double u = 0.0;
-        for (int k = 0; k <= J; ++k) u = fma(Gs[lane * 33 + k], h1[k], u);
-        hi = 2.0 * h1i - u;
-        col[lane] = hi;
+        for (int k = k0; k < k1; ++k) u = fma(Gs[i * lg + k], x[k], u);
+        pr[warp * n + i] = u;
       }
-      __syncwarp();
-      if (lane <= J) {
-        double g = 0.0;
-        for (int k = 0; k <= J; ++k) g = fma(Gs[lane * 33 + k], col[k], g);
-        ghi = g;
+    };
+    gmul(h1);
+    __syncthreads();
+    // sums of the warps' partial rows as a fixed tree (FP64 adds have a
+    // long dependent latency on this GPU)
+    auto wsum = [&](int i) {
+      if (nw == 8)
+        return ((pr[i] + pr[n + i]) + (pr[2 * n + i] + pr[3 * n + i])) +
+               ((pr[4 * n + i] + pr[5 * n + i]) + (pr[6 * n + i] + pr[7 * n + i]));
+      double u = 0.0;
+      for (int v = 0; v < nw; ++v) u += pr[v * n + i];
+      return u;
+    };
+    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = 2.0 * h1[i] - wsum(i);
+    __syncthreads();
+    gmul(col);
+    __syncthreads();
+    if (warp < 2) {   // a = h . h1, b = h . (G h) over the n <= 64 rows
+      double a = 0.0, b = 0.0;
+      const int i = threadIdx.x;
+      if (i < n) {
+        a = col[i] * h1[i];
+        b = col[i] * wsum(i);
       }
-      double a = hi * h1i, b = hi * ghi;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, off);
         b += __shfl_xor_sync(0xffffffffu, b, off);
       }
       if (lane == 0) {
-        red[0] = a;
-        red[1] = b;
+        ab[2 * warp] = a;
+        ab[2 * warp + 1] = b;
       }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      red[0] = ab[0] + ab[2];
+      red[1] = ab[1] + ab[3];
     }
   } else {
     for (int i = threadIdx.x; i <= J; i += blockDim.x) {
@@ -395,13 +436,17 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
   }
   __syncthreads();
   double* Hc = w.H + static_cast<int64_t>(ld) * J;
-  for (int i = threadIdx.x; i <= J; i += blockDim.x) Hc[i] = col[i];
+  int bad = 0;
+  for (int i = threadIdx.x; i <= J; i += blockDim.x) {
+    Hc[i] = col[i];
+    bad |= !isfinite(col[i]);
+  }
   for (int i = J + 2 + threadIdx.x; i < ld; i += blockDim.x) Hc[i] = 0.0;
+  bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     const double bd_tol = o.desc_bd_tol ? *o.desc_bd_tol : o.bd_tol;
     const double hh1 = red[0], hgh = red[1];
-    bool finite = isfinite(s2) && isfinite(hh1) && isfinite(hgh);
-    for (int i = 0; i <= J; ++i) finite = finite && isfinite(col[i]);
+    const bool finite = isfinite(s2) && isfinite(hh1) && isfinite(hgh) && !bad;
     const double hn2 = s2 - 2.0 * hh1 + hgh;
     const double hn = sqrt(hn2 > 0.0 ? hn2 : 0.0);
     const bool breakdown = finite && (hn <= bd_tol * sqrt(s2));
@@ -419,25 +464,44 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
 // Givens update of Eq. 11S for the Hessenberg column the last finish wrote
 // (column J = j - 1), rho_j = |g_{J+1}| / beta_0, the stop rule and the
 // condition of the device-side loop, which never runs more than m + 1
-// bodies.  One thread; runs beside the basis update, which does not depend
-// on it.
+// bodies.  Called by every thread of one block, which runs beside the basis
+// update (it does not depend on it): the block stages the column and the
+// stored rotations in shared memory with one round of loads, then one
+// thread applies the rotations (a dependent FP64 chain).
 __device__ inline void givens_step(const Work& w, const StepOpts& o) {
+  __shared__ double gv_h[kMaxK + 2], gv_c[kMaxK], gv_s[kMaxK];
+  __shared__ int gv_J, gv_do;
   Ctl* ctl = w.ctl;
-  if (ctl->givens) {
-    ctl->givens = 0;
-    const int J = ctl->j - 1;
-    const int ld = w.m + 1;
-    const double tol = o.desc_tol ? *o.desc_tol : o.tol;
+  if (threadIdx.x == 0) {
+    gv_do = ctl->givens;
+    gv_J = ctl->j - 1;
+  }
+  __syncthreads();
+  const int ld = w.m + 1;
+  if (gv_do) {
+    const int J = gv_J;
     const double* Hc = w.H + static_cast<int64_t>(ld) * J;
+    for (int i = threadIdx.x; i <= J + 1; i += blockDim.x) gv_h[i] = Hc[i];
+    for (int i = threadIdx.x; i < J; i += blockDim.x) {
+      gv_c[i] = w.cs[i];
+      gv_s[i] = w.sn[i];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (gv_do) {
+    ctl->givens = 0;
+    const int J = gv_J;
+    const double tol = o.desc_tol ? *o.desc_tol : o.tol;
     double* Rc = w.R + static_cast<int64_t>(ld) * J;
     // rotations 0..J-1 on the new column, then the new rotation
-    double x = Hc[0];
+    double x = gv_h[0];
     for (int i = 0; i < J; ++i) {
-      const double y = Hc[i + 1], c = w.cs[i], sv = w.sn[i];
+      const double y = gv_h[i + 1], c = gv_c[i], sv = gv_s[i];
       Rc[i] = c * x + sv * y;
       x = -sv * x + c * y;
     }
-    const double y = Hc[J + 1];
+    const double y = gv_h[J + 1];
     const double den = hypot(x, y);
     double c = 1.0, sv = 0.0;
     if (den != 0.0) {

@@ -654,8 +654,7 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
   if (a.nc == NC && rr == RR) {                                                                       \
     using Gm = RegGeom<RR, T>;                                                                        \
     const size_t smem = static_cast<size_t>(NC * Gm::Ht * Gm::Wd + Gm::Ht * RTX) * sizeof(T);         \
-    e = cudaFuncSetAttribute(k_apply_reg<T, NC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                             static_cast<int>(smem));                                                  \
+    e = set_smem(k_apply_reg<T, NC, RR>, smem);                                                       \
     if (e != cudaSuccess) return e;                                                                   \
     k_apply_reg<T, NC, RR><<<grid, FTHREADS, smem, s>>>(X, Y, Z, stop, a, b);                            \
     return cudaGetLastError();                                                                        \
@@ -672,8 +671,7 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
     switch (a.nc) {
 #define RTG_FUSED_CASE(NC)                                                                        \
   case NC:                                                                                        \
-    e = cudaFuncSetAttribute(k_apply_fused<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                             static_cast<int>(smem));                                              \
+    e = set_smem(k_apply_fused<T, NC>, smem);                                                     \
     if (e != cudaSuccess) return e;                                                               \
     k_apply_fused<T, NC><<<grid, FTHREADS, smem, s>>>(X, Y, Z, stop, a, b);                          \
     break;
@@ -764,9 +762,7 @@ static cudaError_t apply_st_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha
   if (nc == NC && rr == RR) {                                                                       \
     using Gm = StGeom<RR, TI>;                                                                      \
     const size_t smem = static_cast<size_t>(NC * Gm::Ht * Gm::Wd + Gm::Ht * STX) * sizeof(float);   \
-    cudaError_t e = cudaFuncSetAttribute(k_apply_st<TI, TO, NC, RR>,                                \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                                         static_cast<int>(smem));                                  \
+    cudaError_t e = set_smem(k_apply_st<TI, TO, NC, RR>, smem);                                     \
     if (e != cudaSuccess) return e;                                                                 \
     k_apply_st<TI, TO, NC, RR><<<grid, ST_THREADS, smem, s>>>(X, Y, Z, stop, a, b);                    \
     return cudaGetLastError();                                                                      \

@@ -135,7 +135,7 @@ template <typename T>
 __global__ void k_gk_update(Work w, int phase, PtrRef srcr, StepOpts o) {
   Ctl* ctl = w.ctl;
   if (phase == 2 && blockIdx.x == gridDim.x - 1) {   // Givens of column j - 1 beside the update
-    if (threadIdx.x == 0) givens_step(w, o);
+    givens_step(w, o);
     return;
   }
   if (ctl->stop || ctl->skip_update) return;

@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 
 #include "gs_common.cuh"
+#include "tma_common.cuh"
 
 namespace rtg {
 
@@ -312,54 +313,6 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 constexpr int F_RED = 17;         // padded row of the first stage's cross-warp reduction
 
-// ---- TMA bulk copies completing on an mbarrier (bounded waits)
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-// Waits for phase `parity`; gives up after a bounded number of polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-// Called by every thread after issuing a chunk's copies.  True if a copy
-// did not land within the bounded wait (agreed across the CTA): thread 0
-// then waits once more, bounded, for the copies still in flight, and the
-// timeout is recorded in *status.  The caller stops issuing copies.
-__device__ __forceinline__ bool tc_wait_failed(uint64_t* bar, uint32_t phase, int* status) {
-  const bool landed = mbar_wait(bar, phase);
-  if (!__syncthreads_or(!landed)) return false;
-  if (threadIdx.x == 0) {
-    mbar_wait(bar, phase);
-    if (status != nullptr) atomicExch(status, RTG_ERR_TIMEOUT);
-  }
-  __syncthreads();
-  return true;
-}
-
 template <int CH>
 constexpr size_t first_smem() {
   return size_t(CH) * F_MT * 32 * 16 + size_t(F_COLS) * (CH * 16 + 8) * 4 >
@@ -373,11 +326,20 @@ constexpr size_t first_smem() {
 // index, already split by the caller into (l-offset, i', r').
 struct OutMap {
   int blocked;
+  int small;              // every index part below 2^31: 32-bit divisions
   int64_t L, s;           // this stage
   int64_t M, I2, LT2;     // next stage
 };
 __device__ __forceinline__ int64_t out_pos(const OutMap& om, int64_t l, int64_t q, int64_t r) {
   if (!om.blocked) return l + om.L * (q + om.s * r);
+  if (om.small) {
+    const uint32_t M = static_cast<uint32_t>(om.M), I2 = static_cast<uint32_t>(om.I2);
+    const uint32_t rr = static_cast<uint32_t>(r), rm = rr % M, rq = rr / M;
+    const uint32_t L = static_cast<uint32_t>(om.L);
+    const uint32_t l2 = static_cast<uint32_t>(l) + L * static_cast<uint32_t>(q) + L * static_cast<uint32_t>(om.s) * rm;
+    const uint32_t i2 = rq % I2, r2 = rq / I2;
+    return (static_cast<int64_t>(r2) * om.LT2 + l2 / 16) * om.I2 * XA + static_cast<int64_t>(i2) * XA + (l2 % 16);
+  }
   const int64_t rm = r % om.M, rq = r / om.M;
   const int64_t l2 = l + om.L * q + om.L * om.s * rm;
   const int64_t i2 = rq % om.I2, r2 = rq / om.I2;
@@ -433,14 +395,14 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
     const int64_t i0 = static_cast<int64_t>(kc0) * 16;
     const int rows = static_cast<int>((static_cast<int64_t>(nk) * 16 < I - i0) ? static_cast<int64_t>(nk) * 16 : I - i0);   // valid rows of X
     const int ncol = static_cast<int>((static_cast<int64_t>(F_COLS) < R - c0) ? static_cast<int64_t>(F_COLS) : R - c0);
-    if (tid == 0) {
+    if (warp == 0) {   // lane 0 announces the bytes; the lanes issue one copy each
       const uint32_t fbytes = static_cast<uint32_t>(nk) * F_MT * 32 * 16;
       const uint32_t xbytes = bulk ? static_cast<uint32_t>(ncol) * rows * sizeof(TI) : 0u;
-      mbar_expect(&bar, fbytes + xbytes);
-      bulk_g2s(fA, fragA + (static_cast<int64_t>(mb) * kt_total + kc0) * F_MT * 32, fbytes, &bar);
-      if (bulk)
-        for (int col = 0; col < ncol; ++col)
-          bulk_g2s(&xs[col * XS], X + (c0 + col) * I + i0, static_cast<uint32_t>(rows * sizeof(TI)), &bar);
+      if (lane == 0) mbar_expect(&bar, fbytes + xbytes);
+      __syncwarp();
+      if (lane == 0) bulk_g2s(fA, fragA + (static_cast<int64_t>(mb) * kt_total + kc0) * F_MT * 32, fbytes, &bar);
+      if (bulk && lane < ncol)
+        bulk_g2s(&xs[lane * XS], X + (c0 + lane) * I + i0, static_cast<uint32_t>(rows * sizeof(TI)), &bar);
     }
     // zero the rows and columns the copies do not cover; without bulk, plain loads
     if (!bulk || ncol < F_COLS || rows < nk * 16) {
@@ -764,6 +726,8 @@ static OutMap stage_out_map(const SketchPlan& sp, int t) {
   om.M = om.blocked ? sp.next_M[t] : 1;
   om.I2 = om.blocked ? sp.next_I[t] : 1;
   om.LT2 = om.blocked ? sp.next_LT[t] : 1;
+  // l2 < L s M and r < R (the stage's columns) stay below 2^31
+  om.small = (om.L * om.s * om.M < (int64_t(1) << 31)) && (sp.stage_R[t] < (int64_t(1) << 31)) ? 1 : 0;
   return om;
 }
 
@@ -772,7 +736,7 @@ static cudaError_t launch_first(dim3 grid, PtrRef src, float* dst, const SketchP
                                 const uint32_t* fr, float scale, OutMap om, int* status, const int* stop,
                                 cudaStream_t s, Batch b) {
   constexpr size_t sm = first_smem<CH>();
-  cudaError_t e = cudaFuncSetAttribute(k_sk_first_tc<CH, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  cudaError_t e = set_smem(k_sk_first_tc<CH, TI>, sm);
   if (e != cudaSuccess) return e;
   k_sk_first_tc<CH, TI><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_I[t], sp.stage_R[t], sp.stage_s[t], kt,
                                                      reinterpret_cast<const uint4*>(fr), sp.stage_ntile[t],
@@ -812,7 +776,7 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
       const int inb = sp.stage_in_blocked[t];
       if (kt > 16) {
         constexpr size_t sm = inner_smem<32>();
-        e = cudaFuncSetAttribute(k_sk_inner_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        e = set_smem(k_sk_inner_tc<32>, sm);
         if (e != cudaSuccess) return e;
         k_sk_inner_tc<32><<<grid, TC_THREADS, sm, s>>>(src, inb, dst, sp.stage_L[t], sp.stage_I[t],
                                                        sp.stage_R[t], sp.stage_s[t], kt,
@@ -820,7 +784,7 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
                                                        scale, om, dpass, wk, so, status, stop, b);
       } else {
         constexpr size_t sm = inner_smem<16>();
-        e = cudaFuncSetAttribute(k_sk_inner_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        e = set_smem(k_sk_inner_tc<16>, sm);
         if (e != cudaSuccess) return e;
         k_sk_inner_tc<16><<<grid, TC_THREADS, sm, s>>>(src, inb, dst, sp.stage_L[t], sp.stage_I[t],
                                                        sp.stage_R[t], sp.stage_s[t], kt,

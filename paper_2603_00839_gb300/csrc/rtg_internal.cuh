@@ -287,6 +287,17 @@ struct PtrRef {
 };
 inline PtrRef ref(const void* p) { PtrRef r; r.base = p; return r; }
 
+// A kernel's dynamic shared memory, with the unified L1 / shared array given
+// to shared memory as far as it goes.  Every kernel of a solve asks for the
+// same split, so an SM never drains to re-partition it between launches.
+template <typename K>
+inline cudaError_t set_smem(K* kernel, size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              cudaSharedmemCarveoutMaxShared);
+}
+
 // Sets the thread-local message rtg_last_error() returns (rtg_api.cu).
 void record_error(const char* msg);
 

@@ -1,0 +1,58 @@
+// Bulk asynchronous copies (cp.async.bulk, the TMA's untiled form) that
+// complete on an mbarrier, with bounded waits: a copy that never lands
+// makes the kernel record RTG_ERR_TIMEOUT and stop, never spin forever.
+// Both addresses must be 16-byte aligned and the size a multiple of 16.
+#pragma once
+
+#include "rtg_internal.cuh"
+
+namespace rtg {
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Waits for phase `parity`; gives up after a bounded number of polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Called by every thread after issuing a chunk's copies.  True if a copy
+// did not land within the bounded wait (agreed across the CTA): thread 0
+// then waits once more, bounded, for the copies still in flight, and the
+// timeout is recorded in *status.  The caller stops issuing copies.
+__device__ __forceinline__ bool tc_wait_failed(uint64_t* bar, uint32_t phase, int* status) {
+  const bool landed = mbar_wait(bar, phase);
+  if (!__syncthreads_or(!landed)) return false;
+  if (threadIdx.x == 0) {
+    mbar_wait(bar, phase);
+    if (status != nullptr) atomicExch(status, RTG_ERR_TIMEOUT);
+  }
+  __syncthreads();
+  return true;
+}
+
+}  // namespace rtg
