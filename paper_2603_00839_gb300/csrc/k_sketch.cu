@@ -485,11 +485,14 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
   }
 }
 
+// Dynamic shared memory of the later stage: the K chunk (fragments and
+// blocked input) during the contraction, then the reduction scratch of the
+// fused Gram-Schmidt pass (GS_MAXW rows of partial sums and the totals).
 template <int CH>
 constexpr size_t inner_smem() {
-  return size_t(CH) * N_NT * 32 * 8 + size_t(CH) * 16 * XA * 4 > size_t(8) * 16 * N_NT * 8 * 4
-             ? size_t(CH) * N_NT * 32 * 8 + size_t(CH) * 16 * XA * 4
-             : size_t(8) * 16 * N_NT * 8 * 4;
+  constexpr size_t mma = size_t(CH) * N_NT * 32 * 8 + size_t(CH) * 16 * XA * 4;
+  constexpr size_t red = size_t(GS_MAXW + 1) * kRedCols * 8;
+  return mma > red ? mma : red;
 }
 
 // Later contraction (L > 1): out(l, q, r) = scale * sum_i X(l, i, r) Theta(q, i).
@@ -498,7 +501,7 @@ constexpr size_t inner_smem() {
 // (plain loads).  Warp w takes the K tiles w, w+8, ...  With dots_pass >= 0
 // the CTA then runs that Gram-Schmidt pass on its final tile.
 template <int CH>
-__global__ void __launch_bounds__(TC_THREADS)
+__global__ void __launch_bounds__(TC_THREADS, 3)
 k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int64_t I, int64_t R,
               int64_t s, int kt_total, const uint2* __restrict__ fragB, int nt_total, float scale,
               OutMap om, int dots_pass, Work w, StepOpts o, int* status, const int* stop, Batch bt) {
@@ -518,8 +521,6 @@ k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int
   __shared__ __align__(8) uint64_t bar;
   uint2* fB = reinterpret_cast<uint2*>(smem);                                    // [CH][N_NT][32]
   float* xa = reinterpret_cast<float*>(smem + size_t(CH) * N_NT * 32 * 8);        // [CH*16][XA]
-  __shared__ double red2[GS_MAXW][kRedCols];
-  __shared__ double tot[kRedCols];
   __shared__ int am_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gid = lane >> 2, tig = lane & 3;
   const int64_t ltiles = (L + 15) / 16;
@@ -630,6 +631,10 @@ k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int
   }
   if (dots_pass < 0) return;
   const int J = (dots_pass == 0) ? -1 : w.ctl->j;
+  // the reduction scratch reuses the dynamic shared memory
+  __syncthreads();
+  double(*red2)[kRedCols] = reinterpret_cast<double(*)[kRedCols]>(smem);
+  double* tot = reinterpret_cast<double*>(smem) + GS_MAXW * kRedCols;
   block_partials<float, ITEMS>(w, vals, ix, ITEMS, J, red2);
   if (!last_block_combine(w, gs_ncols(J), tot, &am_last, &red2[0][0])) return;
   if (dots_pass == 0) {
@@ -760,7 +765,9 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
       dim3 grid(static_cast<unsigned>((sp.stage_R[t] + F_COLS - 1) / F_COLS),
                 static_cast<unsigned>((sp.stage_ntile[t] + F_MT - 1) / F_MT), static_cast<unsigned>(b.n));
       const bool bf = (t == 0 && xdtype == RTG_BF16);
-      if (kt > 16)
+      // K chunks of 16 tiles up to I = 512 (about 50 KB of shared memory, four
+      // CTAs per SM: in throughput the occupancy outweighs the second chunk's load)
+      if (kt > 32)
         e = bf ? launch_first<32, __nv_bfloat16>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s, b)
                : launch_first<32, float>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s, b);
       else
