@@ -52,6 +52,11 @@ def parse():
                     help="launch every solve's kernels directly instead of replaying its CUDA graph "
                          "(for profilers that do not see kernels inside conditional graph nodes); "
                          "skips the phase-timed roofline pass")
+    ap.add_argument("--group-max", type=int, default=0,
+                    help="batched form: problems of one lock-step group (0: one graph branch per problem)")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="run the batched form alone (no plain, Golub-Kahan or warm-start forms, no phase "
+                         "passes, no end-to-end pass): for profiler captures of its kernels")
     return ap.parse_args()
 
 
@@ -156,9 +161,15 @@ def solve(h, pr, X, stream=None, host=False):
 # Kernel groups whose minimum traffic the byte model below covers, and the
 # source files that define each (the recorded ncu traffic is dropped when
 # one of them has changed since).
-PHASE_FILES = {"apply": ["k_apply.cu"], "sketch": ["k_sketch.cu", "gs_common.cuh"],
-               "gs": ["k_arnoldi.cu", "gs_common.cuh"], "update": ["k_arnoldi.cu"],
+PHASE_FILES = {"apply": ["k_apply.cu"], "sketch": ["k_sketch.cu", "gs_common.cuh", "tma_common.cuh"],
+               "gs": ["k_arnoldi.cu", "gs_common.cuh"],
+               "update": ["k_arnoldi.cu", "gs_common.cuh", "tma_common.cuh"],
                "assemble": ["k_solve.cu"], "init": ["k_arnoldi.cu", "k_sketch.cu"]}
+KERNEL_NAMES = {"apply": "k_apply_reg<float,3,7> (W = Phi(V_j))",
+                "sketch": "k_sk_first_tc<16> + k_sk_inner_tc<32> (S(W) with fused sketched dots)",
+                "update": "k_update_ring<float,8> (V_{j+1} streamed through a shared-memory ring, "
+                          "its sketched column, Givens block)",
+                "assemble": "k_assemble<float>", "init": "prologue group"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 
 
@@ -239,11 +250,7 @@ def phase_report(h, probs, X, peaks, workload: str):
     us_per_launch = 1e3 * tot_ms[dom] / launches
     ach = bytes_per_launch / (us_per_launch * 1e-6) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
-    names = {"apply": "k_apply_reg<float,3,7> (W = Phi(V_j))",
-             "sketch": "k_sk_first_tc + k_sk_inner_tc (S(W) with fused sketched dots)",
-             "update": "k_update<float> (V_{j+1} and its sketched column)",
-             "assemble": "k_assemble<float>", "init": "prologue group"}
-    roof = {"kernel": names.get(dom, dom), "phase": dom, "bound": "hbm", "achieved": round(ach, 1),
+    roof = {"kernel": KERNEL_NAMES.get(dom, dom), "phase": dom, "bound": "hbm", "achieved": round(ach, 1),
             "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
             "traffic": recorded_traffic(dom, workload), "bytes_per_launch": round(bytes_per_launch),
             "us_per_launch": round(us_per_launch, 3), "launches": launches,
@@ -251,6 +258,48 @@ def phase_report(h, probs, X, peaks, workload: str):
                       "until the group is queued",
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)",
             "mean_iters": float(np.mean(iters))}
+    return roof, table
+
+
+def batched_phase_report(h, batch, grid, peaks, workload: str):
+    """The batch of the chosen form run once more as one lock-step group with
+    direct launches and every kernel group timed by CUDA events (each launch
+    serves all problems of the batch; a stopped problem's blocks return at
+    once).  Returns the roofline of the byte-bound group with the largest
+    device time and the per-group table: algorithmic bytes summed over the
+    problems' own steps."""
+    _, res = h.gmres_solve_batched(batch, mu_grid=grid, phase_times=True, group_max=len(batch))
+    C0 = batch[0]["C"]
+    n = int(np.prod(C0.shape))
+    d = int(np.prod([min(s, i) for s, i in zip(batch[0]["sketch_dims"], C0.shape)]))
+    ms, launches = res[0].phase_ms, res[0].phase_launches
+    tot_bytes = {k: sum(phase_bytes(k, n, d, r.iters, 4) for r in res) for k in ms}
+    table = {}
+    share_total = sum(ms.values())
+    for k in ms:
+        if launches[k] == 0:
+            continue
+        e = {"us_per_batch": round(1e3 * ms[k], 2), "launches_per_batch": launches[k],
+             "share": round(ms[k] / share_total, 3)}
+        if tot_bytes[k] > 0:
+            e["gbs"] = round(tot_bytes[k] / (ms[k] * 1e-3) / 1e9, 1)
+        table[k] = e
+    cand = [k for k in table if tot_bytes.get(k, 0) > 0]
+    dom = max(cand, key=lambda k: ms[k])
+    bytes_per_launch = tot_bytes[dom] / launches[dom]
+    us_per_launch = 1e3 * ms[dom] / launches[dom]
+    ach = bytes_per_launch / (us_per_launch * 1e-6) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    roof = {"kernel": KERNEL_NAMES.get(dom, dom), "phase": dom, "bound": "hbm", "achieved": round(ach, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+            "traffic": recorded_traffic(dom, workload + "_lockstep16"),
+            "bytes_per_launch": round(bytes_per_launch), "us_per_launch": round(us_per_launch, 3),
+            "launches": launches[dom], "problems_per_launch": len(batch),
+            "timing": "CUDA events around each kernel group of the batch run as one lock-step group "
+                      "(direct launches, stream gated until the group is queued)",
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "fallback" not in peaks
+                           else "fallback 6800 GB/s",
+            "iters": [r.iters for r in res]}
     return roof, table
 
 
@@ -460,14 +509,18 @@ def run_ours(args):
     Xb = [api.empty(probs[0]["p"].dims, torch.float32) for _ in range(B)]
     nb = max(1, len(probs) // B)
 
+    def batched(bt):
+        return h.gmres_solve_batched(bt, mu_grid=grid, use_graph=not args.direct, group_max=args.group_max)
+
+    only_b = args.only_batched
     # ---- plain FP32 form: one solve per step, device-timed, L2 flushed between steps
-    for s in range(args.warmup):
+    for s in range(0 if only_b else args.warmup):
         solve(h, probs[s % len(probs)], X)
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     iters, conv_plain = [], []
-    for s in range(args.steps):
+    for s in range(0 if only_b else args.steps):
         flush.zero_()
         evs[s][0].record(stream)
         _, info = solve(h, probs[s % len(probs)], X)
@@ -477,20 +530,20 @@ def run_ours(args):
         if info.device_status != 0:
             raise RuntimeError(f"solve failed: device status {info.device_status}")
     torch.cuda.synchronize()
-    plain_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    plain_ms = float("nan") if only_b else sum(a.elapsed_time(b) for a, b in evs) / args.steps
 
     # ---- sketched Golub-Kahan (Algorithm 4) on the same problems, one solve per step
     def gk(pr):
         p = pr["p"]
         return h.gk_solve(pr["C"], p.m, p.sketch_dims, p.seed, p.lam, pr["A"], pr["B"], X=X,
                           tol=pr["tol"], mu_grid=p.mu_grid)
-    for s in range(args.warmup):
+    for s in range(0 if only_b else args.warmup):
         gk(probs[s % len(probs)])
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     iters_gk, conv_gk = [], []
-    for s in range(args.steps):
+    for s in range(0 if only_b else args.steps):
         flush.zero_()
         evs[s][0].record(stream)
         _, info = gk(probs[s % len(probs)])
@@ -498,11 +551,11 @@ def run_ours(args):
         iters_gk.append(info.iters)
         conv_gk.append(bool(info.converged))
     torch.cuda.synchronize()
-    gk_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    gk_ms = float("nan") if only_b else sum(a.elapsed_time(b) for a, b in evs) / args.steps
 
     # ---- chosen form: batched (B problems per CUDA-graph launch), one batch per step
     for s in range(args.warmup):
-        h.gmres_solve_batched(batch_of(s % nb), mu_grid=grid)
+        batched(batch_of(s % nb))
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
@@ -514,7 +567,7 @@ def run_ours(args):
         for s in range(args.steps):
             flush.zero_()
             evs[s][0].record(stream)
-            _, res = h.gmres_solve_batched(batch_of(s % nb), mu_grid=grid)
+            _, res = batched(batch_of(s % nb))
             evs[s][1].record(stream)
             for r in res:
                 iters_b.append(r.iters)
@@ -550,34 +603,35 @@ def run_ours(args):
         for i in range(B):
             Cdev[i].copy_(probs[(k * B + i) % len(probs)]["C_host"], non_blocking=True)
             bt[i]["C"] = Cdev[i]
-        _, res = h.gmres_solve_batched(bt, mu_grid=grid)
+        _, res = batched(bt)
         for i in range(B):
             Xh[i].copy_(Xb[i], non_blocking=True)
         torch.cuda.synchronize()
         return res
 
-    for s in range(2):
+    for s in range(0 if only_b else 2):
         e2e_step(s % nb)
     t0 = time.perf_counter()
-    for s in range(args.steps):
+    for s in range(0 if only_b else args.steps):
         e2e_step(s % nb)
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = (time.perf_counter() - t0) / args.steps if not only_b else float("nan")
     e2e_t = torch.tensor([e2e_s], device="cuda")
     if world > 1:
         torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
     e2e_val = world * B / float(e2e_t.item())
 
     ws_form = None
-    if rank == 0 and not args.no_warm_start:
+    if rank == 0 and not args.no_warm_start and not only_b:
         ws_form = warm_start_form(h, api, torch, probs)
 
     # phase timing holds the stream at gates the host opens; a profiler that
     # serialises every launch would wait on them, so --direct (the profiler
     # mode) leaves it out
-    roof, phases = (phase_report(h, probs, X, peaks, WORKLOAD) if rank == 0 and not args.direct
-                    else (None, None))
+    phased = rank == 0 and not args.direct and not only_b
+    roof_plain, phases = phase_report(h, probs, X, peaks, WORKLOAD) if phased else (None, None)
+    roof, phases_b = batched_phase_report(h, batch_of(0), grid, peaks, WORKLOAD) if phased else (None, None)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not only_b:
         cpu = cpu_baseline([dict(p=pr["p"]) for pr in probs], args.cpu_seconds)
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 2), "unit": "solves/s", "n_gpus": world,
@@ -591,7 +645,10 @@ def run_ours(args):
                           "reached_stop_level": f"{sum(conv_b)}/{len(conv_b)}", "problems": len(probs),
                           "l2": "flushed (256 MB write) between timed steps",
                           "form": f"batched: {B} problems per CUDA-graph launch (one step = one batch)",
-                          "launch": "cuda graph (one branch per problem, device-side WHILE loops)"},
+                          "launch": ("direct launches" if args.direct else "cuda graph") +
+                                    (f" (lock-step groups of up to {args.group_max} problems)"
+                                     if args.group_max > 1 else
+                                     " (one branch per problem, device-side WHILE loops)")},
                "forms": {"batched_fp32": {"value": round(value, 2), "ms_per_batch": round(ms_max, 4),
                                           "batch": B},
                          "plain_fp32": {"value": round(plain_value, 2), "ms_per_solve": round(plain_max, 4),
@@ -604,11 +661,12 @@ def run_ours(args):
                                               "method": "sketched Golub-Kahan (Algorithm 4)"},
                          "warm_start_fp32": ws_form},
                "e2e": {"value": round(e2e_val, 2), "unit": "solves/s",
-                       # per problem: C and X, plus the 512-byte descriptor and 2560-byte info
-                       # record slots of the batch call
-                       "h2d_bytes_per_step": (4 * n + 512) * B, "d2h_bytes_per_step": (4 * n + 2560) * B},
+                       # per problem: C and X, plus the 328-byte descriptor and the 2368-byte
+                       # info record of the batch call
+                       "h2d_bytes_per_step": (4 * n + 328) * B, "d2h_bytes_per_step": (4 * n + 2368) * B},
                "gpu_launches": launches,
-               "roofline": roof, "kernels": phases, "cpu_baseline": cpu, "clocks": clk.summary()}
+               "roofline": roof, "kernels": phases_b, "roofline_plain": roof_plain, "kernels_plain": phases,
+               "cpu_baseline": cpu, "clocks": clk.summary()}
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

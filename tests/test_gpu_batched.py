@@ -72,10 +72,10 @@ def test_batched_equals_single_solves_uneven_sizes(h):
     probs[3]["tol"] = 0.0             # and one runs all m steps
     grid = w.mu_grid()
     Xs, res = h.gmres_solve_batched(probs, mu_grid=grid)
-    for q, X, r in zip(probs, Xs, res):
+    for i, (q, X, r) in enumerate(zip(probs, Xs, res)):
         Xr, rr = _single(h, q, mu_grid=grid)
         assert r.iters == rr.iters and r.converged == rr.converged and r.device_status == 0
-        assert np.array_equal(r.rho, rr.rho)
+        assert np.array_equal(r.rho, rr.rho), (i, tuple(q["C"].shape), r.rho - rr.rho)
         assert r.mu == rr.mu
         assert np.array_equal(X.cpu().numpy(), Xr.cpu().numpy())
     # replay with new data on the same shapes: still equal to single solves
