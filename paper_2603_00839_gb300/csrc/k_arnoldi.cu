@@ -429,8 +429,8 @@ __global__ void k_update_bf16(Work w0, StepOpts o0) {
 // runs at HBM bandwidth however many basis tensors it reads.  Each thread
 // keeps eight elements; the subtraction order (W, then V_0, V_1, ...)
 // equals the register kernel's, so the results are the same bit for bit.
-// The chunk CTAs also form Q_{j+1} (as in k_update, FP64 accumulation); the
-// last CTA runs givens_step.
+// The next qblocks CTAs form Q_{j+1} (as in k_update), the last one runs
+// givens_step.
 constexpr int UP_CE = 2048;
 constexpr int UP_THREADS = 256;
 
@@ -463,6 +463,19 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_ring(Work w0, StepOpts o0
     hs[i] = static_cast<float>(h);
     hd[i] = h;
   }
+  if (static_cast<int>(blockIdx.x) >= nchunks) {   // Q_{j+1}, accumulated in FP64
+    __syncthreads();
+    float* Q = static_cast<float*>(w.Q);
+    const float* S = static_cast<const float*>(w.S);
+    const int64_t e = static_cast<int64_t>(blockIdx.x - nchunks) * blockDim.x + threadIdx.x;
+    if (e < w.d) {
+      const double invd = 1.0 / ctl->hnext;
+      double v = static_cast<double>(S[e]);
+      for (int i = 0; i < jj; ++i) v -= hd[i] * static_cast<double>(Q[static_cast<int64_t>(i) * w.d + e]);
+      Q[static_cast<int64_t>(jj) * w.d + e] = static_cast<float>(v * invd);
+    }
+    return;
+  }
   extern __shared__ __align__(128) unsigned char smem[];
   TV* ring = reinterpret_cast<TV*>(smem);   // [STAGES][UP_CE]
   const int64_t n = w.n;
@@ -481,21 +494,12 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_ring(Work w0, StepOpts o0
     }
   }
   __syncthreads();
-  // Q_{j+1} = (S - Q h) / h_{j+1,j} in FP64 rides along: this CTA's first
-  // sketch entry, its terms added one per streamed tensor (their loads and
-  // FP64 latency hide behind the ring's waits); further entries, if the
-  // sketch is larger than 256 per chunk, follow the loop
-  const float* Qm = static_cast<const float*>(w.Q);
-  const int64_t eq = static_cast<int64_t>(blockIdx.x) * UP_THREADS + threadIdx.x;
-  const bool has_q = eq < w.d;
-  double qv = has_q ? static_cast<double>(static_cast<const float*>(w.S)[eq]) : 0.0;
   // eight consecutive elements per thread
   const int e0 = threadIdx.x * 8;
   float acc[8];
   bool ok = true;
   int t = 0;
   for (; t < nt; ++t) {
-    if (has_q && t > 0) qv -= hd[t - 1] * static_cast<double>(Qm[static_cast<int64_t>(t - 1) * w.d + eq]);
     const int sl = t % STAGES;
     if (tc_wait_failed(&full[sl], static_cast<uint32_t>((t / STAGES) & 1), &ctl->status)) {
       ok = false;
@@ -531,15 +535,6 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_ring(Work w0, StepOpts o0
       for (int u = t + 1; u < nt && u < t + STAGES; ++u)
         mbar_wait(&full[u % STAGES], static_cast<uint32_t>((u / STAGES) & 1));
     return;
-  }
-  const double invd = 1.0 / ctl->hnext;
-  float* Qo = static_cast<float*>(w.Q) + static_cast<int64_t>(jj) * w.d;
-  if (has_q) Qo[eq] = static_cast<float>(qv * invd);
-  for (int64_t e = eq + static_cast<int64_t>(nchunks) * UP_THREADS; e < w.d;
-       e += static_cast<int64_t>(nchunks) * UP_THREADS) {
-    double v = static_cast<double>(static_cast<const float*>(w.S)[e]);
-    for (int i = 0; i < jj; ++i) v -= hd[i] * static_cast<double>(Qm[static_cast<int64_t>(i) * w.d + e]);
-    Qo[e] = static_cast<float>(v * invd);
   }
   if (e0 >= ce) return;
   const float fi = static_cast<float>(1.0 / ctl->hnext);
@@ -589,7 +584,8 @@ static cudaError_t launch_update_ring(const Work& w, const StepOpts& o, cudaStre
   cudaError_t e = set_smem(k_update_ring<TV, STAGES>, sm);
   if (e != cudaSuccess) return e;
   const int nchunks = static_cast<int>((w.n + UP_CE - 1) / UP_CE);
-  const dim3 grid(static_cast<unsigned>(nchunks + 1), 1, static_cast<unsigned>(w.b.n));
+  const int qblocks = static_cast<int>((w.d + UP_THREADS - 1) / UP_THREADS);
+  const dim3 grid(static_cast<unsigned>(nchunks + qblocks + 1), 1, static_cast<unsigned>(w.b.n));
   k_update_ring<TV, STAGES><<<grid, UP_THREADS, sm, s>>>(w, o, nchunks);
   return cudaGetLastError();
 }
