@@ -423,19 +423,24 @@ __global__ void k_update_bf16(Work w0, StepOpts o0) {
 
 // Basis update streamed through shared memory (FP32 or BF16 storage, FP32
 // arithmetic): V_{j+1} = (W - sum_i h_i V_i) / h_{j+1,j}.  The tensor is cut
-// into chunks of UP_CE elements, one CTA each; a CTA streams W and V_0 ..
-// V_{j-1} of its chunk through a ring of UP_STAGES slots filled by bulk
-// asynchronous copies, so about 64 KB per CTA are in flight and the kernel
-// runs at HBM bandwidth however many basis tensors it reads.  Each thread
-// keeps eight elements; the subtraction order (W, then V_0, V_1, ...)
-// equals the register kernel's, so the results are the same bit for bit.
-// The next qblocks CTAs form Q_{j+1} (as in k_update), the last one runs
-// givens_step.
-constexpr int UP_CE = 2048;
+// into chunks of 16 KB, one CTA each; a CTA streams W and V_0 .. V_{j-1} of
+// its chunk through a ring of UP_STAGES slots filled by bulk asynchronous
+// copies, so 64 KB per CTA are in flight and the kernel runs at HBM
+// bandwidth however many basis tensors it reads.  Each thread keeps 16 (FP32)
+// or 32 (BF16) elements in 16-byte groups; the subtraction order (W, then
+// V_0, V_1, ...) equals the register kernel's, so the results are the same
+// bit for bit.  The next CTAs form Q_{j+1} (as in k_update), the last one
+// runs givens_step.  At 512 x 512 x 3 the grid is one wave (192 chunk CTAs,
+// 192 column CTAs, three CTAs per SM).
+constexpr int UP_SLOT = 16384;   // bytes of one ring slot
+constexpr int UP_STAGES = 4;
 constexpr int UP_THREADS = 256;
 
-template <typename TV, int STAGES>
+template <typename TV>
 __global__ void __launch_bounds__(UP_THREADS) k_update_ring(Work w0, StepOpts o0, int nchunks) {
+  constexpr int CE = UP_SLOT / static_cast<int>(sizeof(TV));   // elements of a chunk
+  constexpr int VEC = 16 / static_cast<int>(sizeof(TV));       // elements per 16-byte group
+  constexpr int NV = CE / VEC / UP_THREADS;                     // groups per thread
   const int64_t bo = bidx(w0.b).off;
   const Work w = w0.at(bo);
   const StepOpts o = o0.at(bo);
@@ -456,7 +461,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_ring(Work w0, StepOpts o0
   }
   __shared__ float hs[kMaxK + 1];
   __shared__ double hd[kMaxK + 1];
-  __shared__ __align__(8) uint64_t full[STAGES];
+  __shared__ __align__(8) uint64_t full[UP_STAGES];
   const int ld = w.m + 1;
   for (int i = threadIdx.x; i < jj; i += blockDim.x) {
     const double h = w.H[static_cast<int64_t>(ld) * (jj - 1) + i];
@@ -468,84 +473,96 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_ring(Work w0, StepOpts o0
     float* Q = static_cast<float*>(w.Q);
     const float* S = static_cast<const float*>(w.S);
     const int64_t e = static_cast<int64_t>(blockIdx.x - nchunks) * blockDim.x + threadIdx.x;
-    if (e < w.d) {
-      const double invd = 1.0 / ctl->hnext;
-      double v = static_cast<double>(S[e]);
-      for (int i = 0; i < jj; ++i) v -= hd[i] * static_cast<double>(Q[static_cast<int64_t>(i) * w.d + e]);
-      Q[static_cast<int64_t>(jj) * w.d + e] = static_cast<float>(v * invd);
+    if (e >= w.d) return;
+    const double invd = 1.0 / ctl->hnext;
+    double v = static_cast<double>(S[e]);
+    int i = 0;
+    for (; i + 8 <= jj; i += 8) {   // eight loads in flight, then the FP64 chain in order
+      float q8[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) q8[u] = Q[static_cast<int64_t>(i + u) * w.d + e];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v -= hd[i + u] * static_cast<double>(q8[u]);
     }
+    for (; i < jj; ++i) v -= hd[i] * static_cast<double>(Q[static_cast<int64_t>(i) * w.d + e]);
+    Q[static_cast<int64_t>(jj) * w.d + e] = static_cast<float>(v * invd);
     return;
   }
   extern __shared__ __align__(128) unsigned char smem[];
-  TV* ring = reinterpret_cast<TV*>(smem);   // [STAGES][UP_CE]
+  TV* ring = reinterpret_cast<TV*>(smem);   // [UP_STAGES][CE]
   const int64_t n = w.n;
-  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * UP_CE;
-  const int ce = static_cast<int>(n - c0 < UP_CE ? n - c0 : UP_CE);   // a multiple of 8
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * CE;
+  const int ce = static_cast<int>(n - c0 < CE ? n - c0 : CE);   // a multiple of 8
   const uint32_t bytes = static_cast<uint32_t>(ce) * sizeof(TV);
   const TV* W = static_cast<const TV*>(w.W) + c0;
   const TV* V = static_cast<const TV*>(w.V) + c0;
   const int nt = jj + 1;   // W, then V_0 .. V_{jj-1}
   auto src = [&](int t) { return t == 0 ? W : V + static_cast<int64_t>(t - 1) * n; };
   if (threadIdx.x == 0) {
-    for (int k = 0; k < STAGES; ++k) mbar_init(&full[k]);
-    for (int t = 0; t < STAGES && t < nt; ++t) {
+    for (int k = 0; k < UP_STAGES; ++k) mbar_init(&full[k]);
+    for (int t = 0; t < UP_STAGES && t < nt; ++t) {
       mbar_expect(&full[t], bytes);
-      bulk_g2s(ring + static_cast<size_t>(t) * UP_CE, src(t), bytes, &full[t]);
+      bulk_g2s(ring + static_cast<size_t>(t) * CE, src(t), bytes, &full[t]);
     }
   }
   __syncthreads();
-  // eight consecutive elements per thread
-  const int e0 = threadIdx.x * 8;
-  float acc[8];
+  // group k of this thread: elements (threadIdx.x + k * UP_THREADS) * VEC ..
+  float acc[NV][VEC];
   bool ok = true;
   int t = 0;
   for (; t < nt; ++t) {
-    const int sl = t % STAGES;
-    if (tc_wait_failed(&full[sl], static_cast<uint32_t>((t / STAGES) & 1), &ctl->status)) {
+    const int sl = t % UP_STAGES;
+    if (tc_wait_failed(&full[sl], static_cast<uint32_t>((t / UP_STAGES) & 1), &ctl->status)) {
       ok = false;
       break;
     }
-    float v[8];
-    const TV* slot = ring + static_cast<size_t>(sl) * UP_CE + e0;
-    if constexpr (sizeof(TV) == 4) {
-      const float4 a = reinterpret_cast<const float4*>(slot)[0], b = reinterpret_cast<const float4*>(slot)[1];
-      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    } else {
-      bf8_to_f(*reinterpret_cast<const uint4*>(slot), v);
-    }
-    if (t == 0) {
+    const uint4* slot = reinterpret_cast<const uint4*>(ring + static_cast<size_t>(sl) * CE);
+    const float h0 = t > 0 ? hs[t - 1] : 0.f;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) acc[k] = v[k];
-    } else {
-      const float h0 = hs[t - 1];
+    for (int k = 0; k < NV; ++k) {
+      const uint4 q = slot[threadIdx.x + k * UP_THREADS];
+      float v[VEC];
+      if constexpr (sizeof(TV) == 4) {
+        v[0] = __uint_as_float(q.x); v[1] = __uint_as_float(q.y); v[2] = __uint_as_float(q.z); v[3] = __uint_as_float(q.w);
+      } else {
+        bf8_to_f(q, v);
+      }
+      if (t == 0) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if constexpr (sizeof(TV) == 4) acc[k] -= h0 * v[k];
-        else acc[k] = fmaf(-h0, v[k], acc[k]);
+        for (int u = 0; u < VEC; ++u) acc[k][u] = v[u];
+      } else {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+          if constexpr (sizeof(TV) == 4) acc[k][u] -= h0 * v[u];
+          else acc[k][u] = fmaf(-h0, v[u], acc[k][u]);
+        }
       }
     }
     __syncthreads();   // every thread is done with slot sl
-    if (threadIdx.x == 0 && t + STAGES < nt) {
+    if (threadIdx.x == 0 && t + UP_STAGES < nt) {
       mbar_expect(&full[sl], bytes);
-      bulk_g2s(ring + static_cast<size_t>(sl) * UP_CE, src(t + STAGES), bytes, &full[sl]);
+      bulk_g2s(ring + static_cast<size_t>(sl) * CE, src(t + UP_STAGES), bytes, &full[sl]);
     }
   }
   if (!ok) {   // a copy timed out: wait (bounded) for the others in flight, write nothing
     if (threadIdx.x == 0)
-      for (int u = t + 1; u < nt && u < t + STAGES; ++u)
-        mbar_wait(&full[u % STAGES], static_cast<uint32_t>((u / STAGES) & 1));
+      for (int u = t + 1; u < nt && u < t + UP_STAGES; ++u)
+        mbar_wait(&full[u % UP_STAGES], static_cast<uint32_t>((u / UP_STAGES) & 1));
     return;
   }
-  if (e0 >= ce) return;
   const float fi = static_cast<float>(1.0 / ctl->hnext);
+  TV* out = static_cast<TV*>(w.V) + static_cast<int64_t>(jj) * n + c0;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) acc[k] *= fi;
-  TV* out = static_cast<TV*>(w.V) + static_cast<int64_t>(jj) * n + c0 + e0;
-  if constexpr (sizeof(TV) == 4) {
-    reinterpret_cast<float4*>(out)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    reinterpret_cast<float4*>(out)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-  } else {
-    *reinterpret_cast<uint4*>(out) = f_to_bf8(acc);
+  for (int k = 0; k < NV; ++k) {
+    const int e0 = (threadIdx.x + k * UP_THREADS) * VEC;
+    if (e0 >= ce) break;
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) acc[k][u] *= fi;
+    if constexpr (sizeof(TV) == 4) {
+      *reinterpret_cast<float4*>(out + e0) = make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+    } else {
+      *reinterpret_cast<uint4*>(out + e0) = f_to_bf8(acc[k]);
+    }
   }
 }
 
@@ -578,23 +595,23 @@ cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s) {
 
 
 
-template <typename TV, int STAGES>
+template <typename TV>
 static cudaError_t launch_update_ring(const Work& w, const StepOpts& o, cudaStream_t s) {
-  constexpr size_t sm = size_t(STAGES) * UP_CE * sizeof(TV);
-  cudaError_t e = set_smem(k_update_ring<TV, STAGES>, sm);
+  constexpr size_t sm = size_t(UP_STAGES) * UP_SLOT;
+  cudaError_t e = set_smem(k_update_ring<TV>, sm);
   if (e != cudaSuccess) return e;
-  const int nchunks = static_cast<int>((w.n + UP_CE - 1) / UP_CE);
+  constexpr int64_t CE = UP_SLOT / sizeof(TV);
+  const int nchunks = static_cast<int>((w.n + CE - 1) / CE);
   const int qblocks = static_cast<int>((w.d + UP_THREADS - 1) / UP_THREADS);
   const dim3 grid(static_cast<unsigned>(nchunks + qblocks + 1), 1, static_cast<unsigned>(w.b.n));
-  k_update_ring<TV, STAGES><<<grid, UP_THREADS, sm, s>>>(w, o, nchunks);
+  k_update_ring<TV><<<grid, UP_THREADS, sm, s>>>(w, o, nchunks);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s) {
   // FP32 solves with whole 8-element groups stream the basis through shared memory
-  if (w.dtype == RTG_F32 && w.n % 8 == 0 && w.n / UP_CE < (int64_t(1) << 30))
-    return w.vdtype == RTG_BF16 ? launch_update_ring<__nv_bfloat16, 16>(w, o, s)
-                                : launch_update_ring<float, 8>(w, o, s);
+  if (w.dtype == RTG_F32 && w.n % 8 == 0 && w.n / 4096 < (int64_t(1) << 30))
+    return w.vdtype == RTG_BF16 ? launch_update_ring<__nv_bfloat16>(w, o, s) : launch_update_ring<float>(w, o, s);
   // one block more than the update needs: it runs the Givens step
   const unsigned nb = static_cast<unsigned>(w.b.n);
   if (w.vdtype == RTG_BF16) k_update_bf16<<<dim3(ew_grid(w.n / 8 + 1) + 1, 1, nb), 256, 0, s>>>(w, o);
