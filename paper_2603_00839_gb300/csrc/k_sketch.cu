@@ -32,7 +32,7 @@ namespace rtg {
 constexpr int TC_THREADS = 256;   // 8 warps split K
 constexpr int F_COLS = 16;        // first stage: columns of X per CTA
 constexpr int F_MT = 4;           // first stage: m16 tiles (64 Theta rows) per CTA
-constexpr int N_NT = 2;           // later stages: n8 tiles (16 Theta rows) per CTA
+constexpr int N_NT = 4;           // later stages: n8 tiles (32 Theta rows) per CTA
 constexpr int XA = 20;            // blocked row: 16 values of l + 4 pad (conflict-free A loads)
 
 // ------------------------------------------------------------------ plan
@@ -496,7 +496,7 @@ constexpr size_t inner_smem() {
 }
 
 // Later contraction (L > 1): out(l, q, r) = scale * sum_i X(l, i, r) Theta(q, i).
-// CTA: 16 values of l x 16 values of q for one r.  Input blocked for this
+// CTA: 16 values of l x 8 N_NT values of q for one r.  Input blocked for this
 // stage (one bulk copy of I rows x 20 floats per K chunk) or natural
 // (plain loads).  Warp w takes the K tiles w, w+8, ...  With dots_pass >= 0
 // the CTA then runs that Gram-Schmidt pass on its final tile.
