@@ -311,7 +311,8 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool val
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-constexpr int F_RED = 17;         // padded row of the first stage's cross-warp reduction
+constexpr int F_NT = F_COLS / 8;  // first stage: n8 tiles per CTA
+constexpr int F_RED = F_COLS + 1; // padded row of the first stage's cross-warp reduction
 
 template <int CH>
 constexpr size_t first_smem() {
@@ -381,11 +382,11 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
   const bool bulk = (I % EV == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
   if (tid == 0) mbar_init(&bar);
   __syncthreads();
-  float acc[F_MT][2][4];
+  float acc[F_MT][F_NT][4];
 #pragma unroll
   for (int a = 0; a < F_MT; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < F_NT; ++b)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
   bool ok = true;
@@ -419,9 +420,9 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
     phase ^= 1u;
     {
       for (int kk = warp; kk < nk; kk += 8) {
-        uint32_t B[2][2][3];
+        uint32_t B[F_NT][2][3];
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
+        for (int nt = 0; nt < F_NT; ++nt)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const TI* xp = &xs[(nt * 8 + gid) * XS + kk * 16 + tig * 2 + h * 8];
@@ -447,7 +448,7 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
 #pragma unroll
           for (int mt = 0; mt < F_MT; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt) mma_bf16(acc[mt][nt], A[mt], B[nt][0][l], B[nt][1][l]);
+            for (int nt = 0; nt < F_NT; ++nt) mma_bf16(acc[mt][nt], A[mt], B[nt][0][l], B[nt][1][l]);
       }
     }
     __syncthreads();
@@ -456,7 +457,7 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
 #pragma unroll
     for (int a = 0; a < F_MT; ++a)
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < F_NT; ++b)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
   }
@@ -466,7 +467,7 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
 #pragma unroll
   for (int mt = 0; mt < F_MT; ++mt)
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
+    for (int nt = 0; nt < F_NT; ++nt)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int row = mt * 16 + gid + h * 8, col = nt * 8 + tig * 2;
