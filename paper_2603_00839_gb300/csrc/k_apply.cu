@@ -27,7 +27,19 @@ struct FusedArgs {
   double t1[kMaxTaps], t2[kMaxTaps];
   double M[kMaxMix * kMaxMix]; // M[p + nc*c]
   double alpha, beta;
+  // the same, rounded to FP32 on the host: an FP64-to-FP32 conversion runs on
+  // this GPU's FP64 pipe (two lanes per SM per cycle), and converting the
+  // taps and the mix in every thread made the FP32 kernels FP64-bound
+  float t1f[kMaxTaps], t2f[kMaxTaps];
+  float Mf[kMaxMix * kMaxMix];
+  float alphaf, betaf;
 };
+// An argument in the kernel's arithmetic type.
+template <typename T>
+__device__ __forceinline__ T argT(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return d;
+}
 
 template <typename T, int NC>
 __global__ void __launch_bounds__(FTHREADS)
@@ -47,8 +59,8 @@ k_apply_fused(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Bat
   const int Ht = FTY + 2 * a.r2;
   T* in_s = reinterpret_cast<T*>(smem_raw);
   T* tmp = in_s + Ht * Wd;
-  for (int t = threadIdx.x; t <= 2 * a.r1; t += FTHREADS) t1s[t] = static_cast<T>(a.t1[t]);
-  for (int t = threadIdx.x; t <= 2 * a.r2; t += FTHREADS) t2s[t] = static_cast<T>(a.t2[t]);
+  for (int t = threadIdx.x; t <= 2 * a.r1; t += FTHREADS) t1s[t] = argT<T>(a.t1[t], a.t1f[t]);
+  for (int t = threadIdx.x; t <= 2 * a.r2; t += FTHREADS) t2s[t] = argT<T>(a.t2[t], a.t2f[t]);
 
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * FTX;
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * FTY;
@@ -94,10 +106,10 @@ k_apply_fused(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Bat
       for (int p = 0; p < NC; ++p) {
         T v = 0;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) v += static_cast<T>(a.M[p + NC * c]) * acc[c][k];
+        for (int c = 0; c < NC; ++c) v += argT<T>(a.M[p + NC * c], a.Mf[p + NC * c]) * acc[c][k];
         const int64_t o = (slab * NC + p) * plane + gy * a.I1 + gx;
-        T out = static_cast<T>(a.alpha) * v;
-        if (Z != nullptr) out += static_cast<T>(a.beta) * Z[o];
+        T out = argT<T>(a.alpha, a.alphaf) * v;
+        if (Z != nullptr) out += argT<T>(a.beta, a.betaf) * Z[o];
         Y[o] = out;
       }
     }
@@ -159,8 +171,8 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
     const int u1 = t - (RR - a.r1), u2 = t - (RR - a.r2);
-    t1[t] = (u1 >= 0 && u1 <= 2 * a.r1) ? static_cast<T>(a.t1[u1]) : static_cast<T>(0);
-    t2[t] = (u2 >= 0 && u2 <= 2 * a.r2) ? static_cast<T>(a.t2[u2]) : static_cast<T>(0);
+    t1[t] = (u1 >= 0 && u1 <= 2 * a.r1) ? argT<T>(a.t1[u1], a.t1f[u1]) : static_cast<T>(0);
+    t2[t] = (u2 >= 0 && u2 <= 2 * a.r2) ? argT<T>(a.t2[u2], a.t2f[u2]) : static_cast<T>(0);
   }
   const int x0 = blockIdx.x * RTX;
   const int y0 = blockIdx.y * RTY;
@@ -260,10 +272,10 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
         for (int p = 0; p < NC; ++p) {
           T v = 0;
 #pragma unroll
-          for (int c = 0; c < NC; ++c) v += static_cast<T>(a.M[p + NC * c]) * acc[c][o];
+          for (int c = 0; c < NC; ++c) v += argT<T>(a.M[p + NC * c], a.Mf[p + NC * c]) * acc[c][o];
           const int64_t idx = (slab * NC + p) * plane + static_cast<int64_t>(gy) * I1 + gx;
-          T out = static_cast<T>(a.alpha) * v;
-          if (Z != nullptr) out += static_cast<T>(a.beta) * Z[idx];
+          T out = argT<T>(a.alpha, a.alphaf) * v;
+          if (Z != nullptr) out += argT<T>(a.beta, a.betaf) * Z[idx];
           Y[idx] = out;
         }
       }
@@ -510,6 +522,7 @@ static int reg_bucket(int r) {
 
 struct TapArgs {
   double t[kMaxTaps];
+  float tf[kMaxTaps];   // rounded to FP32 on the host (see FusedArgs)
 };
 
 // out(l, i, r) = sum_t taps[r+t] X(l, i+t, r), zero outside [0, I)
@@ -532,7 +545,7 @@ __global__ void k_pass_band(PtrRef Xr, PtrRef Yr, int64_t L, int64_t I, int64_t 
     T s = 0;
     for (int t = -rad; t <= rad; ++t) {
       const int64_t ii = i + t;
-      if (ii >= 0 && ii < I) s += static_cast<T>(taps.t[rad + t]) * X[l + L * (ii + I * r)];
+      if (ii >= 0 && ii < I) s += argT<T>(taps.t[rad + t], taps.tf[rad + t]) * X[l + L * (ii + I * r)];
     }
     Y[o] = s;
   }
@@ -574,10 +587,11 @@ __global__ void k_axpby(PtrRef Ar, PtrRef Yr, PtrRef Zr, double alpha, double be
   const T* A = Ar.get<const T>();
   T* Y = Yr.get<T>();
   const T* Z = Zr.get<const T>();
+  const T al = static_cast<T>(alpha), be = static_cast<T>(beta);   // once per thread
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
        o += (int64_t)gridDim.x * blockDim.x) {
-    T v = static_cast<T>(alpha) * A[o];
-    if (Z != nullptr) v += static_cast<T>(beta) * Z[o];
+    T v = al * A[o];
+    if (Z != nullptr) v += be * Z[o];
     Y[o] = v;
   }
 }
@@ -634,6 +648,12 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
     for (int t = 0; t <= 2 * op.r2; ++t) a.t2[t] = op.t2[t];
     a.alpha = alpha;
     a.beta = has_ptr(Z) ? beta : 0.0;
+    for (int t = 0; t < kMaxTaps; ++t) {
+      a.t1f[t] = static_cast<float>(a.t1[t]);
+      a.t2f[t] = static_cast<float>(a.t2[t]);
+    }
+    a.alphaf = static_cast<float>(a.alpha);
+    a.betaf = static_cast<float>(a.beta);
     if (op.mix > 0) {
       a.nc = op.mix;
       a.nslab = rest;
@@ -643,6 +663,7 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
       a.nslab = I3 * rest;
       a.M[0] = 1.0;
     }
+    for (int i = 0; i < kMaxMix * kMaxMix; ++i) a.Mf[i] = static_cast<float>(a.M[i]);
     const int rr = reg_bucket(op.r1 > op.r2 ? op.r1 : op.r2);
     const bool fits = a.I1 < (int64_t(1) << 30) && a.I2 < (int64_t(1) << 30) &&
                       (sizeof(T) == 8 || (a.I1 % 4) == 0);
@@ -700,7 +721,10 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
     const int64_t I = op.dims[ps.mode];
     if (ps.kind == PK_BAND) {
       TapArgs ta{};
-      for (int t = 0; t <= 2 * ps.radius; ++t) ta.t[t] = ps.taps[t];
+      for (int t = 0; t <= 2 * ps.radius; ++t) {
+        ta.t[t] = ps.taps[t];
+        ta.tf[t] = static_cast<float>(ps.taps[t]);
+      }
       k_pass_band<T><<<dim3(grid_for(n, 256), 1, b.n), 256, 0, s>>>(src, dst, L, I, R, ps.radius, ta, stop, b);
     } else {
       k_pass_dense<T><<<dim3(grid_for(n, 256), 1, b.n), 256, 0, s>>>(src, dst, L, I, R, ps.dense, stop, b);

@@ -32,7 +32,7 @@ namespace rtg {
 constexpr int TC_THREADS = 256;   // 8 warps split K
 constexpr int F_COLS = 16;        // first stage: columns of X per CTA
 constexpr int F_MT = 4;           // first stage: m16 tiles (64 Theta rows) per CTA
-constexpr int N_NT = 4;           // later stages: n8 tiles (32 Theta rows) per CTA
+constexpr int N_NT = 2;           // later stages: n8 tiles (16 Theta rows) per CTA
 constexpr int XA = 20;            // blocked row: 16 values of l + 4 pad (conflict-free A loads)
 
 // ------------------------------------------------------------------ plan
@@ -557,8 +557,8 @@ k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int
       if (k < rows && bulk_in) continue;
       float v = 0.f;
       if (k < rows) {
-        if (in_blocked) v = X[((r * ltiles + lt) * I + i0 + k) * XA + ll];
-        else if (l0 + ll < L) v = X[l0 + ll + L * (i0 + k) + L * I * r];
+        if (in_blocked) v = __ldcg(&X[((r * ltiles + lt) * I + i0 + k) * XA + ll]);
+        else if (l0 + ll < L) v = __ldcg(&X[l0 + ll + L * (i0 + k) + L * I * r]);
       }
       xa[k * XA + ll] = v;
     }
