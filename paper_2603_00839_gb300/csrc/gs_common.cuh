@@ -5,6 +5,8 @@
 // epilogue of each pass (Section 4.3; the Block GMRES algorithm's steps).
 #pragma once
 
+#include <type_traits>
+
 #include "rtg_internal.cuh"
 
 namespace rtg {
@@ -133,11 +135,23 @@ __device__ __forceinline__ double warps_total(const double (*red)[kRedCols], int
   return acc;
 }
 
+// Sum of the per-warp float-float values of one column in a fixed order.
+__device__ __forceinline__ FF ff_warps_total(const FF (*red)[kRedCols], int nw, int i) {
+  if (nw == 8)
+    return ff_add(ff_add(ff_add(red[0][i], red[1][i]), ff_add(red[2][i], red[3][i])),
+                  ff_add(ff_add(red[4][i], red[5][i]), ff_add(red[6][i], red[7][i])));
+  FF acc{0.f, 0.f};
+  for (int u = 0; u < nw; ++u) acc = ff_add(acc, red[u][i]);
+  return acc;
+}
+
 // Per-block partial sums of the columns above: products of the stored
 // values accumulated in double-float (FP32 data) or FP64 (FP64 data).
 // Each thread passes up to ITEMS entries (vals at sketch indices idx);
 // entries past cnt or with a negative index are ignored.  Writes row
-// (linear block id) of w.part.  red: shared [GS_MAXW][kRedCols].
+// (linear block id) of w.part: float-float pairs for FP32 data (summed by
+// last_block_combine<true> on the FP32 pipe), doubles for FP64 data.
+// red: shared [GS_MAXW][kRedCols] doubles (float-float pairs for FP32).
 template <typename T, int ITEMS>
 __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx, int cnt, int J,
                                double (*red)[kRedCols]) {
@@ -153,12 +167,18 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
     sv[k] = ok ? vals[k] : static_cast<T>(0);
     qJ[k] = (ok && J >= 0) ? Q[static_cast<int64_t>(J) * d + idx[k]] : static_cast<T>(0);
   }
+  FF (*rf)[kRedCols] = reinterpret_cast<FF (*)[kRedCols]>(red);
   {   // s . s
     DotAcc<T> a;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) a.add(sv[k], sv[k]);
-    const double t = a.warp_total();
-    if (lane == 0) red[warp][J + 1] = t;
+    if constexpr (sizeof(T) == 4) {
+      const FF t = ff_warp_sum(a.v);
+      if (lane == 0) rf[warp][J + 1] = t;
+    } else {
+      const double t = a.warp_total();
+      if (lane == 0) red[warp][J + 1] = t;
+    }
   }
   if constexpr (sizeof(T) == 4) {
     // 16 columns of Q at a time: s . Q_i and Q_J . Q_i for each, 32 values
@@ -186,7 +206,7 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
       }
       ff_reduce_scatter32(v);
       const int g = lane & 15;
-      if (i0 + g <= J) red[warp][lane < 16 ? i0 + g : J + 2 + i0 + g] = ff_to_double(v[0]);
+      if (i0 + g <= J) rf[warp][lane < 16 ? i0 + g : J + 2 + i0 + g] = v[0];
     }
   } else {
     // columns of Q in groups of 8: all loads of a group go out before any use
@@ -219,18 +239,27 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
   }
   __syncthreads();
   const int rowlen = 2 * w.m + 4;
-  for (int i = threadIdx.x; i < ncols; i += blockDim.x)
-    w.part[static_cast<int64_t>(blockIdx.x + gridDim.x * blockIdx.y) * rowlen + i] = warps_total(red, nw, i);
+  const int64_t row = static_cast<int64_t>(blockIdx.x + gridDim.x * blockIdx.y) * rowlen;
+  for (int i = threadIdx.x; i < ncols; i += blockDim.x) {
+    if constexpr (sizeof(T) == 4) reinterpret_cast<FF*>(w.part)[row + i] = ff_warps_total(rf, nw, i);
+    else w.part[row + i] = warps_total(red, nw, i);
+  }
 }
 
 // Ticket: returns true in every thread of the last block to finish, after
 // tot[0..ncols) holds the sum of all blocks' rows.  Thread t takes column
 // t % nc and every G-th row starting at t / nc, sixteen rows per round of
-// loads, then one thread per column adds the G group sums (pairwise trees:
-// FP64 adds have a long dependent latency on this GPU).  The order is fixed, so the result is deterministic.
-// The counter wraps back to zero by itself.  scratch: >= blockDim doubles.
+// loads, then one thread per column adds the G group sums in a pairwise
+// tree.  FFROWS: the rows hold float-float pairs, summed with float-float
+// adds on the FP32 pipe (an FP64 add occupies its SM sub-partition's FP64
+// unit for about 64 cycles on this GPU; the pairs already carry the
+// partial sums' precision); else doubles.  The order is fixed, so the
+// result is deterministic.  The counter wraps back to zero by itself.
+// scratch: >= blockDim doubles.
+template <bool FFROWS>
 __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot, int* am_last,
                                           double* scratch) {
+  using V = typename std::conditional<FFROWS, FF, double>::type;
   __threadfence();
   __syncthreads();
   const unsigned nblk = gridDim.x * gridDim.y;
@@ -238,6 +267,20 @@ __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot,
   __syncthreads();
   if (!*am_last) return false;
   __threadfence();
+  auto add = [](V x, V y) -> V {
+    if constexpr (FFROWS) return ff_add(x, y);
+    else return x + y;
+  };
+  auto load = [](const V* q) -> V {
+    if constexpr (FFROWS) {
+      const float2 f = __ldcg(reinterpret_cast<const float2*>(q));
+      return FF{f.x, f.y};
+    } else {
+      return __ldcg(q);
+    }
+  };
+  const V zero{};
+  V* sc = reinterpret_cast<V*>(scratch);
   const int rowlen = 2 * w.m + 4;
   const int nt = blockDim.x;
   for (int c0 = 0; c0 < ncols; c0 += nt) {
@@ -250,33 +293,36 @@ __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot,
       // rows g, g + G, ...: sixteen loads in flight per round (one L2
       // round trip per sixteen rows), summed in a fixed tree
       constexpr int U = 16;
-      double acc = 0.0;
-      const double* p = w.part + c0 + c;
+      V acc = zero;
+      const V* p = reinterpret_cast<const V*>(w.part) + c0 + c;
       for (unsigned b = g; b < nblk; b += U * G) {
-        double v[U];
+        V v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const unsigned bb = b + u * G;
-          v[u] = bb < nblk ? __ldcg(p + static_cast<int64_t>(bb) * rowlen) : 0.0;
+          v[u] = bb < nblk ? load(p + static_cast<int64_t>(bb) * rowlen) : zero;
         }
 #pragma unroll
         for (int h = U / 2; h > 0; h >>= 1)
 #pragma unroll
-          for (int u = 0; u < h; ++u) v[u] += v[u + h];
-        acc += v[0];
+          for (int u = 0; u < h; ++u) v[u] = add(v[u], v[u + h]);
+        acc = add(acc, v[0]);
       }
-      scratch[g * nc + c] = acc;
+      sc[g * nc + c] = acc;
     }
     __syncthreads();
-    if (t < nc) {   // pairwise tree over the G group sums
-      double v[32];
+    if (t < nc) {   // pairwise tree over the G group sums (levels that would add only zeros skipped)
+      V v[32];
 #pragma unroll
-      for (int u = 0; u < 32; ++u) v[u] = u < G ? scratch[u * nc + t] : 0.0;
+      for (int u = 0; u < 32; ++u) v[u] = u < G ? sc[u * nc + t] : zero;
 #pragma unroll
       for (int h = 16; h > 0; h >>= 1)
+        if (h < G) {
 #pragma unroll
-        for (int u = 0; u < h; ++u) v[u] += v[u + h];
-      tot[c0 + t] = v[0];
+          for (int u = 0; u < h; ++u) v[u] = add(v[u], v[u + h]);
+        }
+      if constexpr (FFROWS) tot[c0 + t] = ff_to_double(v[0]);
+      else tot[c0 + t] = v[0];
     }
     __syncthreads();
   }
@@ -342,9 +388,19 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
     double* Gs = red + 4;              // n x n
     double* pr = Gs + n * lg;          // [nw][n] partial products
     double* ab = pr + nw * n;          // [2][2] the two warps' sums of a and b
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int i = e % n, k = e / n;
-      Gs[i * lg + k] = (i == J) ? grow[k] : (k == J ? grow[i] : G[i + static_cast<int64_t>(ld) * k]);
+    for (int e0 = 0; e0 < n * n; e0 += 8 * static_cast<int>(blockDim.x)) {   // eight loads in flight
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x + threadIdx.x;
+        const int i = e % n, k = e / n;
+        v[u] = (e >= n * n) ? 0.0 : (i == J) ? grow[k] : (k == J ? grow[i] : G[i + static_cast<int64_t>(ld) * k]);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x + threadIdx.x;
+        if (e < n * n) Gs[(e % n) * lg + e / n] = v[u];
+      }
     }
     for (int i = threadIdx.x; i <= J; i += blockDim.x) {   // new row/column, for later steps
       G[i + static_cast<int64_t>(ld) * J] = grow[i];
@@ -449,7 +505,7 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
     const bool finite = isfinite(s2) && isfinite(hh1) && isfinite(hgh) && !bad;
     const double hn2 = s2 - 2.0 * hh1 + hgh;
     const double hn = sqrt(hn2 > 0.0 ? hn2 : 0.0);
-    const bool breakdown = finite && (hn <= bd_tol * sqrt(s2));
+    const bool breakdown = finite && (hn <= (bd_tol == 0.0 ? 0.0 : bd_tol * sqrt(s2)));
     Hc[J + 1] = breakdown ? 0.0 : hn;
     ctl->pre2 = s2;
     ctl->hnext = hn;

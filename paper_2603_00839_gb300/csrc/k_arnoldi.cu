@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(Work w0, int pass, StepO
     }
   }
   block_partials<T, GS_ITEMS>(w, sv, ix, cnt, J, red);
-  if (!last_block_combine(w, gs_ncols(J), tot, &am_last, &red[0][0])) return;
+  if (!last_block_combine<sizeof(T) == 4>(w, gs_ncols(J), tot, &am_last, &red[0][0])) return;
   if (pass == 0) {
     if (threadIdx.x == 0) gs_finish_start(w, o, tot);
   } else {
@@ -459,33 +459,51 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_ring(Work w0, StepOpts o0
     }
     return;
   }
+  // h_{i,j} as FP32 (hs) and, for the sketched column, as float-float
+  // hs + hl; 1/h_{j+1,j} likewise, computed once per CTA (an FP64 division
+  // in every thread would load the slow FP64 pipe).
   __shared__ float hs[kMaxK + 1];
-  __shared__ double hd[kMaxK + 1];
+  __shared__ float hl[kMaxK + 1];
+  __shared__ float rinv[2];
   __shared__ __align__(8) uint64_t full[UP_STAGES];
   const int ld = w.m + 1;
+  const bool qcta = static_cast<int>(blockIdx.x) >= nchunks;
   for (int i = threadIdx.x; i < jj; i += blockDim.x) {
     const double h = w.H[static_cast<int64_t>(ld) * (jj - 1) + i];
-    hs[i] = static_cast<float>(h);
-    hd[i] = h;
+    const float f = static_cast<float>(h);
+    hs[i] = f;
+    if (qcta) hl[i] = static_cast<float>(h - static_cast<double>(f));
   }
-  if (static_cast<int>(blockIdx.x) >= nchunks) {   // Q_{j+1}, accumulated in FP64
+  if (threadIdx.x == blockDim.x - 1) {
+    const double r = 1.0 / ctl->hnext;
+    const float f = static_cast<float>(r);
+    rinv[0] = f;
+    rinv[1] = static_cast<float>(r - static_cast<double>(f));
+  }
+  if (qcta) {   // Q_{j+1} = (S - sum_i h_i Q_i) / h_{j+1,j}, accumulated in float-float
     __syncthreads();
     float* Q = static_cast<float*>(w.Q);
     const float* S = static_cast<const float*>(w.S);
     const int64_t e = static_cast<int64_t>(blockIdx.x - nchunks) * blockDim.x + threadIdx.x;
     if (e >= w.d) return;
-    const double invd = 1.0 / ctl->hnext;
-    double v = static_cast<double>(S[e]);
+    FF v{S[e], 0.f};
+    auto sub = [&](int i, float q) {   // v -= (hs_i + hl_i) q
+      const FF p = ff_prod(hs[i], q);
+      v = ff_add(v, FF{-p.hi, -__fmaf_rn(hl[i], q, p.lo)});
+    };
     int i = 0;
-    for (; i + 8 <= jj; i += 8) {   // eight loads in flight, then the FP64 chain in order
+    for (; i + 8 <= jj; i += 8) {   // eight loads in flight, then the chain in order
       float q8[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) q8[u] = Q[static_cast<int64_t>(i + u) * w.d + e];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v -= hd[i + u] * static_cast<double>(q8[u]);
+      for (int u = 0; u < 8; ++u) sub(i + u, q8[u]);
     }
-    for (; i < jj; ++i) v -= hd[i] * static_cast<double>(Q[static_cast<int64_t>(i) * w.d + e]);
-    Q[static_cast<int64_t>(jj) * w.d + e] = static_cast<float>(v * invd);
+    for (; i < jj; ++i) sub(i, Q[static_cast<int64_t>(i) * w.d + e]);
+    // (v.hi + v.lo)(r0 + r1), rounded once to FP32
+    const FF p = ff_prod(v.hi, rinv[0]);
+    const float lo = __fmaf_rn(v.hi, rinv[1], __fmaf_rn(v.lo, rinv[0], p.lo));
+    Q[static_cast<int64_t>(jj) * w.d + e] = __fadd_rn(p.hi, lo);
     return;
   }
   extern __shared__ __align__(128) unsigned char smem[];
@@ -550,7 +568,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_ring(Work w0, StepOpts o0
         mbar_wait(&full[u % UP_STAGES], static_cast<uint32_t>((u / UP_STAGES) & 1));
     return;
   }
-  const float fi = static_cast<float>(1.0 / ctl->hnext);
+  const float fi = rinv[0];
   TV* out = static_cast<TV*>(w.V) + static_cast<int64_t>(jj) * n + c0;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {

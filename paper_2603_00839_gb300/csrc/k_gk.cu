@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(GK_THREADS) k_gk_norm(Work w, int phase, StepO
   if (threadIdx.x < 2)
     w.part[static_cast<int64_t>(blockIdx.x) * rowlen + threadIdx.x] =
         warps_total(red, blockDim.x >> 5, threadIdx.x);
-  if (!last_block_combine(w, 2, tot, &am_last, &red[0][0])) return;
+  if (!last_block_combine<false>(w, 2, tot, &am_last, &red[0][0])) return;
   if (threadIdx.x != 0) return;
   const double nrm = sqrt(tot[0] > 0.0 ? tot[0] : 0.0);
   const double pre = sqrt(tot[1] > 0.0 ? tot[1] : 0.0);

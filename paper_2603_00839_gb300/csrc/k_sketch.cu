@@ -637,7 +637,7 @@ k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int
   double(*red2)[kRedCols] = reinterpret_cast<double(*)[kRedCols]>(smem);
   double* tot = reinterpret_cast<double*>(smem) + GS_MAXW * kRedCols;
   block_partials<float, ITEMS>(w, vals, ix, ITEMS, J, red2);
-  if (!last_block_combine(w, gs_ncols(J), tot, &am_last, &red2[0][0])) return;
+  if (!last_block_combine<true>(w, gs_ncols(J), tot, &am_last, &red2[0][0])) return;
   if (dots_pass == 0) {
     if (tid == 0) gs_finish_start(w, o, tot);
   } else {

@@ -16,36 +16,49 @@
 
 namespace rtg {
 
-// One warp per candidate mu: FP64 on this GPU has a long dependent
-// latency, so the kernel keeps its chains short (reciprocal pivots computed
-// in parallel, warp shuffles instead of block barriers).
-constexpr int TK_THREADS = 32;
+// Four warps per candidate mu.  An FP64 warp instruction occupies its SM
+// sub-partition's FP64 unit for about 64 cycles on this GPU, so the cost of
+// this kernel is the number of FP64 warp instructions each sub-partition
+// issues: the work of every step is spread over all 128 lanes (rows and
+// columns at once), and the scalars of a reflection are computed by every
+// warp at the same time instead of being broadcast.
+constexpr int TK_THREADS = 128;
+constexpr int TK_WARPS = TK_THREADS / 32;
 
-__device__ double block_sum(double v, double* sh) {
-  (void)sh;
+__device__ __forceinline__ double tk_block_sum(double v, double* wsum) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  const double t = (wsum[0] + wsum[1]) + (wsum[2] + wsum[3]);
+  __syncthreads();
+  return t;
 }
 
 // Back substitution y = U^{-1} b for an upper-triangular k x k U (leading
 // dimension ldu) with precomputed reciprocal pivots rinv (0 for a zero
 // pivot: y_i = 0, the smallest-norm least-squares choice on that
-// direction); b is overwritten.
+// direction), run by one warp; b is overwritten.
 __device__ void back_subst(const double* U, int ldu, const double* rinv, double* b, double* y,
                            int k) {
+  const int lane = threadIdx.x & 31;
   for (int i = k - 1; i >= 0; --i) {
     __syncwarp();
     const double yi = b[i] * rinv[i];
-    if (threadIdx.x == 0) y[i] = yi;
-    for (int t = threadIdx.x; t < i; t += blockDim.x) b[t] -= U[t + static_cast<int64_t>(ldu) * i] * yi;
+    if (lane == 0) y[i] = yi;
+    for (int t = lane; t < i; t += 32) b[t] -= U[t + static_cast<int64_t>(ldu) * i] * yi;
   }
   __syncwarp();
 }
 
 // mode 0: least squares (mu = 0); 1: fixed mu = lambda; 2: GCV over the grid.
-// scratch: per block 2*m*m + 4*m doubles.
+// Working set per CTA (tk_scratch_doubles(m) doubles): T and B, both
+// (m+1) x (m+1) with row stride m+1, then y and rinv.  T holds R (becoming
+// R_mu) with g_{0:k} as column k; B holds the sqrt(mu) I block with its
+// right-hand side (0) as column k, and after the factorisation the
+// inverse R_mu^{-1} is built in it.  With in_smem the working set is the
+// CTA's dynamic shared memory, else the per-CTA global scratch.
 __global__ void __launch_bounds__(TK_THREADS)
-k_tikhonov(Work w0, const SolveDesc* desc0, int mode, double* scratch0) {
+k_tikhonov(Work w0, const SolveDesc* desc0, int mode, double* scratch0, int in_smem) {
   const int64_t bo = bidx(w0.b).off;
   const Work w = w0.at(bo);
   const SolveDesc* desc = bsh(desc0, bo);
@@ -53,120 +66,164 @@ k_tikhonov(Work w0, const SolveDesc* desc0, int mode, double* scratch0) {
   Ctl* ctl = w.ctl;
   const int k = ctl->j;
   const int m = w.m, ld = m + 1;
-  __shared__ double sh[32];
+  __shared__ double red[TK_WARPS][kMaxK + 1];   // per-warp partial dot products of a step
+  __shared__ double sp[TK_WARPS];               // per-warp partial squares of the next column
+  __shared__ double wsum[TK_WARPS];
   __shared__ int am_last;
+  extern __shared__ __align__(16) double tk_smem[];
   if (k == 0) {
     if (threadIdx.x == 0 && blockIdx.x == 0) ctl->mu = (mode == 1) ? desc->lambda : 0.0;
     return;
   }
   const double mu = (mode == 0) ? 0.0 : (mode == 1 ? desc->lambda : desc->mu_grid[blockIdx.x]);
-  double* Top = scratch + static_cast<int64_t>(blockIdx.x) * (2 * m * m + 4 * m);  // k x k, ld m
-  double* Bot = Top + m * m;                                                     // k x k, ld m
-  double* c = Bot + m * m;                                                       // k
-  double* y = c + m;                                                             // k
-  double* cb = y + m;                                                            // k
-  double* rinv = cb + m;                                                         // k
+  const int lm = m + 1;
+  double* T = in_smem ? tk_smem : scratch + static_cast<int64_t>(blockIdx.x) * tk_scratch_doubles(m);
+  double* Bm = T + lm * lm;
+  double* y = Bm + lm * lm;
+  double* rinv = y + lm;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const double smu = sqrt(mu);
-  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
-    const int i = idx % k, j = idx / k;
-    Top[i + m * j] = (i <= j) ? w.R[i + static_cast<int64_t>(ld) * j] : 0.0;
-    Bot[i + m * j] = (i == j) ? smu : 0.0;
+  for (int idx = tid; idx < k * (k + 1); idx += TK_THREADS) {
+    const int col = idx / k, i = idx - col * k;
+    T[i + lm * col] = (col == k) ? w.g[i] : (i <= col ? w.R[i + static_cast<int64_t>(ld) * col] : 0.0);
+    Bm[i + lm * col] = (i == col) ? smu : 0.0;
   }
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    c[i] = w.g[i];
-    cb[i] = 0.0;
-  }
+  if (tid < TK_WARPS) sp[tid] = 0.0;
   __syncthreads();
   if (mode != 0) {
-    // Householder on column j: rows {j of Top} U {0..j of Bot}
+    // Householder on column j: rows {j of T} U {0..j of B}; row j of B is
+    // still sqrt(mu), rows 0..j-1 were filled by the earlier reflections.
     for (int j = 0; j < k; ++j) {
-      double part = 0.0;
-      for (int i = threadIdx.x; i <= j; i += blockDim.x) part += Bot[i + m * j] * Bot[i + m * j];
-      const double sigma = block_sum(part, sh);
-      const double alpha = Top[j + m * j];
+      const int nc = k - j;   // columns j+1 .. k (k: the right-hand side)
+      // a warp covers cw column slots and 32/cw row stripes
+      const int cw = nc >= 32 ? 32 : 1 << (32 - __clz(nc - 1));
+      const int nst = TK_WARPS * (32 / cw);
+      const int st = warp * (32 / cw) + lane / cw;
+      const int cs = lane % cw;
+      const double sigma = ((sp[0] + sp[1]) + (sp[2] + sp[3])) + smu * smu;
+      const double alpha = T[j + lm * j];
       const double nrm = sqrt(alpha * alpha + sigma);
-      __syncthreads();
-      if (nrm != 0.0 && sigma != 0.0) {
-        const double sgn = (alpha >= 0.0) ? 1.0 : -1.0;
-        const double v0 = alpha + sgn * nrm;
-        const double tau = 2.0 / (v0 * v0 + sigma);
-        for (int col = j + 1 + threadIdx.x; col <= k; col += blockDim.x) {   // col == k: rhs
-          double* tc = (col < k) ? &Top[j + m * col] : &c[j];
-          double wdot = v0 * (*tc);
-          for (int i = 0; i <= j; ++i) wdot += Bot[i + m * j] * ((col < k) ? Bot[i + m * col] : cb[i]);
-          wdot *= tau;
-          *tc -= wdot * v0;
-          for (int i = 0; i <= j; ++i) {
-            if (col < k) Bot[i + m * col] -= wdot * Bot[i + m * j];
-            else cb[i] -= wdot * Bot[i + m * j];
+      const bool refl = nrm != 0.0 && sigma != 0.0;
+      const double sgn = (alpha >= 0.0) ? 1.0 : -1.0;
+      const double v0 = alpha + sgn * nrm;
+      const double tau = refl ? 2.0 / (v0 * v0 + sigma) : 0.0;
+      if (refl) {   // v . column, per stripe, then over the warp's stripes
+        for (int c0 = 0; c0 < nc; c0 += cw) {
+          const int c = c0 + cs, col = j + 1 + c;
+          double a = 0.0;
+          if (c < nc) {
+            if (st == 0) a = v0 * T[j + lm * col];
+            for (int i = st; i <= j; i += nst) a = fma(Bm[i + lm * j], Bm[i + lm * col], a);
           }
+          for (int o = cw; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          if (lane < cw && c < nc) red[warp][c] = a;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) Top[j + m * j] = -sgn * nrm;
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) Bot[i + m * j] = 0.0;
       }
+      __syncthreads();
+      double s2 = 0.0;   // squares of the updated column j+1 (slot 0) over this thread's rows
+      for (int c0 = 0; c0 < nc; c0 += cw) {
+        const int c = c0 + cs, col = j + 1 + c;
+        if (c >= nc) continue;
+        double wv = 0.0;
+        if (refl) {
+          wv = tau * ((red[0][c] + red[1][c]) + (red[2][c] + red[3][c]));
+          if (st == 0) T[j + lm * col] -= wv * v0;
+        }
+        for (int i = st; i <= j; i += nst) {
+          double bv = Bm[i + lm * col];
+          if (refl) {
+            bv = fma(-wv, Bm[i + lm * j], bv);
+            Bm[i + lm * col] = bv;
+          }
+          if (c == 0) s2 = fma(bv, bv, s2);
+        }
+      }
+      for (int o = cw; o < 32; o <<= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if (lane == 0) sp[warp] = s2;
+      if (tid == 0 && refl) T[j + lm * j] = -sgn * nrm;
       __syncthreads();
     }
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const double piv = Top[i + m * i];
+  for (int i = tid; i < k; i += TK_THREADS) {
+    const double piv = T[i + lm * i];
     rinv[i] = (piv != 0.0) ? 1.0 / piv : 0.0;
   }
   __syncthreads();
-  back_subst(Top, m, rinv, c, y, k);
-  // residual ||g_{0:k} - R y||^2 + g_k^2
+  if (warp == 0) back_subst(T, lm, rinv, T + lm * k, y, k);
+  __syncthreads();
+  // residual ||g_{0:k} - R y||^2 + g_k^2 with the unregularised R
   double part = 0.0;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    double r = w.g[i];
-    for (int j = i; j < k; ++j) r -= w.R[i + static_cast<int64_t>(ld) * j] * y[j];
+  for (int i = tid; i < k; i += TK_THREADS) {
+    double r0 = w.g[i], r1 = 0.0;
+    int jj = i;
+    for (; jj + 1 < k; jj += 2) {
+      r0 -= w.R[i + static_cast<int64_t>(ld) * jj] * y[jj];
+      r1 -= w.R[i + static_cast<int64_t>(ld) * (jj + 1)] * y[jj + 1];
+    }
+    if (jj < k) r0 -= w.R[i + static_cast<int64_t>(ld) * jj] * y[jj];
+    const double r = r0 + r1;
     part += r * r;
   }
-  const double res2 = block_sum(part, sh) + w.g[k] * w.g[k];
+  const double res2 = tk_block_sum(part, wsum) + w.g[k] * w.g[k];
   if (mode == 2) {
-    // ||R_mu^{-1}||_F^2, one column of the inverse per thread (column stored in Bot)
-    double inv2 = 0.0;
-    for (int col = threadIdx.x; col < k; col += blockDim.x) {
-      double* z = Bot + m * col;
-      for (int i = col; i >= 0; --i) {
-        double acc = (i == col) ? 1.0 : 0.0;
-        for (int l = i + 1; l <= col; ++l) acc -= Top[i + m * l] * z[l];
-        z[i] = acc * rinv[i];
-        inv2 += z[i] * z[i];
-      }
+    // ||Z||_F^2 with Z = R_mu^{-1}: right-looking substitution on W = I
+    // (stored in B), rows of Z from the last up.  Row l of Z is
+    // W[l, l:] / R_mu[l,l]; with the columns of R_mu above the diagonal
+    // pre-scaled by the pivot's reciprocal, each update of W is one FMA.
+    for (int idx = tid; idx < k * k; idx += TK_THREADS) {
+      const int col = idx / k, i = idx - col * k;
+      Bm[i + lm * col] = (i == col) ? 1.0 : 0.0;
+      if (i < col) T[i + lm * col] *= rinv[col];
     }
-    const double trace = 1.0 + mu * block_sum(inv2, sh);
+    __syncthreads();
+    double inv2 = 0.0;
+    for (int l = k - 1; l >= 0; --l) {
+      const int nc = k - l;
+      const double rl = rinv[l];
+      for (int idx = tid; idx < (l + 1) * nc; idx += TK_THREADS) {
+        const int i = idx / nc, col = l + (idx - i * nc);
+        const double wl = Bm[l + lm * col];
+        if (i == l) {
+          const double z = wl * rl;
+          inv2 = fma(z, z, inv2);
+        } else {
+          Bm[i + lm * col] = fma(-T[i + lm * l], wl, Bm[i + lm * col]);
+        }
+      }
+      __syncthreads();
+    }
+    const double trace = 1.0 + mu * tk_block_sum(inv2, wsum);
     const double gcv = res2 / (trace * trace);
-    if (threadIdx.x == 0) w.gcv[blockIdx.x] = gcv;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) w.ysel[static_cast<int64_t>(blockIdx.x) * m + i] = y[i];
+    if (tid == 0) w.gcv[blockIdx.x] = gcv;
+    for (int i = tid; i < k; i += TK_THREADS) w.ysel[static_cast<int64_t>(blockIdx.x) * m + i] = y[i];
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) am_last = (atomicInc(w.counter, gridDim.x - 1) == gridDim.x - 1);
+    if (tid == 0) am_last = (atomicInc(w.counter, gridDim.x - 1) == gridDim.x - 1);
     __syncthreads();
     if (!am_last) return;
     __threadfence();
     __shared__ int best;
-    if (threadIdx.x == 0) {
-      int b = 0;
+    if (tid == 0) {
+      int bi = 0;
       double bv = __ldcg(w.gcv), bm = desc->mu_grid[0];
       for (unsigned u = 1; u < gridDim.x; ++u) {
         const double v = __ldcg(w.gcv + u), mm = desc->mu_grid[u];
         if (v < bv || (v == bv && mm > bm)) {
           bv = v;
           bm = mm;
-          b = static_cast<int>(u);
+          bi = static_cast<int>(u);
         }
       }
-      best = b;
+      best = bi;
       ctl->mu = bm;
       ctl->gcv_best = bv;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < k; i += blockDim.x) w.y[i] = __ldcg(w.ysel + static_cast<int64_t>(best) * m + i);
+    for (int i = tid; i < k; i += TK_THREADS) w.y[i] = __ldcg(w.ysel + static_cast<int64_t>(best) * m + i);
     return;
   }
-  for (int i = threadIdx.x; i < k; i += blockDim.x) w.y[i] = y[i];
-  if (threadIdx.x == 0) ctl->mu = mu;
+  for (int i = tid; i < k; i += TK_THREADS) w.y[i] = y[i];
+  if (tid == 0) ctl->mu = mu;
 }
 
 // X = X0 + sum_{i<k} y_i V_i  (Eq. 10S)
@@ -244,7 +301,14 @@ static unsigned ew_grid(int64_t n) {
 
 cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s) {
   const unsigned blocks = (f.mode == 2) ? static_cast<unsigned>(f.n_mu) : 1u;
-  k_tikhonov<<<dim3(blocks, 1, w.b.n), TK_THREADS, 0, s>>>(w, f.desc, f.mode, w.ysel + kMaxMu * w.m);
+  const size_t sm = static_cast<size_t>(tk_scratch_doubles(w.m)) * sizeof(double);
+  const int in_smem = sm <= size_t(200) * 1024 ? 1 : 0;
+  if (in_smem) {
+    cudaError_t e = set_smem(k_tikhonov, sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_tikhonov<<<dim3(blocks, 1, w.b.n), TK_THREADS, in_smem ? sm : 0, s>>>(w, f.desc, f.mode,
+                                                                         w.ysel + kMaxMu * w.m, in_smem);
   return cudaGetLastError();
 }
 

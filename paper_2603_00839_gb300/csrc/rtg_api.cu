@@ -401,7 +401,7 @@ size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, 
   w.rho_hist = c.take<double>(kMaxK);
   w.y = c.take<double>(m);
   w.gcv = c.take<double>(kMaxMu);
-  w.ysel = c.take<double>(size_t(kMaxMu) * m + size_t(tk_blocks) * (2 * size_t(m) * m + 4 * m));
+  w.ysel = c.take<double>(size_t(kMaxMu) * m + size_t(tk_blocks) * size_t(tk_scratch_doubles(m)));
   *tA = c.take<char>(size_t(apply_elems) * e);
   *tB = c.take<char>(size_t(apply_elems) * e);
   if (mem == nullptr) *sk = SketchScratch{};

@@ -136,6 +136,12 @@ struct InfoDev {
 };
 
 // Workspace of one Arnoldi process.  T is the data type (double / float).
+// Doubles of the reduced solve's per-CTA working set: two (m+1) x (m+1)
+// matrices and two vectors of m+1.
+__host__ __device__ inline int64_t tk_scratch_doubles(int m) {
+  return 2 * static_cast<int64_t>(m + 1) * (m + 1) + 2 * static_cast<int64_t>(m + 1);
+}
+
 struct Work {
   int dtype;                   // RTG_F64 / RTG_F32: C, X, S, Q and the arithmetic
   int vdtype;                  // storage of V and W: dtype, or RTG_BF16 for an FP32 solve
