@@ -170,8 +170,10 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
   FF (*rf)[kRedCols] = reinterpret_cast<FF (*)[kRedCols]>(red);
   {   // s . s
     DotAcc<T> a;
+    if constexpr (sizeof(T) == 4) a.v = ff_prod(sv[0], sv[0]);
+    else a.add(sv[0], sv[0]);
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) a.add(sv[k], sv[k]);
+    for (int k = 1; k < ITEMS; ++k) a.add(sv[k], sv[k]);
     if constexpr (sizeof(T) == 4) {
       const FF t = ff_warp_sum(a.v);
       if (lane == 0) rf[warp][J + 1] = t;
@@ -195,9 +197,11 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
       FF v[32];
 #pragma unroll
       for (int g = 0; g < 16; ++g) {
-        FF p{0.f, 0.f}, q{0.f, 0.f};
+        // the first product starts the pair (an exact product is already a
+        // normalised pair, so adding it to zero would change nothing)
+        FF p = ff_prod(sv[0], qv[g][0]), q = ff_prod(qJ[0], qv[g][0]);
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
+        for (int k = 1; k < ITEMS; ++k) {
           p = ff_add(p, ff_prod(sv[k], qv[g][k]));
           q = ff_add(q, ff_prod(qJ[k], qv[g][k]));
         }
