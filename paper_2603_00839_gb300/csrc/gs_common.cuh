@@ -62,6 +62,15 @@ __device__ __forceinline__ FF ff_add(FF x, FF y) {
   const float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
   return ff_two_sum(s.hi, e);
 }
+// Sum of two pairs inside a reduction: the two-sum of the high parts is
+// exact and the low parts are added in FP32, without renormalising the
+// result (the pair still stands for hi + lo; every reduction here ends in
+// a conversion to double, which needs no normalised pair).  8 FP32
+// operations instead of ff_add's 14.
+__device__ __forceinline__ FF ff_add_lazy(FF x, FF y) {
+  const FF s = ff_two_sum(x.hi, y.hi);
+  return {s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
 __device__ __forceinline__ FF ff_prod(float a, float b) {
   const float p = __fmul_rn(a, b);
   return {p, __fmaf_rn(a, b, -p)};
@@ -72,7 +81,7 @@ __device__ __forceinline__ FF ff_warp_sum(FF v) {
     FF w;
     w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
     w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-    v = ff_add(v, w);
+    v = ff_add_lazy(v, w);
   }
   return v;
 }
@@ -86,7 +95,7 @@ struct DotAcc;
 template <>
 struct DotAcc<float> {
   FF v{0.f, 0.f};
-  __device__ __forceinline__ void add(float a, float b) { v = ff_add(v, ff_prod(a, b)); }
+  __device__ __forceinline__ void add(float a, float b) { v = ff_add_lazy(v, ff_prod(a, b)); }
   __device__ __forceinline__ double warp_total() { return ff_to_double(ff_warp_sum(v)); }
 };
 template <>
@@ -120,7 +129,7 @@ __device__ __forceinline__ void ff_reduce_scatter32(FF (&v)[32]) {
       FF got;
       got.hi = __shfl_xor_sync(0xffffffffu, give.hi, half);
       got.lo = __shfl_xor_sync(0xffffffffu, give.lo, half);
-      v[k] = ff_add(keep, got);
+      v[k] = ff_add_lazy(keep, got);
     }
   }
 }
@@ -138,10 +147,10 @@ __device__ __forceinline__ double warps_total(const double (*red)[kRedCols], int
 // Sum of the per-warp float-float values of one column in a fixed order.
 __device__ __forceinline__ FF ff_warps_total(const FF (*red)[kRedCols], int nw, int i) {
   if (nw == 8)
-    return ff_add(ff_add(ff_add(red[0][i], red[1][i]), ff_add(red[2][i], red[3][i])),
-                  ff_add(ff_add(red[4][i], red[5][i]), ff_add(red[6][i], red[7][i])));
+    return ff_add_lazy(ff_add_lazy(ff_add_lazy(red[0][i], red[1][i]), ff_add_lazy(red[2][i], red[3][i])),
+                       ff_add_lazy(ff_add_lazy(red[4][i], red[5][i]), ff_add_lazy(red[6][i], red[7][i])));
   FF acc{0.f, 0.f};
-  for (int u = 0; u < nw; ++u) acc = ff_add(acc, red[u][i]);
+  for (int u = 0; u < nw; ++u) acc = ff_add_lazy(acc, red[u][i]);
   return acc;
 }
 
@@ -202,8 +211,8 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
         FF p = ff_prod(sv[0], qv[g][0]), q = ff_prod(qJ[0], qv[g][0]);
 #pragma unroll
         for (int k = 1; k < ITEMS; ++k) {
-          p = ff_add(p, ff_prod(sv[k], qv[g][k]));
-          q = ff_add(q, ff_prod(qJ[k], qv[g][k]));
+          p = ff_add_lazy(p, ff_prod(sv[k], qv[g][k]));
+          q = ff_add_lazy(q, ff_prod(qJ[k], qv[g][k]));
         }
         v[g] = p;
         v[16 + g] = q;
@@ -272,7 +281,7 @@ __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot,
   if (!*am_last) return false;
   __threadfence();
   auto add = [](V x, V y) -> V {
-    if constexpr (FFROWS) return ff_add(x, y);
+    if constexpr (FFROWS) return ff_add_lazy(x, y);
     else return x + y;
   };
   auto load = [](const V* q) -> V {
