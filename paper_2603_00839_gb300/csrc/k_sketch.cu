@@ -8,9 +8,10 @@
 // FP32 data: every contraction is a GEMM on the tensor cores
 // (mma.sync m16n8k16, BF16 in, FP32 accumulate).  Theta_k has entries
 // exactly +-1 in BF16; each FP32 value x is split into three BF16 limbs
-// h + m + l with h = bf16(x), m = bf16(x - h), l = bf16(x - h - m) (both
-// differences exact in FP32), so the three products per pair carry the
-// full 24-bit significand and the sum is accumulated in FP32.  The first
+// h + m + l by truncation (h the top 8 significant bits of x, m the top 8
+// of x - h, l the rest; both differences exact in FP32), so the three
+// products per pair carry the full 24-bit significand and the sum is
+// accumulated in FP32.  The first
 // contraction on mode 1 (L = 1) is Theta (A operand, rows q) times the
 // columns of X (B operand); later ones multiply X (A operand, rows l) by
 // Theta^T (B operand).  Theta is expanded once per sketch into fragment
@@ -266,25 +267,23 @@ cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, 
 
 // ------------------------------------------------------------------ tensor-core contractions
 
-__device__ __forceinline__ void split3(float x, uint16_t& h, uint16_t& m, uint16_t& l) {
-  const __nv_bfloat16 bh = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(bh);
-  const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(bm);
-  const __nv_bfloat16 bl = __float2bfloat16_rn(r2);
-  h = __bfloat16_as_ushort(bh);
-  m = __bfloat16_as_ushort(bm);
-  l = __bfloat16_as_ushort(bl);
-}
-
-// pack limbs of (x0, x1) into three bf16x2 registers
+// Exact three-limb split of a pair of FP32 values into BF16 limbs by
+// truncation: h keeps the top 8 significant bits of x (the low 16 bits of
+// its encoding cleared), m the top 8 of the exact remainder x - h, and
+// l = x - h - m has at most 8 significant bits, so it is a BF16 value too;
+// x = h + m + l exactly (normal x).  Each limb is the high half of an FP32
+// encoding, so the pairs are packed with one byte permute: out[0] holds
+// (h0, h1), out[1] (m0, m1), out[2] (l0, l1), element 0 in the low half.
 __device__ __forceinline__ void split_pair(float x0, float x1, uint32_t out[3]) {
-  uint16_t h0, m0, l0, h1, m1, l1;
-  split3(x0, h0, m0, l0);
-  split3(x1, h1, m1, l1);
-  out[0] = uint32_t(h0) | (uint32_t(h1) << 16);
-  out[1] = uint32_t(m0) | (uint32_t(m1) << 16);
-  out[2] = uint32_t(l0) | (uint32_t(l1) << 16);
+  const uint32_t u0 = __float_as_uint(x0), u1 = __float_as_uint(x1);
+  const float r0 = x0 - __uint_as_float(u0 & 0xffff0000u);
+  const float r1 = x1 - __uint_as_float(u1 & 0xffff0000u);
+  const uint32_t v0 = __float_as_uint(r0), v1 = __float_as_uint(r1);
+  const float l0 = r0 - __uint_as_float(v0 & 0xffff0000u);
+  const float l1 = r1 - __uint_as_float(v1 & 0xffff0000u);
+  out[0] = __byte_perm(u0, u1, 0x7632);
+  out[1] = __byte_perm(v0, v1, 0x7632);
+  out[2] = __byte_perm(__float_as_uint(l0), __float_as_uint(l1), 0x7632);
 }
 
 __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
@@ -366,7 +365,7 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
     stop = bsh(stop, bo);
   }
   if (stop != nullptr && *stop) return;
-  // BF16 data are exact in one limb; FP32 data take three (see split3)
+  // BF16 data are exact in one limb; FP32 data take three (see split_pair)
   constexpr int LIMBS = sizeof(TI) == 4 ? 3 : 1;
   constexpr int EV = 16 / static_cast<int>(sizeof(TI));   // elements per 16 bytes
   const TI* __restrict__ X = Xr.get<const TI>();
