@@ -269,9 +269,9 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
 // partial sums' precision); else doubles.  The order is fixed, so the
 // result is deterministic.  The counter wraps back to zero by itself.
 // scratch: >= blockDim doubles.
-template <bool FFROWS>
+template <bool FFROWS, typename Pre = void (*)()>
 __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot, int* am_last,
-                                          double* scratch) {
+                                          double* scratch, Pre pre = nullptr) {
   using V = typename std::conditional<FFROWS, FF, double>::type;
   __threadfence();
   __syncthreads();
@@ -280,6 +280,7 @@ __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot,
   __syncthreads();
   if (!*am_last) return false;
   __threadfence();
+  if constexpr (!std::is_same<Pre, void (*)()>::value) pre();   // e.g. start the Gram staging copies
   auto add = [](V x, V y) -> V {
     if constexpr (FFROWS) return ff_add_lazy(x, y);
     else return x + y;
@@ -369,6 +370,26 @@ __device__ inline void gs_finish_start(const Work& w, const StepOpts& o, const d
   set_cond(o, !ctl->stop, ctl);
 }
 
+// Starts the asynchronous copies (cp.async, 8 bytes each) of the stored
+// Gram matrix rows and columns 0..J-1 into the finish's shared staging area,
+// so that they travel while the last block combines the partial rows; the
+// finish called with staged = true waits for them.  Only where the finish
+// stages G (J + 1 <= kGramSmemRows).  sh: the finish's scratch, whose
+// staging area starts after kMaxK + 6 doubles (past the combine's scratch).
+__device__ inline void gs_stage_gram_async(const Work& w, int J, double* sh) {
+  const int n = J + 1;
+  if (J < 1 || n > kGramSmemRows) return;
+  const int lg = n + 1, ld = w.m + 1;
+  double* Gs = sh + (kMaxK + 2) + 4;
+  for (int e = threadIdx.x; e < J * J; e += blockDim.x) {
+    const int i = e % J, k = e / J;
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(&Gs[i * lg + k]));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(w.G + i + static_cast<int64_t>(ld) * k)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 // Step finish from one reduction (every thread of the last block).
 // Classical Gram-Schmidt with one re-orthogonalisation pass, written with
 // the Gram matrix G = Q^T Q of the stored sketched basis so that a single
@@ -381,7 +402,8 @@ __device__ inline void gs_finish_start(const Work& w, const StepOpts& o, const d
 // staged in shared memory and every warp takes part in the two products
 // with it; beyond, one warp per row reads it from global memory.  sh:
 // shared scratch of GS_MAXW * kRedCols doubles, 256 threads.
-__device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const double* tot, double* sh) {
+__device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const double* tot, double* sh,
+                                      bool staged = false) {
   Ctl* ctl = w.ctl;
   const int J = ctl->j;
   const int ld = w.m + 1;
@@ -401,6 +423,13 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
     double* Gs = red + 4;              // n x n
     double* pr = Gs + n * lg;          // [nw][n] partial products
     double* ab = pr + nw * n;          // [2][2] the two warps' sums of a and b
+    if (staged) {   // rows and columns < J arrived by gs_stage_gram_async; J from the new row
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        Gs[J * lg + i] = grow[i];
+        Gs[i * lg + J] = grow[i];
+      }
+    } else
     for (int e0 = 0; e0 < n * n; e0 += 8 * static_cast<int>(blockDim.x)) {   // eight loads in flight
       double v[8];
 #pragma unroll

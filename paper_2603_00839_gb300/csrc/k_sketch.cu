@@ -636,11 +636,13 @@ k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int
   double(*red2)[kRedCols] = reinterpret_cast<double(*)[kRedCols]>(smem);
   double* tot = reinterpret_cast<double*>(smem) + GS_MAXW * kRedCols;
   block_partials<float, ITEMS>(w, vals, ix, ITEMS, J, red2);
-  if (!last_block_combine<true>(w, gs_ncols(J), tot, &am_last, &red2[0][0])) return;
+  double* fin_sh = &red2[0][0];
+  auto stage = [&]() { if (dots_pass > 0) gs_stage_gram_async(w, J, fin_sh); };
+  if (!last_block_combine<true>(w, gs_ncols(J), tot, &am_last, &red2[0][0], stage)) return;
   if (dots_pass == 0) {
     if (tid == 0) gs_finish_start(w, o, tot);
   } else {
-    gs_finish_gram(w, o, tot, &red2[0][0]);
+    gs_finish_gram(w, o, tot, &red2[0][0], true);
   }
 }
 
