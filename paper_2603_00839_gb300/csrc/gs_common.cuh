@@ -268,7 +268,9 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
 // unit for about 64 cycles on this GPU; the pairs already carry the
 // partial sums' precision); else doubles.  The order is fixed, so the
 // result is deterministic.  The counter wraps back to zero by itself.
-// scratch: >= blockDim doubles.
+// scratch: >= blockDim doubles.  pre (optional): called by every thread of
+// the last block right after the ticket, before its loads, e.g. to start
+// asynchronous copies that the caller needs after the combine.
 template <bool FFROWS, typename Pre = void (*)()>
 __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot, int* am_last,
                                           double* scratch, Pre pre = nullptr) {
