@@ -65,6 +65,23 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def job_times(local, world: int, device: str):
+    """The slowest rank's value of each of this rank's times (MAX all-reduce
+    over the process group when world > 1); `device` holds the reduced
+    tensor ("cuda" under NCCL, "cpu" under gloo)."""
+    import torch
+    t = torch.tensor([float(x) for x in local], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput of replicas: every rank's units over the slowest time."""
+    return world * units_per_rank / seconds
+
+
 def rho_star(nu_c: float) -> float:
     # stop level of the relative sketched residual: 1e-3, or the noise floor
     # of the observation when that lies above it (discrepancy principle)
@@ -579,12 +596,9 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    ms_t = torch.tensor([ms, plain_ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max, plain_max = float(ms_t[0].item()), float(ms_t[1].item())
-    value = world * B * 1e3 / ms_max
-    plain_value = world * 1e3 / plain_max
+    ms_max, plain_max = job_times([ms, plain_ms], world, "cuda")
+    value = job_rate(world, B, ms_max / 1e3)
+    plain_value = job_rate(world, 1, plain_max / 1e3)
 
     # ---- end to end through the C ABI with pinned host buffers, every step:
     # H2D of the batch's observations, the batched solve, D2H of the solutions
@@ -615,10 +629,7 @@ def run_ours(args):
     for s in range(0 if only_b else args.steps):
         e2e_step(s % nb)
     e2e_s = (time.perf_counter() - t0) / args.steps if not only_b else float("nan")
-    e2e_t = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-    e2e_val = world * B / float(e2e_t.item())
+    e2e_val = job_rate(world, B, job_times([e2e_s], world, "cuda")[0])
 
     ws_form = None
     if rank == 0 and not args.no_warm_start and not only_b:
