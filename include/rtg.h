@@ -28,7 +28,10 @@
  *    process or traps the GPU; device-side anomalies (non-finite values,
  *    breakdown) are reported through rtg_info.
  *  - A handle is bound to one device and is not thread-safe: use one
- *    handle per host thread.
+ *    handle per host thread.  Calls of one handle on different streams
+ *    may overlap on the GPU: rtg_operator_apply and rtg_sketch keep their
+ *    scratch per stream, and solves in flight at once use different
+ *    workspace slots (rtg_opts.slot).
  */
 #ifndef RTG_H
 #define RTG_H
@@ -207,7 +210,11 @@ rtg_status rtg_operator_apply(rtg_handle handle,
  * A mode with s_k >= I_k is not sketched (Theta_k = I, s'_k = I_k).
  * SX: device array of prod(s'_k) elements of `dtype`, column-major; for
  * dtype BF16 (X in BF16, exact in one tensor-core limb) SX is FP32, and
- * mode 1 must be sketched.
+ * mode 1 must be sketched.  The handle keeps the signs and the chain's
+ * intermediates per (shape, sketch sizes, problem_id, dtype, stream) and
+ * draws the signs again whenever a call brings another seed.  The bounded
+ * device-side waits of the FP32 chain never fail in normal operation; if
+ * one gave up, the entries of SX that its thread block computes are NaN.
  * Errors: INVALID_ARG (s_k < 1, shape), UNSUPPORTED (BF16 with mode 1 not
  * sketched), CUDA.
  */
@@ -453,14 +460,16 @@ rtg_status rtg_gmres_solve_batched(rtg_handle handle, int32_t nprob, const rtg_p
  * intermediates) lives in one 16 MiB array of the library's static device
  * memory, which every GPU that loads the library holds until the process
  * exits.  Sizes whose scratch (signs, Theta fragments and two partial-sum
- * intermediates) exceeds 16 MiB are rejected with RTG_ERR_INVALID_ARG and a message in rtg_last_error().
+ * intermediates) exceeds 16 MiB are rejected with RTG_ERR_INVALID_ARG and a message in rtg_last_error(),
+ * and so are tensors of more than 2^40 elements and an SX that overlaps X (as for rtg_sketch).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  All calls share the one array and it keeps
  * the last call's contents (each call writes every scratch byte it reads,
  * so nothing needs clearing); calls that overlap on the GPU (different
  * streams, or different host threads) race on it.  X, SX: device arrays as
- * for rtg_sketch; the call is asynchronous on `stream`.
+ * for rtg_sketch; the call is asynchronous on `stream`, and a bounded
+ * device-side wait that gave up leaves NaN in SX as for rtg_sketch.
  */
 rtg_status rtg_sketch_noalloc(rtg_shape shape, rtg_dtype dtype, const int64_t* sketch_dims,
                               uint64_t seed, uint64_t problem_id, const void* X, void* SX,

@@ -158,8 +158,6 @@ SketchScratch carve_sketch_scratch(const SketchPlan& sp, void* base) {
   sc.tmp0 = p;
   p += al256(size_t(sp.part_elems) * elt);
   sc.tmp1 = p;
-  p += al256(size_t(sp.part_elems) * elt);
-  sc.status = reinterpret_cast<int*>(p);
   return sc;
 }
 
@@ -355,7 +353,7 @@ template <int CH, typename TI>
 __global__ void __launch_bounds__(TC_THREADS)
 k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t s, int kt_total,
               const uint4* __restrict__ fragA, int mt_total, float scale, OutMap om,
-              int* status, const int* stop, Batch bt) {
+              int* status, int poison, const int* stop, Batch bt) {
   {
     const int64_t bo = bidx(bt).off;
     Xr = Xr.at(bo);
@@ -452,13 +450,14 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
     }
     __syncthreads();
   }
-  if (!ok) {   // timed out: this CTA contributes zeros
+  if (!ok) {   // timed out: zeros where the solve records the timeout, else NaN (never a silent partial sum)
+    const float fill = poison ? __int_as_float(0x7fc00000) : 0.f;
 #pragma unroll
     for (int a = 0; a < F_MT; ++a)
 #pragma unroll
       for (int b = 0; b < F_NT; ++b)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+        for (int c = 0; c < 4; ++c) acc[a][b][c] = fill;
   }
   __syncthreads();
   constexpr int ROWS = F_MT * 16;
@@ -504,7 +503,8 @@ template <int CH>
 __global__ void __launch_bounds__(TC_THREADS, 3)
 k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int64_t I, int64_t R,
               int64_t s, int kt_total, const uint2* __restrict__ fragB, int nt_total, float scale,
-              OutMap om, int dots_pass, Work w, StepOpts o, int* status, const int* stop, Batch bt) {
+              OutMap om, int dots_pass, Work w, StepOpts o, int* status, int poison, const int* stop,
+              Batch bt) {
   {
     const int64_t bo = bidx(bt).off;
     Xr = Xr.at(bo);
@@ -590,11 +590,13 @@ k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int
     }
     __syncthreads();
   }
-  if (!ok) {   // timed out: this CTA contributes zeros and still takes part in the dots
+  if (!ok) {   // timed out: zeros where the solve records the timeout (the CTA still takes
+               // part in the dots), else NaN (never a silent partial sum)
+    const float fill = poison ? __int_as_float(0x7fc00000) : 0.f;
 #pragma unroll
     for (int nt = 0; nt < N_NT; ++nt)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[nt][c] = 0.f;
+      for (int c = 0; c < 4; ++c) acc[nt][c] = fill;
   }
   __syncthreads();
   float* red = reinterpret_cast<float*>(smem);               // [8][16][N_NT*8]
@@ -740,14 +742,14 @@ static OutMap stage_out_map(const SketchPlan& sp, int t) {
 
 template <int CH, typename TI>
 static cudaError_t launch_first(dim3 grid, PtrRef src, float* dst, const SketchPlan& sp, int t, int kt,
-                                const uint32_t* fr, float scale, OutMap om, int* status, const int* stop,
-                                cudaStream_t s, Batch b) {
+                                const uint32_t* fr, float scale, OutMap om, int* status, int poison,
+                                const int* stop, cudaStream_t s, Batch b) {
   constexpr size_t sm = first_smem<CH>();
   cudaError_t e = set_smem(k_sk_first_tc<CH, TI>, sm);
   if (e != cudaSuccess) return e;
   k_sk_first_tc<CH, TI><<<grid, TC_THREADS, sm, s>>>(src, dst, sp.stage_I[t], sp.stage_R[t], sp.stage_s[t], kt,
                                                      reinterpret_cast<const uint4*>(fr), sp.stage_ntile[t],
-                                                     scale, om, status, stop, b);
+                                                     scale, om, status, poison, stop, b);
   return cudaGetLastError();
 }
 
@@ -761,7 +763,11 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
     const int kt = sp.stage_kt[t];
     const uint32_t* fr = sc.frags + sp.frag_off[t];
     const OutMap om = stage_out_map(sp, t);
-    int* status = (dots != nullptr) ? &dots->w->ctl->status : sc.status;
+    // a bounded wait that gives up is recorded in the solve's status when the
+    // chain belongs to a solve with fused dots; elsewhere nothing would read a
+    // status word, so the affected outputs become NaN instead
+    int* status = (dots != nullptr) ? &dots->w->ctl->status : nullptr;
+    const int poison = (dots != nullptr) ? 0 : 1;
     cudaError_t e = cudaSuccess;
     if (sp.stage_first[t]) {
       dim3 grid(static_cast<unsigned>((sp.stage_R[t] + F_COLS - 1) / F_COLS),
@@ -770,11 +776,11 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
       // K chunks of 16 tiles up to I = 512 (about 50 KB of shared memory, four
       // CTAs per SM: in throughput the occupancy outweighs the second chunk's load)
       if (kt > 32)
-        e = bf ? launch_first<32, __nv_bfloat16>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s, b)
-               : launch_first<32, float>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s, b);
+        e = bf ? launch_first<32, __nv_bfloat16>(grid, src, dst, sp, t, kt, fr, scale, om, status, poison, stop, s, b)
+               : launch_first<32, float>(grid, src, dst, sp, t, kt, fr, scale, om, status, poison, stop, s, b);
       else
-        e = bf ? launch_first<16, __nv_bfloat16>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s, b)
-               : launch_first<16, float>(grid, src, dst, sp, t, kt, fr, scale, om, status, stop, s, b);
+        e = bf ? launch_first<16, __nv_bfloat16>(grid, src, dst, sp, t, kt, fr, scale, om, status, poison, stop, s, b)
+               : launch_first<16, float>(grid, src, dst, sp, t, kt, fr, scale, om, status, poison, stop, s, b);
     } else {
       const int64_t ltiles = (sp.stage_L[t] + 15) / 16;
       dim3 grid(static_cast<unsigned>(ltiles * sp.stage_R[t]),
@@ -790,7 +796,7 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
         k_sk_inner_tc<32><<<grid, TC_THREADS, sm, s>>>(src, inb, dst, sp.stage_L[t], sp.stage_I[t],
                                                        sp.stage_R[t], sp.stage_s[t], kt,
                                                        reinterpret_cast<const uint2*>(fr), sp.stage_ntile[t],
-                                                       scale, om, dpass, wk, so, status, stop, b);
+                                                       scale, om, dpass, wk, so, status, poison, stop, b);
       } else {
         constexpr size_t sm = inner_smem<16>();
         e = set_smem(k_sk_inner_tc<16>, sm);
@@ -798,7 +804,7 @@ static cudaError_t sketch_f32(const SketchPlan& sp, const SketchScratch& sc, Ptr
         k_sk_inner_tc<16><<<grid, TC_THREADS, sm, s>>>(src, inb, dst, sp.stage_L[t], sp.stage_I[t],
                                                        sp.stage_R[t], sp.stage_s[t], kt,
                                                        reinterpret_cast<const uint2*>(fr), sp.stage_ntile[t],
-                                                       scale, om, dpass, wk, so, status, stop, b);
+                                                       scale, om, dpass, wk, so, status, poison, stop, b);
       }
     }
     e = cudaGetLastError();

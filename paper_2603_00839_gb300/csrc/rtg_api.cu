@@ -11,6 +11,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -412,6 +413,23 @@ size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, 
 
 void rtg::record_error(const char* msg) { g_err = msg; }
 
+cudaError_t rtg::raise_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> set;   // (device, kernel) -> bytes set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = set.find({dev, kernel});
+  if (it != set.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  set[{dev, kernel}] = bytes;
+  return cudaSuccess;
+}
+
 // ------------------------------------------------------------------ handle
 
 struct rtg_context;
@@ -571,11 +589,27 @@ struct PhaseScope {
   }
 };
 
+// Scratch of rtg_sketch for one (shape, sketch sizes, problem id, dtype,
+// stream): the packed signs, Theta fragments and chain intermediates, and
+// the seed the signs were last drawn for (they are drawn again when a call
+// brings another seed).
+struct SketchCache {
+  DevBuf buf;
+  uint64_t seed = 0;
+  bool drawn = false;
+};
+
+// Scratch of rtg_operator_apply's unfused path on one stream.
+struct ApplyScratch {
+  DevBuf tA, tB;
+};
+
 struct rtg_context {
   int device = 0;
   std::map<std::string, std::unique_ptr<OpHolder>> ops;
-  std::map<std::string, std::unique_ptr<DevBuf>> sketches;   // signs, fragments and scratch per sketch
-  DevBuf tA, tB;
+  // keyed by stream too, so that calls on different streams never share scratch
+  std::map<std::string, std::unique_ptr<SketchCache>> sketches;
+  std::map<cudaStream_t, std::unique_ptr<ApplyScratch>> apply_scratch;
   std::map<std::string, std::shared_ptr<SolvePlan>> plans;
   std::map<std::string, std::unique_ptr<BatchPlan>> batches;
   std::unique_ptr<PhaseTimer> timer;
@@ -1133,10 +1167,17 @@ rtg_status rtg_operator_apply(rtg_handle h, const rtg_factor* A, int32_t nA, con
   if (apply_uses_st(op->op, dtype, dtype, dtype) && reinterpret_cast<uintptr_t>(X) % 16 != 0)
     return fail(RTG_ERR_INVALID_ARG, "X must be 16-byte aligned for this operator");
   const int64_t sc = apply_scratch_elems(op->op);
-  RK(h->tA.ensure(size_t(sc) * elt_size(dtype)));
-  RK(h->tB.ensure(size_t(sc) * elt_size(dtype)));
-  CK(launch_apply(op->op, dtype, ref(X), ref(Y), 1.0, 0.0, PtrRef{}, h->tA.p, h->tB.p, nullptr,
-                  reinterpret_cast<cudaStream_t>(stream)));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void *ta = nullptr, *tb = nullptr;
+  if (sc > 0) {   // the unfused path's intermediates, owned per stream
+    std::unique_ptr<ApplyScratch>& as = h->apply_scratch[s];
+    if (!as) as = std::make_unique<ApplyScratch>();
+    RK(as->tA.ensure(size_t(sc) * elt_size(dtype)));
+    RK(as->tB.ensure(size_t(sc) * elt_size(dtype)));
+    ta = as->tA.p;
+    tb = as->tB.p;
+  }
+  CK(launch_apply(op->op, dtype, ref(X), ref(Y), 1.0, 0.0, PtrRef{}, ta, tb, nullptr, s));
   return RTG_OK;
 }
 
@@ -1156,30 +1197,36 @@ rtg_status rtg_sketch(rtg_handle h, rtg_shape shape, rtg_dtype dtype, const int6
   if (overlaps(X, SX, size_t(std::min<int64_t>(n, sp.d)) * elt_size(pdt)))
     return fail(RTG_ERR_INVALID_ARG, "SX must not overlap X");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // The signs depend on (seed, problem id); the scratch is kept per shape,
+  // sketch sizes, problem id, dtype and stream, and its signs are drawn
+  // again whenever the seed differs from the one they were drawn for.
   std::string key;
   append_bytes(key, &sp.order, sizeof sp.order);
   append_bytes(key, sp.dims, sizeof sp.dims);
   append_bytes(key, sp.sdims, sizeof sp.sdims);
   append_bytes(key, &pid, sizeof pid);
   append_bytes(key, &sp.dtype, sizeof sp.dtype);
+  append_bytes(key, &s, sizeof s);
   auto it = h->sketches.find(key);
-  DevBuf* buf = nullptr;
-  bool fresh = false;
+  SketchCache* ce = nullptr;
   if (it == h->sketches.end()) {
     if (h->sketches.size() > 16) {
       cudaDeviceSynchronize();
       h->sketches.clear();
     }
-    auto b = std::make_unique<DevBuf>();
-    RK(b->ensure(sketch_scratch_bytes(sp)));
-    buf = b.get();
+    auto b = std::make_unique<SketchCache>();
+    RK(b->buf.ensure(sketch_scratch_bytes(sp)));
+    ce = b.get();
     h->sketches[key] = std::move(b);
-    fresh = true;
   } else {
-    buf = it->second.get();
+    ce = it->second.get();
   }
-  const SketchScratch sc = carve_sketch_scratch(sp, buf->p);
-  if (fresh) CK(launch_theta(sp, sc.bits, sc.frags, s));
+  const SketchScratch sc = carve_sketch_scratch(sp, ce->buf.p);
+  if (!ce->drawn || ce->seed != seed) {
+    CK(launch_theta(sp, sc.bits, sc.frags, s));
+    ce->seed = seed;
+    ce->drawn = true;
+  }
   CK(launch_sketch(sp, sc, ref(X), SX, nullptr, nullptr, s, dtype));
   return RTG_OK;
 }

@@ -252,7 +252,6 @@ struct SketchScratch {
   uint32_t* frags = nullptr;
   void* tmp0 = nullptr;
   void* tmp1 = nullptr;
-  int* status = nullptr;      // device word: a bounded wait gave up (RTG_ERR_TIMEOUT)
 };
 
 // Fills sp; returns an error message or nullptr (k_sketch.cu).
@@ -293,15 +292,16 @@ struct PtrRef {
 };
 inline PtrRef ref(const void* p) { PtrRef r; r.base = p; return r; }
 
-// A kernel's dynamic shared memory, with the unified L1 / shared array given
-// to shared memory as far as it goes.  Every kernel of a solve asks for the
-// same split, so an SM never drains to re-partition it between launches.
+// Raises a kernel's largest dynamic shared memory on the current device to
+// at least `bytes` (never lowers it: graphs captured earlier may launch the
+// kernel with a larger size than the current call needs) and gives the
+// unified L1 / shared array to shared memory as far as it goes.  Every kernel
+// of a solve asks for the same split, so an SM never drains to re-partition
+// it between launches.  Thread-safe (rtg_api.cu).
+cudaError_t raise_smem(const void* kernel, size_t bytes);
 template <typename K>
 inline cudaError_t set_smem(K* kernel, size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              cudaSharedmemCarveoutMaxShared);
+  return raise_smem(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 // Sets the thread-local message rtg_last_error() returns (rtg_api.cu).

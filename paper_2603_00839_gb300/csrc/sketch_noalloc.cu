@@ -65,14 +65,27 @@ extern "C" rtg_status rtg_sketch_noalloc(rtg_shape shape, rtg_dtype dtype,
   using namespace rtg;
   if (dtype != RTG_F64 && dtype != RTG_F32) return noalloc_fail(RTG_ERR_UNSUPPORTED, "dtype must be RTG_F64 or RTG_F32");
   if (shape.order < 1 || shape.order > kMaxOrder) return noalloc_fail(RTG_ERR_INVALID_ARG, "shape.order must be 1..4");
-  if (sketch_dims == nullptr || X == nullptr || SX == nullptr || X == SX)
-    return noalloc_fail(RTG_ERR_INVALID_ARG, "sketch_dims, X and SX must be non-NULL and SX must not alias X");
+  if (sketch_dims == nullptr || X == nullptr || SX == nullptr)
+    return noalloc_fail(RTG_ERR_INVALID_ARG, "sketch_dims, X and SX must be non-NULL");
   if (!on_device(X) || !on_device(SX)) return noalloc_fail(RTG_ERR_INVALID_ARG, "X and SX must be device pointers");
-  for (int k = 0; k < shape.order; ++k)
-    if (shape.dims[k] < 1 || shape.dims[k] > (int64_t(1) << 31)) return noalloc_fail(RTG_ERR_INVALID_ARG, "shape.dims must be in 1..2^31");
+  // the same size bound as rtg_sketch: at most 2^40 elements, checked before
+  // each product so that no int64 product of the plan can wrap
+  int64_t n = 1;
+  for (int k = 0; k < shape.order; ++k) {
+    if (shape.dims[k] < 1) return noalloc_fail(RTG_ERR_INVALID_ARG, "shape.dims must be >= 1");
+    if (n > (int64_t(1) << 40) / shape.dims[k]) return noalloc_fail(RTG_ERR_INVALID_ARG, "tensor too large");
+    n *= shape.dims[k];
+  }
   SketchPlan sp;
   const char* perr = make_sketch_plan(shape.order, shape.dims, sketch_dims, seed, problem_id, dtype, sp);
   if (perr != nullptr) return noalloc_fail(RTG_ERR_INVALID_ARG, perr);
+  {   // SX may not overlap the part of X the chain reads while it writes SX
+    const size_t elt = dtype == RTG_F64 ? 8 : 4;
+    const size_t span = size_t(n < sp.d ? n : sp.d) * elt;
+    const char* x = static_cast<const char*>(X);
+    const char* y = static_cast<const char*>(SX);
+    if (x < y + span && y < x + span) return noalloc_fail(RTG_ERR_INVALID_ARG, "SX must not overlap X");
+  }
   // scratch: packed signs, Theta fragments and two contraction intermediates
   const size_t need = sketch_scratch_bytes(sp);
   if (need > kNoAllocBytes) {

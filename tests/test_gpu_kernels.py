@@ -211,3 +211,41 @@ def test_sketch_problem_id_changes_signs(h):
     th = oracle.sketch_matrices((64, 64, 3), (16, 16, 3), 1, problem_id=1)
     assert not np.allclose(a, b)
     assert _rel(b, oracle.sketch(X.cpu().numpy(), th)) < 1e-12
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_sketch_seed_sequence_on_one_handle(h, dt):
+    """S(X) with seeds 0, 5, 0 on one handle and shape (Section 3, the global
+    sketching operator): every call uses the signs of its own seed."""
+    api = _api()
+    dims, sk = (96, 80, 3), (32, 24, 3)
+    Xh = np.random.default_rng(3).standard_normal(dims)
+    X = api.to_device(Xh, dt)
+    tol = TOL[dt] * (10 if dt == torch.float32 else 1)
+    outs = []
+    for seed in (0, 5, 0, 5, 5):
+        SX = h.sketch(X, sk, seed).cpu().double().numpy()
+        ref = oracle.sketch(Xh, oracle.sketch_matrices(dims, sk, seed))
+        assert _rel(SX, ref) < tol, seed
+        outs.append(SX)
+    assert not np.allclose(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
+
+
+def test_sketch_and_apply_on_two_streams_of_one_handle(h):
+    """Calls of one handle on two streams: each stream has its own scratch."""
+    api = _api()
+    dims, sk = (64, 48, 3), (16, 16, 3)
+    Xh = [np.random.default_rng(10 + i).standard_normal(dims) for i in range(2)]
+    X = [api.to_device(x, torch.float32) for x in Xh]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    SX = [None, None]
+    for rep in range(4):
+        for i in range(2):
+            with torch.cuda.stream(streams[i]):
+                SX[i] = h.sketch(X[i], sk, seed=7 * i + rep, stream=streams[i])
+        torch.cuda.synchronize()
+        for i in range(2):
+            ref = oracle.sketch(Xh[i], oracle.sketch_matrices(dims, sk, 7 * i + rep))
+            assert _rel(SX[i].cpu().double().numpy(), ref) < 2e-5

@@ -72,3 +72,29 @@ def test_noalloc_rejects_scratch_beyond_the_static_array(lib):
     st, _ = _noalloc(lib, X, (1024, 64, 3), 1, 0)
     assert st == lib.ERR_INVALID_ARG
     assert b"static scratch holds" in lib.load().rtg_last_error()
+
+
+def test_noalloc_rejects_overlap_and_oversized_shapes(lib):
+    """The same argument checks as rtg_sketch: no partial overlap of SX with
+    X, no tensor above 2^40 elements (nothing is launched for either)."""
+    from paper_2603_00839_gb300 import api
+    buf = api.empty((64 * 48 * 3 + 256,), torch.float32)
+    L = lib.load()
+    shape = lib.Shape()
+    shape.order = 3
+    for k, d in enumerate((64, 48, 3)):
+        shape.dims[k] = d
+    sk = (ctypes.c_int64 * 3)(16, 16, 3)
+    stream = torch.cuda.current_stream().cuda_stream
+    # SX starts 64 floats into X: a partial overlap
+    st = L.rtg_sketch_noalloc(shape, lib.F32, sk, ctypes.c_uint64(1), ctypes.c_uint64(0),
+                              buf.data_ptr(), buf.data_ptr() + 256, stream)
+    assert st == lib.ERR_INVALID_ARG and b"overlap" in L.rtg_last_error()
+    big = lib.Shape()
+    big.order = 3
+    for k, d in enumerate((1 << 21, 1 << 21, 2)):
+        big.dims[k] = d
+    st = L.rtg_sketch_noalloc(big, lib.F32, sk, ctypes.c_uint64(1), ctypes.c_uint64(0),
+                              buf.data_ptr(), buf.data_ptr() + 4 * 64 * 48 * 3, stream)
+    assert st == lib.ERR_INVALID_ARG and b"too large" in L.rtg_last_error()
+    torch.cuda.synchronize()
