@@ -98,7 +98,10 @@ typedef struct rtg_opts {
     double tol;                      /* stop at the first j with rho_j <= tol (0: run m steps) */
     const double* mu_grid;           /* host array of n_mu GCV candidates (lambda < 0) */
     int32_t n_mu;                    /* 1..RTG_MAX_MU when lambda < 0 */
-    int32_t max_restarts;            /* restarts from the least-squares iterate (>= 0) */
+    int32_t max_restarts;            /* restarted cycles (>= 0; rtg_gmres_solve and the batched
+                                        solve): a cycle that reaches j = m without meeting tol
+                                        restarts from its least-squares iterate;
+                                        m * (max_restarts + 1) <= RTG_MAX_KRYLOV */
     double breakdown_tol;            /* breakdown if h_{j+1,j} <= breakdown_tol * ||S(Phi V_j)||;
                                         0 selects 1e-12 (F64) / 1e-6 (F32) */
     int32_t flags;                   /* RTG_FLAG_* */
@@ -114,7 +117,14 @@ typedef struct rtg_opts {
 #define RTG_MAX_SLOTS 64
 
 #define RTG_FLAG_NO_GRAPH      1     /* launch kernels directly instead of a CUDA graph */
-#define RTG_FLAG_TRUE_RESIDUAL 2     /* also compute ||C - Phi(X)||_F / ||C||_F into info */
+#define RTG_FLAG_TRUE_RESIDUAL 2     /* the final residual of the Block GMRES algorithm
+                                        (Section 4.4, its last steps): after the assembly,
+                                        R = C - Phi(X) for the returned X, then
+                                        info->true_rel_resid = ||R||_F / ||C||_F and
+                                        info->true_rel_resid_theta = ||R||_Theta / ||R_0||_Theta
+                                        (one more apply, sketch and reduction; with an operator
+                                        that takes the spatio-temporal kernel X must be 16-byte
+                                        aligned) */
 #define RTG_FLAG_PHASE_TIMES   4     /* time every kernel group with CUDA events into
                                         info->phase_ms (implies RTG_FLAG_NO_GRAPH); see below */
 #define RTG_FLAG_BF16_BASIS    8     /* precision form (dtype RTG_F32 only): the basis V_i and
@@ -152,7 +162,7 @@ typedef struct rtg_info {
     double rho_final;                /* last rho_j */
     double* rho_hist;                /* optional caller host array of length >= m*(max_restarts+1) */
     double* gcv;                     /* optional caller host array of length n_mu (GCV values) */
-    double true_rel_resid;           /* with RTG_FLAG_TRUE_RESIDUAL, else -1 */
+    double true_rel_resid;           /* ||C - Phi(X)||_F / ||C||_F with RTG_FLAG_TRUE_RESIDUAL, else -1 */
     double elapsed_ms;               /* device time of the solve (CUDA events) */
     int32_t device_status;           /* rtg_status seen on the device (NONFINITE, ...) */
     int32_t launches;                /* kernels this library launched for the solve */
@@ -164,6 +174,8 @@ typedef struct rtg_info {
      * between the events.  Zero without the flag. */
     double phase_ms[RTG_PHASE_COUNT];
     int32_t phase_launches[RTG_PHASE_COUNT];
+    double true_rel_resid_theta;     /* ||C - Phi(X)||_Theta / ||R_0||_Theta with RTG_FLAG_TRUE_RESIDUAL,
+                                        else -1 */
 } rtg_info;
 
 typedef struct rtg_context* rtg_handle;
@@ -290,8 +302,14 @@ rtg_status rtg_krylov_query(rtg_handle handle, rtg_krylov krylov, rtg_krylov_vie
  *     lambda > 0: mu = lambda;  lambda == 0: mu = 0 (Eq. 11S);
  *     lambda < 0: mu = argmin GCV(mu) over opts->mu_grid (ties: larger mu);
  *   X = X_0 + sum_j y_j V_j (Eq. 10S).
- * Restarted cycles (opts->max_restarts > 0) are not implemented on the
- * GPU: the call returns RTG_ERR_UNSUPPORTED.
+ * With opts->max_restarts = R > 0, a cycle that ends at j = m with
+ * rho_j > tol (no breakdown) restarts: y = argmin ||beta e1 - Hbar y||
+ * (Eq. 11S), X_0 <- X_0 + sum_j y_j V_j, R_0 = C - Phi(X_0), and a new
+ * sketched Arnoldi cycle, at most R times; rho_j stays relative to the
+ * first cycle's ||R_0||_Theta, and the regularised solve above is taken on
+ * the last cycle.  The whole sequence stays inside the solve's CUDA graph
+ * (its restart kernels return at once in steps that do not restart).
+ * info->rho_hist then needs m * (R + 1) entries.
  * C, X0 (may be NULL), X: device or host arrays of prod(dims) elements of
  * dtype (F64 or F32); X may alias X0.  info may be NULL.  The call
  * synchronises `stream` once at the end; it equals rtg_gmres_submit
@@ -341,7 +359,8 @@ rtg_status rtg_gmres_wait(rtg_handle handle, int32_t slot, rtg_info* info);
  * bidiagonal Btilde_k takes the place of Hbar_k: rho_k, the stop rule, the
  * projected Tikhonov / GCV solve (Eq. 13) and X = X_0 + sum y_k V_k are as
  * for RTG-GMRES.  Stops also when alpha_{k+1} falls to the breakdown level.
- * Memory: m+1 tensors V plus two U.  RTG_FLAG_BF16_BASIS is not available.
+ * Memory: m+1 tensors V plus two U.  RTG_FLAG_BF16_BASIS and restarts are
+ * not available (UNSUPPORTED).
  * Errors: as rtg_gmres_solve.
  */
 rtg_status rtg_gk_solve(rtg_handle handle,

@@ -152,6 +152,8 @@ class SolveResult:
     launches: int
     phase_ms: Optional[dict] = None        # group -> device ms (phase_times=True)
     phase_launches: Optional[dict] = None  # group -> kernel launches (phase_times=True)
+    true_rel_resid: float = -1.0           # ||C - Phi(X)||_F / ||C||_F (true_residual=True)
+    true_rel_resid_theta: float = -1.0     # ||C - Phi(X)||_Theta / ||R_0||_Theta (true_residual=True)
 
 
 class Handle:
@@ -220,7 +222,7 @@ class Handle:
                     A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (),
                     X0=None, X=None, tol: float = 0.0, mu_grid=None, max_restarts: int = 0,
                     breakdown_tol: float = 0.0, use_graph: bool = True, phase_times: bool = False,
-                    slot: int = 0, bf16_basis: bool = False, stream=None):
+                    slot: int = 0, bf16_basis: bool = False, true_residual: bool = False, stream=None):
         """RTG-GMRES; C_obs, X0, X may be device tensors or host numpy arrays (Fortran order).
 
         phase_times=True launches directly and times each kernel group with
@@ -230,13 +232,14 @@ class Handle:
                                  tol=tol, mu_grid=mu_grid, max_restarts=max_restarts,
                                  breakdown_tol=breakdown_tol, use_graph=use_graph,
                                  phase_times=phase_times, slot=slot, bf16_basis=bf16_basis,
-                                 stream=stream)
+                                 true_residual=true_residual, stream=stream)
         return self.gmres_wait(pend)
 
     def gk_solve(self, C_obs, m: int, sketch_dims: Sequence[int], seed: int, lam: float,
                  A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (),
                  X0=None, X=None, tol: float = 0.0, mu_grid=None, breakdown_tol: float = 0.0,
-                 use_graph: bool = True, phase_times: bool = False, slot: int = 0, stream=None):
+                 use_graph: bool = True, phase_times: bool = False, slot: int = 0,
+                 true_residual: bool = False, stream=None):
         """Sketched Golub-Kahan (rtg_gk_solve): same problem and arguments as
         gmres_solve (device tensors).  Returns (X, SolveResult)."""
         dims = tuple(C_obs.shape)
@@ -254,7 +257,8 @@ class Handle:
             opts.mu_grid = grid.ctypes.data_as(C.POINTER(C.c_double))
             opts.n_mu = len(grid)
         opts.breakdown_tol = float(breakdown_tol)
-        opts.flags = (0 if use_graph else L.FLAG_NO_GRAPH) | (L.FLAG_PHASE_TIMES if phase_times else 0)
+        opts.flags = ((0 if use_graph else L.FLAG_NO_GRAPH) | (L.FLAG_PHASE_TIMES if phase_times else 0)
+                      | (L.FLAG_TRUE_RESIDUAL if true_residual else 0))
         opts.slot = int(slot)
         info = L.Info()
         rho = np.zeros(m + 1)
@@ -274,7 +278,8 @@ class Handle:
                      A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (),
                      X0=None, X=None, tol: float = 0.0, mu_grid=None, max_restarts: int = 0,
                      breakdown_tol: float = 0.0, use_graph: bool = True, phase_times: bool = False,
-                     slot: int = 0, bf16_basis: bool = False, stream=None) -> "PendingSolve":
+                     slot: int = 0, bf16_basis: bool = False, true_residual: bool = False,
+                     stream=None) -> "PendingSolve":
         """Queue a solve on `stream` without waiting (rtg_gmres_submit).  Solves
         in flight at once on different streams need different workspace slots;
         gmres_wait(pending) returns (X, SolveResult)."""
@@ -304,7 +309,8 @@ class Handle:
         opts.max_restarts = int(max_restarts)
         opts.breakdown_tol = float(breakdown_tol)
         opts.flags = ((0 if use_graph else L.FLAG_NO_GRAPH) | (L.FLAG_PHASE_TIMES if phase_times else 0)
-                      | (L.FLAG_BF16_BASIS if bf16_basis else 0))
+                      | (L.FLAG_BF16_BASIS if bf16_basis else 0)
+                      | (L.FLAG_TRUE_RESIDUAL if true_residual else 0))
         opts.slot = int(slot)
         L.check(self.lib.rtg_gmres_submit(self._h, a, na, b, nb, _shape(dims), dt, _ptr(C_obs), int(m),
                                           sk, C.c_uint64(seed), float(lam), _ptr(X0), _ptr(X),
@@ -315,7 +321,8 @@ class Handle:
 
     def gmres_solve_batched(self, problems: Sequence[dict], mu_grid=None, breakdown_tol: float = 0.0,
                             bf16_basis: bool = False, use_graph: bool = True, phase_times: bool = False,
-                            group_max: int = 0, stream=None):
+                            group_max: int = 0, true_residual: bool = False, max_restarts: int = 0,
+                            stream=None):
         """Batched form (rtg_gmres_solve_batched): every problem is a dict with
         C (device tensor), m, sketch_dims, seed, lam, and optionally A, B
         (factor lists), tol, X0, X.  All problems share C's dtype; each may
@@ -362,12 +369,13 @@ class Handle:
             opts.n_mu = len(grid)
         opts.breakdown_tol = float(breakdown_tol)
         opts.group_max = int(group_max)
+        opts.max_restarts = int(max_restarts)
         opts.flags = ((L.FLAG_BF16_BASIS if bf16_basis else 0) | (0 if use_graph else L.FLAG_NO_GRAPH) |
-                      (L.FLAG_PHASE_TIMES if phase_times else 0))
+                      (L.FLAG_PHASE_TIMES if phase_times else 0) | (L.FLAG_TRUE_RESIDUAL if true_residual else 0))
         infos = (L.Info * len(problems))()
         bufs = []
         for i, q in enumerate(problems):
-            rho = np.zeros(int(q["m"]) + 1)
+            rho = np.zeros(int(q["m"]) * (int(max_restarts) + 1) + 1)
             gcv = np.zeros(L.MAX_MU)
             infos[i].rho_hist = rho.ctypes.data_as(C.POINTER(C.c_double))
             infos[i].gcv = gcv.ctypes.data_as(C.POINTER(C.c_double))
@@ -390,11 +398,7 @@ class Handle:
         gcv = np.zeros(L.MAX_MU)
         info.gcv = gcv.ctypes.data_as(C.POINTER(C.c_double))
         L.check(self.lib.rtg_gmres_wait(self._h, pend.slot, C.byref(info)))
-        grid = pend.grid
-        res = SolveResult(info.iters, info.restarts, bool(info.breakdown), bool(info.converged),
-                          info.beta, info.mu, info.rho_final, rho[:info.iters].copy(),
-                          gcv[:len(grid)].copy() if (grid is not None and pend.lam < 0) else None,
-                          info.elapsed_ms, info.device_status, info.launches)
+        res = _solve_result(info, rho, gcv, pend.grid, pend.lam)
         if pend.phase_times:
             res.phase_ms = {k: info.phase_ms[i] for i, k in enumerate(L.PHASES)}
             res.phase_launches = {k: info.phase_launches[i] for i, k in enumerate(L.PHASES)}
@@ -405,7 +409,8 @@ def _solve_result(info, rho, gcv, grid, lam):
     return SolveResult(info.iters, info.restarts, bool(info.breakdown), bool(info.converged),
                        info.beta, info.mu, info.rho_final, rho[:info.iters].copy(),
                        gcv[:len(grid)].copy() if (grid is not None and lam < 0) else None,
-                       info.elapsed_ms, info.device_status, info.launches)
+                       info.elapsed_ms, info.device_status, info.launches,
+                       true_rel_resid=info.true_rel_resid, true_rel_resid_theta=info.true_rel_resid_theta)
 
 
 @dataclasses.dataclass

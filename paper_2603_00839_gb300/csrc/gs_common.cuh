@@ -625,12 +625,22 @@ __device__ inline void givens_step(const Work& w, const StepOpts& o) {
     const bool conv = finite && rho <= tol;
     if (conv || breakdown) ctl->converged = 1;
     // a nonzero status (a bounded wait that gave up upstream) ends the solve
-    if (!finite || breakdown || conv || J + 1 >= w.m || ctl->status != 0) ctl->stop = 1;
+    if (!finite || breakdown || conv || ctl->status != 0) {
+      ctl->stop = 1;
+    } else if (J + 1 >= w.m) {
+      // end of a cycle: restart from the least-squares iterate while cycles
+      // remain (the body's restart kernels run when rs_skip is 0), else stop
+      if (ctl->cycle + 1 < w.cycles) ctl->rs_skip = 0;
+      else ctl->stop = 1;
+    }
   }
+  // the body runs at most m times per cycle
   const int loops = ++ctl->loops;
-  if (loops > w.m) {
+  const int cap = w.m * w.cycles;
+  if (loops > cap) {
     ctl->stop = 1;
-    if (o.use_cond && loops > w.m + 1 && ctl->status == 0) ctl->status = RTG_ERR_TIMEOUT;
+    ctl->rs_skip = 1;
+    if (o.use_cond && loops > cap + 1 && ctl->status == 0) ctl->status = RTG_ERR_TIMEOUT;
   }
   set_cond(o, !ctl->stop, ctl);
 }

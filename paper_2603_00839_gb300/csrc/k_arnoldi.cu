@@ -43,11 +43,13 @@ int gs_grid(int64_t d) {
 // chain's partial sketches; pass 1: one Arnoldi step's Gram-Schmidt
 // reduction on S (s . Q_i, s . s and the new Gram row) and its finish.
 template <typename T>
-__global__ void __launch_bounds__(GS_THREADS) k_gs_pass(Work w0, int pass, StepOpts o0) {
+__global__ void __launch_bounds__(GS_THREADS) k_gs_pass(Work w0, int pass, StepOpts o0, const int* gate) {
   const int64_t bo = bidx(w0.b).off;
   const Work w = w0.at(bo);
   const StepOpts o = o0.at(bo);
   Ctl* ctl = w.ctl;
+  gate = bsh(gate, bo);
+  if (gate != nullptr && *gate) return;
   if (ctl->stop) return;
   const int J = (pass == 0) ? -1 : ctl->j;
   const int d = w.d;
@@ -87,11 +89,13 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(Work w0, int pass, StepO
 
 // V_0 = src / beta, Q_0 = S / beta
 template <typename T>
-__global__ void k_start_scale(Work w0, PtrRef srcr0) {
+__global__ void k_start_scale(Work w0, PtrRef srcr0, const int* gate) {
   const int64_t bo = bidx(w0.b).off;
   const Work w = w0.at(bo);
   const PtrRef srcr = srcr0.at(bo);
   const Ctl* ctl = w.ctl;
+  gate = bsh(gate, bo);
+  if (gate != nullptr && *gate) return;
   if (ctl->stop) return;
   const T* src = srcr.get<const T>();
   const T inv = static_cast<T>(1.0 / ctl->beta);
@@ -236,15 +240,19 @@ __global__ void k_update(Work w0, StepOpts o0) {
   }
 }
 
-__global__ void k_reset(Work w0, int new_cycle, unsigned* group_left) {
+// new_cycle = 0: start of a solve; 1: start of a restarted cycle (gated by
+// rs_skip inside the step body: it keeps the body count, the lock-step
+// count of running problems and the restart flag, which the restart
+// sequence clears last).
+__global__ void k_reset(Work w0, int new_cycle, unsigned* group_left, const int* gate) {
   const BIdx bi = bidx(w0.b);
   Ctl* ctl = bsh(w0.ctl, bi.off);
+  gate = bsh(gate, bi.off);
+  if (gate != nullptr && *gate) return;
   unsigned* counter = bsh(w0.counter, bi.off);
-  if (group_left != nullptr && bi.p == 0) *group_left = static_cast<unsigned>(w0.b.n);
   // last-block counters wrap to zero by themselves; clearing them here also
   // recovers from a solve that ended inside a kernel
   for (int i = 0; i < 8; ++i) counter[i] = 0u;
-  ctl->counted = 0;
   ctl->j = 0;
   ctl->stop = 0;
   ctl->breakdown = 0;
@@ -252,11 +260,14 @@ __global__ void k_reset(Work w0, int new_cycle, unsigned* group_left) {
   ctl->skip_update = 0;
   ctl->pre2 = 0.0;
   ctl->hnext = 0.0;
-  ctl->loops = 0;
   ctl->givens = 0;
   if (new_cycle) {
     ctl->cycle += 1;
   } else {
+    if (group_left != nullptr && bi.p == 0) *group_left = static_cast<unsigned>(w0.b.n);
+    ctl->counted = 0;
+    ctl->loops = 0;
+    ctl->rs_skip = 1;
     ctl->status = 0;
     ctl->iters_total = 0;
     ctl->cycle = 0;
@@ -264,6 +275,8 @@ __global__ void k_reset(Work w0, int new_cycle, unsigned* group_left) {
     ctl->beta = 0.0;
     ctl->rho = 1.0;
     ctl->mu = 0.0;
+    ctl->true_rr = -1.0;
+    ctl->true_th = -1.0;
   }
 }
 
@@ -273,8 +286,18 @@ static unsigned ew_grid(int64_t n) {
   return static_cast<unsigned>(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s, unsigned* group_left) {
-  k_reset<<<dim3(1, 1, w.b.n), 1, 0, s>>>(w, new_cycle, group_left);
+cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s, unsigned* group_left, const int* gate) {
+  k_reset<<<dim3(1, 1, w.b.n), 1, 0, s>>>(w, new_cycle, group_left, gate);
+  return cudaGetLastError();
+}
+
+__global__ void k_restart_done(Work w0) {
+  Ctl* ctl = bsh(w0.ctl, bidx(w0.b).off);
+  ctl->rs_skip = 1;
+}
+
+cudaError_t launch_restart_done(const Work& w, cudaStream_t s) {
+  k_restart_done<<<dim3(1, 1, w.b.n), 1, 0, s>>>(w);
   return cudaGetLastError();
 }
 
@@ -299,11 +322,13 @@ __device__ __forceinline__ uint4 f_to_bf8(const float* f) {
 }
 
 template <bool SRC_BF16>
-__global__ void k_start_scale_bf16(Work w0, PtrRef srcr0) {
+__global__ void k_start_scale_bf16(Work w0, PtrRef srcr0, const int* gate) {
   const int64_t bo = bidx(w0.b).off;
   const Work w = w0.at(bo);
   const PtrRef srcr = srcr0.at(bo);
   const Ctl* ctl = w.ctl;
+  gate = bsh(gate, bo);
+  if (gate != nullptr && *gate) return;
   if (ctl->stop) return;
   const float fi = static_cast<float>(1.0 / ctl->beta);
   uint4* V8 = static_cast<uint4*>(w.V);
@@ -585,29 +610,29 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_ring(Work w0, StepOpts o0
 }
 
 cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fused, cudaStream_t s,
-                         int sdtype) {
+                         int sdtype, const int* gate) {
   const unsigned g = static_cast<unsigned>(gs_grid(w.d)), nb = static_cast<unsigned>(w.b.n);
   if (sdtype < 0) sdtype = w.dtype;
   if (w.vdtype == RTG_BF16) {
-    if (!fused) k_gs_pass<float><<<dim3(g, 1, nb), GS_THREADS, 0, s>>>(w, 0, o);
-    if (sdtype == RTG_BF16) k_start_scale_bf16<true><<<dim3(ew_grid(w.n / 8 + 1), 1, nb), 256, 0, s>>>(w, src);
-    else k_start_scale_bf16<false><<<dim3(ew_grid(w.n / 8 + 1), 1, nb), 256, 0, s>>>(w, src);
+    if (!fused) k_gs_pass<float><<<dim3(g, 1, nb), GS_THREADS, 0, s>>>(w, 0, o, gate);
+    if (sdtype == RTG_BF16) k_start_scale_bf16<true><<<dim3(ew_grid(w.n / 8 + 1), 1, nb), 256, 0, s>>>(w, src, gate);
+    else k_start_scale_bf16<false><<<dim3(ew_grid(w.n / 8 + 1), 1, nb), 256, 0, s>>>(w, src, gate);
     return cudaGetLastError();
   }
   if (w.dtype == RTG_F64) {
-    if (!fused) k_gs_pass<double><<<dim3(g, 1, nb), GS_THREADS, 0, s>>>(w, 0, o);
-    k_start_scale<double><<<dim3(ew_grid(w.n), 1, nb), 256, 0, s>>>(w, src);
+    if (!fused) k_gs_pass<double><<<dim3(g, 1, nb), GS_THREADS, 0, s>>>(w, 0, o, gate);
+    k_start_scale<double><<<dim3(ew_grid(w.n), 1, nb), 256, 0, s>>>(w, src, gate);
   } else {
-    if (!fused) k_gs_pass<float><<<dim3(g, 1, nb), GS_THREADS, 0, s>>>(w, 0, o);
-    k_start_scale<float><<<dim3(ew_grid(w.n / 4 + 1), 1, nb), 256, 0, s>>>(w, src);
+    if (!fused) k_gs_pass<float><<<dim3(g, 1, nb), GS_THREADS, 0, s>>>(w, 0, o, gate);
+    k_start_scale<float><<<dim3(ew_grid(w.n / 4 + 1), 1, nb), 256, 0, s>>>(w, src, gate);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s) {
   const dim3 g(static_cast<unsigned>(gs_grid(w.d)), 1, static_cast<unsigned>(w.b.n));
-  if (w.dtype == RTG_F64) k_gs_pass<double><<<g, GS_THREADS, 0, s>>>(w, 1, o);
-  else k_gs_pass<float><<<g, GS_THREADS, 0, s>>>(w, 1, o);
+  if (w.dtype == RTG_F64) k_gs_pass<double><<<g, GS_THREADS, 0, s>>>(w, 1, o, nullptr);
+  else k_gs_pass<float><<<g, GS_THREADS, 0, s>>>(w, 1, o, nullptr);
   return cudaGetLastError();
 }
 

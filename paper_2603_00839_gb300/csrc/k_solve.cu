@@ -12,7 +12,7 @@
 // (k+1 minus k plus mu tr((R_mu^T R_mu)^{-1})).  One CTA per candidate mu;
 // the last CTA to finish picks the smallest GCV (ties: the larger mu).
 // Everything here is FP64.
-#include "rtg_internal.cuh"
+#include "gs_common.cuh"
 
 namespace rtg {
 
@@ -58,12 +58,14 @@ __device__ void back_subst(const double* U, int ldu, const double* rinv, double*
 // inverse R_mu^{-1} is built in it.  With in_smem the working set is the
 // CTA's dynamic shared memory, else the per-CTA global scratch.
 __global__ void __launch_bounds__(TK_THREADS)
-k_tikhonov(Work w0, const SolveDesc* desc0, int mode, double* scratch0, int in_smem) {
+k_tikhonov(Work w0, const SolveDesc* desc0, int mode, double* scratch0, int in_smem, const int* gate) {
   const int64_t bo = bidx(w0.b).off;
   const Work w = w0.at(bo);
   const SolveDesc* desc = bsh(desc0, bo);
   double* scratch = bsh(scratch0, bo);
   Ctl* ctl = w.ctl;
+  gate = bsh(gate, bo);
+  if (gate != nullptr && *gate) return;
   const int k = ctl->j;
   const int m = w.m, ld = m + 1;
   __shared__ double red[TK_WARPS][kMaxK + 1];   // per-warp partial dot products of a step
@@ -226,18 +228,21 @@ k_tikhonov(Work w0, const SolveDesc* desc0, int mode, double* scratch0, int in_s
   if (tid == 0) ctl->mu = mu;
 }
 
-// X = X0 + sum_{i<k} y_i V_i  (Eq. 10S)
+// X = X0 + sum_{i<k} y_i V_i  (Eq. 10S); after a restart X holds the iterate
+// the cycle started from and takes the place of X0 (elementwise in place)
 template <typename T>
-__global__ void k_assemble(Work w0, PtrRef X0r0, PtrRef Xr0) {
+__global__ void k_assemble(Work w0, PtrRef X0r0, PtrRef Xr0, const int* gate) {
   const int64_t bo = bidx(w0.b).off;
   const Work w = w0.at(bo);
   const PtrRef X0r = X0r0.at(bo), Xr = Xr0.at(bo);
+  gate = bsh(gate, bo);
+  if (gate != nullptr && *gate) return;
   const int k = w.ctl->j;
   __shared__ T ys[kMaxK];
   for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = static_cast<T>(w.y[i]);
   __syncthreads();
-  const T* X0 = X0r.get<const T>();
   T* X = Xr.get<T>();
+  const T* X0 = w.ctl->cycle > 0 ? X : X0r.get<const T>();
   const T* V = static_cast<const T*>(w.V);
   const int64_t n = w.n;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
@@ -264,6 +269,8 @@ __global__ void k_finalize(Work w0, InfoDev* info0) {
     info->beta = c->beta0;
     info->mu = c->mu;
     info->rho_final = c->rho;
+    info->true_rel_resid = c->true_rr;
+    info->true_rel_resid_theta = c->true_th;
   }
   for (int i = t; i < c->iters_total && i < kMaxK; i += blockDim.x) info->rho_hist[i] = w.rho_hist[i];
   for (int i = t; i < kMaxMu; i += blockDim.x) info->gcv[i] = w.gcv[i];
@@ -299,7 +306,7 @@ static unsigned ew_grid(int64_t n) {
   return static_cast<unsigned>(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s) {
+cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s, const int* gate) {
   const unsigned blocks = (f.mode == 2) ? static_cast<unsigned>(f.n_mu) : 1u;
   const size_t sm = static_cast<size_t>(tk_scratch_doubles(w.m)) * sizeof(double);
   const int in_smem = sm <= size_t(200) * 1024 ? 1 : 0;
@@ -308,21 +315,24 @@ cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s) 
     if (e != cudaSuccess) return e;
   }
   k_tikhonov<<<dim3(blocks, 1, w.b.n), TK_THREADS, in_smem ? sm : 0, s>>>(w, f.desc, f.mode,
-                                                                         w.ysel + kMaxMu * w.m, in_smem);
+                                                                         w.ysel + kMaxMu * w.m, in_smem, gate);
   return cudaGetLastError();
 }
 
-// X = X0 + sum_{i<k} y_i V_i with V in BF16 (FP32 arithmetic, 8 values per load)
-__global__ void k_assemble_bf16(Work w0, PtrRef X0r0, PtrRef Xr0) {
+// X = X0 + sum_{i<k} y_i V_i with V in BF16 (FP32 arithmetic, 8 values per load);
+// X0 after a restart as in k_assemble
+__global__ void k_assemble_bf16(Work w0, PtrRef X0r0, PtrRef Xr0, const int* gate) {
   const int64_t bo = bidx(w0.b).off;
   const Work w = w0.at(bo);
   const PtrRef X0r = X0r0.at(bo), Xr = Xr0.at(bo);
+  gate = bsh(gate, bo);
+  if (gate != nullptr && *gate) return;
   const int k = w.ctl->j;
   __shared__ float ys[kMaxK];
   for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = static_cast<float>(w.y[i]);
   __syncthreads();
-  const float* X0 = X0r.get<const float>();
   float* X = Xr.get<float>();
+  const float* X0 = w.ctl->cycle > 0 ? X : X0r.get<const float>();
   const uint4* V8 = static_cast<const uint4*>(w.V);
   const int64_t n8 = w.n / 8;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n8;
@@ -344,13 +354,85 @@ __global__ void k_assemble_bf16(Work w0, PtrRef X0r0, PtrRef Xr0) {
   }
 }
 
-cudaError_t launch_assemble(const Work& w, PtrRef X0, PtrRef X, cudaStream_t s) {
+cudaError_t launch_assemble(const Work& w, PtrRef X0, PtrRef X, cudaStream_t s, const int* gate) {
   if (w.vdtype == RTG_BF16) {
-    k_assemble_bf16<<<dim3(ew_grid(w.n / 8 + 1), 1, w.b.n), 256, 0, s>>>(w, X0, X);
+    k_assemble_bf16<<<dim3(ew_grid(w.n / 8 + 1), 1, w.b.n), 256, 0, s>>>(w, X0, X, gate);
     return cudaGetLastError();
   }
-  if (w.dtype == RTG_F64) k_assemble<double><<<dim3(ew_grid(w.n), 1, w.b.n), 256, 0, s>>>(w, X0, X);
-  else k_assemble<float><<<dim3(ew_grid(w.n), 1, w.b.n), 256, 0, s>>>(w, X0, X);
+  if (w.dtype == RTG_F64) k_assemble<double><<<dim3(ew_grid(w.n), 1, w.b.n), 256, 0, s>>>(w, X0, X, gate);
+  else k_assemble<float><<<dim3(ew_grid(w.n), 1, w.b.n), 256, 0, s>>>(w, X0, X, gate);
+  return cudaGetLastError();
+}
+
+// Final residual of the Block GMRES algorithm (Section 4.4, its last steps:
+// R_m = C - A *_N X_m and its Theta-norm).  R (in the V_0 slot) and S(R) (in
+// Spart) come from the apply and sketch launched before this kernel.  Each
+// block sums R.R, C.C (grid-stride over n) and S(R).S(R) (over d) in
+// float-float (FP32) or FP64, writes one row of three partial sums, and the
+// last block adds the rows in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_true_resid(Work w0, PtrRef Cr0) {
+  const int64_t bo = bidx(w0.b).off;
+  const Work w = w0.at(bo);
+  const T* C = Cr0.at(bo).get<const T>();
+  const T* R = static_cast<const T*>(w.V);
+  const T* SR = static_cast<const T*>(w.Spart);
+  __shared__ double red[8][3];
+  __shared__ int am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  DotAcc<T> rr, cc, ss;
+  for (int64_t o = t0; o < w.n; o += stride) {
+    const T r = R[o], c = C[o];
+    rr.add(r, r);
+    cc.add(c, c);
+  }
+  for (int64_t o = t0; o < w.d; o += stride) {
+    const T v = SR[o];
+    ss.add(v, v);
+  }
+  const double a = rr.warp_total(), b = cc.warp_total(), c = ss.warp_total();
+  if (lane == 0) {
+    red[warp][0] = a;
+    red[warp][1] = b;
+    red[warp][2] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double v = 0.0;
+    for (int u = 0; u < 8; ++u) v += red[u][threadIdx.x];
+    w.part[static_cast<int64_t>(blockIdx.x) * 3 + threadIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicInc(w.counter + 1, gridDim.x - 1) == gridDim.x - 1);
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  if (warp == 0) {   // lane l sums rows l, l + 32, ...; then a fixed warp tree
+    double s3[3] = {0.0, 0.0, 0.0};
+    for (unsigned r = lane; r < gridDim.x; r += 32)
+      for (int q = 0; q < 3; ++q) s3[q] += __ldcg(w.part + static_cast<int64_t>(r) * 3 + q);
+    for (int q = 0; q < 3; ++q) s3[q] = warp_sum(s3[q]);
+    if (lane == 0) {
+      Ctl* ctl = w.ctl;
+      ctl->true_rr = s3[1] > 0.0 ? sqrt(s3[0] / s3[1]) : (s3[0] > 0.0 ? INFINITY : 0.0);
+      ctl->true_th = ctl->beta0 > 0.0 ? sqrt(s3[2]) / ctl->beta0 : (s3[2] > 0.0 ? INFINITY : 0.0);
+    }
+  }
+}
+
+cudaError_t launch_true_resid(const Work& w, PtrRef C, cudaStream_t s) {
+  // rows of three partial sums must fit the partial-sum buffer
+  int64_t blocks = ew_grid(w.n / 4 + 1);
+  const int64_t cap = static_cast<int64_t>(w.part_rows) * (2 * w.m + 4) / 3;
+  if (blocks > cap) blocks = cap;
+  if (blocks > 304) blocks = 304;
+  if (blocks < 1) blocks = 1;
+  const dim3 g(static_cast<unsigned>(blocks), 1, static_cast<unsigned>(w.b.n));
+  if (w.dtype == RTG_F64) k_true_resid<double><<<g, 256, 0, s>>>(w, C);
+  else k_true_resid<float><<<g, 256, 0, s>>>(w, C);
   return cudaGetLastError();
 }
 

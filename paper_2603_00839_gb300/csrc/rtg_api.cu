@@ -729,6 +729,38 @@ rtg_status enqueue_step(const OpHolder& op, const SketchPlan& sp, const Work& w,
   return RTG_OK;
 }
 
+// Restart sequence at the end of the step body of a plan with restarts
+// (GMRES restarted from the least-squares iterate): every kernel returns at
+// once unless the body's Givens block ended a cycle with cycles left
+// (ctl->rs_skip == 0).  y = argmin ||beta e1 - Hbar y|| (Eq. 11S), X = X_0 + V y,
+// R_0 = C - Phi(X) into the V_0 slot, a new cycle (reset, beta = ||R_0||_Theta,
+// V_0 = R_0 / beta, the first sketched column), and rs_skip = 1 again.
+rtg_status enqueue_restart(SolvePlan& P, const StepOpts& so, cudaStream_t s) {
+  Work& w = P.w;
+  const int* gate = &w.ctl->rs_skip;
+  FinishOpts f{};
+  f.desc = P.desc_dev;
+  f.n_mu = 0;
+  f.mode = 0;
+  CK(launch_tikhonov(w, f, s, gate));
+  PtrRef X0 = P.has_x0 ? desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X0)) : PtrRef{};
+  PtrRef X = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X));
+  PtrRef C = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->C));
+  CK(launch_assemble(w, X0, X, s, gate));
+  CK(launch_apply(P.op.op, P.dtype, X, ref(w.V), -1.0, 1.0, C, P.tA, P.tB, gate, s, P.dtype, P.vdtype, w.b));
+  CK(launch_reset(w, 1, s, nullptr, gate));
+  const bool fused = P.sp.fused_dots != 0;
+  SketchDots dots{&w, 0, so};
+  CK(launch_sketch(P.sp, P.sk, ref(w.V), fused ? w.S : w.Spart, fused ? &dots : nullptr, gate, s, P.vdtype, w.b));
+  CK(launch_start(w, ref(w.V), so, fused, s, P.vdtype, gate));
+  CK(launch_restart_done(w, s));
+  return RTG_OK;
+}
+
+int restart_launches(const OpPlan& op, const SketchPlan& sp, int dtype, int vdtype) {
+  return 2 + apply_launches(op, true, dtype, dtype, vdtype) + 1 + sketch_launches(sp) + (sp.fused_dots ? 1 : 2) + 1;
+}
+
 // Sketched Golub-Kahan (Algorithm 4): prologue U_0, alpha_0, V_0 and one step
 // (forward half: beta_{j+1}, U_{j+1}, Givens; backward half: alpha_{j+1}, V_{j+1}).
 rtg_status enqueue_gk_prologue(SolvePlan& P, const StepOpts& so, cudaStream_t s, PhaseTimer* pt = nullptr) {
@@ -814,10 +846,17 @@ rtg_status enqueue_epilogue(SolvePlan& P, cudaStream_t s, PhaseTimer* pt = nullp
     PhaseScope ps(pt, RTG_PHASE_TIKHONOV, -1, 1);
     CK(launch_tikhonov(P.w, f, s));
   }
-  PhaseScope ps(pt, RTG_PHASE_ASSEMBLE, -1, 2);
+  PhaseScope ps(pt, RTG_PHASE_ASSEMBLE, -1, P.launches_epi - 1);
   PtrRef X0 = P.has_x0 ? desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X0)) : PtrRef{};
   PtrRef X = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->X));
   CK(launch_assemble(P.w, X0, X, s));
+  if (P.true_resid) {   // R = C - Phi(X) into the V_0 slot (the basis is no longer needed), S(R), norms
+    PtrRef C = desc_ref(reinterpret_cast<const void* const*>(&P.desc_dev->C));
+    CK(launch_apply(P.op.op, P.dtype, X, ref(P.w.V), -1.0, 1.0, C, P.tA, P.tB, nullptr, s, P.dtype, P.dtype,
+                    P.w.b));
+    CK(launch_sketch(P.sp, P.sk, ref(P.w.V), P.w.Spart, nullptr, nullptr, s, P.dtype, P.w.b));
+    CK(launch_true_resid(P.w, C, s));
+  }
   CK(launch_finalize(P.w, P.info_dev, s));
   return RTG_OK;
 }
@@ -869,6 +908,7 @@ rtg_status build_branch(SolvePlan& P, cudaGraph_t g) {
     if (st == RTG_OK) {
       st = P.method == 1 ? enqueue_gk_step(P, so, cs2)
                          : enqueue_step(P.op, P.sp, P.w, P.dtype, P.tA, P.tB, P.sk, so, cs2);
+      if (st == RTG_OK && P.w.cycles > 1) st = enqueue_restart(P, so, cs2);
       cudaGraph_t bodyout = nullptr;
       e = cudaStreamEndCapture(cs2, &bodyout);
       if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture(body)");
@@ -913,6 +953,8 @@ struct PlanSpec {
   int mode, n_mu;
   bool has_x0, use_graph;
   int method = 0;   // 0 RTG-GMRES, 1 sketched Golub-Kahan
+  bool true_resid = false;   // epilogue computes C - Phi(X) and its norms
+  int cycles = 1;            // restarts + 1
 };
 
 // Factors of the adjoint operator: every mode matrix transposed (banded:
@@ -961,6 +1003,7 @@ rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDe
   P->use_graph = use_graph;
   P->sp = sp;
   P->method = ps.method;
+  P->true_resid = ps.true_resid;
   RK(build_op(A, nA, B, nB, shape, P->op));
   if (ps.method == 1) {
     TransposedFactors tA(A, nA), tB(B, nB);
@@ -1004,6 +1047,7 @@ rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDe
     CK(cudaMemset(P->mem.p, 0, bytes));
     carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk, vdtype, nU);
   }
+  P->w.cycles = ps.cycles;
   if (nbatch > 0) {
   } else if (ddev != nullptr) {   // descriptor and info record in a batch's buffers
     P->ext_desc = true;
@@ -1031,8 +1075,10 @@ rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDe
     P->launches_pro = P->launches_setup +
                       (has_x0 ? apply_launches(P->op.op, true, dtype, dtype, vdtype) : 0) +
                       sketch_launches(sp) + gs + 1;
-    P->launches_step = apply_launches(P->op.op, false, dtype, vdtype, vdtype) + sketch_launches(sp) + gs + 1;
-    P->launches_epi = 3;
+    P->launches_step = apply_launches(P->op.op, false, dtype, vdtype, vdtype) + sketch_launches(sp) + gs + 1 +
+                       (ps.cycles > 1 ? restart_launches(P->op.op, sp, dtype, vdtype) : 0);
+    P->launches_epi = 3 + (ps.true_resid ? apply_launches(P->op.op, true, dtype, dtype, dtype) +
+                                               sketch_launches(sp) + 1 : 0);
     if (ps.method == 1) {
       const int al = apply_launches(P->op.op, false, dtype, dtype, dtype);
       const int alT = apply_launches(P->opT.op, false, dtype, dtype, dtype);
@@ -1060,7 +1106,8 @@ void fill_info(const SolvePlan& P, const InfoDev& I, int mode, int n_mu, bool us
     for (int i = 0; i < I.iters && i < kMaxK; ++i) info->rho_hist[i] = I.rho_hist[i];
   if (info->gcv && mode == 2)
     for (int i = 0; i < n_mu; ++i) info->gcv[i] = I.gcv[i];
-  info->true_rel_resid = -1.0;
+  info->true_rel_resid = P.true_resid ? I.true_rel_resid : -1.0;
+  info->true_rel_resid_theta = P.true_resid ? I.true_rel_resid_theta : -1.0;
   info->elapsed_ms = ms;
   info->device_status = I.status;
   info->launches = P.launches_pro + P.launches_epi + (use_graph ? I.iters : P.direct_steps) * P.launches_step;
@@ -1350,7 +1397,12 @@ static rtg_status submit_impl(int method, rtg_handle h, const rtg_factor* A, int
   rtg_opts opts{};
   if (opts_in) opts = *opts_in;
   if (!(opts.tol >= 0.0) || !std::isfinite(opts.tol)) return fail(RTG_ERR_INVALID_ARG, "opts.tol must be finite and >= 0");
-  if (opts.max_restarts != 0) return fail(RTG_ERR_UNSUPPORTED, "restarts are not supported on the GPU path (max_restarts=%d)", opts.max_restarts);
+  if (opts.max_restarts < 0) return fail(RTG_ERR_INVALID_ARG, "opts.max_restarts=%d must be >= 0", opts.max_restarts);
+  if (opts.max_restarts > 0 && method == 1)
+    return fail(RTG_ERR_UNSUPPORTED, "restarts are for rtg_gmres_solve (max_restarts=%d)", opts.max_restarts);
+  if (int64_t(m) * (opts.max_restarts + 1) > kMaxK)
+    return fail(RTG_ERR_INVALID_ARG, "m * (max_restarts + 1) = %lld exceeds %d steps",
+                (long long)m * (opts.max_restarts + 1), kMaxK);
   if (!(opts.breakdown_tol >= 0.0)) return fail(RTG_ERR_INVALID_ARG, "opts.breakdown_tol must be >= 0");
   if (opts.slot < 0 || opts.slot >= RTG_MAX_SLOTS) return fail(RTG_ERR_INVALID_ARG, "opts.slot=%d not in 0..%d", opts.slot, RTG_MAX_SLOTS - 1);
   const int mode = lambda > 0 ? 1 : (lambda == 0 ? 0 : 2);
@@ -1393,6 +1445,10 @@ static rtg_status submit_impl(int method, rtg_handle h, const rtg_factor* A, int
   append_bytes(key, &opts.slot, sizeof opts.slot);
   append_bytes(key, &vdtype, sizeof vdtype);
   append_bytes(key, &method, sizeof method);
+  const bool true_resid = (opts.flags & RTG_FLAG_TRUE_RESIDUAL) != 0;
+  key.push_back(true_resid ? 't' : '-');
+  const int cycles = opts.max_restarts + 1;
+  append_bytes(key, &cycles, sizeof cycles);
 
   rtg_context::Pending& pend = h->pending[opts.slot];
   if (pend.active) return fail(RTG_ERR_INVALID_ARG, "slot %d has a submitted solve that was not waited for", opts.slot);
@@ -1414,7 +1470,8 @@ static rtg_status submit_impl(int method, rtg_handle h, const rtg_factor* A, int
     // does so only while no other solve of this handle is in flight.
     for (const auto& q : h->pending)
       if (q.active) CK(cudaStreamSynchronize(q.stream));
-    PlanSpec ps{A, nA, B, nB, shape, dtype, vdtype, n, m, sp, mode, nmu_key, has_x0, use_graph, method};
+    PlanSpec ps{A, nA, B, nB, shape, dtype, vdtype, n, m, sp, mode, nmu_key, has_x0, use_graph, method,
+                true_resid, cycles};
     std::shared_ptr<SolvePlan> np;
     RK(make_plan(ps, nullptr, nullptr, nullptr, nullptr, &np));
     P = np.get();
@@ -1453,6 +1510,10 @@ static rtg_status submit_impl(int method, rtg_handle h, const rtg_factor* A, int
       return fail(RTG_ERR_INVALID_ARG, "X0 must be 16-byte aligned for this operator");
     if (P->vdtype == RTG_BF16 && reinterpret_cast<uintptr_t>(D.C) % 16 != 0)
       return fail(RTG_ERR_INVALID_ARG, "C must be 16-byte aligned with RTG_FLAG_BF16_BASIS");
+    if ((P->true_resid || P->w.cycles > 1) && apply_uses_st(P->op.op, dtype, dtype, P->vdtype) &&
+        reinterpret_cast<uintptr_t>(D.X) % 16 != 0)
+      return fail(RTG_ERR_INVALID_ARG, "X must be 16-byte aligned for this operator with "
+                                       "RTG_FLAG_TRUE_RESIDUAL or restarts");
   }
   D.key[0] = seed;
   D.key[1] = 0;
@@ -1491,11 +1552,16 @@ static rtg_status submit_impl(int method, rtg_handle h, const rtg_factor* A, int
     RK(group([&] { return P->method == 1 ? enqueue_gk_prologue(*P, so, s, pt) : enqueue_prologue(*P, so, s, pt); }));
     RK(stopped());
     int steps = 0;
-    while (steps < m && *P->stop_host == 0) {
+    while (steps < m * P->w.cycles && *P->stop_host == 0) {
       const int j = steps++;
       RK(group([&] {
-        return P->method == 1 ? enqueue_gk_step(*P, so, s, pt, j)
-                              : enqueue_step(P->op, P->sp, P->w, dtype, P->tA, P->tB, P->sk, so, s, pt, j);
+        if (P->method == 1) return enqueue_gk_step(*P, so, s, pt, j);
+        RK(enqueue_step(P->op, P->sp, P->w, dtype, P->tA, P->tB, P->sk, so, s, pt, j));
+        if (P->w.cycles > 1) {
+          PhaseScope rs(pt, RTG_PHASE_INIT, j, restart_launches(P->op.op, P->sp, dtype, P->vdtype));
+          RK(enqueue_restart(*P, so, s));
+        }
+        return RTG_OK;
       }));
       RK(stopped());
     }
@@ -1566,7 +1632,7 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
   RK(check_dtype(dtype));
   rtg_opts opts{};
   if (opts_in) opts = *opts_in;
-  if (opts.max_restarts != 0) return fail(RTG_ERR_UNSUPPORTED, "restarts are not supported on the GPU path");
+  if (opts.max_restarts < 0) return fail(RTG_ERR_INVALID_ARG, "opts.max_restarts=%d must be >= 0", opts.max_restarts);
   const bool use_graph = !(opts.flags & (RTG_FLAG_NO_GRAPH | RTG_FLAG_PHASE_TIMES));
   const bool phase_times = (opts.flags & RTG_FLAG_PHASE_TIMES) != 0;
   if (!(opts.breakdown_tol >= 0.0)) return fail(RTG_ERR_INVALID_ARG, "opts.breakdown_tol must be >= 0");
@@ -1581,6 +1647,9 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
   std::string bkey;
   if (opts.group_max < 0) return fail(RTG_ERR_INVALID_ARG, "opts.group_max must be >= 0");
   append_bytes(bkey, &opts.group_max, sizeof opts.group_max);
+  const int bflags = opts.flags & RTG_FLAG_TRUE_RESIDUAL;
+  append_bytes(bkey, &bflags, sizeof bflags);
+  append_bytes(bkey, &opts.max_restarts, sizeof opts.max_restarts);
   append_bytes(bkey, &dtype, sizeof dtype);
   append_bytes(bkey, &vdtype, sizeof vdtype);
   for (int i = 0; i < nprob; ++i) {
@@ -1590,6 +1659,8 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
     RK(check_factors(q.A_factors, q.nA, q.shape, "A_factors"));
     RK(check_factors(q.B_factors, q.nB, q.shape, "B_factors"));
     if (q.m < 1 || q.m > kMaxK) return fail(RTG_ERR_INVALID_ARG, "problem %d: m=%d not in 1..%d", i, q.m, kMaxK);
+    if (int64_t(q.m) * (opts.max_restarts + 1) > kMaxK)
+      return fail(RTG_ERR_INVALID_ARG, "problem %d: m * (max_restarts + 1) exceeds %d steps", i, kMaxK);
     if (q.C == nullptr || q.X == nullptr) return fail(RTG_ERR_INVALID_ARG, "problem %d: C and X must not be NULL", i);
     if (!is_device_ptr(q.C) || !is_device_ptr(q.X) || (q.X0 && !is_device_ptr(q.X0)))
       return fail(RTG_ERR_INVALID_ARG, "problem %d: batched solves take device pointers", i);
@@ -1611,7 +1682,8 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
       return fail(RTG_ERR_UNSUPPORTED, "problem %d: RTG_FLAG_BF16_BASIS needs mode 1 sketched", i);
     const int nmu = mode == 2 ? opts.n_mu : 0;
     specs[i] = PlanSpec{q.A_factors, q.nA, q.B_factors, q.nB, q.shape, dtype, vdtype, n, q.m, sp, mode, nmu,
-                        q.X0 != nullptr, true};
+                        q.X0 != nullptr, true, 0, (opts.flags & RTG_FLAG_TRUE_RESIDUAL) != 0,
+                        opts.max_restarts + 1};
     std::string key = op_key(q.A_factors, q.nA, q.B_factors, q.nB, q.shape);
     append_bytes(key, &q.m, sizeof q.m);
     append_bytes(key, sp.sdims, sizeof sp.sdims);
@@ -1684,6 +1756,10 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
       return fail(RTG_ERR_INVALID_ARG, "problem %d: X0 must be 16-byte aligned for this operator", i);
     if (vdtype == RTG_BF16 && reinterpret_cast<uintptr_t>(q.C) % 16 != 0)
       return fail(RTG_ERR_INVALID_ARG, "problem %d: C must be 16-byte aligned with RTG_FLAG_BF16_BASIS", i);
+    if ((P.true_resid || P.w.cycles > 1) && apply_uses_st(P.op.op, dtype, dtype, vdtype) &&
+        reinterpret_cast<uintptr_t>(q.X) % 16 != 0)
+      return fail(RTG_ERR_INVALID_ARG, "problem %d: X must be 16-byte aligned for this operator with "
+                                       "RTG_FLAG_TRUE_RESIDUAL", i);
     fill_desc(dh[BP->slot_of[i]], q.C, q.X0, q.X, q.seed, q.tol, opts.breakdown_tol, dtype, q.lam,
               P.mode == 2 ? opts.n_mu : 0, opts.mu_grid);
   }
@@ -1726,9 +1802,16 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
       RK(group([&] { return enqueue_prologue(P, so, s, pt); }));
       RK(left());
       int steps = 0;
-      while (steps < P.w.m && *P.stop_host != 0) {
+      while (steps < P.w.m * P.w.cycles && *P.stop_host != 0) {
         const int j = steps++;
-        RK(group([&] { return enqueue_step(P.op, P.sp, P.w, dtype, P.tA, P.tB, P.sk, so, s, pt, j); }));
+        RK(group([&] {
+          RK(enqueue_step(P.op, P.sp, P.w, dtype, P.tA, P.tB, P.sk, so, s, pt, j));
+          if (P.w.cycles > 1) {
+            PhaseScope rs(pt, RTG_PHASE_INIT, j, restart_launches(P.op.op, P.sp, dtype, vdtype));
+            RK(enqueue_restart(P, so, s));
+          }
+          return RTG_OK;
+        }));
         RK(left());
       }
       P.direct_steps = steps;

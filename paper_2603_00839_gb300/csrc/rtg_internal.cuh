@@ -103,6 +103,7 @@ struct Ctl {
   int loops;        // executions of the step body since the reset (hard cap m+1)
   int givens;       // a finished Hessenberg column awaits its Givens update
   int counted;      // lock-step batch: this problem's stop has been counted
+  int rs_skip;      // 1 unless a restart is pending: the body's restart kernels return at once
   double beta;      // ||R_0||_Theta of this cycle
   double beta0;     // of the first cycle (scale of rho)
   double rho;       // last rho_j
@@ -111,6 +112,8 @@ struct Ctl {
   double mu;        // chosen regularisation
   double gcv_best;
   double gk_scale;  // Golub-Kahan: the norm the next update divides by
+  double true_rr;   // ||C - Phi(X)||_F / ||C||_F of the returned X (true-residual epilogue)
+  double true_th;   // ||C - Phi(X)||_Theta / ||R_0||_Theta of the first cycle
 };
 
 // Per-call parameters of a solve, read by the graph's kernels.
@@ -130,7 +133,7 @@ struct SolveDesc {
 // Host-visible summary written at the end of a solve (one D2H copy).
 struct InfoDev {
   int iters, restarts, breakdown, converged, status, k, pad0, pad1;
-  double beta, mu, rho_final, true_rel_resid;
+  double beta, mu, rho_final, true_rel_resid, true_rel_resid_theta;
   double rho_hist[kMaxK];
   double gcv[kMaxMu];
 };
@@ -148,6 +151,7 @@ struct Work {
   int64_t n;                   // elements per tensor
   int d;                       // sketch size prod(s'_k)
   int m;                       // Krylov dimension
+  int cycles = 1;              // most Arnoldi cycles of a solve (restarts + 1)
   void* V;                     // (m+1) * n
   void* W;                     // n
   void* U;                     // Golub-Kahan: ring of 2 left-basis tensors (else null)
@@ -381,13 +385,18 @@ struct SketchDots {
 };
 // pass 0 on w.Spart (unless the sketch already ran it) and the scaling V_0, Q_0
 // src has type sdtype (dtype, or vdtype when it is the V_0 slot).
+// gate (optional): device flag; the kernels return at once while it is nonzero
+// (the restart sequence passes &ctl->rs_skip)
 cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fused, cudaStream_t s,
-                         int sdtype = -1);
+                         int sdtype = -1, const int* gate = nullptr);
 cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s);
 int gs_grid(int64_t d);
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s);
 // group_left (lock-step batch): set to the number of problems
-cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s, unsigned* group_left = nullptr);
+cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s, unsigned* group_left = nullptr,
+                         const int* gate = nullptr);
+// end of a restart sequence: rs_skip = 1 again
+cudaError_t launch_restart_done(const Work& w, cudaStream_t s);
 
 // k_solve.cu: projected Tikhonov / GCV, assembly and the info summary.
 struct FinishOpts {
@@ -395,9 +404,15 @@ struct FinishOpts {
   int n_mu;                  // structural: GCV blocks (lambda < 0)
   int mode;                  // 0: least squares, 1: fixed mu, 2: GCV
 };
-cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s);
-cudaError_t launch_assemble(const Work& w, PtrRef X0, PtrRef X, cudaStream_t s);
+cudaError_t launch_tikhonov(const Work& w, const FinishOpts& f, cudaStream_t s, const int* gate = nullptr);
+// X = X0 + sum_j y_j V_j; after a restart (ctl->cycle > 0) X itself is the X0 (it holds the
+// accumulated iterate)
+cudaError_t launch_assemble(const Work& w, PtrRef X0, PtrRef X, cudaStream_t s, const int* gate = nullptr);
 cudaError_t launch_finalize(const Work& w, InfoDev* info, cudaStream_t s);
+// The final residual of the Block GMRES algorithm: with R = C - Phi(X) in the
+// V_0 slot (type dtype) and S(R) in w.Spart, ||R||_F / ||C||_F and
+// ||S(R)|| / beta_0 into the control block (deterministic reduction).
+cudaError_t launch_true_resid(const Work& w, PtrRef C, cudaStream_t s);
 // k_gk.cu: sketched Golub-Kahan (Algorithm 4).  phase 0: beta_0 = ||S(R_0)||;
 // 1: alpha_0 = ||S(Phi^T U_0)||; 2: beta_{j+1} = ||S(Phi V_j) - alpha_j S(U_j)||;
 // 3: alpha_{j+1} = ||S(Phi^T U_{j+1}) - beta_{j+1} S(V_j)||.  The sketch of the

@@ -352,4 +352,69 @@ def test_solve_rejects_bad_arguments(h):
     with pytest.raises(RtgError):
         h.gmres_solve(Cd, 5, (4, 4, 3), 0, -1.0)                      # GCV without a grid
     with pytest.raises(RtgError):
-        h.gmres_solve(Cd, 5, (4, 4, 3), 0, 1e-3, max_restarts=1)      # restarts: unsupported
+        h.gmres_solve(Cd, 5, (4, 4, 3), 0, 1e-3, max_restarts=-1)     # negative restarts
+    with pytest.raises(RtgError):
+        h.gmres_solve(Cd, 100, (4, 4, 3), 0, 1e-3, max_restarts=2)    # 300 steps > 256
+
+
+def test_solve_image512_f32_all_50_steps(h):
+    """The 512x512x3 FP32 workload run to j = m = 50 (tol 0, GCV): the rho
+    history elementwise, Hbar at several j (through the Krylov state), the
+    GCV values and X, compared with the FP64 oracle at the same mu as the
+    GPU picked (and at the oracle's own mu).  Bar 1e-4 relative (FP32)."""
+    p = w.image_config(2)
+    mats, C, nu_c, th = _setup(p)
+    ref = oracle.rtg_gmres(mats, C, p.m, th, tol=0.0, lam=p.lam, mu_grid=p.mu_grid)
+    assert ref["iters"] == p.m
+    api = _api()
+    A, B = _api_factors(p)
+    Cd = api.to_device(C, torch.float32)
+    X, info = h.gmres_solve(Cd, p.m, p.sketch_dims, p.seed, p.lam, A, B, tol=0.0, mu_grid=p.mu_grid)
+    assert info.iters == p.m and info.device_status == 0
+    assert np.allclose(info.rho, ref["rho"], rtol=1e-4, atol=0)
+    assert np.allclose(info.gcv, ref["gcv"], rtol=1e-4)
+    K = api.Krylov(h, p.dims, torch.float32, p.m, p.sketch_dims, p.seed, A, B)
+    K.start(Cd)
+    for _ in range(p.m):
+        K.step()
+    view, H = K.query()
+    assert view.j == p.m
+    for j in (0, 4, 9, 24, 49):
+        col, rc = H[:j + 2, j], ref["H"][:j + 2, j]
+        assert np.max(np.abs(col - rc)) <= 1e-4 * np.max(np.abs(rc)), j
+    Xg = X.cpu().double().numpy()
+    y = oracle.tikhonov_stacked(ref["H"], ref["beta"], info.mu)
+    X_mu = sum(y[i] * ref["V"][i] for i in range(p.m))
+    assert _relnorm(Xg, X_mu) < 1e-4
+    if info.mu == ref["mu"]:
+        assert _relnorm(Xg, ref["X"]) < 1e-4
+
+
+def test_batched_uneven_f32_problem_matches_oracle(h):
+    """One FP32 problem of uneven sides (97 x 203, sketch only on mode 2)
+    solved inside a batch of three uneven problems: rho history and X
+    against the FP64 oracle at 1e-4."""
+    api = _api()
+    rng = np.random.default_rng(21)
+    probs, refs = [], []
+    for k, (I1, I2, sig) in enumerate([(97, 203, 1.2), (144, 88, 2.0), (72, 72, 0.8)]):
+        r = int(np.ceil(3 * sig))
+        a = w.gaussian_taps(sig, r)
+        fac = [(1, "banded", a), (2, "banded", a)]
+        rfac = [(3, "dense", w.channel_mix())]
+        dims = (I1, I2, 3)
+        sk = (min(I1, 128), min(I2, 128), 3)
+        mats = oracle.factor_matrices(dims, fac, rfac)
+        x = w.piecewise_image(I1, I2, 3, seed=30 + k)
+        C, _, nu_c = oracle.make_observation(x, mats, w.noise_draw(dims, 30 + k), 2e-3)
+        th = oracle.sketch_matrices(dims, sk, 40 + k)
+        tol = oracle.rho_star(nu_c)
+        refs.append(oracle.rtg_gmres(mats, C, 30, th, tol=tol, lam=1e-3))
+        probs.append(dict(C=api.to_device(C, torch.float32), m=30, sketch_dims=sk, seed=40 + k, lam=1e-3,
+                          tol=tol, A=[api.banded(1, I1, a), api.banded(2, I2, a)],
+                          B=[api.dense(3, w.channel_mix())]))
+    Xs, res = h.gmres_solve_batched(probs)
+    for Xb, rb, ref in zip(Xs, res, refs):
+        assert rb.iters == ref["iters"] and rb.device_status == 0
+        assert np.allclose(rb.rho, ref["rho"], rtol=1e-4, atol=0)
+        assert _relnorm(Xb.cpu().double().numpy(), ref["X"]) < 1e-4
