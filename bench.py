@@ -57,6 +57,15 @@ def parse():
     ap.add_argument("--only-batched", action="store_true",
                     help="run the batched form alone (no plain, Golub-Kahan or warm-start forms, no phase "
                          "passes, no end-to-end pass): for profiler captures of its kernels")
+    ap.add_argument("--restarts", type=int, default=3,
+                    help="restarted cycles allowed per solve (every form), so that a solve that reaches "
+                         "j = m above rho* restarts from its least-squares iterate instead of stopping")
+    ap.add_argument("--no-extra-forms", action="store_true",
+                    help="skip the video precision form, the batched BF16-basis form and the uneven "
+                         "256-problem batch")
+    ap.add_argument("--uneven", type=int, default=256, help="problems of the uneven batched workload")
+    ap.add_argument("--cpu-leg", type=int, default=0,
+                    help="internal: time the oracle alone with this many BLAS threads and print JSON")
     return ap.parse_args()
 
 
@@ -166,11 +175,15 @@ def make_problems(h, api, torch, count: int, seed0: int):
 USE_GRAPH = True
 
 
-def solve(h, pr, X, stream=None, host=False):
+RESTARTS = 3
+
+
+def solve(h, pr, X, stream=None, host=False, bf16=False):
     p = pr["p"]
     C = pr["C_host"] if host else pr["C"]
     return h.gmres_solve(C, p.m, p.sketch_dims, p.seed, p.lam, pr["A"], pr["B"], X=X, tol=pr["tol"],
-                         mu_grid=p.mu_grid, use_graph=USE_GRAPH, stream=stream)
+                         mu_grid=p.mu_grid, use_graph=USE_GRAPH, max_restarts=RESTARTS, bf16_basis=bf16,
+                         stream=stream)
 
 
 # ----------------------------------------------------------------------------- roofline
@@ -214,20 +227,30 @@ def recorded_traffic(phase: str, workload: str):
     return None
 
 
-def phase_bytes(phase: str, n: int, d: int, k: int, b: int) -> float:
+def cycle_steps(k: int, m: int):
+    """Per-cycle step counts of a solve of k Arnoldi steps in cycles of at most m."""
+    out = [m] * (k // m)
+    if k % m or not out:
+        out.append(k % m)
+    return out
+
+
+def phase_bytes(phase: str, n: int, d: int, k: int, b: int, m: int = 10 ** 9) -> float:
     """Minimum (algorithmic) bytes of one kernel group summed over a solve of k
-    Arnoldi steps; n tensor entries, d sketch entries, b bytes per entry.
-    Step j (0-based) builds V_{j+1} from W = Phi(V_j) and V_0..V_j."""
+    Arnoldi steps (cycles of at most m steps: j restarts at 0 in each);
+    n tensor entries, d sketch entries, b bytes per entry.  Step j
+    (0-based) builds V_{j+1} from W = Phi(V_j) and V_0..V_j."""
+    cyc = cycle_steps(k, m)
     if phase == "apply":      # read V_j, write W
         return k * 2 * n * b
     if phase == "sketch":     # read W, write S(W), read Q_0..Q_j for the fused dots
-        return sum(n * b + d * b + (j + 1) * d * b for j in range(k))
+        return sum(n * b + d * b + (j + 1) * d * b for c in cyc for j in range(c))
     if phase == "update":     # read W and V_0..V_j, write V_{j+1}; Q column from S and Q_0..Q_j
-        return sum((j + 3) * n * b + (j + 3) * d * b for j in range(k))
-    if phase == "assemble":   # read V_0..V_{k-1}, write X
-        return (k + 1) * n * b
-    if phase == "init":       # read C, write V_0 (scaled), sketch read of C
-        return 3 * n * b
+        return sum((j + 3) * n * b + (j + 3) * d * b for c in cyc for j in range(c))
+    if phase == "assemble":   # read V_0..V_{k-1}, write X (last cycle)
+        return (cyc[-1] + 1) * n * b
+    if phase == "init":       # read C, write V_0 (scaled), sketch read of C; per restart also X += V y
+        return 3 * n * b + sum((c + 1) * n * b + 4 * n * b for c in cyc[:-1])
     return 0.0
 
 
@@ -242,12 +265,12 @@ def phase_report(h, probs, X, peaks, workload: str):
     for pr in probs:
         p = pr["p"]
         _, info = h.gmres_solve(pr["C"], p.m, p.sketch_dims, p.seed, p.lam, pr["A"], pr["B"], X=X,
-                                tol=pr["tol"], mu_grid=p.mu_grid, phase_times=True)
+                                tol=pr["tol"], mu_grid=p.mu_grid, phase_times=True, max_restarts=RESTARTS)
         iters.append(info.iters)
         for k, v in info.phase_ms.items():
             tot_ms[k] = tot_ms.get(k, 0.0) + v
             tot_l[k] = tot_l.get(k, 0) + info.phase_launches[k]
-            tot_bytes[k] = tot_bytes.get(k, 0.0) + phase_bytes(k, n, d, info.iters, 4)
+            tot_bytes[k] = tot_bytes.get(k, 0.0) + phase_bytes(k, n, d, info.iters, 4, p.m)
     solves = len(probs)
     table = {}
     for k in tot_ms:
@@ -285,12 +308,13 @@ def batched_phase_report(h, batch, grid, peaks, workload: str):
     once).  Returns the roofline of the byte-bound group with the largest
     device time and the per-group table: algorithmic bytes summed over the
     problems' own steps."""
-    _, res = h.gmres_solve_batched(batch, mu_grid=grid, phase_times=True, group_max=len(batch))
+    _, res = h.gmres_solve_batched(batch, mu_grid=grid, phase_times=True, group_max=len(batch),
+                                   max_restarts=RESTARTS)
     C0 = batch[0]["C"]
     n = int(np.prod(C0.shape))
     d = int(np.prod([min(s, i) for s, i in zip(batch[0]["sketch_dims"], C0.shape)]))
     ms, launches = res[0].phase_ms, res[0].phase_launches
-    tot_bytes = {k: sum(phase_bytes(k, n, d, r.iters, 4) for r in res) for k in ms}
+    tot_bytes = {k: sum(phase_bytes(k, n, d, r.iters, 4, batch[0]["m"]) for r in res) for k in ms}
     table = {}
     share_total = sum(ms.values())
     for k in ms:
@@ -421,28 +445,58 @@ def warm_start_form(h, api, torch, probs, train_n=512, steps=400, I=128, base=32
 
 # ----------------------------------------------------------------------------- CPU baseline
 
-def cpu_baseline(probs_host, seconds: float):
-    """FP64 CPU oracle as it stands, on this host's cores, on a bounded sample of the workload."""
+def oracle_solves(seconds: float, problems: int = 16):
+    """FP64 CPU oracle as it stands on the 512x512x3 workload (observation,
+    signs and a restarted solve to rho*), for about `seconds`; returns
+    (solves, elapsed, mean steps)."""
     import oracle
-    done, t0 = 0, time.perf_counter()
-    iters = []
+    done, iters, t0 = 0, [], time.perf_counter()
     while True:
-        pr = probs_host[done % len(probs_host)]
-        p = pr["p"]
+        p = workloads.image_config(2, seed=done % problems)
         mats = oracle.factor_matrices(p.dims, p.factors, p.right_factors)
         C, _, nu_c = oracle.make_observation(p.x_true, mats, p.noise, p.nu)
         th = oracle.sketch_matrices(p.dims, p.sketch_dims, p.seed, p.problem_id)
-        ts = time.perf_counter()
-        r = oracle.rtg_gmres(mats, C, p.m, th, tol=rho_star(nu_c), lam=p.lam, mu_grid=p.mu_grid)
+        r = oracle.rtg_gmres(mats, C, p.m, th, tol=rho_star(nu_c), lam=p.lam, mu_grid=p.mu_grid,
+                             max_restarts=RESTARTS)
         iters.append(r["iters"])
         done += 1
         if time.perf_counter() - t0 >= seconds:
             break
-    el = time.perf_counter() - t0
-    return {"value": round(done / el, 4), "unit": "solves/s", "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": f"{done} full FP64 oracle solves of the 512x512x3 workload "
-                      f"(mean {np.mean(iters):.1f} Arnoldi steps), numpy BLAS default threads"}
+    return done, time.perf_counter() - t0, float(np.mean(iters))
+
+
+def cpu_leg_main(threads: int, seconds: float):
+    """Entry of the single-thread leg (run in a child process whose BLAS
+    thread count was fixed by its environment before numpy loaded)."""
+    done, el, it = oracle_solves(seconds)
+    print(json.dumps({"solves": done, "seconds": el, "mean_iters": it, "threads": threads}), flush=True)
+
+
+def cpu_baseline(seconds: float):
+    """The oracle timed twice on this host: BLAS threads = all cores (this
+    process) and 1 thread (a child process started with the thread count set
+    in its environment).  The headline value is the all-cores leg."""
+    done, el, it = oracle_solves(seconds)
+    one = None
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", "1", "--cpu-seconds",
+                            str(seconds)], capture_output=True, text=True, env=env, timeout=20 * seconds + 120)
+        for ln in r.stdout.splitlines():
+            if ln.startswith("{"):
+                one = json.loads(ln)
+    except (OSError, subprocess.SubprocessError, ValueError):
+        one = None
+    out = {"value": round(done / el, 4), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{done} full FP64 oracle solves of the 512x512x3 workload (observation, signs, "
+                     f"restarted solve to rho*, mean {it:.1f} Arnoldi steps), numpy BLAS default threads"}
+    if one is not None:
+        out["single_thread"] = {"value": round(one["solves"] / one["seconds"], 4), "unit": "solves/s",
+                                "cores": 1, "sample": f"{one['solves']} solves, mean {one['mean_iters']:.1f} "
+                                                      "steps, BLAS threads = 1"}
+    return out
 
 
 # ----------------------------------------------------------------------------- arms
@@ -462,7 +516,8 @@ def run_reference(args):
         mats = oracle.factor_matrices(p.dims, p.factors, p.right_factors)
         C, _, nu_c = oracle.make_observation(p.x_true, mats, p.noise, p.nu)
         th = oracle.sketch_matrices(p.dims, p.sketch_dims, p.seed, p.problem_id)
-        r = oracle.rtg_gmres(mats, C, p.m, th, tol=rho_star(nu_c), lam=p.lam, mu_grid=p.mu_grid)
+        r = oracle.rtg_gmres(mats, C, p.m, th, tol=rho_star(nu_c), lam=p.lam, mu_grid=p.mu_grid,
+                             max_restarts=RESTARTS)
         t = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(t)
@@ -475,7 +530,7 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "dims": [512, 512, 3], "m": 50,
                       "sketch": [128, 128, 3], "gcv_grid": 8, "mean_iters": float(np.mean(iters)),
-                      "stop": "rho <= max(1e-3, 1.01*nu_C)"},
+                      "stop": "rho <= max(1e-3, 1.01*nu_C)", "restarts": RESTARTS},
            "cpu_baseline": {"value": round(val, 4), "unit": "solves/s", "cores": os.cpu_count(),
                             "kind": "oracle",
                             "sample": f"{args.steps} timed FP64 oracle solves (observation build "
@@ -483,6 +538,122 @@ def run_reference(args):
            "e2e": {"value": round(val, 4), "unit": "solves/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def device_timed(fn, steps: int, stream, flush):
+    """Runs fn(step) `steps` times, L2 flushed before each, each bracketed by
+    CUDA events on `stream`; returns (mean ms, [fn results])."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    out = []
+    torch.cuda.synchronize()
+    for s in range(steps):
+        flush.zero_()
+        evs[s][0].record(stream)
+        out.append(fn(s))
+        evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / max(steps, 1), out
+
+
+def reached(res) -> str:
+    return f"{sum(bool(r.converged) for r in res)}/{len(res)}"
+
+
+def video_form(h, api, torch, stream, flush, reps: int = 4):
+    """Precision form on the video workload (256x256x3x64, spatial sigma 2
+    radius 6, channel mix, temporal box of width 5, noise 5e-3, m = 40,
+    sketch (96, 96, 3, 32), GCV): plain FP32 solves against the BF16 basis,
+    solves/s at the same rho*, and the BF16 result's difference from the
+    FP32 one and both relative errors to the true video."""
+    p = workloads.video_config(0)
+    A = [api.banded(mm, p.dims[mm - 1], t) for mm, _, t in p.factors]
+    B = [api.dense(mm, t) for mm, _, t in p.right_factors]
+    X = api.to_device(p.x_true, torch.float32)
+    Ch = h.operator_apply(X, A, B)
+    E = api.to_device(p.noise, torch.float32)
+    C = api.empty(p.dims, torch.float32)
+    C.copy_(Ch + E * (p.nu * torch.linalg.vector_norm(Ch) / torch.linalg.vector_norm(E)))
+    nu_c = float(p.nu * torch.linalg.vector_norm(Ch) / torch.linalg.vector_norm(C))
+    tol = rho_star(nu_c)
+    out = {}
+    Xs = {}
+    for name, bf in (("fp32", False), ("bf16_basis", True)):
+        Xo = api.empty(p.dims, torch.float32)
+
+        def one(_):
+            return h.gmres_solve(C, p.m, p.sketch_dims, p.seed, p.lam, A, B, X=Xo, tol=tol, mu_grid=p.mu_grid,
+                                 max_restarts=RESTARTS, bf16_basis=bf)[1]
+        for _ in range(2):
+            one(0)
+        ms, res = device_timed(one, reps, stream, flush)
+        Xs[name] = Xo
+        re = float(torch.linalg.vector_norm(Xo - X) / torch.linalg.vector_norm(X))
+        out[name] = {"value": round(1e3 / ms, 2), "ms_per_solve": round(ms, 3),
+                     "mean_iters": float(np.mean([r.iters for r in res])), "reached_stop_level": reached(res),
+                     "rel_error_to_true_video": round(re, 5)}
+    out["bf16_vs_fp32_rel_diff"] = round(float(torch.linalg.vector_norm(Xs["bf16_basis"] - Xs["fp32"]) /
+                                               torch.linalg.vector_norm(Xs["fp32"])), 5)
+    out["speedup_bf16_over_fp32"] = round(out["bf16_basis"]["value"] / out["fp32"]["value"], 3)
+    out["workload"] = "video256x256x3x64: sigma 2 r 6, 3x3 mix, temporal box 5, noise 5e-3, m 40, sketch (96,96,3,32)"
+    out["error_vs_fp64_oracle"] = ("tests/test_gpu_precision.py: 64x64x3x8 video, 20 steps, BF16 basis rho history "
+                                   "within 10 %, X within 2 % of the FP64 oracle")
+    del Xs
+    return out
+
+
+def uneven_form(h, api, torch, stream, flush, count: int, reps: int = 2):
+    """Batched form on the uneven workload: `count` colour-image problems with
+    sides drawn in [64, 1024], blur sigma in [0.5, 3] (radius ceil(3 sigma)),
+    noise in [1e-3, 2e-2], fixed lambda in [1e-4, 1e-1], m = 30, sketch
+    min(I_k, 128) per spatial mode, FP32, stop at rho*: one graph launch of
+    all problems against a loop of single plain solves of the same problems."""
+    cfgs = workloads.batched_configs(count, seed=0)
+    probs = []
+    elems = 0
+    for c in cfgs:
+        I1, I2, _ = c["dims"]
+        taps = workloads.gaussian_taps(c["sigma"], c["radius"])
+        A = [api.banded(1, I1, taps), api.banded(2, I2, taps)]
+        x = workloads.piecewise_image(I1, I2, 3, c["image_seed"])
+        Xt = api.to_device(x, torch.float32)
+        Ch = h.operator_apply(Xt, A, [])
+        E = api.to_device(workloads.noise_draw(x.shape, c["image_seed"]), torch.float32)
+        C = api.empty(c["dims"], torch.float32)
+        C.copy_(Ch + E * (c["nu"] * torch.linalg.vector_norm(Ch) / torch.linalg.vector_norm(E)))
+        nu_c = float(c["nu"] * torch.linalg.vector_norm(Ch) / torch.linalg.vector_norm(C))
+        probs.append(dict(C=C, A=A, B=[], m=c["m"], sketch_dims=c["sketch_dims"], seed=c["problem_id"],
+                          lam=c["mu"], tol=rho_star(nu_c), X=api.empty(c["dims"], torch.float32)))
+        elems += I1 * I2 * 3
+        del Xt, Ch, E
+    torch.cuda.synchronize()
+
+    def batched(_):
+        return h.gmres_solve_batched(probs, max_restarts=RESTARTS)[1]
+
+    def loop(_):
+        return [h.gmres_solve(q["C"], q["m"], q["sketch_dims"], q["seed"], q["lam"], q["A"], q["B"], X=q["X"],
+                              tol=q["tol"], max_restarts=RESTARTS)[1] for q in probs]
+    t0 = time.perf_counter()
+    batched(0)
+    build_b = time.perf_counter() - t0
+    batched(0)
+    t0 = time.perf_counter()
+    loop(0)
+    build_l = time.perf_counter() - t0
+    ms_b, rb = device_timed(batched, reps, stream, flush)
+    ms_l, rl = device_timed(loop, reps, stream, flush)
+    rb, rl = rb[-1], rl[-1]
+    same = all(a.iters == b.iters for a, b in zip(rb, rl))
+    return {"value": round(count / (ms_b / 1e3), 2), "unit": "solves/s", "ms_per_batch": round(ms_b, 3),
+            "loop_of_single_solves": {"value": round(count / (ms_l / 1e3), 2), "ms_per_pass": round(ms_l, 3)},
+            "speedup_over_loop": round(ms_l / ms_b, 3), "problems": count, "total_elements": elems,
+            "mean_iters": float(np.mean([r.iters for r in rb])), "reached_stop_level": reached(rb),
+            "iters_equal_to_single_solves": same, "first_call_s": {"batched": round(build_b, 2),
+                                                                   "loop": round(build_l, 2)},
+            "launch": "one CUDA graph, one branch per problem (device-side WHILE loops)",
+            "workload": "256 colour images, sides U{64..1024}, sigma U[0.5,3], noise 1e-3..2e-2, "
+                        "lambda 1e-4..1e-1, m 30, sketch min(I_k,128), FP32"}
 
 
 def run_ours(args):
@@ -512,8 +683,11 @@ def run_ours(args):
     X = api.empty(probs[0]["p"].dims, torch.float32)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-
     grid = workloads.mu_grid()
+    B = args.batch
+    Xb = [api.empty(probs[0]["p"].dims, torch.float32) for _ in range(B)]
+    nb = max(1, len(probs) // B)
+    only_b = args.only_batched
 
     def batch_of(k):
         return [dict(C=probs[(k * B + i) % len(probs)]["C"], A=probs[(k * B + i) % len(probs)]["A"],
@@ -522,80 +696,47 @@ def run_ours(args):
                      lam=probs[0]["p"].lam, tol=probs[(k * B + i) % len(probs)]["tol"], X=Xb[i])
                 for i in range(B)]
 
-    B = args.batch
-    Xb = [api.empty(probs[0]["p"].dims, torch.float32) for _ in range(B)]
-    nb = max(1, len(probs) // B)
+    def batched(bt, bf16=False):
+        return h.gmres_solve_batched(bt, mu_grid=grid, use_graph=not args.direct, group_max=args.group_max,
+                                     max_restarts=RESTARTS, bf16_basis=bf16)
 
-    def batched(bt):
-        return h.gmres_solve_batched(bt, mu_grid=grid, use_graph=not args.direct, group_max=args.group_max)
+    # ---- plain FP32 form: one solve per step
+    plain_ms, plain_res = float("nan"), []
+    if not only_b:
+        for s in range(args.warmup):
+            solve(h, probs[s % len(probs)], X)
+        plain_ms, plain_res = device_timed(lambda s: solve(h, probs[s % len(probs)], X)[1], args.steps, stream,
+                                           flush)
+        for r in plain_res:
+            if r.device_status != 0:
+                raise RuntimeError(f"solve failed: device status {r.device_status}")
 
-    only_b = args.only_batched
-    # ---- plain FP32 form: one solve per step, device-timed, L2 flushed between steps
-    for s in range(0 if only_b else args.warmup):
-        solve(h, probs[s % len(probs)], X)
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    iters, conv_plain = [], []
-    for s in range(0 if only_b else args.steps):
-        flush.zero_()
-        evs[s][0].record(stream)
-        _, info = solve(h, probs[s % len(probs)], X)
-        evs[s][1].record(stream)
-        iters.append(info.iters)
-        conv_plain.append(bool(info.converged))
-        if info.device_status != 0:
-            raise RuntimeError(f"solve failed: device status {info.device_status}")
-    torch.cuda.synchronize()
-    plain_ms = float("nan") if only_b else sum(a.elapsed_time(b) for a, b in evs) / args.steps
-
-    # ---- sketched Golub-Kahan (Algorithm 4) on the same problems, one solve per step
+    # ---- sketched Golub-Kahan (Algorithm 4) on the same problems (no restarts)
     def gk(pr):
         p = pr["p"]
         return h.gk_solve(pr["C"], p.m, p.sketch_dims, p.seed, p.lam, pr["A"], pr["B"], X=X,
-                          tol=pr["tol"], mu_grid=p.mu_grid)
-    for s in range(0 if only_b else args.warmup):
-        gk(probs[s % len(probs)])
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    iters_gk, conv_gk = [], []
-    for s in range(0 if only_b else args.steps):
-        flush.zero_()
-        evs[s][0].record(stream)
-        _, info = gk(probs[s % len(probs)])
-        evs[s][1].record(stream)
-        iters_gk.append(info.iters)
-        conv_gk.append(bool(info.converged))
-    torch.cuda.synchronize()
-    gk_ms = float("nan") if only_b else sum(a.elapsed_time(b) for a, b in evs) / args.steps
+                          tol=pr["tol"], mu_grid=p.mu_grid)[1]
+    gk_ms, gk_res = float("nan"), []
+    if not only_b:
+        for s in range(args.warmup):
+            gk(probs[s % len(probs)])
+        gk_ms, gk_res = device_timed(lambda s: gk(probs[s % len(probs)]), args.steps, stream, flush)
 
     # ---- chosen form: batched (B problems per CUDA-graph launch), one batch per step
     for s in range(args.warmup):
         batched(batch_of(s % nb))
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    iters_b, conv_b, launches = [], [], 0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        for s in range(args.steps):
-            flush.zero_()
-            evs[s][0].record(stream)
-            _, res = batched(batch_of(s % nb))
-            evs[s][1].record(stream)
-            for r in res:
-                iters_b.append(r.iters)
-                conv_b.append(bool(r.converged))
-                launches += r.launches
-                if r.device_status != 0:
-                    raise RuntimeError(f"batched solve failed: device status {r.device_status}")
-        torch.cuda.synchronize()
+        ms, outs = device_timed(lambda s: batched(batch_of(s % nb))[1], args.steps, stream, flush)
+    res_b = [r for o in outs for r in o]
+    for r in res_b:
+        if r.device_status != 0:
+            raise RuntimeError(f"batched solve failed: device status {r.device_status}")
+    launches = sum(r.launches for r in res_b)
     if world > 1:
         torch.distributed.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
     ms_max, plain_max = job_times([ms, plain_ms], world, "cuda")
     value = job_rate(world, B, ms_max / 1e3)
     plain_value = job_rate(world, 1, plain_max / 1e3)
@@ -631,6 +772,20 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / args.steps if not only_b else float("nan")
     e2e_val = job_rate(world, B, job_times([e2e_s], world, "cuda")[0])
 
+    extra = rank == 0 and not only_b and not args.no_extra_forms
+    # ---- batched form with the BF16 basis (precision form on the image workload)
+    bf_form = None
+    if extra:
+        for s in range(2):
+            batched(batch_of(s % nb), bf16=True)
+        ms_bf, outs_bf = device_timed(lambda s: batched(batch_of(s % nb), bf16=True)[1], args.steps, stream, flush)
+        rbf = [r for o in outs_bf for r in o]
+        bf_form = {"value": round(B / (ms_bf / 1e3), 2), "ms_per_batch": round(ms_bf, 4), "batch": B,
+                   "mean_iters": float(np.mean([r.iters for r in rbf])), "reached_stop_level": reached(rbf),
+                   "basis": "BF16 (FP32 arithmetic, FP64 Gram-Schmidt / Givens / Tikhonov)"}
+    vid = video_form(h, api, torch, stream, flush) if extra else None
+    uneven = uneven_form(h, api, torch, stream, flush, args.uneven) if extra else None
+
     ws_form = None
     if rank == 0 and not args.no_warm_start and not only_b:
         ws_form = warm_start_form(h, api, torch, probs)
@@ -643,17 +798,18 @@ def run_ours(args):
     roof, phases_b = batched_phase_report(h, batch_of(0), grid, peaks, WORKLOAD) if phased else (None, None)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not only_b:
-        cpu = cpu_baseline([dict(p=pr["p"]) for pr in probs], args.cpu_seconds)
+        cpu = cpu_baseline(args.cpu_seconds)
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 2), "unit": "solves/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
-               "config": {"workload": WORKLOAD, "dims": [512, 512, 3], "m": 50,
+               "config": {"workload": WORKLOAD, "dims": [512, 512, 3], "m": 50, "restarts": RESTARTS,
                           "sketch": [128, 128, 3], "blur": "gaussian sigma 2.5 radius 7 + 3x3 mix",
-                          "noise": 1e-2, "gcv_grid": 8, "mean_iters": float(np.mean(iters_b)),
-                          "stop": "rho <= max(1e-3, 1.01*nu_C), else m steps",
-                          "reached_stop_level": f"{sum(conv_b)}/{len(conv_b)}", "problems": len(probs),
+                          "noise": 1e-2, "gcv_grid": 8, "mean_iters": float(np.mean([r.iters for r in res_b])),
+                          "stop": "rho <= max(1e-3, 1.01*nu_C); a cycle ending at j = m above it restarts "
+                                  "from its least-squares iterate (up to `restarts` times)",
+                          "reached_stop_level": reached(res_b), "problems": len(probs),
                           "l2": "flushed (256 MB write) between timed steps",
                           "form": f"batched: {B} problems per CUDA-graph launch (one step = one batch)",
                           "launch": ("direct launches" if args.direct else "cuda graph") +
@@ -661,20 +817,26 @@ def run_ours(args):
                                      if args.group_max > 1 else
                                      " (one branch per problem, device-side WHILE loops)")},
                "forms": {"batched_fp32": {"value": round(value, 2), "ms_per_batch": round(ms_max, 4),
-                                          "batch": B},
+                                          "batch": B, "reached_stop_level": reached(res_b),
+                                          "vs_plain_fp32": round(value / plain_value, 3) if plain_value else None},
                          "plain_fp32": {"value": round(plain_value, 2), "ms_per_solve": round(plain_max, 4),
-                                        "mean_iters": float(np.mean(iters)),
-                                        "reached_stop_level": f"{sum(conv_plain)}/{len(conv_plain)}",
+                                        "mean_iters": float(np.mean([r.iters for r in plain_res])) if plain_res else None,
+                                        "reached_stop_level": reached(plain_res),
                                         "launch": "direct" if args.direct else "cuda graph"},
+                         "batched_bf16_basis": dict(bf_form, vs_plain_fp32=round(bf_form["value"] / plain_value, 3))
+                                               if bf_form else None,
                          "golub_kahan_fp32": {"value": round(1e3 / gk_ms, 2), "ms_per_solve": round(gk_ms, 4),
-                                              "mean_iters": float(np.mean(iters_gk)),
-                                              "reached_stop_level": f"{sum(conv_gk)}/{len(conv_gk)}",
-                                              "method": "sketched Golub-Kahan (Algorithm 4)"},
+                                              "mean_iters": float(np.mean([r.iters for r in gk_res])) if gk_res else None,
+                                              "reached_stop_level": reached(gk_res),
+                                              "vs_plain_fp32": round((1e3 / gk_ms) / plain_value, 3) if gk_res else None,
+                                              "method": "sketched Golub-Kahan (Algorithm 4), no restarts"},
+                         "precision_video": vid,
+                         "batched_uneven_256": uneven,
                          "warm_start_fp32": ws_form},
                "e2e": {"value": round(e2e_val, 2), "unit": "solves/s",
-                       # per problem: C and X, plus the 328-byte descriptor and the 2368-byte
+                       # per problem: C and X, plus the 328-byte descriptor and the 2376-byte
                        # info record of the batch call
-                       "h2d_bytes_per_step": (4 * n + 328) * B, "d2h_bytes_per_step": (4 * n + 2368) * B},
+                       "h2d_bytes_per_step": (4 * n + 328) * B, "d2h_bytes_per_step": (4 * n + 2376) * B},
                "gpu_launches": launches,
                "roofline": roof, "kernels": phases_b, "roofline_plain": roof_plain, "kernels_plain": phases,
                "cpu_baseline": cpu, "clocks": clk.summary()}
@@ -684,7 +846,12 @@ def run_ours(args):
 
 
 def main():
+    global RESTARTS
     args = parse()
+    RESTARTS = args.restarts
+    if args.cpu_leg > 0:
+        cpu_leg_main(args.cpu_leg, args.cpu_seconds)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -1459,7 +1459,17 @@ static rtg_status submit_impl(int method, rtg_handle h, const rtg_factor* A, int
   SolvePlan* P = nullptr;
   std::shared_ptr<SolvePlan> hold;
   if (it == h->plans.end()) {
-    if (h->plans.size() >= 8 + RTG_MAX_SLOTS) {
+    // the plan cache holds many shapes (a loop of solves over a set of uneven
+    // problems keeps each plan); it is emptied when it would exceed 1024 plans
+    // or a quarter of the device memory
+    size_t held = 0;
+    for (const auto& q : h->plans) held += q.second->mem.bytes;
+    size_t freeb = 0, totalb = 0;
+    if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) {
+      cudaGetLastError();
+      totalb = 0;
+    }
+    if (h->plans.size() >= 1024 || (totalb > 0 && held > totalb / 4)) {
       // plans of other slots may still run on their streams: wait for the device
       cudaDeviceSynchronize();
       for (auto& q : h->pending)
