@@ -406,6 +406,43 @@ rtg_status rtg_ws_train_step(rtg_ws ws, int32_t n_img, int32_t I1, int32_t I2, c
                              const float* Xstar, const float* logmu, float lr, float* X0_scratch,
                              double* loss_out, rtg_stream stream);
 
+/* Decision record of rtg_ws_solve. */
+typedef struct rtg_ws_result {
+    int32_t fell_back;               /* 1: ||S(C - Phi(X_0))|| >= ||S(C)||: solved from X_0 = 0 with GCV */
+    int32_t pad;
+    double lambda;                   /* exp(predicted log lambda), or -1 when GCV chose mu (fallback) */
+    double tol;                      /* stop level handed to the solve: tol ||S(C)|| / ||S(R_0)|| */
+    double sketch_norm_C;            /* ||S(C)|| */
+    double sketch_norm_R0;           /* ||S(C - Phi(X_0))|| of the prediction */
+} rtg_ws_result;
+
+/*
+ * Warm-started RTG-GMRES (no paper counterpart: the solve path of the
+ * learned warm start).  On `stream`, with no host round trip until the
+ * solve has finished:
+ *   X_0 = C + net(C) and log lambda (rtg_ws_predict, into X);
+ *   R_0 = C - Phi(X_0); s_R = ||S(R_0)||, s_C = ||S(C)|| (the solve's sketch);
+ *   if s_R >= s_C (or non-finite): X_0 = 0 and mu by GCV over opts->mu_grid
+ *   (the plain cold solve, the fallback); else mu = exp(log lambda) and the
+ *   stop level becomes opts->tol * s_C / s_R, so that both paths stop at
+ *   ||S(C - Phi X)|| <= opts->tol ||S(C)|| (the rho of the solve is relative
+ *   to its own ||S(R_0)||);
+ *   then rtg_gmres_solve with X_0 as the initial guess (opts->max_restarts
+ *   and RTG_FLAG_TRUE_RESIDUAL apply; a warm start that already meets the
+ *   stop level returns X_0 after no step).
+ * C, X: device FP32 arrays of an I1 x I2 x 3 image (mode 1 fastest), I1 and
+ * I2 multiples of 8; X receives the solution.  opts->mu_grid is required.
+ * The call synchronises `stream` once at the end; info as for
+ * rtg_gmres_solve (info->mu: the mu used); result (may be NULL): the decision.
+ * Errors: as rtg_gmres_solve and rtg_ws_predict.
+ */
+rtg_status rtg_ws_solve(rtg_ws ws, rtg_handle handle,
+                        const rtg_factor* A_factors, int32_t nA,
+                        const rtg_factor* B_factors, int32_t nB,
+                        rtg_shape shape, const float* C, int32_t m, const int64_t* sketch_dims,
+                        uint64_t seed, float* X, const rtg_opts* opts, rtg_info* info,
+                        rtg_ws_result* result, rtg_stream stream);
+
 /*
  * One 3x3 convolution layer of the warm-start network with the same
  * kernels (zero padding 1, stride 1 or 2, channels-last FP32 activations

@@ -62,6 +62,11 @@ class Info(C.Structure):
                 ("phase_launches", C.c_int32 * PHASE_COUNT), ("true_rel_resid_theta", C.c_double)]
 
 
+class WsResult(C.Structure):
+    _fields_ = [("fell_back", C.c_int32), ("pad", C.c_int32), ("lam", C.c_double), ("tol", C.c_double),
+                ("sketch_norm_C", C.c_double), ("sketch_norm_R0", C.c_double)]
+
+
 class KrylovView(C.Structure):
     _fields_ = [("j", C.c_int32), ("m", C.c_int32), ("breakdown", C.c_int32),
                 ("sketch_size", C.c_int32), ("n", C.c_int64), ("beta", C.c_double),
@@ -113,6 +118,9 @@ _SIGS = {
     "rtg_ws_train_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_float, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "rtg_nn_conv3x3": (C.c_int, [C.c_int32] * 7 + [C.c_void_p] * 8 + [C.c_void_p]),
+    "rtg_ws_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Factor), C.c_int32, C.POINTER(Factor),
+                               C.c_int32, Shape, C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.c_uint64,
+                               C.c_void_p, C.POINTER(Opts), C.POINTER(Info), C.POINTER(WsResult), C.c_void_p]),
     "rtg_sketch_noalloc": (C.c_int, [Shape, C.c_int, C.POINTER(C.c_int64), C.c_uint64, C.c_uint64,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
 }

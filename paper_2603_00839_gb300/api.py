@@ -553,6 +553,40 @@ class WarmStart:
                                         _stream(stream)))
         return X0, ll
 
+    def solve(self, handle: "Handle", C_obs, m: int, sketch_dims: Sequence[int], seed: int,
+              A_factors: Sequence[Factor] = (), B_factors: Sequence[Factor] = (), X=None, tol: float = 0.0,
+              mu_grid=None, max_restarts: int = 0, true_residual: bool = False, slot: int = 0, stream=None):
+        """Warm-started RTG-GMRES (rtg_ws_solve): prediction, fallback test and
+        stop-level rescale on the device, then the solve.  Returns
+        (X, SolveResult, decision dict)."""
+        dims = tuple(C_obs.shape)
+        _check_tensor(C_obs, dims, "C")
+        if X is None:
+            X = empty(dims, C_obs.dtype, C_obs.device)
+        a, na, ka = _factor_array(A_factors)
+        b, nb, kb = _factor_array(B_factors)
+        sk = (C.c_int64 * len(dims))(*[int(s) for s in sketch_dims])
+        opts = L.Opts()
+        opts.tol = float(tol)
+        grid = np.ascontiguousarray(mu_grid, dtype=np.float64)
+        opts.mu_grid = grid.ctypes.data_as(C.POINTER(C.c_double))
+        opts.n_mu = len(grid)
+        opts.max_restarts = int(max_restarts)
+        opts.flags = L.FLAG_TRUE_RESIDUAL if true_residual else 0
+        opts.slot = int(slot)
+        info = L.Info()
+        rho = np.zeros(m * (max_restarts + 1) + 1)
+        info.rho_hist = rho.ctypes.data_as(C.POINTER(C.c_double))
+        gcv = np.zeros(L.MAX_MU)
+        info.gcv = gcv.ctypes.data_as(C.POINTER(C.c_double))
+        dec = L.WsResult()
+        L.check(self.lib.rtg_ws_solve(self._h, handle._h, a, na, b, nb, _shape(dims), C_obs.data_ptr(), int(m), sk,
+                                      C.c_uint64(seed), X.data_ptr(), C.byref(opts), C.byref(info), C.byref(dec),
+                                      _stream(stream)))
+        res = _solve_result(info, rho, gcv, grid, -1.0 if dec.fell_back else 1.0)
+        return X, res, {"fell_back": bool(dec.fell_back), "lam": dec.lam, "tol": dec.tol,
+                        "sketch_norm_C": dec.sketch_norm_C, "sketch_norm_R0": dec.sketch_norm_R0}
+
     def train_step(self, Cb, Xs, logmu, I1: int, I2: int, lr: float, stream=None):
         torch = _torch()
         n = Cb.numel() // (I1 * I2 * 3)

@@ -363,7 +363,7 @@ __device__ inline void gs_finish_start(const Work& w, const StepOpts& o, const d
     if (ctl->cycle == 0) ctl->beta0 = beta;
     w.g[0] = beta;
     ctl->rho = beta / ctl->beta0;
-    if (ctl->rho <= tol && ctl->cycle > 0) {
+    if (ctl->rho <= tol) {   // (a warm start or a restart may already meet the stop level)
       ctl->converged = 1;
       ctl->stop = 1;
     }

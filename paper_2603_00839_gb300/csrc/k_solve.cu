@@ -66,6 +66,12 @@ k_tikhonov(Work w0, const SolveDesc* desc0, int mode, double* scratch0, int in_s
   Ctl* ctl = w.ctl;
   gate = bsh(gate, bo);
   if (gate != nullptr && *gate) return;
+  // a GCV plan whose descriptor carries lambda > 0 (the learned warm start's
+  // prediction) solves with that fixed mu on its first block
+  if (mode == 2 && desc->lambda > 0.0) {
+    if (blockIdx.x != 0) return;
+    mode = 1;
+  }
   const int k = ctl->j;
   const int m = w.m, ld = m + 1;
   __shared__ double red[TK_WARPS][kMaxK + 1];   // per-warp partial dot products of a step
@@ -433,6 +439,75 @@ cudaError_t launch_true_resid(const Work& w, PtrRef C, cudaStream_t s) {
   const dim3 g(static_cast<unsigned>(blocks), 1, static_cast<unsigned>(w.b.n));
   if (w.dtype == RTG_F64) k_true_resid<double><<<g, 256, 0, s>>>(w, C);
   else k_true_resid<float><<<g, 256, 0, s>>>(w, C);
+  return cudaGetLastError();
+}
+
+// Learned warm start: ||S(R_0)|| and ||S(C)|| (float-float sums over the d
+// sketch entries, one block), then the decision: fall back to X_0 = 0 with
+// GCV when the prediction's sketched residual is not below the cold start's,
+// else keep X_0, take lambda = exp(predicted log lambda) and rescale the stop
+// level so that both stop at ||S(C - Phi X)|| <= tol ||S(C)||.
+__global__ void __launch_bounds__(1024) k_ws_decide(const float* SR, const float* SC, int64_t d,
+                                                    const float* loglam, double tol, WsDecision* dec) {
+  __shared__ double red[32][2];
+  DotAcc<float> r, c;
+  for (int64_t i = threadIdx.x; i < d; i += blockDim.x) {
+    const float a = SR[i], b = SC[i];
+    r.add(a, a);
+    c.add(b, b);
+  }
+  const double rr = r.warp_total(), cc = c.warp_total();
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = rr;
+    red[threadIdx.x >> 5][1] = cc;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double sr = 0.0, sc = 0.0;
+  for (int u = 0; u < (int)(blockDim.x >> 5); ++u) {
+    sr += red[u][0];
+    sc += red[u][1];
+  }
+  sr = sqrt(sr);
+  sc = sqrt(sc);
+  const bool warm = isfinite(sr) && sr < sc;
+  dec->fell_back = warm ? 0 : 1;
+  dec->sC = sc;
+  dec->sR = sr;
+  if (warm) {
+    const double ll = static_cast<double>(*loglam);
+    dec->lambda = isfinite(ll) ? exp(fmin(fmax(ll, -40.0), 20.0)) : 1e-3;
+    dec->tol = sr > 0.0 ? tol * sc / sr : tol;
+  } else {
+    dec->lambda = -1.0;
+    dec->tol = tol;
+  }
+}
+
+__global__ void k_ws_zero_if(const WsDecision* dec, float* X, int64_t n) {
+  if (!dec->fell_back) return;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x)
+    X[o] = 0.f;
+}
+
+__global__ void k_ws_write_desc(const WsDecision* dec, SolveDesc* desc) {
+  desc->tol = dec->tol;
+  desc->lambda = dec->lambda;
+}
+
+cudaError_t launch_ws_decide(const float* SR, const float* SC, int64_t d, const float* loglam, double tol,
+                             WsDecision* dec, cudaStream_t s) {
+  k_ws_decide<<<1, 1024, 0, s>>>(SR, SC, d, loglam, tol, dec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ws_zero_if(const WsDecision* dec, float* X, int64_t n, cudaStream_t s) {
+  k_ws_zero_if<<<ew_grid(n), 256, 0, s>>>(dec, X, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ws_write_desc(const WsDecision* dec, SolveDesc* desc, cudaStream_t s) {
+  k_ws_write_desc<<<1, 1, 0, s>>>(dec, desc);
   return cudaGetLastError();
 }
 

@@ -610,6 +610,12 @@ struct rtg_context {
   // keyed by stream too, so that calls on different streams never share scratch
   std::map<std::string, std::unique_ptr<SketchCache>> sketches;
   std::map<cudaStream_t, std::unique_ptr<ApplyScratch>> apply_scratch;
+  // rtg_ws_solve: R_0 of the prediction, S(R_0), S(C), log lambda and the decision
+  DevBuf ws_work;
+  WsDecision* ws_dec_host = nullptr;   // pinned
+  ~rtg_context() {
+    if (ws_dec_host) cudaFreeHost(ws_dec_host);
+  }
   std::map<std::string, std::shared_ptr<SolvePlan>> plans;
   std::map<std::string, std::unique_ptr<BatchPlan>> batches;
   std::unique_ptr<PhaseTimer> timer;
@@ -937,6 +943,9 @@ rtg_status build_graph(SolvePlan& P) {
 
 }  // namespace
 
+static rtg_status sketch_scratch_for(rtg_handle h, const SketchPlan& sp, uint64_t seed, uint64_t pid,
+                                     cudaStream_t s, SketchScratch* out);
+
 // ================================================================== C ABI
 
 // Everything a solve plan is built from.
@@ -1244,9 +1253,19 @@ rtg_status rtg_sketch(rtg_handle h, rtg_shape shape, rtg_dtype dtype, const int6
   if (overlaps(X, SX, size_t(std::min<int64_t>(n, sp.d)) * elt_size(pdt)))
     return fail(RTG_ERR_INVALID_ARG, "SX must not overlap X");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // The signs depend on (seed, problem id); the scratch is kept per shape,
-  // sketch sizes, problem id, dtype and stream, and its signs are drawn
-  // again whenever the seed differs from the one they were drawn for.
+  SketchScratch sc;
+  RK(sketch_scratch_for(h, sp, seed, pid, s, &sc));
+  CK(launch_sketch(sp, sc, ref(X), SX, nullptr, nullptr, s, dtype));
+  return RTG_OK;
+}
+
+}  // extern "C"
+
+// The signs depend on (seed, problem id); the scratch of rtg_sketch is kept
+// per shape, sketch sizes, problem id, dtype and stream, and its signs are
+// drawn again (on s) whenever the seed differs from the one they were drawn for.
+static rtg_status sketch_scratch_for(rtg_handle h, const SketchPlan& sp, uint64_t seed, uint64_t pid,
+                                     cudaStream_t s, SketchScratch* out) {
   std::string key;
   append_bytes(key, &sp.order, sizeof sp.order);
   append_bytes(key, sp.dims, sizeof sp.dims);
@@ -1274,9 +1293,11 @@ rtg_status rtg_sketch(rtg_handle h, rtg_shape shape, rtg_dtype dtype, const int6
     ce->seed = seed;
     ce->drawn = true;
   }
-  CK(launch_sketch(sp, sc, ref(X), SX, nullptr, nullptr, s, dtype));
+  *out = sc;
   return RTG_OK;
 }
+
+extern "C" {
 
 rtg_status rtg_krylov_create(rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
                              int32_t nB, rtg_shape shape, rtg_dtype dtype, int32_t m,
@@ -1380,11 +1401,19 @@ rtg_status rtg_krylov_query(rtg_handle h, rtg_krylov K, rtg_krylov_view* view, d
 
 }  // extern "C"
 
+// Called after the solve's descriptor has been uploaded and before its
+// graph (or first kernel) is queued, on the solve's stream.
+struct PreLaunch {
+  rtg_status (*fn)(SolvePlan& P, cudaStream_t s, void* ctx);
+  void* ctx;
+};
+
 // method 0: RTG-GMRES; 1: sketched Golub-Kahan.
 static rtg_status submit_impl(int method, rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
                               int32_t nB, rtg_shape shape, rtg_dtype dtype, const void* C, int32_t m,
                               const int64_t* sketch_dims, uint64_t seed, double lambda, const void* X0,
-                              void* X, const rtg_opts* opts_in, rtg_stream stream) {
+                              void* X, const rtg_opts* opts_in, rtg_stream stream,
+                              const PreLaunch* pre = nullptr) {
   if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
   int64_t n = 0;
   RK(check_shape(shape, &n));
@@ -1533,6 +1562,7 @@ static rtg_status submit_impl(int method, rtg_handle h, const rtg_factor* A, int
   D.n_mu = mode == 2 ? opts.n_mu : 0;
   for (int i = 0; i < D.n_mu; ++i) D.mu_grid[i] = opts.mu_grid[i];
   CK(cudaMemcpyAsync(P->desc_dev, P->desc_host, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
+  if (pre != nullptr) RK(pre->fn(*P, s, pre->ctx));
   CK(cudaEventRecord(P->ev0, s));
   if (use_graph) {
     CK(cudaGraphLaunch(P->exec, s));
@@ -1869,3 +1899,97 @@ rtg_status rtg_gmres_solve(rtg_handle h, const rtg_factor* A, int32_t nA, const 
 }
 
 }  // extern "C"
+
+// ================================================================== learned warm start
+
+namespace {
+struct WsHook {
+  WsDecision* dec;
+};
+rtg_status ws_hook(SolvePlan& P, cudaStream_t s, void* ctx) {
+  CK(launch_ws_write_desc(static_cast<WsHook*>(ctx)->dec, P.desc_dev, s));
+  return RTG_OK;
+}
+}  // namespace
+
+extern "C" rtg_status rtg_ws_solve(rtg_ws ws, rtg_handle h, const rtg_factor* A, int32_t nA, const rtg_factor* B,
+                                   int32_t nB, rtg_shape shape, const float* C, int32_t m,
+                                   const int64_t* sketch_dims, uint64_t seed, float* X, const rtg_opts* opts_in,
+                                   rtg_info* info, rtg_ws_result* result, rtg_stream stream) {
+  if (ws == nullptr || h == nullptr) return fail(RTG_ERR_INVALID_ARG, "warm-start or solver handle is NULL");
+  int64_t n = 0;
+  RK(check_shape(shape, &n));
+  if (shape.order != 3 || shape.dims[2] != 3)
+    return fail(RTG_ERR_INVALID_ARG, "the warm start takes I1 x I2 x 3 images");
+  if (shape.dims[0] % 8 || shape.dims[1] % 8 || shape.dims[0] < 8 || shape.dims[1] < 8)
+    return fail(RTG_ERR_INVALID_ARG, "the warm start needs image sides that are multiples of 8");
+  RK(check_factors(A, nA, shape, "A_factors"));
+  RK(check_factors(B, nB, shape, "B_factors"));
+  if (C == nullptr || X == nullptr) return fail(RTG_ERR_INVALID_ARG, "C and X must not be NULL");
+  rtg_opts opts{};
+  if (opts_in) opts = *opts_in;
+  if (opts.n_mu < 1 || opts.mu_grid == nullptr)
+    return fail(RTG_ERR_INVALID_ARG, "rtg_ws_solve needs opts.mu_grid (the fallback chooses mu by GCV)");
+  if (!(opts.tol >= 0.0) || !std::isfinite(opts.tol)) return fail(RTG_ERR_INVALID_ARG, "opts.tol must be finite and >= 0");
+  if (opts.flags & (RTG_FLAG_PHASE_TIMES | RTG_FLAG_BF16_BASIS))
+    return fail(RTG_ERR_UNSUPPORTED, "rtg_ws_solve takes neither RTG_FLAG_PHASE_TIMES nor RTG_FLAG_BF16_BASIS");
+  DeviceGuard dg(h->device);
+  if (!is_device_ptr(C) || !is_device_ptr(X)) return fail(RTG_ERR_INVALID_ARG, "C and X must be device pointers");
+  if (overlaps(C, X, size_t(n) * 4)) return fail(RTG_ERR_INVALID_ARG, "X overlaps C");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SketchPlan sp;
+  RK(build_sketch(shape, sketch_dims, seed, 0, RTG_F32, sp));
+  OpHolder* op = nullptr;
+  RK(get_op(h, A, nA, B, nB, shape, &op));
+  if (apply_uses_st(op->op, RTG_F32, RTG_F32, RTG_F32) &&
+      (reinterpret_cast<uintptr_t>(X) % 16 != 0 || reinterpret_cast<uintptr_t>(C) % 16 != 0))
+    return fail(RTG_ERR_INVALID_ARG, "C and X must be 16-byte aligned for this operator");
+  // workspace: R_0 (n), S(R_0) and S(C) (d each), log lambda, the decision
+  const size_t off_sr = (size_t(n) * 4 + 255) & ~size_t(255);
+  const size_t off_sc = off_sr + ((size_t(sp.d) * 4 + 255) & ~size_t(255));
+  const size_t off_ll = off_sc + ((size_t(sp.d) * 4 + 255) & ~size_t(255));
+  const size_t off_dec = off_ll + 256;
+  RK(h->ws_work.ensure(off_dec + 256));
+  if (h->ws_dec_host == nullptr) CK(cudaMallocHost(&h->ws_dec_host, sizeof(WsDecision)));
+  char* base = static_cast<char*>(h->ws_work.p);
+  float* R0 = reinterpret_cast<float*>(base);
+  float* SR = reinterpret_cast<float*>(base + off_sr);
+  float* SC = reinterpret_cast<float*>(base + off_sc);
+  float* loglam = reinterpret_cast<float*>(base + off_ll);
+  WsDecision* dec = reinterpret_cast<WsDecision*>(base + off_dec);
+  // X_0 = C + net(C) and log lambda (the network's forward kernels, into X)
+  RK(rtg_ws_predict(ws, 1, static_cast<int32_t>(shape.dims[0]), static_cast<int32_t>(shape.dims[1]), C, X, loglam,
+                    stream));
+  // R_0 = C - Phi(X_0), ||S(R_0)|| and ||S(C)||, the decision, X_0 = 0 on fallback
+  const int64_t sc_el = apply_scratch_elems(op->op);
+  void *ta = nullptr, *tb = nullptr;
+  if (sc_el > 0) {
+    std::unique_ptr<ApplyScratch>& as = h->apply_scratch[s];
+    if (!as) as = std::make_unique<ApplyScratch>();
+    RK(as->tA.ensure(size_t(sc_el) * 4));
+    RK(as->tB.ensure(size_t(sc_el) * 4));
+    ta = as->tA.p;
+    tb = as->tB.p;
+  }
+  CK(launch_apply(op->op, RTG_F32, ref(X), ref(R0), -1.0, 1.0, ref(C), ta, tb, nullptr, s));
+  SketchScratch skc;
+  RK(sketch_scratch_for(h, sp, seed, 0, s, &skc));
+  CK(launch_sketch(sp, skc, ref(R0), SR, nullptr, nullptr, s, RTG_F32));
+  CK(launch_sketch(sp, skc, ref(C), SC, nullptr, nullptr, s, RTG_F32));
+  CK(launch_ws_decide(SR, SC, sp.d, loglam, opts.tol, dec, s));
+  CK(launch_ws_zero_if(dec, X, n, s));
+  // the solve: X_0 = X (aliased), a GCV plan whose descriptor gets the decided
+  // lambda (> 0: fixed mu) and stop level on the device, right before its graph
+  WsHook hk{dec};
+  PreLaunch pre{ws_hook, &hk};
+  const int slot = opts.slot;
+  RK(submit_impl(0, h, A, nA, B, nB, shape, RTG_F32, C, m, sketch_dims, seed, -1.0, X, X, &opts, stream, &pre));
+  CK(cudaMemcpyAsync(h->ws_dec_host, dec, sizeof(WsDecision), cudaMemcpyDeviceToHost, s));
+  RK(rtg_gmres_wait(h, slot, info));
+  if (result != nullptr) {
+    static_assert(sizeof(rtg_ws_result) == sizeof(WsDecision), "rtg_ws_result mirrors the device decision");
+    std::memcpy(result, h->ws_dec_host, sizeof(WsDecision));
+  }
+  if (info != nullptr && h->ws_dec_host->lambda > 0.0) info->mu = h->ws_dec_host->lambda;
+  return RTG_OK;
+}

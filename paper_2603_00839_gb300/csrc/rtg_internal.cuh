@@ -130,6 +130,17 @@ struct SolveDesc {
   uint64_t key[2];  // Philox seed and problem id of the sketch signs
 };
 
+// Learned warm start (rtg_ws_solve): the device-side decision taken from
+// ||S(R_0)|| and ||S(C)|| before the solve's graph runs.  Same layout as
+// rtg_ws_result.
+struct WsDecision {
+  int fell_back;    // 1: ||S(C - Phi(X_0))|| >= ||S(C)||: X_0 = 0, GCV
+  int pad;
+  double lambda;    // > 0: exp(predicted log lambda); < 0: GCV over the grid
+  double tol;       // stop level of rho (relative to ||R_0||_Theta of the solve)
+  double sC, sR;    // ||S(C)||, ||S(C - Phi(X_0))|| of the prediction
+};
+
 // Host-visible summary written at the end of a solve (one D2H copy).
 struct InfoDev {
   int iters, restarts, breakdown, converged, status, k, pad0, pad1;
@@ -422,6 +433,16 @@ cudaError_t launch_gk_norm(const Work& w, int phase, const StepOpts& o, cudaStre
 // (and the Givens step of column j beside it); 3: V_{j+1} = (W - beta_{j+1} V_j) / alpha_{j+1};
 // the sketched vectors follow the same recurrences.
 cudaError_t launch_gk_update(const Work& w, int phase, PtrRef src, const StepOpts& o, cudaStream_t s);
+
+// k_solve.cu, learned warm start: decision from the sketches S(R_0) (SR) and
+// S(C) (SC) of d entries and the predicted log lambda; tol is the stop level
+// relative to ||S(C)||.
+cudaError_t launch_ws_decide(const float* SR, const float* SC, int64_t d, const float* loglam, double tol,
+                             WsDecision* dec, cudaStream_t s);
+// X = 0 when the decision fell back
+cudaError_t launch_ws_zero_if(const WsDecision* dec, float* X, int64_t n, cudaStream_t s);
+// the decided lambda and tol into the solve's descriptor (after its upload)
+cudaError_t launch_ws_write_desc(const WsDecision* dec, SolveDesc* desc, cudaStream_t s);
 
 // Phase timing: bounded wait of the stream on a host-written flag.
 cudaError_t launch_gate(const unsigned* flag, unsigned want, unsigned* status, cudaStream_t s);

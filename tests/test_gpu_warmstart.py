@@ -197,3 +197,107 @@ def test_trained_warm_start_saves_steps(api):
             warm.append(rw.iters)
         cold.append(rc.iters)
     assert np.mean(warm) < np.mean(cold)
+
+
+def _bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as FP64."""
+    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("N,H,W", [(2, 16, 24), (1, 32, 32)])
+def test_gradients_match_bf16_rounding_reference(api, N, H, W, monkeypatch):
+    """Whole network against the oracle's forward and backward run with the
+    kernels' roundings: every convolution sees its activations, weights and
+    upstream gradients rounded to BF16 exactly as the tensor-core products
+    do (the bias gradient sums the unrounded FP32 gradient), everything else
+    in FP64.  What remains is FP32 accumulation and the rare ReLU mask of a
+    pre-activation within rounding of zero, so every parameter gradient,
+    encoder layers included, is held to 1e-2 relative (outputs to 1e-3)."""
+    base = 8
+    P = _perturbed(base, 3)
+    rng = np.random.default_rng(4)
+    Cn = rng.standard_normal((N, H, W, 3)).astype(np.float32).astype(np.float64)
+    Xs = (Cn + 0.2 * rng.standard_normal((N, H, W, 3))).astype(np.float32).astype(np.float64)
+    lm = rng.standard_normal(N).astype(np.float32).astype(np.float64)
+    P32 = {k: v.astype(np.float32).astype(np.float64) for k, v in P.items()}
+    conv0, back0 = WS.conv, WS.conv_backward
+
+    def conv_r(x, wt, b, stride):
+        return conv0(_bf16(x), _bf16(wt), b, stride)
+
+    def back_r(x, wt, dy, stride):
+        dx, dw, _ = back0(_bf16(x), _bf16(wt), _bf16(dy), stride)
+        return dx, dw, dy.sum(axis=(0, 1, 2))
+    monkeypatch.setattr(WS, "conv", conv_r)
+    monkeypatch.setattr(WS, "conv_backward", back_r)
+    X0_ref, ll_ref, _ = WS.forward(P32, Cn, base)
+    loss_ref, G_ref = WS.loss_and_grads(P32, Cn, Xs, lm, base)
+    monkeypatch.undo()
+    net = api.WarmStart(base, w.flatten_params(P32))
+    dev = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    Cb, Xb, lmb = dev(_to_solver(Cn)), dev(_to_solver(Xs)), dev(lm)
+    X0, ll = net.predict(Cb, W, H)
+    assert _rel(X0.cpu().double().numpy() - Cb.cpu().double().numpy(),
+                _to_solver(X0_ref) - _to_solver(Cn)) < 1e-3
+    assert np.max(np.abs(ll.cpu().double().numpy() - ll_ref)) < 1e-3 * max(1.0, np.max(np.abs(ll_ref)))
+    loss = net.train_step(Cb, Xb, lmb, W, H, lr=0.0)
+    assert abs(loss - loss_ref) <= 1e-3 * loss_ref
+    _, g = net.get()
+    off = 0
+    for k in P.keys():
+        v = G_ref[k]
+        gv = g[off:off + v.size].reshape(v.shape).astype(np.float64)
+        off += v.size
+        assert _rel(gv, v) < 1e-2, k
+
+
+def _ws_problem(api, h, I=64, seed=5):
+    rng = np.random.default_rng(seed)
+    x, taps, nu = _training_problem(rng, I, seed)
+    return _make(api, h, x, taps, nu, seed)
+
+
+def test_ws_solve_device_path_equals_host_glue(api):
+    """rtg_ws_solve (prediction, fallback test and stop-level rescale on the
+    device) gives the decision and the solve the host-side recipe gives:
+    s_C = ||S(C)||, s_R = ||S(C - Phi(X_0))||, then the solve from X_0 with
+    mu = exp(log lambda) and tol * s_C / s_R, bit for bit."""
+    h = api.Handle(0)
+    base, I, sk, grid = 8, 64, (32, 32, 3), w.mu_grid()
+    P = w.warmstart_params(base, 11)
+    P["out.w"] = P["out.w"] + 0.01 * np.random.default_rng(2).standard_normal(P["out.w"].shape)
+    P["lam.b"] = np.array([np.log(3e-3)])
+    net = api.WarmStart(base, w.flatten_params(P))
+    q = _ws_problem(api, h)
+    X, info, dec = net.solve(h, q["C"], 30, sk, 7, q["A"], [], tol=q["tol"], mu_grid=grid)
+    X0b, ll = net.predict(api.stack_images([q["C"]]), I, I)
+    X0 = api.empty(q["C"].shape, torch.float32)
+    X0.copy_(api.unstack_images(X0b, 1, I, I)[0])
+    R0 = api.empty(q["C"].shape, torch.float32)
+    R0.copy_(q["C"] - h.operator_apply(X0, q["A"], []))
+    sC = float(torch.linalg.vector_norm(h.sketch(q["C"], sk, 7).double()))
+    sR = float(torch.linalg.vector_norm(h.sketch(R0, sk, 7).double()))
+    assert abs(dec["sketch_norm_C"] - sC) <= 1e-6 * sC and abs(dec["sketch_norm_R0"] - sR) <= 1e-6 * sR
+    assert not dec["fell_back"] and sR < sC
+    lam = float(np.exp(np.float64(ll.item())))
+    assert abs(dec["lam"] - lam) <= 1e-6 * lam
+    Xr, ir = h.gmres_solve(q["C"], 30, sk, 7, dec["lam"], q["A"], [], X0=X0, tol=dec["tol"])
+    assert info.iters == ir.iters and info.device_status == 0
+    assert np.array_equal(X.cpu().numpy(), Xr.cpu().numpy())
+
+
+def test_ws_solve_falls_back_to_the_cold_solve(api):
+    """A prediction whose sketched residual is not below ||S(C)|| (the
+    output layer's bias set far off): the device falls back to X_0 = 0 and
+    GCV, and the result equals the plain cold solve bit for bit."""
+    h = api.Handle(0)
+    base, I, sk, grid = 8, 64, (32, 32, 3), w.mu_grid()
+    P = w.warmstart_params(base, 11)
+    P["out.b"] = np.full(3, 50.0)
+    net = api.WarmStart(base, w.flatten_params(P))
+    q = _ws_problem(api, h, seed=6)
+    X, info, dec = net.solve(h, q["C"], 30, sk, 7, q["A"], [], tol=q["tol"], mu_grid=grid, max_restarts=1)
+    assert dec["fell_back"] and dec["lam"] < 0
+    Xc, ic = h.gmres_solve(q["C"], 30, sk, 7, -1.0, q["A"], [], tol=q["tol"], mu_grid=grid, max_restarts=1)
+    assert info.iters == ic.iters and info.mu == ic.mu
+    assert np.array_equal(X.cpu().numpy(), Xc.cpu().numpy())
