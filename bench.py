@@ -286,7 +286,7 @@ def phase_report(h, probs, X, peaks, workload: str):
     share_total = sum(tot_ms.values())
     for k in table:
         table[k]["share"] = round(tot_ms[k] / share_total, 3)
-    cand = [k for k in table if tot_bytes.get(k, 0) > 0]
+    cand = [k for k in table if tot_bytes.get(k, 0) > 0 and k in ("apply", "sketch", "update")]
     dom = max(cand, key=lambda k: tot_ms[k])
     launches = tot_l[dom]
     bytes_per_launch = tot_bytes[dom] / launches
@@ -328,7 +328,7 @@ def batched_phase_report(h, batch, grid, peaks, workload: str):
         if tot_bytes[k] > 0:
             e["gbs"] = round(tot_bytes[k] / (ms[k] * 1e-3) / 1e9, 1)
         table[k] = e
-    cand = [k for k in table if tot_bytes.get(k, 0) > 0]
+    cand = [k for k in table if tot_bytes.get(k, 0) > 0 and k in ("apply", "sketch", "update")]
     dom = max(cand, key=lambda k: ms[k])
     bytes_per_launch = tot_bytes[dom] / launches[dom]
     us_per_launch = 1e3 * ms[dom] / launches[dom]

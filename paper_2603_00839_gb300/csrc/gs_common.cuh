@@ -14,11 +14,15 @@ namespace rtg {
 constexpr int GS_MAXW = 8;   // warps per block of the reducing kernels (256 threads)
 constexpr int kRedCols = 2 * kMaxK + 4;   // columns of one reduction (see gs_ncols)
 // Gram matrices of up to this many rows are staged in shared memory by the
-// step finish (it needs (kMaxK + 6) + r (r + 1) + GS_MAXW r + 4 doubles of scratch)
+// step finish (rows of gram_smem_ld(r) <= r + 2 doubles; it needs
+// (kMaxK + 6) + r (r + 2) + GS_MAXW r + 4 doubles of scratch)
 constexpr int kGramSmemRows = 56;
-static_assert((kMaxK + 6) + kGramSmemRows * (kGramSmemRows + 1) + GS_MAXW * kGramSmemRows + 4 <=
+static_assert((kMaxK + 6) + kGramSmemRows * (kGramSmemRows + 2) + GS_MAXW * kGramSmemRows + 4 <=
                   GS_MAXW * kRedCols,
               "Gram staging must fit the reduction scratch");
+// row stride of the staged n x n Gram matrix: even, so that 16-byte copies
+// land on 16-byte boundaries
+__device__ __forceinline__ int gram_smem_ld(int n) { return (n + 2) & ~1; }
 
 template <typename A>
 __device__ __forceinline__ A warp_sum(A v) {
@@ -372,21 +376,28 @@ __device__ inline void gs_finish_start(const Work& w, const StepOpts& o, const d
   set_cond(o, !ctl->stop, ctl);
 }
 
-// Starts the asynchronous copies (cp.async, 8 bytes each) of the stored
-// Gram matrix rows and columns 0..J-1 into the finish's shared staging area,
-// so that they travel while the last block combines the partial rows; the
-// finish called with staged = true waits for them.  Only where the finish
-// stages G (J + 1 <= kGramSmemRows).  sh: the finish's scratch, whose
-// staging area starts after kMaxK + 6 doubles (past the combine's scratch).
+// Starts the asynchronous copies of the stored Gram matrix rows and columns
+// 0..J-1 into the finish's shared staging area, so that they travel while
+// the last block combines the partial rows; the finish called with
+// staged = true waits for them.  Only where the finish stages G
+// (J + 1 <= kGramSmemRows).  G is symmetric, so column k of G (contiguous
+// in global memory) is copied to row k of the staging area, in 16-byte
+// copies that bypass L1 (cp.async.cg): G's addresses are rewritten with
+// other values by every cycle and every solve of the plan, and only L2 is
+// coherent across the SMs that run successive finishes.  When J is odd the
+// last pair of a column also brings G(J, k), which the finish overwrites
+// with the new row.  sh: the finish's scratch, whose staging area starts
+// after kMaxK + 6 doubles (past the combine's scratch, 16-byte aligned).
 __device__ inline void gs_stage_gram_async(const Work& w, int J, double* sh) {
   const int n = J + 1;
   if (J < 1 || n > kGramSmemRows) return;
-  const int lg = n + 1, ld = w.m + 1;
+  const int lg = gram_smem_ld(n), ldg = gram_ld(w.m), pairs = (J + 1) / 2;
   double* Gs = sh + (kMaxK + 2) + 4;
-  for (int e = threadIdx.x; e < J * J; e += blockDim.x) {
-    const int i = e % J, k = e / J;
-    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(&Gs[i * lg + k]));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(w.G + i + static_cast<int64_t>(ld) * k)
+  for (int e = threadIdx.x; e < J * pairs; e += blockDim.x) {
+    const int p = e % pairs, k = e / pairs;
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(&Gs[k * lg + 2 * p]));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa),
+                 "l"(w.G + static_cast<int64_t>(ldg) * k + 2 * p)
                  : "memory");
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -408,7 +419,7 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
                                       bool staged = false) {
   Ctl* ctl = w.ctl;
   const int J = ctl->j;
-  const int ld = w.m + 1;
+  const int ld = w.m + 1, ldg = gram_ld(w.m);
   const double* h1 = tot;
   const double s2 = tot[J + 1];
   const double* grow = tot + J + 2;
@@ -418,10 +429,10 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n = J + 1;
   if (n <= kGramSmemRows) {
-    // G staged in shared memory (row stride n + 1); each product G x runs
+    // G staged in shared memory (even row stride); each product G x runs
     // on every warp: warp w takes a slice of the columns, lane the rows
     // lane and lane + 32, and the warps' partial rows are summed in order
-    const int lg = n + 1;
+    const int lg = gram_smem_ld(n);
     double* Gs = red + 4;              // n x n
     double* pr = Gs + n * lg;          // [nw][n] partial products
     double* ab = pr + nw * n;          // [2][2] the two warps' sums of a and b
@@ -438,7 +449,7 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
       for (int u = 0; u < 8; ++u) {
         const int e = e0 + u * blockDim.x + threadIdx.x;
         const int i = e % n, k = e / n;
-        v[u] = (e >= n * n) ? 0.0 : (i == J) ? grow[k] : (k == J ? grow[i] : G[i + static_cast<int64_t>(ld) * k]);
+        v[u] = (e >= n * n) ? 0.0 : (i == J) ? grow[k] : (k == J ? grow[i] : __ldcg(G + i + static_cast<int64_t>(ldg) * k));
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -447,8 +458,8 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
       }
     }
     for (int i = threadIdx.x; i <= J; i += blockDim.x) {   // new row/column, for later steps
-      G[i + static_cast<int64_t>(ld) * J] = grow[i];
-      G[J + static_cast<int64_t>(ld) * i] = grow[i];
+      G[i + static_cast<int64_t>(ldg) * J] = grow[i];
+      G[J + static_cast<int64_t>(ldg) * i] = grow[i];
     }
     __syncthreads();
     const int ks = (n + nw - 1) / nw;
@@ -500,14 +511,14 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
     }
   } else {
     for (int i = threadIdx.x; i <= J; i += blockDim.x) {
-      G[i + static_cast<int64_t>(ld) * J] = grow[i];
-      G[J + static_cast<int64_t>(ld) * i] = grow[i];
+      G[i + static_cast<int64_t>(ldg) * J] = grow[i];
+      G[J + static_cast<int64_t>(ldg) * i] = grow[i];
     }
     __syncthreads();
     // h = 2 h1 - G h1: one warp per row, lanes across the columns
     for (int i = warp; i <= J; i += nw) {
       double gh = 0.0;
-      for (int k = lane; k <= J; k += 32) gh += G[i + static_cast<int64_t>(ld) * k] * h1[k];
+      for (int k = lane; k <= J; k += 32) gh += __ldcg(G + i + static_cast<int64_t>(ldg) * k) * h1[k];
       gh = warp_sum(gh);
       if (lane == 0) col[i] = 2.0 * h1[i] - gh;
     }
@@ -515,7 +526,7 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
     double* hgh_row = red + 4;         // (G h)_i * h_i per row
     for (int i = warp; i <= J; i += nw) {
       double gh = 0.0;
-      for (int k = lane; k <= J; k += 32) gh += G[i + static_cast<int64_t>(ld) * k] * col[k];
+      for (int k = lane; k <= J; k += 32) gh += __ldcg(G + i + static_cast<int64_t>(ldg) * k) * col[k];
       gh = warp_sum(gh);
       if (lane == 0) hgh_row[i] = gh * col[i];
     }
@@ -630,8 +641,12 @@ __device__ inline void givens_step(const Work& w, const StepOpts& o) {
     } else if (J + 1 >= w.m) {
       // end of a cycle: restart from the least-squares iterate while cycles
       // remain (the body's restart kernels run when rs_skip is 0), else stop
-      if (ctl->cycle + 1 < w.cycles) ctl->rs_skip = 0;
-      else ctl->stop = 1;
+      if (ctl->cycle + 1 < w.cycles) {
+        ctl->rs_skip = 0;
+        if (o.use_rs_cond) cudaGraphSetConditional(static_cast<cudaGraphConditionalHandle>(o.rs_cond), 1u);
+      } else {
+        ctl->stop = 1;
+      }
     }
   }
   // the body runs at most m times per cycle

@@ -50,9 +50,9 @@ k_apply_fused(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Bat
   Zr = Zr.at(bi.off);
   stop = bsh(stop, bi.off);
   if (stop != nullptr && *stop) return;
-  const T* __restrict__ X = Xr.get<const T>();
+  const T* X = Xr.get<const T>();
   T* __restrict__ Y = Yr.get<T>();
-  const T* __restrict__ Z = Zr.get<const T>();
+  const T* Z = Zr.get<const T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T t1s[kMaxTaps], t2s[kMaxTaps];
   const int Wd = FTX + 2 * a.r1;
@@ -128,16 +128,6 @@ constexpr int RTY = 16;
 constexpr int RSEG = 8;    // mode-1 outputs per thread
 constexpr int VSEG = 4;    // mode-2 outputs per thread
 
-__device__ __forceinline__ void cp_async4z(void* smem, const void* gmem, bool valid) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  const int sz = valid ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
-}
-__device__ __forceinline__ void cp_async8z(void* smem, const void* gmem, bool valid) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  const int sz = valid ? 8 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
-}
 
 template <int RR, typename T>
 struct RegGeom {
@@ -158,9 +148,9 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
   Zr = Zr.at(bi.off);
   stop = bsh(stop, bi.off);
   if (stop != nullptr && *stop) return;
-  const T* __restrict__ X = Xr.get<const T>();
+  const T* X = Xr.get<const T>();
   T* __restrict__ Y = Yr.get<T>();
-  const T* __restrict__ Z = Zr.get<const T>();
+  const T* Z = Zr.get<const T>();
   using G = RegGeom<RR, T>;
   constexpr int NT = 2 * RR + 1;
   constexpr int Wd = G::Wd, Ht = G::Ht, RA = G::RA, OFF = G::OFF;
@@ -202,8 +192,9 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
         const int gy = y0 - RR + yy, gx = x0 - RA + xx;
         const bool v = gy >= 0 && gy < I2 && gx >= 0 && gx < I1;
         const T* src = v ? Xs + c * plane + static_cast<int64_t>(gy) * I1 + gx : X;
-        if (sizeof(T) == 8) cp_async8z(&in_s[idx], src, v);
-        else cp_async4z(&in_s[idx], src, v);
+        // element loads through L2 (the basis slots are rewritten by every
+        // cycle and solve; only L2 is coherent across SMs)
+        in_s[idx] = v ? __ldcg(src) : static_cast<T>(0);
       }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -348,9 +339,9 @@ k_apply_st(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, StArgs a, Batch bt)
   Zr = Zr.at(bi.off);
   stop = bsh(stop, bi.off);
   if (stop != nullptr && *stop) return;
-  const TI* __restrict__ X = Xr.get<const TI>();
+  const TI* X = Xr.get<const TI>();
   TO* __restrict__ Y = Yr.get<TO>();
-  const float* __restrict__ Z = Zr.get<const float>();
+  const float* Z = Zr.get<const float>();
   using G = StGeom<RR, TI>;
   constexpr int V = G::V, Wd = G::Wd, Ht = G::Ht, RA = G::RA, OFF = G::OFF;
   constexpr int NT = 2 * RR + 1;
@@ -381,7 +372,7 @@ k_apply_st(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, StArgs a, Batch bt)
       const int gy = y0 - RR + yy, gx = x0 - RA + V * f;
       if (gy < 0 || gy >= I2 || gx < 0 || gx >= I1) continue;
       const int64_t pl = (static_cast<int64_t>(group) * NC + c) + a.I3 * u;
-      pre[q] = __ldg(reinterpret_cast<const uint4*>(X + pl * plane + static_cast<int64_t>(gy) * I1 + gx));
+      pre[q] = __ldcg(reinterpret_cast<const uint4*>(X + pl * plane + static_cast<int64_t>(gy) * I1 + gx));
     }
   };
   auto store_frame = [&]() {
@@ -534,7 +525,7 @@ __global__ void k_pass_band(PtrRef Xr, PtrRef Yr, int64_t L, int64_t I, int64_t 
   Yr = Yr.at(bo);
   stop = bsh(stop, bo);
   if (stop != nullptr && *stop) return;
-  const T* __restrict__ X = Xr.get<const T>();
+  const T* X = Xr.get<const T>();
   T* __restrict__ Y = Yr.get<T>();
   const int64_t total = L * I * R;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
@@ -554,13 +545,13 @@ __global__ void k_pass_band(PtrRef Xr, PtrRef Yr, int64_t L, int64_t I, int64_t 
 // out(l, p, r) = sum_i M(p, i) X(l, i, r), M column-major on the device
 template <typename T>
 __global__ void k_pass_dense(PtrRef Xr, PtrRef Yr, int64_t L, int64_t I, int64_t R,
-                             const double* __restrict__ M, const int* stop, Batch bt) {
+                             const double* M, const int* stop, Batch bt) {
   const int64_t bo = bidx(bt).off;
   Xr = Xr.at(bo);
   Yr = Yr.at(bo);
   stop = bsh(stop, bo);
   if (stop != nullptr && *stop) return;
-  const T* __restrict__ X = Xr.get<const T>();
+  const T* X = Xr.get<const T>();
   T* __restrict__ Y = Yr.get<T>();
   const int64_t total = L * I * R;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;

@@ -291,13 +291,14 @@ cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s, unsigned*
   return cudaGetLastError();
 }
 
-__global__ void k_restart_done(Work w0) {
+__global__ void k_restart_done(Work w0, StepOpts o) {
   Ctl* ctl = bsh(w0.ctl, bidx(w0.b).off);
   ctl->rs_skip = 1;
+  if (o.use_rs_cond) cudaGraphSetConditional(static_cast<cudaGraphConditionalHandle>(o.rs_cond), 0u);
 }
 
-cudaError_t launch_restart_done(const Work& w, cudaStream_t s) {
-  k_restart_done<<<dim3(1, 1, w.b.n), 1, 0, s>>>(w);
+cudaError_t launch_restart_done(const Work& w, const StepOpts& o, cudaStream_t s) {
+  k_restart_done<<<dim3(1, 1, w.b.n), 1, 0, s>>>(w, o);
   return cudaGetLastError();
 }
 

@@ -186,9 +186,9 @@ struct FragArgs {
 // One thread per (tile, k-tile, lane) of every stage: the fragment
 // registers of mma.m16n8k16 for Theta (A operand, first stage) or
 // Theta^T (B operand, later stages).
-__global__ void k_theta_frags(FragArgs a, const uint32_t* __restrict__ bits0, uint32_t* frags0, Batch bt) {
+__global__ void k_theta_frags(FragArgs a, const uint32_t* bits0, uint32_t* frags0, Batch bt) {
   const int64_t bo = bidx(bt).off;
-  const uint32_t* __restrict__ bits = bsh(bits0, bo);
+  const uint32_t* bits = bsh(bits0, bo);
   uint32_t* frags = bsh(frags0, bo);
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= a.total_lanes) return;
@@ -296,16 +296,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
 }
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
-}
-// 4-byte copy; src_size 0 writes a zero and reads nothing
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool valid) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  const int sz = valid ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
-}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 constexpr int F_NT = F_COLS / 8;  // first stage: n8 tiles per CTA
@@ -352,7 +342,7 @@ __device__ __forceinline__ int64_t out_pos(const OutMap& om, int64_t l, int64_t 
 template <int CH, typename TI>
 __global__ void __launch_bounds__(TC_THREADS)
 k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t s, int kt_total,
-              const uint4* __restrict__ fragA, int mt_total, float scale, OutMap om,
+              const uint4* fragA, int mt_total, float scale, OutMap om,
               int* status, int poison, const int* stop, Batch bt) {
   {
     const int64_t bo = bidx(bt).off;
@@ -366,7 +356,7 @@ k_sk_first_tc(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_t 
   // BF16 data are exact in one limb; FP32 data take three (see split_pair)
   constexpr int LIMBS = sizeof(TI) == 4 ? 3 : 1;
   constexpr int EV = 16 / static_cast<int>(sizeof(TI));   // elements per 16 bytes
-  const TI* __restrict__ X = Xr.get<const TI>();
+  const TI* X = Xr.get<const TI>();
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   constexpr int XS = CH * 16 + 8;
@@ -502,7 +492,7 @@ constexpr size_t inner_smem() {
 template <int CH>
 __global__ void __launch_bounds__(TC_THREADS, 3)
 k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int64_t I, int64_t R,
-              int64_t s, int kt_total, const uint2* __restrict__ fragB, int nt_total, float scale,
+              int64_t s, int kt_total, const uint2* fragB, int nt_total, float scale,
               OutMap om, int dots_pass, Work w, StepOpts o, int* status, int poison, const int* stop,
               Batch bt) {
   {
@@ -516,7 +506,7 @@ k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int
     stop = bsh(stop, bo);
   }
   if (stop != nullptr && *stop) return;
-  const float* __restrict__ X = Xr.get<const float>();
+  const float* X = Xr.get<const float>();
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   uint2* fB = reinterpret_cast<uint2*>(smem);                                    // [CH][N_NT][32]
@@ -653,7 +643,7 @@ k_sk_inner_tc(PtrRef Xr, int in_blocked, float* __restrict__ out, int64_t L, int
 // Y(l, q, r) = scale * sum_i (-1)^bit(q, i) X(l, i, r)
 template <typename T>
 __global__ void k_sketch_mode(PtrRef Xr, T* __restrict__ Y, int64_t L, int64_t I, int64_t R,
-                              int64_t s, const uint32_t* __restrict__ bits, int wpr, T scale,
+                              int64_t s, const uint32_t* bits, int wpr, T scale,
                               const int* stop, Batch bt) {
   {
     const int64_t bo = bidx(bt).off;
@@ -663,7 +653,7 @@ __global__ void k_sketch_mode(PtrRef Xr, T* __restrict__ Y, int64_t L, int64_t I
     stop = bsh(stop, bo);
   }
   if (stop != nullptr && *stop) return;
-  const T* __restrict__ X = Xr.get<const T>();
+  const T* X = Xr.get<const T>();
   const int64_t total = L * s * R;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
        o += (int64_t)gridDim.x * blockDim.x) {
@@ -674,7 +664,7 @@ __global__ void k_sketch_mode(PtrRef Xr, T* __restrict__ Y, int64_t L, int64_t I
     const uint32_t* brow = bits + q * wpr;
     T acc = 0;
     for (int w = 0; w < wpr; ++w) {
-      const uint32_t b = __ldg(brow + w);
+      const uint32_t b = __ldcg(brow + w);
       const int64_t i0 = static_cast<int64_t>(w) * 32;
       const int cnt = (I - i0) < 32 ? static_cast<int>(I - i0) : 32;
       for (int u = 0; u < cnt; ++u) {

@@ -398,7 +398,7 @@ size_t carve_work(void* mem, int dtype, int64_t n, const SketchPlan& sp, int m, 
   w.cs = c.take<double>(m);
   w.sn = c.take<double>(m);
   w.g = c.take<double>(m + 1);
-  w.G = c.take<double>(size_t(m + 1) * (m + 1));
+  w.G = c.take<double>(size_t(gram_ld(m)) * (m + 1));
   w.rho_hist = c.take<double>(kMaxK);
   w.y = c.take<double>(m);
   w.gcv = c.take<double>(kMaxMu);
@@ -462,6 +462,7 @@ struct SolvePlan {
   int vdtype = RTG_F32;                                           // storage of V and W
   int launches_pro = 0, launches_step = 0, launches_epi = 0;   // kernels per phase
   int launches_setup = 0;                                         // reset + Theta, part of the prologue
+  int launches_restart = 0;   // one restart sequence (graph: per restart; direct: every step)
   int direct_steps = 0;                                           // steps launched by the last direct solve
   int* stop_host = nullptr;                                       // pinned: ctl->stop read back per direct step
   bool ext_desc = false;  // desc/info live in a batch's buffers (not owned)
@@ -759,8 +760,40 @@ rtg_status enqueue_restart(SolvePlan& P, const StepOpts& so, cudaStream_t s) {
   SketchDots dots{&w, 0, so};
   CK(launch_sketch(P.sp, P.sk, ref(w.V), fused ? w.S : w.Spart, fused ? &dots : nullptr, gate, s, P.vdtype, w.b));
   CK(launch_start(w, ref(w.V), so, fused, s, P.vdtype, gate));
-  CK(launch_restart_done(w, s));
+  CK(launch_restart_done(w, so, s));
   return RTG_OK;
+}
+
+// The restart sequence as the body of an IF node appended to the capture on
+// cs (so.rs_cond is the node's condition handle).
+rtg_status capture_restart_if(SolvePlan& P, const StepOpts& so, cudaStream_t cs) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t gcap = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &gcap, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = static_cast<cudaGraphConditionalHandle>(so.rs_cond);
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  CK(cudaGraphAddNode(&node, gcap, deps, nullptr, nd, &cp));
+  CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaStream_t c3 = nullptr;
+  CK(cudaStreamCreateWithFlags(&c3, cudaStreamNonBlocking));
+  rtg_status st = RTG_OK;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(c3, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCaptureToGraph(restart)");
+  if (st == RTG_OK) {
+    st = enqueue_restart(P, so, c3);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(c3, &out);
+    if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture(restart)");
+  }
+  cudaStreamDestroy(c3);
+  return st;
 }
 
 int restart_launches(const OpPlan& op, const SketchPlan& sp, int dtype, int vdtype) {
@@ -882,7 +915,7 @@ rtg_status build_branch(SolvePlan& P, cudaGraph_t g) {
   } sg{cs, cs2};
   cudaGraphConditionalHandle hnd;
   CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
-  const StepOpts so = solve_step_opts(P, 1, hnd);
+  StepOpts so = solve_step_opts(P, 1, hnd);
   CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   rtg_status st = P.method == 1 ? enqueue_gk_prologue(P, so, cs) : enqueue_prologue(P, so, cs);
   cudaStreamCaptureStatus cst;
@@ -909,12 +942,21 @@ rtg_status build_branch(SolvePlan& P, cudaGraph_t g) {
   }
   if (st == RTG_OK) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // restarts: an IF node at the end of the body holds the restart
+    // sequence; the Givens block that ends a cycle sets its condition
+    if (P.w.cycles > 1) {
+      cudaGraphConditionalHandle rh;
+      cudaError_t e = cudaGraphConditionalHandleCreate(&rh, body, 0, cudaGraphCondAssignDefault);
+      if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphConditionalHandleCreate(restart)");
+      so.use_rs_cond = 1;
+      so.rs_cond = static_cast<unsigned long long>(rh);
+    }
     cudaError_t e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCaptureToGraph(body)");
+    if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCaptureToGraph(body)");
     if (st == RTG_OK) {
       st = P.method == 1 ? enqueue_gk_step(P, so, cs2)
                          : enqueue_step(P.op, P.sp, P.w, P.dtype, P.tA, P.tB, P.sk, so, cs2);
-      if (st == RTG_OK && P.w.cycles > 1) st = enqueue_restart(P, so, cs2);
+      if (st == RTG_OK && P.w.cycles > 1) st = capture_restart_if(P, so, cs2);
       cudaGraph_t bodyout = nullptr;
       e = cudaStreamEndCapture(cs2, &bodyout);
       if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture(body)");
@@ -1084,8 +1126,8 @@ rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDe
     P->launches_pro = P->launches_setup +
                       (has_x0 ? apply_launches(P->op.op, true, dtype, dtype, vdtype) : 0) +
                       sketch_launches(sp) + gs + 1;
-    P->launches_step = apply_launches(P->op.op, false, dtype, vdtype, vdtype) + sketch_launches(sp) + gs + 1 +
-                       (ps.cycles > 1 ? restart_launches(P->op.op, sp, dtype, vdtype) : 0);
+    P->launches_step = apply_launches(P->op.op, false, dtype, vdtype, vdtype) + sketch_launches(sp) + gs + 1;
+    P->launches_restart = ps.cycles > 1 ? restart_launches(P->op.op, sp, dtype, vdtype) : 0;
     P->launches_epi = 3 + (ps.true_resid ? apply_launches(P->op.op, true, dtype, dtype, dtype) +
                                                sketch_launches(sp) + 1 : 0);
     if (ps.method == 1) {
@@ -1119,7 +1161,8 @@ void fill_info(const SolvePlan& P, const InfoDev& I, int mode, int n_mu, bool us
   info->true_rel_resid_theta = P.true_resid ? I.true_rel_resid_theta : -1.0;
   info->elapsed_ms = ms;
   info->device_status = I.status;
-  info->launches = P.launches_pro + P.launches_epi + (use_graph ? I.iters : P.direct_steps) * P.launches_step;
+  info->launches = P.launches_pro + P.launches_epi + (use_graph ? I.iters : P.direct_steps) * P.launches_step +
+                   (use_graph ? I.restarts : P.direct_steps) * P.launches_restart;
   for (int k = 0; k < RTG_PHASE_COUNT; ++k) {
     info->phase_ms[k] = 0.0;
     info->phase_launches[k] = 0;

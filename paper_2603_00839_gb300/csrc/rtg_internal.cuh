@@ -149,6 +149,11 @@ struct InfoDev {
   double gcv[kMaxMu];
 };
 
+// Leading dimension of the Gram matrix G of the stored sketched basis: even,
+// so that every column starts on a 16-byte boundary (the step finish stages
+// it in shared memory with 16-byte copies that bypass L1).
+__host__ __device__ inline int gram_ld(int m) { return (m + 2) & ~1; }
+
 // Workspace of one Arnoldi process.  T is the data type (double / float).
 // Doubles of the reduced solve's per-CTA working set: two (m+1) x (m+1)
 // matrices and two vectors of m+1.
@@ -180,7 +185,8 @@ struct Work {
   double* cs;                  // Givens cosines (m)
   double* sn;                  // Givens sines (m)
   double* g;                   // rotated right-hand side (m+1)
-  double* G;                   // (m+1) x (m+1) Gram matrix of the stored sketched basis
+  double* G;                   // (m+1) x (m+1) Gram matrix of the stored sketched basis, leading
+                               // dimension gram_ld(m)
   double* rho_hist;            // (m) per cycle
   double* y;                   // solution coefficients (m)
   double* gcv;                 // GCV values (kMaxMu)
@@ -377,6 +383,11 @@ struct StepOpts {
   int solve_mode;        // 1: skip V_{j+1} once the solve stops
   int use_cond;
   unsigned long long cond;   // cudaGraphConditionalHandle
+  // restarts in a graph: the IF node around the body's restart sequence
+  // (set to 1 by the Givens block that ends a cycle, back to 0 by the
+  // sequence's last kernel)
+  int use_rs_cond;
+  unsigned long long rs_cond;
   // lock-step batch: problems still running (the loop ends when it reaches 0);
   // shared by the batch, not moved with a problem's memory
   unsigned* group_left;
@@ -406,8 +417,8 @@ cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s);
 // group_left (lock-step batch): set to the number of problems
 cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s, unsigned* group_left = nullptr,
                          const int* gate = nullptr);
-// end of a restart sequence: rs_skip = 1 again
-cudaError_t launch_restart_done(const Work& w, cudaStream_t s);
+// end of a restart sequence: rs_skip = 1 again (and the IF node's condition 0)
+cudaError_t launch_restart_done(const Work& w, const StepOpts& o, cudaStream_t s);
 
 // k_solve.cu: projected Tikhonov / GCV, assembly and the info summary.
 struct FinishOpts {

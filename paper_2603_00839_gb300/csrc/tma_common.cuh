@@ -19,7 +19,14 @@ __device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
+// Every caller refills shared memory that its threads read with ordinary
+// (generic-proxy) loads before the barrier that precedes the copy; the copy
+// writes through the async proxy, so a proxy fence must order those reads
+// before it.  Without the fence a copy can land before reads that the
+// barrier has not yet performed -- observed as corrupted stretches of ring
+// slots when CTAs of other kernels shared the SM (concurrent graph branches).
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   asm volatile(
       "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
           smem_u32(dst)),

@@ -236,3 +236,30 @@ def test_lockstep_direct_and_phase_timed_launches_equal_the_graph(h):
     assert rd[0].phase_launches["apply"] == max(r.iters for r in rd[:3])
     assert rd[3].phase_launches["apply"] == max(r.iters for r in rd[3:])
     assert all(v >= 0 for v in rd[0].phase_ms.values()) and rd[0].phase_ms["sketch"] > 0
+
+
+def test_many_identical_branches_equal_the_single_solve(h):
+    """128 identical 512x512x3 FP32 problems as concurrent graph branches: every
+    result equals the single solve bit for bit.  Regression test for the ring
+    refill of the basis update: its bulk copies into shared memory need a proxy
+    fence after the threads' reads of the slot, and without it a few of these
+    copies (CTAs of other kernels sharing the SM) read corrupted slots."""
+    api = _api()
+    I1 = I2 = 512
+    dims, sk = (I1, I2, 3), (128, 128, 3)
+    a = w.gaussian_taps(2.0, 6)
+    A = [api.banded(1, I1, a), api.banded(2, I2, a)]
+    B = [api.dense(3, w.channel_mix())]
+    x = w.piecewise_image(I1, I2, 3, 7)
+    Xt = api.to_device(x, torch.float32)
+    Ch = h.operator_apply(Xt, A, B)
+    E = api.to_device(w.noise_draw(dims, 7), torch.float32)
+    C = api.empty(dims, torch.float32)
+    C.copy_(Ch + E * (1e-2 * torch.linalg.vector_norm(Ch) / torch.linalg.vector_norm(E)))
+    Xs, rs = h.gmres_solve(C, 30, sk, 3, 1e-3, A, B, tol=0.0)
+    Xs = Xs.cpu().numpy()
+    probs = [dict(C=C, A=A, B=B, m=30, sketch_dims=sk, seed=3, lam=1e-3, tol=0.0) for _ in range(128)]
+    for _ in range(2):
+        Xb, rb = h.gmres_solve_batched(probs)
+        bad = [i for i in range(len(probs)) if not np.array_equal(Xb[i].cpu().numpy(), Xs)]
+        assert not bad, f"{len(bad)} of {len(probs)} branches differ from the single solve"
