@@ -531,6 +531,20 @@ rtg_status rtg_sketch_noalloc(rtg_shape shape, rtg_dtype dtype, const int64_t* s
                               uint64_t seed, uint64_t problem_id, const void* X, void* SX,
                               rtg_stream stream);
 
+/*
+ * Diagnostics (no paper counterpart).  Every device-side wait of the
+ * library on a flag that another agent sets (the host-opened gates of phase
+ * timing) is bounded by globaltimer and, on expiry, records RTG_ERR_TIMEOUT
+ * where the host reads it and returns, leaving the context usable.  This
+ * call exercises that path on `device`: a wait of limit_ms (1..10000) on a
+ * flag in mapped host memory that nothing sets, then a wait whose flag is
+ * already met on the same stream.  *status_out receives the status the first
+ * wait recorded (RTG_ERR_TIMEOUT expected); the call returns RTG_ERR_CUDA if
+ * the stream did not come back or the second wait reported a timeout.
+ * Synchronous; allocates a few bytes of pinned host memory.
+ */
+rtg_status rtg_selftest_bounded_wait(int32_t device, int32_t limit_ms, int32_t* status_out);
+
 #ifdef __cplusplus
 }
 #endif

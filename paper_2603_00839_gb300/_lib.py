@@ -118,6 +118,7 @@ _SIGS = {
     "rtg_ws_train_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_float, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "rtg_nn_conv3x3": (C.c_int, [C.c_int32] * 7 + [C.c_void_p] * 8 + [C.c_void_p]),
+    "rtg_selftest_bounded_wait": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "rtg_ws_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Factor), C.c_int32, C.POINTER(Factor),
                                C.c_int32, Shape, C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.c_uint64,
                                C.c_void_p, C.POINTER(Opts), C.POINTER(Info), C.POINTER(WsResult), C.c_void_p]),

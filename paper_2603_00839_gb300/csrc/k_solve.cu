@@ -284,16 +284,17 @@ __global__ void k_finalize(Work w0, InfoDev* info0) {
 
 // Holds the stream until the host has queued a whole kernel group (phase
 // timing): one thread polls a flag in mapped host memory.  The wait is
-// bounded (10 s of globaltimer, room for the lazy loading of modules on a
-// first launch); on expiry the kernel records
+// bounded (limit_ns of globaltimer; phase timing gives 10 s, room for the
+// lazy loading of modules on a first launch); on expiry the kernel records
 // RTG_ERR_TIMEOUT in *status and returns, so the stream never stalls.
-__global__ void k_gate(const volatile unsigned* flag, unsigned want, volatile unsigned* status) {
+__global__ void k_gate(const volatile unsigned* flag, unsigned want, volatile unsigned* status,
+                       unsigned long long limit_ns) {
   unsigned long long t0;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
   while (*flag < want) {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > 10000000000ull) {
+    if (t - t0 > limit_ns) {
       *status = RTG_ERR_TIMEOUT;
       return;
     }
@@ -301,8 +302,9 @@ __global__ void k_gate(const volatile unsigned* flag, unsigned want, volatile un
   }
 }
 
-cudaError_t launch_gate(const unsigned* flag, unsigned want, unsigned* status, cudaStream_t s) {
-  k_gate<<<1, 1, 0, s>>>(flag, want, status);
+cudaError_t launch_gate(const unsigned* flag, unsigned want, unsigned* status, cudaStream_t s,
+                        unsigned long long limit_ns) {
+  k_gate<<<1, 1, 0, s>>>(flag, want, status, limit_ns);
   return cudaGetLastError();
 }
 

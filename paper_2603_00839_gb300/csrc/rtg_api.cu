@@ -2036,3 +2036,41 @@ extern "C" rtg_status rtg_ws_solve(rtg_ws ws, rtg_handle h, const rtg_factor* A,
   if (info != nullptr && h->ws_dec_host->lambda > 0.0) info->mu = h->ws_dec_host->lambda;
   return RTG_OK;
 }
+
+// ================================================================== diagnostics
+
+extern "C" rtg_status rtg_selftest_bounded_wait(int32_t device, int32_t limit_ms, int32_t* status_out) {
+  if (status_out == nullptr) return fail(RTG_ERR_INVALID_ARG, "status_out is NULL");
+  if (limit_ms < 1 || limit_ms > 10000) return fail(RTG_ERR_INVALID_ARG, "limit_ms=%d not in 1..10000", limit_ms);
+  int count = 0;
+  CK(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return fail(RTG_ERR_INVALID_ARG, "device %d not in 0..%d", device, count - 1);
+  DeviceGuard dg(device);
+  void* p = nullptr;
+  CK(cudaHostAlloc(&p, 2 * sizeof(unsigned), cudaHostAllocMapped));
+  struct Free {
+    void* p;
+    ~Free() { cudaFreeHost(p); }
+  } fr{p};
+  unsigned* host = static_cast<unsigned*>(p);
+  host[0] = 0;   // the flag: nothing sets it
+  host[1] = 0;   // the status the kernel writes
+  unsigned* dev = nullptr;
+  CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&dev), host, 0));
+  cudaStream_t s = nullptr;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  // the wait on a flag nothing sets, then a wait whose flag is already met
+  // (the stream and the context stay usable after the expiry)
+  cudaError_t e = launch_gate(dev, 1u, dev + 1, s, static_cast<unsigned long long>(limit_ms) * 1000000ull);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  const unsigned first = __atomic_load_n(host + 1, __ATOMIC_ACQUIRE);
+  __atomic_store_n(host + 1, 0u, __ATOMIC_RELEASE);
+  if (e == cudaSuccess) e = launch_gate(dev, 0u, dev + 1, s, 1000000000ull);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test");
+  if (__atomic_load_n(host + 1, __ATOMIC_ACQUIRE) != 0u)
+    return fail(RTG_ERR_CUDA, "a wait on a flag that was already set reported a timeout");
+  *status_out = static_cast<int32_t>(first);
+  return RTG_OK;
+}

@@ -456,5 +456,6 @@ cudaError_t launch_ws_zero_if(const WsDecision* dec, float* X, int64_t n, cudaSt
 cudaError_t launch_ws_write_desc(const WsDecision* dec, SolveDesc* desc, cudaStream_t s);
 
 // Phase timing: bounded wait of the stream on a host-written flag.
-cudaError_t launch_gate(const unsigned* flag, unsigned want, unsigned* status, cudaStream_t s);
+cudaError_t launch_gate(const unsigned* flag, unsigned want, unsigned* status, cudaStream_t s,
+                        unsigned long long limit_ns = 10000000000ull);
 }  // namespace rtg

@@ -188,3 +188,25 @@ def test_overflow_during_the_iteration_is_reported(h):
     X, info = h.gmres_solve(api.to_device(C, torch.float32), 10, sk, 2, 1e-3, [], big, tol=1e-3)
     assert info.device_status == 6
     assert np.isfinite(info.beta) and info.iters <= 1
+
+
+# ------------------------------------------------------------------------ bounded waits
+
+def test_bounded_device_wait_times_out_and_the_context_stays_usable(h):
+    """A device-side wait on a flag that nothing sets gives up after its
+    limit with RTG_ERR_TIMEOUT (no trap, no fault), the same stream then runs
+    a wait whose flag is met, and a solve afterwards is correct."""
+    import ctypes
+    import time
+    from paper_2603_00839_gb300 import _lib as L
+    st = ctypes.c_int32(-1)
+    t0 = time.perf_counter()
+    L.check(L.load().rtg_selftest_bounded_wait(0, 200, ctypes.byref(st)))
+    el = time.perf_counter() - t0
+    assert st.value == L.ERR_TIMEOUT
+    assert 0.19 <= el < 5.0
+    mats, C, th, A, B, sk = _small_problem()
+    ref = oracle.rtg_gmres(mats, C, 8, th, tol=0.0, lam=1e-3)
+    api = _api()
+    X, info = h.gmres_solve(api.to_device(C, torch.float64), 8, sk, 2, 1e-3, A, B)
+    assert info.device_status == 0 and _relnorm(X.cpu().numpy(), ref["X"]) < 1e-9
