@@ -31,6 +31,17 @@ __device__ __forceinline__ A warp_sum(A v) {
   return v;
 }
 
+// Last-block ticket: an atomic increment (wrapping to zero after `last`)
+// with acquire-release semantics at GPU scope.  The barrier before it makes
+// the block's writes (its partial row) precede the release; the barrier
+// after it orders the last block's reads after the acquire.  Cheaper than
+// two full fences around a relaxed atomic.
+__device__ __forceinline__ unsigned ticket_acq_rel(unsigned* counter, unsigned last) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.inc.u32 %0, [%1], %2;" : "=r"(old) : "l"(counter), "r"(last) : "memory");
+  return old;
+}
+
 // Condition of the device-side loop.  A lock-step batch (o.group_left set)
 // keeps looping while any of its problems runs: each problem's stop is
 // counted once, and the count reaching zero ends the loop.
@@ -279,13 +290,11 @@ template <bool FFROWS, typename Pre = void (*)()>
 __device__ inline bool last_block_combine(const Work& w, int ncols, double* tot, int* am_last,
                                           double* scratch, Pre pre = nullptr) {
   using V = typename std::conditional<FFROWS, FF, double>::type;
-  __threadfence();
   __syncthreads();
   const unsigned nblk = gridDim.x * gridDim.y;
-  if (threadIdx.x == 0) *am_last = (atomicInc(w.counter, nblk - 1) == nblk - 1);
+  if (threadIdx.x == 0) *am_last = (ticket_acq_rel(w.counter, nblk - 1) == nblk - 1);
   __syncthreads();
   if (!*am_last) return false;
-  __threadfence();
   if constexpr (!std::is_same<Pre, void (*)()>::value) pre();   // e.g. start the Gram staging copies
   auto add = [](V x, V y) -> V {
     if constexpr (FFROWS) return ff_add_lazy(x, y);
@@ -420,6 +429,7 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
   Ctl* ctl = w.ctl;
   const int J = ctl->j;
   const int ld = w.m + 1, ldg = gram_ld(w.m);
+  const double bd_tol = o.desc_bd_tol ? *o.desc_bd_tol : o.bd_tol;   // loaded early, used at the end
   const double* h1 = tot;
   const double s2 = tot[J + 1];
   const double* grow = tot + J + 2;
@@ -555,12 +565,13 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
   for (int i = J + 2 + threadIdx.x; i < ld; i += blockDim.x) Hc[i] = 0.0;
   bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
-    const double bd_tol = o.desc_bd_tol ? *o.desc_bd_tol : o.bd_tol;
     const double hh1 = red[0], hgh = red[1];
     const bool finite = isfinite(s2) && isfinite(hh1) && isfinite(hgh) && !bad;
     const double hn2 = s2 - 2.0 * hh1 + hgh;
-    const double hn = sqrt(hn2 > 0.0 ? hn2 : 0.0);
-    const bool breakdown = finite && (hn <= (bd_tol == 0.0 ? 0.0 : bd_tol * sqrt(s2)));
+    const double hn2p = hn2 > 0.0 ? hn2 : 0.0;
+    const double hn = sqrt(hn2p);
+    // h_{j+1,j} <= bd_tol ||S(Phi V_j)||, compared in squares (one square root fewer)
+    const bool breakdown = finite && (hn2p <= bd_tol * bd_tol * s2);
     Hc[J + 1] = breakdown ? 0.0 : hn;
     ctl->pre2 = s2;
     ctl->hnext = hn;

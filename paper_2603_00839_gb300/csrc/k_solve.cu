@@ -204,12 +204,10 @@ k_tikhonov(Work w0, const SolveDesc* desc0, int mode, double* scratch0, int in_s
     const double gcv = res2 / (trace * trace);
     if (tid == 0) w.gcv[blockIdx.x] = gcv;
     for (int i = tid; i < k; i += TK_THREADS) w.ysel[static_cast<int64_t>(blockIdx.x) * m + i] = y[i];
-    __threadfence();
     __syncthreads();
-    if (tid == 0) am_last = (atomicInc(w.counter, gridDim.x - 1) == gridDim.x - 1);
+    if (tid == 0) am_last = (ticket_acq_rel(w.counter, gridDim.x - 1) == gridDim.x - 1);
     __syncthreads();
     if (!am_last) return;
-    __threadfence();
     __shared__ int best;
     if (tid == 0) {
       int bi = 0;
@@ -412,12 +410,10 @@ __global__ void __launch_bounds__(256) k_true_resid(Work w0, PtrRef Cr0) {
     for (int u = 0; u < 8; ++u) v += red[u][threadIdx.x];
     w.part[static_cast<int64_t>(blockIdx.x) * 3 + threadIdx.x] = v;
   }
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) am_last = (atomicInc(w.counter + 1, gridDim.x - 1) == gridDim.x - 1);
+  if (threadIdx.x == 0) am_last = (ticket_acq_rel(w.counter + 1, gridDim.x - 1) == gridDim.x - 1);
   __syncthreads();
   if (!am_last) return;
-  __threadfence();
   if (warp == 0) {   // lane l sums rows l, l + 32, ...; then a fixed warp tree
     double s3[3] = {0.0, 0.0, 0.0};
     for (unsigned r = lane; r < gridDim.x; r += 32)
