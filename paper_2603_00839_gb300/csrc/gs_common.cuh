@@ -497,27 +497,22 @@ __device__ inline void gs_finish_gram(const Work& w, const StepOpts& o, const do
     __syncthreads();
     gmul(col);
     __syncthreads();
-    if (warp < 2) {   // a = h . h1, b = h . (G h) over the n <= 64 rows
-      double a = 0.0, b = 0.0;
-      const int i = threadIdx.x;
-      if (i < n) {
-        a = col[i] * h1[i];
-        b = col[i] * wsum(i);
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, off);
-        b += __shfl_xor_sync(0xffffffffu, b, off);
-      }
-      if (lane == 0) {
-        ab[2 * warp] = a;
-        ab[2 * warp + 1] = b;
-      }
+    if (warp < 4) {   // a = h . h1 (warps 0, 1), b = h . (G h) (warps 2, 3) over the n <= 64 rows
+      // the FP64 products are split exactly into float pairs and summed by a
+      // float-float warp tree on the FP32 pipe (a tree of FP64 shuffles and
+      // adds is several times slower on this GPU)
+      const int i = threadIdx.x & 63, which = warp >> 1;
+      double p = 0.0;
+      if (i < n) p = which == 0 ? col[i] * h1[i] : col[i] * wsum(i);
+      const float hi = __double2float_rn(p);
+      FF v{hi, __double2float_rn(p - static_cast<double>(hi))};
+      v = ff_warp_sum(v);
+      if (lane == 0) ab[warp] = ff_to_double(v);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      red[0] = ab[0] + ab[2];
-      red[1] = ab[1] + ab[3];
+      red[0] = ab[0] + ab[1];
+      red[1] = ab[2] + ab[3];
     }
   } else {
     for (int i = threadIdx.x; i <= J; i += blockDim.x) {
