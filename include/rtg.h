@@ -166,7 +166,8 @@ typedef struct rtg_info {
     double elapsed_ms;               /* device time of the solve (CUDA events) */
     int32_t device_status;           /* rtg_status seen on the device (NONFINITE, ...) */
     int32_t launches;                /* kernels this library launched for the solve */
-    int32_t reserved;
+    int32_t tile_config;             /* basis-update tile geometry the autotuner chose for this
+                                        plan (0: the default; see the solve's description) */
     /* With RTG_FLAG_PHASE_TIMES: device time (ms) and kernel launches of each
      * RTG_PHASE_* group, summed over the solve.  Each group is bracketed by
      * CUDA events on the solve's stream, and the GPU is held at a gate until
@@ -310,6 +311,12 @@ rtg_status rtg_krylov_query(rtg_handle handle, rtg_krylov krylov, rtg_krylov_vie
  * the last cycle.  The whole sequence stays inside the solve's CUDA graph
  * (its restart kernels return at once in steps that do not restart).
  * info->rho_hist then needs m * (R + 1) entries.
+ * Tiles: when a plan (one per shape, operator, sizes, options and slot) is
+ * first built, a timing search picks the basis update's tile geometry
+ * (slot size and depth of its shared-memory ring) on the plan's own
+ * workspace; every geometry gives identical results.  The environment
+ * variable RTG_NO_AUTOTUNE=1 keeps the default geometry and RTG_TILE_CONFIG=k
+ * (k = 0..4) fixes geometry k; both are read when a plan is built.
  * C, X0 (may be NULL), X: device or host arrays of prod(dims) elements of
  * dtype (F64 or F32); X may alias X0.  info may be NULL.  The call
  * synchronises `stream` once at the end; it equals rtg_gmres_submit

@@ -58,7 +58,7 @@ class Info(C.Structure):
                 ("rho_final", C.c_double), ("rho_hist", C.POINTER(C.c_double)),
                 ("gcv", C.POINTER(C.c_double)), ("true_rel_resid", C.c_double),
                 ("elapsed_ms", C.c_double), ("device_status", C.c_int32), ("launches", C.c_int32),
-                ("reserved", C.c_int32), ("phase_ms", C.c_double * PHASE_COUNT),
+                ("tile_config", C.c_int32), ("phase_ms", C.c_double * PHASE_COUNT),
                 ("phase_launches", C.c_int32 * PHASE_COUNT), ("true_rel_resid_theta", C.c_double)]
 
 

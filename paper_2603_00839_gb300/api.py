@@ -152,6 +152,7 @@ class SolveResult:
     launches: int
     phase_ms: Optional[dict] = None        # group -> device ms (phase_times=True)
     phase_launches: Optional[dict] = None  # group -> kernel launches (phase_times=True)
+    tile_config: int = 0                   # basis-update tile geometry chosen by the autotuner
     true_rel_resid: float = -1.0           # ||C - Phi(X)||_F / ||C||_F (true_residual=True)
     true_rel_resid_theta: float = -1.0     # ||C - Phi(X)||_Theta / ||R_0||_Theta (true_residual=True)
 
@@ -409,7 +410,7 @@ def _solve_result(info, rho, gcv, grid, lam):
     return SolveResult(info.iters, info.restarts, bool(info.breakdown), bool(info.converged),
                        info.beta, info.mu, info.rho_final, rho[:info.iters].copy(),
                        gcv[:len(grid)].copy() if (grid is not None and lam < 0) else None,
-                       info.elapsed_ms, info.device_status, info.launches,
+                       info.elapsed_ms, info.device_status, info.launches, tile_config=info.tile_config,
                        true_rel_resid=info.true_rel_resid, true_rel_resid_theta=info.true_rel_resid_theta)
 
 

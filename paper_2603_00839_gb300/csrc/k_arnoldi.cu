@@ -458,11 +458,20 @@ __global__ void k_update_bf16(Work w0, StepOpts o0) {
 // bit for bit.  The next CTAs form Q_{j+1} (as in k_update), the last one
 // runs givens_step.  At 512 x 512 x 3 the grid is one wave (192 chunk CTAs,
 // 192 column CTAs, three CTAs per SM).
-constexpr int UP_SLOT = 16384;   // bytes of one ring slot
-constexpr int UP_STAGES = 4;
 constexpr int UP_THREADS = 256;
 
-template <typename TV>
+// Ring geometries the autotuner chooses from: bytes of one slot (the chunk a
+// CTA streams) and slots in flight.  Every geometry gives the same results
+// bit for bit (each element is updated in the same order).  Index 0 is the
+// default when no tuning has run.
+struct UpCfg {
+  int slot, stages;
+};
+constexpr UpCfg kUpCfgs[] = {{16384, 4}, {8192, 4}, {8192, 8}, {16384, 2}, {32768, 2}};
+constexpr int kUpCfgCount = sizeof(kUpCfgs) / sizeof(kUpCfgs[0]);
+int update_configs() { return kUpCfgCount; }
+
+template <typename TV, int UP_SLOT, int UP_STAGES>
 __global__ void __launch_bounds__(UP_THREADS) k_update_ring(Work w0, StepOpts o0, int nchunks) {
   constexpr int CE = UP_SLOT / static_cast<int>(sizeof(TV));   // elements of a chunk
   constexpr int VEC = 16 / static_cast<int>(sizeof(TV));       // elements per 16-byte group
@@ -639,22 +648,37 @@ cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s) {
 
 
 
-template <typename TV>
-static cudaError_t launch_update_ring(const Work& w, const StepOpts& o, cudaStream_t s) {
-  constexpr size_t sm = size_t(UP_STAGES) * UP_SLOT;
-  cudaError_t e = set_smem(k_update_ring<TV>, sm);
+template <typename TV, int SLOT, int STAGES>
+static cudaError_t launch_update_ring_cfg(const Work& w, const StepOpts& o, cudaStream_t s) {
+  constexpr size_t sm = size_t(STAGES) * SLOT;
+  cudaError_t e = set_smem(k_update_ring<TV, SLOT, STAGES>, sm);
   if (e != cudaSuccess) return e;
-  constexpr int64_t CE = UP_SLOT / sizeof(TV);
+  constexpr int64_t CE = SLOT / sizeof(TV);
   const int nchunks = static_cast<int>((w.n + CE - 1) / CE);
   const int qblocks = static_cast<int>((w.d + UP_THREADS - 1) / UP_THREADS);
   const dim3 grid(static_cast<unsigned>(nchunks + qblocks + 1), 1, static_cast<unsigned>(w.b.n));
-  k_update_ring<TV><<<grid, UP_THREADS, sm, s>>>(w, o, nchunks);
+  k_update_ring<TV, SLOT, STAGES><<<grid, UP_THREADS, sm, s>>>(w, o, nchunks);
   return cudaGetLastError();
+}
+
+template <typename TV>
+static cudaError_t launch_update_ring(const Work& w, const StepOpts& o, cudaStream_t s) {
+  switch (w.upcfg) {
+    case 1: return launch_update_ring_cfg<TV, kUpCfgs[1].slot, kUpCfgs[1].stages>(w, o, s);
+    case 2: return launch_update_ring_cfg<TV, kUpCfgs[2].slot, kUpCfgs[2].stages>(w, o, s);
+    case 3: return launch_update_ring_cfg<TV, kUpCfgs[3].slot, kUpCfgs[3].stages>(w, o, s);
+    case 4: return launch_update_ring_cfg<TV, kUpCfgs[4].slot, kUpCfgs[4].stages>(w, o, s);
+    default: return launch_update_ring_cfg<TV, kUpCfgs[0].slot, kUpCfgs[0].stages>(w, o, s);
+  }
+}
+
+bool update_uses_ring(const Work& w) {
+  return w.dtype == RTG_F32 && w.n % 8 == 0 && w.n / 4096 < (int64_t(1) << 30);
 }
 
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s) {
   // FP32 solves with whole 8-element groups stream the basis through shared memory
-  if (w.dtype == RTG_F32 && w.n % 8 == 0 && w.n / 4096 < (int64_t(1) << 30))
+  if (update_uses_ring(w))
     return w.vdtype == RTG_BF16 ? launch_update_ring<__nv_bfloat16>(w, o, s) : launch_update_ring<float>(w, o, s);
   // one block more than the update needs: it runs the Givens step
   const unsigned nb = static_cast<unsigned>(w.b.n);

@@ -611,6 +611,8 @@ struct rtg_context {
   // keyed by stream too, so that calls on different streams never share scratch
   std::map<std::string, std::unique_ptr<SketchCache>> sketches;
   std::map<cudaStream_t, std::unique_ptr<ApplyScratch>> apply_scratch;
+  // autotuned basis-update ring geometry per (tensor size, sketch size, storage, problems per group)
+  std::map<std::string, int> tuned;
   // rtg_ws_solve: R_0 of the prediction, S(R_0), S(C), log lambda and the decision
   DevBuf ws_work;
   WsDecision* ws_dec_host = nullptr;   // pinned
@@ -1032,11 +1034,91 @@ struct TransposedFactors {
   }
 };
 
+// Autotuner of the basis update's tiles (a project-written timing search):
+// the shared-memory ring's slot size (the chunk of the tensor one CTA
+// streams) and depth.  Every geometry gives the same results bit for bit,
+// so the choice only changes speed.  Each candidate runs on the plan's own
+// workspace and grid (all problems of a lock-step group) from a synthetic
+// step state (j = min(m, 16): the update reads j + 1 tensors), five timed
+// launches each after one untimed; the fastest median wins and is cached
+// per (n, d, storage, problems per launch) in the handle.  The workspace is
+// cleared afterwards (every solve starts by resetting its state anyway).
+// RTG_NO_AUTOTUNE=1 in the environment keeps the default geometry;
+// RTG_TILE_CONFIG=k fixes geometry k.
+static rtg_status tune_update(SolvePlan& P, std::map<std::string, int>* cache) {
+  Work& w = P.w;
+  w.upcfg = 0;
+  if (cache == nullptr || !update_uses_ring(w)) return RTG_OK;
+  const char* off = std::getenv("RTG_NO_AUTOTUNE");
+  if (off != nullptr && off[0] == '1') return RTG_OK;
+  const char* force = std::getenv("RTG_TILE_CONFIG");   // a fixed geometry (tests, measurements)
+  if (force != nullptr && force[0] >= '0' && force[0] < '0' + update_configs() && force[1] == 0) {
+    w.upcfg = force[0] - '0';
+    return RTG_OK;
+  }
+  std::string key;
+  append_bytes(key, &w.n, sizeof w.n);
+  append_bytes(key, &w.d, sizeof w.d);
+  append_bytes(key, &w.vdtype, sizeof w.vdtype);
+  append_bytes(key, &w.b.n, sizeof w.b.n);
+  auto hit = cache->find(key);
+  if (hit != cache->end()) {
+    w.upcfg = hit->second;
+    return RTG_OK;
+  }
+  cudaStream_t s = nullptr;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  struct Cleanup {
+    cudaStream_t s;
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~Cleanup() {
+      for (auto x : e)
+        if (x) cudaEventDestroy(x);
+      cudaStreamDestroy(s);
+    }
+  } cl{s};
+  CK(cudaEventCreate(&cl.e[0]));
+  CK(cudaEventCreate(&cl.e[1]));
+  Ctl c{};
+  c.j = w.m < 16 ? w.m : 16;
+  c.hnext = 1.0;
+  c.rs_skip = 1;
+  for (int p = 0; p < w.b.n; ++p)
+    CK(cudaMemcpyAsync(reinterpret_cast<char*>(w.ctl) + int64_t(p) * w.b.stride, &c, sizeof(Ctl),
+                       cudaMemcpyHostToDevice, s));
+  StepOpts o{};   // no graph condition, no lock-step count
+  int best = 0;
+  float best_ms = 0.f;
+  for (int cfg = 0; cfg < update_configs(); ++cfg) {
+    w.upcfg = cfg;
+    CK(launch_update(w, o, s));
+    float t[5];
+    for (int r = 0; r < 5; ++r) {
+      CK(cudaEventRecord(cl.e[0], s));
+      CK(launch_update(w, o, s));
+      CK(cudaEventRecord(cl.e[1], s));
+      CK(cudaEventSynchronize(cl.e[1]));
+      CK(cudaEventElapsedTime(&t[r], cl.e[0], cl.e[1]));
+    }
+    std::sort(t, t + 5);
+    if (cfg == 0 || t[2] < best_ms) {
+      best_ms = t[2];
+      best = cfg;
+    }
+  }
+  CK(cudaMemsetAsync(P.mem.p, 0, P.mem.bytes, s));
+  CK(cudaStreamSynchronize(s));
+  w.upcfg = best;
+  (*cache)[key] = best;
+  return RTG_OK;
+}
+
 // Builds a plan: operator, workspace, descriptor / info record (in the
 // given batch buffers, or its own), launch counts and, for a stand-alone
 // graph solve, its CUDA graph.  Builds only while nothing of the handle runs.
 rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDesc* dhost, InfoDev* ihost,
-                     std::shared_ptr<SolvePlan>* out, int nbatch = 0) {
+                     std::shared_ptr<SolvePlan>* out, int nbatch = 0,
+                     std::map<std::string, int>* tune_cache = nullptr) {
   const rtg_factor* A = ps.A;
   const rtg_factor* B = ps.B;
   const int nA = ps.nA, nB = ps.nB, dtype = ps.dtype, vdtype = ps.vdtype, m = ps.m, mode = ps.mode;
@@ -1099,6 +1181,7 @@ rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDe
     carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk, vdtype, nU);
   }
   P->w.cycles = ps.cycles;
+  RK(tune_update(*P, tune_cache));
   if (nbatch > 0) {
   } else if (ddev != nullptr) {   // descriptor and info record in a batch's buffers
     P->ext_desc = true;
@@ -1161,6 +1244,7 @@ void fill_info(const SolvePlan& P, const InfoDev& I, int mode, int n_mu, bool us
   info->true_rel_resid_theta = P.true_resid ? I.true_rel_resid_theta : -1.0;
   info->elapsed_ms = ms;
   info->device_status = I.status;
+  info->tile_config = P.w.upcfg;
   info->launches = P.launches_pro + P.launches_epi + (use_graph ? I.iters : P.direct_steps) * P.launches_step +
                    (use_graph ? I.restarts : P.direct_steps) * P.launches_restart;
   for (int k = 0; k < RTG_PHASE_COUNT; ++k) {
@@ -1555,7 +1639,7 @@ static rtg_status submit_impl(int method, rtg_handle h, const rtg_factor* A, int
     PlanSpec ps{A, nA, B, nB, shape, dtype, vdtype, n, m, sp, mode, nmu_key, has_x0, use_graph, method,
                 true_resid, cycles};
     std::shared_ptr<SolvePlan> np;
-    RK(make_plan(ps, nullptr, nullptr, nullptr, nullptr, &np));
+    RK(make_plan(ps, nullptr, nullptr, nullptr, nullptr, &np, 0, &h->tuned));
     P = np.get();
     h->plans[key] = np;
     hold = np;
@@ -1819,7 +1903,7 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
       std::shared_ptr<SolvePlan> pl;
       const int first = BP->gfirst[k];
       RK(make_plan(specs[members[k][0]], nullptr, nullptr, dh + first, ih + first, &pl,
-                   static_cast<int>(members[k].size())));
+                   static_cast<int>(members[k].size()), &h->tuned));
       RK(build_branch(*pl, BP->graph));
       BP->plans.push_back(std::move(pl));
     }

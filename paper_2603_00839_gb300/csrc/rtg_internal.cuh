@@ -168,6 +168,7 @@ struct Work {
   int d;                       // sketch size prod(s'_k)
   int m;                       // Krylov dimension
   int cycles = 1;              // most Arnoldi cycles of a solve (restarts + 1)
+  int upcfg = 0;               // basis-update ring geometry (index into the autotuner's list)
   void* V;                     // (m+1) * n
   void* W;                     // n
   void* U;                     // Golub-Kahan: ring of 2 left-basis tensors (else null)
@@ -414,6 +415,10 @@ cudaError_t launch_start(const Work& w, PtrRef src, const StepOpts& o, bool fuse
 cudaError_t launch_pass1(const Work& w, const StepOpts& o, cudaStream_t s);
 int gs_grid(int64_t d);
 cudaError_t launch_update(const Work& w, const StepOpts& o, cudaStream_t s);
+// the update streams the basis through the shared-memory ring (w.upcfg applies)
+bool update_uses_ring(const Work& w);
+// number of ring geometries (w.upcfg in 0..count-1)
+int update_configs();
 // group_left (lock-step batch): set to the number of problems
 cudaError_t launch_reset(const Work& w, int new_cycle, cudaStream_t s, unsigned* group_left = nullptr,
                          const int* gate = nullptr);

@@ -263,3 +263,34 @@ def test_many_identical_branches_equal_the_single_solve(h):
         Xb, rb = h.gmres_solve_batched(probs)
         bad = [i for i in range(len(probs)) if not np.array_equal(Xb[i].cpu().numpy(), Xs)]
         assert not bad, f"{len(bad)} of {len(probs)} branches differ from the single solve"
+
+
+def test_every_tile_geometry_gives_the_same_solve(h):
+    """The autotuner's candidates (slot size and depth of the basis update's
+    ring) change only speed: a solve and a lock-step batch give the same
+    results bit for bit with every geometry, and the tuned choice is one of
+    them."""
+    import os
+    api = _api()
+    cfgs = w.batched_configs(3, seed=5, side_lo=96, side_hi=320)
+    for c in cfgs:   # whole 8-element groups: the ring update (whose tiles are tuned) applies
+        I1, I2 = c["dims"][0] // 8 * 8, c["dims"][1] // 8 * 8
+        c["dims"] = (I1, I2, 3)
+        c["sketch_dims"] = (min(I1, 128), min(I2, 128), 3)
+    probs = [_problem(h, c) for c in cfgs]
+    results = []
+    for k in range(5):
+        os.environ["RTG_TILE_CONFIG"] = str(k)
+        try:
+            hk = api.Handle(0)
+            X, info = _single(hk, probs[0])
+            Xb, rb = hk.gmres_solve_batched([probs[1]] * 3, group_max=3)
+            assert info.tile_config == k and rb[0].tile_config == k
+            results.append((X.cpu().numpy(), [x.cpu().numpy() for x in Xb]))
+        finally:
+            del os.environ["RTG_TILE_CONFIG"]
+    for X, Xb in results[1:]:
+        assert np.array_equal(X, results[0][0])
+        assert all(np.array_equal(a, b) for a, b in zip(Xb, results[0][1]))
+    X, info = _single(api.Handle(0), probs[0])
+    assert 0 <= info.tile_config < 5 and np.array_equal(X.cpu().numpy(), results[0][0])
