@@ -200,7 +200,7 @@ PHASE_FILES = {"apply": ["k_apply.cu"], "sketch": ["k_sketch.cu", "gs_common.cuh
                "update": ["k_arnoldi.cu", "gs_common.cuh", "tma_common.cuh"],
                "assemble": ["k_solve.cu"], "init": ["k_arnoldi.cu", "k_sketch.cu"]}
 KERNEL_NAMES = {"apply": "k_apply_reg<float,3,7> (W = Phi(V_j))",
-                "sketch": "k_sk_first_tc<16> + k_sk_inner_tc<32> (S(W) with fused sketched dots)",
+                "sketch": "k_sk_first_umma<float> (tcgen05) + k_sk_inner_tc<32> (S(W) with fused sketched dots)",
                 "update": "k_update_ring<float,8> (V_{j+1} streamed through a shared-memory ring, "
                           "its sketched column, Givens block)",
                 "assemble": "k_assemble<float>", "init": "prologue group"}

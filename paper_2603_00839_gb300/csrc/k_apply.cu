@@ -33,6 +33,12 @@ struct FusedArgs {
   float t1f[kMaxTaps], t2f[kMaxTaps];
   float Mf[kMaxMix * kMaxMix];
   float alphaf, betaf;
+  // the taps zero-padded to the register kernel's compile-time radius RR
+  // (tap t of the padded filter is tap t - (RR - r) of the real one): with
+  // compile-time indices they stay in the constant bank as FMA operands
+  // instead of taking two registers per tap
+  double t1p[kMaxTaps], t2p[kMaxTaps];
+  float t1pf[kMaxTaps], t2pf[kMaxTaps];
 };
 // An argument in the kernel's arithmetic type.
 template <typename T>
@@ -140,7 +146,7 @@ struct RegGeom {
 };
 
 template <typename T, int NC, int RR>
-__global__ void __launch_bounds__(FTHREADS, (RR <= 7 ? 3 : 1))
+__global__ void __launch_bounds__(FTHREADS, (RR <= 7 ? 4 : 1))
 k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch bt) {
   const BIdx bi = bidx(bt);
   Xr = Xr.at(bi.off);
@@ -157,13 +163,8 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* in_s = reinterpret_cast<T*>(smem_raw);      // NC x Ht x Wd
   T* tmp = in_s + NC * Ht * Wd;                  // Ht x RTX
-  T t1[NT], t2[NT];
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    const int u1 = t - (RR - a.r1), u2 = t - (RR - a.r2);
-    t1[t] = (u1 >= 0 && u1 <= 2 * a.r1) ? argT<T>(a.t1[u1], a.t1f[u1]) : static_cast<T>(0);
-    t2[t] = (u2 >= 0 && u2 <= 2 * a.r2) ? argT<T>(a.t2[u2], a.t2f[u2]) : static_cast<T>(0);
-  }
+#define t1(t) argT<T>(a.t1p[t], a.t1pf[t])
+#define t2(t) argT<T>(a.t2p[t], a.t2pf[t])
   const int x0 = blockIdx.x * RTX;
   const int y0 = blockIdx.y * RTY;
   const int I1 = static_cast<int>(a.I1), I2 = static_cast<int>(a.I2);
@@ -233,7 +234,7 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
         for (int o = 0; o < RSEG; ++o) {
           T sacc = 0;
 #pragma unroll
-          for (int t = 0; t < NT; ++t) sacc += t1[t] * win[o + t];
+          for (int t = 0; t < NT; ++t) sacc += t1(t) * win[o + t];
           tmp[yy * RTX + xs + o] = sacc;
         }
       }
@@ -247,7 +248,7 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
         for (int o = 0; o < VSEG; ++o) {
           T sacc = 0;
 #pragma unroll
-          for (int t = 0; t < NT; ++t) sacc += t2[t] * win[o + t];
+          for (int t = 0; t < NT; ++t) sacc += t2(t) * win[o + t];
           acc[c][o] = sacc;
         }
       }
@@ -273,6 +274,9 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
     }
   }
 }
+
+#undef t1
+#undef t2
 
 // ---------------------------------------------------------------- spatio-temporal path
 // One HBM pass for the video operator (order 4: blur on modes 1-2, channel
@@ -659,6 +663,13 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
     const bool fits = a.I1 < (int64_t(1) << 30) && a.I2 < (int64_t(1) << 30) &&
                       (sizeof(T) == 8 || (a.I1 % 4) == 0);
     if (rr > 0 && fits && (a.nc == 1 || a.nc == 3)) {
+      for (int t = 0; t <= 2 * rr; ++t) {
+        const int u1 = t - (rr - op.r1), u2 = t - (rr - op.r2);
+        a.t1p[t] = (u1 >= 0 && u1 <= 2 * op.r1) ? a.t1[u1] : 0.0;
+        a.t2p[t] = (u2 >= 0 && u2 <= 2 * op.r2) ? a.t2[u2] : 0.0;
+        a.t1pf[t] = static_cast<float>(a.t1p[t]);
+        a.t2pf[t] = static_cast<float>(a.t2p[t]);
+      }
       dim3 grid(static_cast<unsigned>((a.I1 + RTX - 1) / RTX), static_cast<unsigned>((a.I2 + RTY - 1) / RTY),
                 batch_z(a.nslab, b));
       cudaError_t e = cudaSuccess;

@@ -247,7 +247,9 @@ struct SketchPlan {
   int stage_first[kMaxOrder];  // 1: L == 1 (first-mode tensor-core kernel)
   int stage_split[kMaxOrder];  // K split (partial outputs)
   int stage_kt[kMaxOrder];     // K tiles of 16
-  int stage_ntile[kMaxOrder];  // m16 (first) or n8 (later) tiles of the sketch size
+  int stage_ntile[kMaxOrder];  // 128-row tiles (L == 1 stages, tcgen05) or n8 tiles (later stages) of the sketch size
+  int stage_kb[kMaxOrder];     // K blocks of 64 (tcgen05 stages)
+  int stage_umma[kMaxOrder];   // an L == 1 stage of the FP32 chain that runs on tcgen05
   int64_t stage_L[kMaxOrder], stage_I[kMaxOrder], stage_R[kMaxOrder], stage_s[kMaxOrder];
   int64_t stage_out[kMaxOrder];   // elements of one stage output
   // FP32 chain layouts: an inner stage reads its input either in the

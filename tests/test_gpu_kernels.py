@@ -158,6 +158,9 @@ SKETCH_CASES = [
     ((64, 512, 20), (32, 64, 20), 2),     # >= 608 column tiles: the multi-tile first stage
     ((36, 300, 35), (20, 50, 35), 6),     # multi-tile, ragged rows and a 4-column last tile
     ((320, 64, 160), (80, 16, 16), 7),    # multi-tile, 20 K tiles, two row blocks
+    ((300, 21, 3), (200, 10, 3), 8),      # s_1 > 128 (two row tiles), ragged K block and column tile
+    ((300, 41, 200), (200, 10, 3), 10),   # the same on the tcgen05 first stage (>= 8192 columns)
+    ((150, 64, 130), (40, 16, 13), 11),   # tcgen05 first stage, K not a multiple of 4 (plain loads)
 ]
 
 
