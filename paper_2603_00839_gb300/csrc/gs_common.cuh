@@ -149,6 +149,71 @@ __device__ __forceinline__ void ff_reduce_scatter32(FF (&v)[32]) {
   }
 }
 
+// The same for NV = 2, 4, ..., 32 values: log2(NV) halving rounds inside
+// aligned groups of NV lanes, then butterfly sums across the groups;
+// afterwards v[0] of lane l is the warp total of value l % NV.
+template <int NV>
+__device__ __forceinline__ void ff_reduce_scatter(FF (&v)[NV]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int half = NV / 2; half >= 1; half >>= 1) {
+    const bool up = (lane & half) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const FF give = up ? v[k] : v[k + half];
+      const FF keep = up ? v[k + half] : v[k];
+      FF got;
+      got.hi = __shfl_xor_sync(0xffffffffu, give.hi, half);
+      got.lo = __shfl_xor_sync(0xffffffffu, give.lo, half);
+      v[k] = ff_add_lazy(keep, got);
+    }
+  }
+#pragma unroll
+  for (int o = NV; o < 32; o <<= 1) {
+    FF got;
+    got.hi = __shfl_xor_sync(0xffffffffu, v[0].hi, o);
+    got.lo = __shfl_xor_sync(0xffffffffu, v[0].lo, o);
+    v[0] = ff_add_lazy(v[0], got);
+  }
+}
+
+// One group of W columns i0 .. i0 + W - 1 (those <= J) of the FP32 partial
+// sums: s . Q_i and Q_J . Q_i over this thread's ITEMS entries, reduced
+// across the warp by one reduce-scatter of 2 W float-float values; lane
+// l < 2 W writes column i0 + l % W of its warp's row (s . Q_i for l < W).
+template <int W, int ITEMS>
+__device__ __forceinline__ void ff_dot_group(const float* Q, int64_t d, const float (&sv)[ITEMS],
+                                             const float (&qJ)[ITEMS], const int64_t* idx, int cnt, int i0, int J,
+                                             FF (*rf)[kRedCols], int warp, int lane) {
+  float qv[W][ITEMS];
+#pragma unroll
+  for (int g = 0; g < W; ++g)
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const bool ok = k < cnt && idx[k] >= 0 && i0 + g <= J;
+      qv[g][k] = ok ? Q[static_cast<int64_t>(i0 + g) * d + idx[k]] : 0.f;
+    }
+  FF v[2 * W];
+#pragma unroll
+  for (int g = 0; g < W; ++g) {
+    // the first product starts the pair (an exact product is already a
+    // normalised pair, so adding it to zero would change nothing)
+    FF p = ff_prod(sv[0], qv[g][0]), q = ff_prod(qJ[0], qv[g][0]);
+#pragma unroll
+    for (int k = 1; k < ITEMS; ++k) {
+      p = ff_add_lazy(p, ff_prod(sv[k], qv[g][k]));
+      q = ff_add_lazy(q, ff_prod(qJ[k], qv[g][k]));
+    }
+    v[g] = p;
+    v[W + g] = q;
+  }
+  ff_reduce_scatter<2 * W>(v);
+  if (lane < 2 * W) {
+    const int g = lane % W;
+    if (i0 + g <= J) rf[warp][lane < W ? i0 + g : J + 2 + i0 + g] = v[0];
+  }
+}
+
 // Sum of the per-warp values of one column in a fixed order.
 __device__ __forceinline__ double warps_total(const double (*red)[kRedCols], int nw, int i) {
   if (nw == 8)
@@ -207,34 +272,15 @@ __device__ void block_partials(const Work& w, const T* vals, const int64_t* idx,
     }
   }
   if constexpr (sizeof(T) == 4) {
-    // 16 columns of Q at a time: s . Q_i and Q_J . Q_i for each, 32 values
-    // per thread, reduced across the warp in one reduce-scatter
+    // 16 columns of Q at a time (the last group only as wide as it needs,
+    // rounded up to a power of two): s . Q_i and Q_J . Q_i for each
     for (int i0 = 0; i0 <= J; i0 += 16) {
-      float qv[16][ITEMS];
-#pragma unroll
-      for (int g = 0; g < 16; ++g)
-#pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-          const bool ok = k < cnt && idx[k] >= 0 && i0 + g <= J;
-          qv[g][k] = ok ? Q[static_cast<int64_t>(i0 + g) * d + idx[k]] : 0.f;
-        }
-      FF v[32];
-#pragma unroll
-      for (int g = 0; g < 16; ++g) {
-        // the first product starts the pair (an exact product is already a
-        // normalised pair, so adding it to zero would change nothing)
-        FF p = ff_prod(sv[0], qv[g][0]), q = ff_prod(qJ[0], qv[g][0]);
-#pragma unroll
-        for (int k = 1; k < ITEMS; ++k) {
-          p = ff_add_lazy(p, ff_prod(sv[k], qv[g][k]));
-          q = ff_add_lazy(q, ff_prod(qJ[k], qv[g][k]));
-        }
-        v[g] = p;
-        v[16 + g] = q;
-      }
-      ff_reduce_scatter32(v);
-      const int g = lane & 15;
-      if (i0 + g <= J) rf[warp][lane < 16 ? i0 + g : J + 2 + i0 + g] = v[0];
+      const int nv = J + 1 - i0;
+      if (nv > 8) ff_dot_group<16, ITEMS>(Q, d, sv, qJ, idx, cnt, i0, J, rf, warp, lane);
+      else if (nv > 4) ff_dot_group<8, ITEMS>(Q, d, sv, qJ, idx, cnt, i0, J, rf, warp, lane);
+      else if (nv > 2) ff_dot_group<4, ITEMS>(Q, d, sv, qJ, idx, cnt, i0, J, rf, warp, lane);
+      else if (nv > 1) ff_dot_group<2, ITEMS>(Q, d, sv, qJ, idx, cnt, i0, J, rf, warp, lane);
+      else ff_dot_group<1, ITEMS>(Q, d, sv, qJ, idx, cnt, i0, J, rf, warp, lane);
     }
   } else {
     // columns of Q in groups of 8: all loads of a group go out before any use

@@ -126,13 +126,16 @@ k_apply_fused(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Bat
 // to 2*RR+1) and NC jointly mixed channels.  Tile 64 x 16 of modes 1-2,
 // 256 threads.  All NC halo tiles are staged in shared memory at once with
 // cp.async (zero fill outside the tensor: the zero boundary of Eq. 57), so
-// the CTA waits on global memory once.  Mode-1 pass: a thread filters 8
-// consecutive outputs of a row from a register window of 8+2RR values;
-// mode-2 pass: a thread filters 4 consecutive rows of one column.
+// the CTA waits on global memory once.  Per channel the mode-2 filter runs
+// first, over the 16 output rows and every staged column (a task: two
+// adjacent columns x 4 rows, paired FP32 FMAs), then the mode-1 filter over
+// the 16 x 64 outputs (a thread: 4 consecutive outputs of one row from a
+// register window of 4+2RR values): filtering the halo rows along mode 2
+// first costs 16 (64 + 2RR) + 16 x 64 products per tap instead of
+// (16 + 2RR) 64 + 16 x 64, and the thread's 4 outputs leave in one 16-byte
+// store after the channel mix.
 constexpr int RTX = 64;
 constexpr int RTY = 16;
-constexpr int RSEG = 8;    // mode-1 outputs per thread
-constexpr int VSEG = 4;    // mode-2 outputs per thread
 
 
 template <int RR, typename T>
@@ -144,6 +147,32 @@ struct RegGeom {
   static constexpr int Wd = RTX + 2 * RA;
   static constexpr int Ht = RTY + 2 * RR;
 };
+
+// Paired FP32 FMA (fma.rn.f32x2): two lanes of independent multiply-adds
+// in one instruction.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+template <typename T>
+struct Pair {
+  T x, y;
+};
+__device__ __forceinline__ Pair<float> pfma(float t, Pair<float> v, Pair<float> acc) {
+  const float2 r = ffma2(make_float2(t, t), make_float2(v.x, v.y), make_float2(acc.x, acc.y));
+  return {r.x, r.y};
+}
+__device__ __forceinline__ Pair<double> pfma(double t, Pair<double> v, Pair<double> acc) {
+  return {fma(t, v.x, acc.x), fma(t, v.y, acc.y)};
+}
+
+// the taps as kernel-parameter (constant-bank) operands, see FusedArgs
+#define t1(t) argT<T>(a.t1p[t], a.t1pf[t])
+#define t2(t) argT<T>(a.t2p[t], a.t2pf[t])
 
 template <typename T, int NC, int RR>
 __global__ void __launch_bounds__(FTHREADS, (RR <= 7 ? 4 : 1))
@@ -160,17 +189,20 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
   using G = RegGeom<RR, T>;
   constexpr int NT = 2 * RR + 1;
   constexpr int Wd = G::Wd, Ht = G::Ht, RA = G::RA, OFF = G::OFF;
+  constexpr int NPAIR = Wd / 2;                 // mode-2 pass: column pairs
+  constexpr int V2 = 4;                          // mode-2 pass: output rows per task
+  constexpr int M1 = 4;                          // mode-1 pass: outputs per thread
+  static_assert(Wd % 2 == 0 && NPAIR * (RTY / V2) <= 2 * FTHREADS, "mode-2 tasks");
+  static_assert(RTY * (RTX / M1) == FTHREADS, "mode-1 tasks: one per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* in_s = reinterpret_cast<T*>(smem_raw);      // NC x Ht x Wd
-  T* tmp = in_s + NC * Ht * Wd;                  // Ht x RTX
-#define t1(t) argT<T>(a.t1p[t], a.t1pf[t])
-#define t2(t) argT<T>(a.t2p[t], a.t2pf[t])
+  T* tmp = in_s + NC * Ht * Wd;                  // RTY x Wd
   const int x0 = blockIdx.x * RTX;
   const int y0 = blockIdx.y * RTY;
   const int I1 = static_cast<int>(a.I1), I2 = static_cast<int>(a.I2);
   const int64_t plane = a.I1 * a.I2;
-  const int vx = threadIdx.x & (RTX - 1);        // mode-2 pass: column
-  const int vy = (threadIdx.x / RTX) * VSEG;     // mode-2 pass: first of 4 rows
+  const int oy = threadIdx.x / (RTX / M1);       // mode-1 pass: output row
+  const int ox = (threadIdx.x % (RTX / M1)) * M1; // mode-1 pass: first of 4 outputs
   for (int64_t slab = bi.z; slab < a.nslab; slab += bi.nz) {
     __syncthreads();
     const T* Xs = X + slab * NC * plane;
@@ -200,20 +232,48 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
-    T acc[NC][VSEG];
+    T acc[NC][M1];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const T* ins = in_s + c * Ht * Wd;
-      // mode 1: Ht rows x 8 segments of 8 outputs
-      for (int task = threadIdx.x; task < Ht * (RTX / RSEG); task += FTHREADS) {
-        const int yy = task / (RTX / RSEG);
-        const int xs = (task - yy * (RTX / RSEG)) * RSEG;
-        T win[RSEG + 2 * RR];
+      // mode 2 first (along y, all Wd staged columns): task = (column pair,
+      // 4 output rows), paired FMAs over the two columns
+      for (int task = threadIdx.x; task < NPAIR * (RTY / V2); task += FTHREADS) {
+        const int pr = task % NPAIR, g = task / NPAIR;
+        Pair<T> win[V2 + 2 * RR];
+#pragma unroll
+        for (int u = 0; u < V2 + 2 * RR; ++u) {
+          const T* p = ins + (g * V2 + u) * Wd + 2 * pr;
+          if constexpr (sizeof(T) == 4) {
+            const float2 q = *reinterpret_cast<const float2*>(p);
+            win[u] = {q.x, q.y};
+          } else {
+            win[u] = {p[0], p[1]};
+          }
+        }
+#pragma unroll
+        for (int o = 0; o < V2; ++o) {
+          Pair<T> s{static_cast<T>(0), static_cast<T>(0)};
+#pragma unroll
+          for (int t = 0; t < NT; ++t) s = pfma(t2(t), win[o + t], s);
+          T* q = tmp + (g * V2 + o) * Wd + 2 * pr;
+          if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float2*>(q) = make_float2(s.x, s.y);
+          } else {
+            q[0] = s.x;
+            q[1] = s.y;
+          }
+        }
+      }
+      __syncthreads();
+      // mode 1 (along x): 4 consecutive outputs of one row per thread
+      {
+        T win[M1 + 2 * RR];
         if (sizeof(T) == 4) {
           // aligned 16-byte loads covering the window, which starts OFF & 3 floats in
           constexpr int A0 = OFF & ~3, SH = OFF & 3;
-          constexpr int NV = (SH + RSEG + 2 * RR + 3) / 4;
-          const float4* rp = reinterpret_cast<const float4*>(ins + yy * Wd + xs + A0);
+          constexpr int NV = (SH + M1 + 2 * RR + 3) / 4;
+          const float4* rp = reinterpret_cast<const float4*>(tmp + oy * Wd + ox + A0);
           float buf[NV * 4];
 #pragma unroll
           for (int v4 = 0; v4 < NV; ++v4) {
@@ -224,57 +284,60 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
             buf[4 * v4 + 3] = q.w;
           }
 #pragma unroll
-          for (int u = 0; u < RSEG + 2 * RR; ++u) win[u] = static_cast<T>(buf[SH + u]);
+          for (int u = 0; u < M1 + 2 * RR; ++u) win[u] = static_cast<T>(buf[SH + u]);
         } else {
-          const T* row = ins + yy * Wd + xs + OFF;
+          const T* row = tmp + oy * Wd + ox + OFF;
 #pragma unroll
-          for (int u = 0; u < RSEG + 2 * RR; ++u) win[u] = row[u];
+          for (int u = 0; u < M1 + 2 * RR; ++u) win[u] = row[u];
         }
 #pragma unroll
-        for (int o = 0; o < RSEG; ++o) {
+        for (int o = 0; o < M1; ++o) {
           T sacc = 0;
 #pragma unroll
           for (int t = 0; t < NT; ++t) sacc += t1(t) * win[o + t];
-          tmp[yy * RTX + xs + o] = sacc;
-        }
-      }
-      __syncthreads();
-      // mode 2: 4 rows of one column
-      {
-        T win[VSEG + 2 * RR];
-#pragma unroll
-        for (int u = 0; u < VSEG + 2 * RR; ++u) win[u] = tmp[(vy + u) * RTX + vx];
-#pragma unroll
-        for (int o = 0; o < VSEG; ++o) {
-          T sacc = 0;
-#pragma unroll
-          for (int t = 0; t < NT; ++t) sacc += t2(t) * win[o + t];
           acc[c][o] = sacc;
         }
       }
       __syncthreads();
     }
-    const int gx = x0 + vx;
-    if (gx < I1) {
+    const int gy = y0 + oy;
+    if (gy < I2) {
+      T out[M1];
 #pragma unroll
-      for (int o = 0; o < VSEG; ++o) {
-        const int gy = y0 + vy + o;
-        if (gy >= I2) break;
+      for (int p = 0; p < NC; ++p) {
+        const int64_t base = (slab * NC + p) * plane + static_cast<int64_t>(gy) * I1 + x0 + ox;
 #pragma unroll
-        for (int p = 0; p < NC; ++p) {
+        for (int o = 0; o < M1; ++o) {
           T v = 0;
 #pragma unroll
           for (int c = 0; c < NC; ++c) v += argT<T>(a.M[p + NC * c], a.Mf[p + NC * c]) * acc[c][o];
-          const int64_t idx = (slab * NC + p) * plane + static_cast<int64_t>(gy) * I1 + gx;
-          T out = argT<T>(a.alpha, a.alphaf) * v;
-          if (Z != nullptr) out += argT<T>(a.beta, a.betaf) * Z[idx];
-          Y[idx] = out;
+          out[o] = argT<T>(a.alpha, a.alphaf) * v;
+        }
+        if (sizeof(T) == 4 && x0 + ox + M1 <= I1 && ((reinterpret_cast<uintptr_t>(Y + base)) & 15) == 0 &&
+            (Z == nullptr || ((reinterpret_cast<uintptr_t>(Z + base)) & 15) == 0)) {
+          if (Z != nullptr) {
+            const float4 z = __ldcg(reinterpret_cast<const float4*>(Z + base));
+            const T bz = argT<T>(a.beta, a.betaf);
+            out[0] += bz * static_cast<T>(z.x);
+            out[1] += bz * static_cast<T>(z.y);
+            out[2] += bz * static_cast<T>(z.z);
+            out[3] += bz * static_cast<T>(z.w);
+          }
+          *reinterpret_cast<float4*>(Y + base) = make_float4(static_cast<float>(out[0]), static_cast<float>(out[1]),
+                                                             static_cast<float>(out[2]), static_cast<float>(out[3]));
+        } else {
+#pragma unroll
+          for (int o = 0; o < M1; ++o) {
+            if (x0 + ox + o >= I1) break;
+            T v = out[o];
+            if (Z != nullptr) v += argT<T>(a.beta, a.betaf) * Z[base + o];
+            Y[base + o] = v;
+          }
         }
       }
     }
   }
 }
-
 #undef t1
 #undef t2
 
@@ -676,7 +739,7 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
 #define RTG_REG_CASE(NC, RR)                                                                          \
   if (a.nc == NC && rr == RR) {                                                                       \
     using Gm = RegGeom<RR, T>;                                                                        \
-    const size_t smem = static_cast<size_t>(NC * Gm::Ht * Gm::Wd + Gm::Ht * RTX) * sizeof(T);         \
+    const size_t smem = static_cast<size_t>(NC * Gm::Ht * Gm::Wd + RTY * Gm::Wd) * sizeof(T);         \
     e = set_smem(k_apply_reg<T, NC, RR>, smem);                                                       \
     if (e != cudaSuccess) return e;                                                                   \
     k_apply_reg<T, NC, RR><<<grid, FTHREADS, smem, s>>>(X, Y, Z, stop, a, b);                            \

@@ -421,7 +421,7 @@ k_sk_first_umma(PtrRef Xr, float* __restrict__ out, int64_t I, int64_t R, int64_
   constexpr int UPC = 64 / EV;                            // 16-byte units per column block
   constexpr int UNITS = U_BN * UPC / U_SPLIT;             // units per split thread per block
   static_assert(UNITS * U_SPLIT == U_BN * UPC, "units must divide evenly");
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];   // tiles aligned to 1024 below
   __shared__ __align__(8) uint64_t full[U_TSTAGES], empty[U_TSTAGES], lready[U_LBUF], lfree[U_LBUF];
   __shared__ uint32_t tmem_holder;
   __shared__ int s_bad;
