@@ -195,14 +195,14 @@ def solve(h, pr, X, stream=None, host=False, bf16=False):
 # Kernel groups whose minimum traffic the byte model below covers, and the
 # source files that define each (the recorded ncu traffic is dropped when
 # one of them has changed since).
-PHASE_FILES = {"apply": ["k_apply.cu"], "sketch": ["k_sketch.cu", "gs_common.cuh", "tma_common.cuh"],
+PHASE_FILES = {"apply": ["k_apply.cu"], "sketch": ["k_sketch.cu", "gs_common.cuh", "tma_common.cuh", "umma_common.cuh"],
                "gs": ["k_arnoldi.cu", "gs_common.cuh"],
                "update": ["k_arnoldi.cu", "gs_common.cuh", "tma_common.cuh"],
                "assemble": ["k_solve.cu"], "init": ["k_arnoldi.cu", "k_sketch.cu"]}
 KERNEL_NAMES = {"apply": "k_apply_reg<float,3,7> (W = Phi(V_j))",
                 "sketch": "k_sk_first_umma<float> (tcgen05) + k_sk_inner_tc<32> (S(W) with fused sketched dots)",
-                "update": "k_update_ring<float,8> (V_{j+1} streamed through a shared-memory ring, "
-                          "its sketched column, Givens block)",
+                "update": "k_update_ring<float, slot, depth> (V_{j+1} streamed through a shared-memory ring of "
+                          "the autotuned geometry, its sketched column, Givens block)",
                 "assemble": "k_assemble<float>", "init": "prologue group"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 
@@ -216,18 +216,23 @@ def source_sha(phase: str) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(phase: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if its kernel source is unchanged."""
+def recorded_traffic(phase: str, workload: str, bytes_per_launch: float):
+    """DRAM bytes per launch: the ratio of DRAM to algorithmic bytes that the
+    committed ncu summary measured for this kernel group and workload, times
+    this run's algorithmic bytes per launch (the group's traffic grows with
+    the tensors it reads); None when the kernel source changed since."""
     try:
         lines = open(TRAFFIC_FILE).read().splitlines()
     except OSError:
         return None
     for ln in lines:
+        if ln.startswith("#"):
+            continue
         kv = dict(t.split("=", 1) for t in ln.split() if "=" in t)
         if kv.get("phase") == phase and kv.get("workload") == workload:
             if kv.get("source_sha") != source_sha(phase):
                 return None
-            return float(kv["dram_bytes_per_launch"])
+            return round(float(kv["dram_ratio"]) * bytes_per_launch)
     return None
 
 
@@ -296,7 +301,7 @@ def phase_report(h, probs, X, peaks, workload: str):
     peak = peaks.get("hbm_gbs", 6800.0)
     roof = {"kernel": KERNEL_NAMES.get(dom, dom), "phase": dom, "bound": "hbm", "achieved": round(ach, 1),
             "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-            "traffic": recorded_traffic(dom, workload), "bytes_per_launch": round(bytes_per_launch),
+            "traffic": recorded_traffic(dom, workload, bytes_per_launch), "bytes_per_launch": round(bytes_per_launch),
             "us_per_launch": round(us_per_launch, 3), "launches": launches,
             "timing": "CUDA events around each kernel group of direct-launch solves, stream gated "
                       "until the group is queued",
@@ -337,7 +342,7 @@ def batched_phase_report(h, batch, grid, peaks, workload: str):
     peak = peaks.get("hbm_gbs", 6800.0)
     roof = {"kernel": KERNEL_NAMES.get(dom, dom), "phase": dom, "bound": "hbm", "achieved": round(ach, 1),
             "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-            "traffic": recorded_traffic(dom, workload + "_lockstep16"),
+            "traffic": recorded_traffic(dom, workload + "_lockstep16", bytes_per_launch),
             "bytes_per_launch": round(bytes_per_launch), "us_per_launch": round(us_per_launch, 3),
             "launches": launches[dom], "problems_per_launch": len(batch),
             "timing": "CUDA events around each kernel group of the batch run as one lock-step group "
