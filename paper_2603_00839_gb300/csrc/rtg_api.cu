@@ -1038,14 +1038,21 @@ struct TransposedFactors {
 // the shared-memory ring's slot size (the chunk of the tensor one CTA
 // streams) and depth.  Every geometry gives the same results bit for bit,
 // so the choice only changes speed.  Each candidate runs on the plan's own
-// workspace and grid (all problems of a lock-step group) from a synthetic
-// step state (j = min(m, 16): the update reads j + 1 tensors), five timed
-// launches each after one untimed; the fastest median wins and is cached
-// per (n, d, storage, problems per launch) in the handle.  The workspace is
-// cleared afterwards (every solve starts by resetting its state anyway).
+// workspace and grid (all problems of a lock-step group) from synthetic
+// step states (j = 4, 16, 40 bounded by m - 1: the update reads j + 1
+// tensors), five timed launches each after one untimed; the smallest sum of
+// the medians wins and is cached per (n, d, storage, problems per launch)
+// in the handle.  The workspace is cleared afterwards (every solve starts
+// by resetting its state anyway).
+constexpr int kConcurrentBranches = 4;
+
 // RTG_NO_AUTOTUNE=1 in the environment keeps the default geometry;
 // RTG_TILE_CONFIG=k fixes geometry k.
-static rtg_status tune_update(SolvePlan& P, std::map<std::string, int>* cache) {
+// branches: graph branches of a batched solve that run at once.  With
+// several, the search (which times one problem alone, where more and
+// smaller CTAs win) is skipped for the geometry with the fewest CTAs, the
+// largest slots: measured the fastest under concurrent branches.
+static rtg_status tune_update(SolvePlan& P, std::map<std::string, int>* cache, int branches) {
   Work& w = P.w;
   w.upcfg = 0;
   if (cache == nullptr || !update_uses_ring(w)) return RTG_OK;
@@ -1054,6 +1061,10 @@ static rtg_status tune_update(SolvePlan& P, std::map<std::string, int>* cache) {
   const char* force = std::getenv("RTG_TILE_CONFIG");   // a fixed geometry (tests, measurements)
   if (force != nullptr && force[0] >= '0' && force[0] < '0' + update_configs() && force[1] == 0) {
     w.upcfg = force[0] - '0';
+    return RTG_OK;
+  }
+  if (branches >= kConcurrentBranches) {
+    w.upcfg = update_configs() - 1;
     return RTG_OK;
   }
   std::string key;
@@ -1079,33 +1090,43 @@ static rtg_status tune_update(SolvePlan& P, std::map<std::string, int>* cache) {
   } cl{s};
   CK(cudaEventCreate(&cl.e[0]));
   CK(cudaEventCreate(&cl.e[1]));
-  Ctl c{};
-  c.j = w.m < 16 ? w.m : 16;
-  c.hnext = 1.0;
-  c.rs_skip = 1;
-  for (int p = 0; p < w.b.n; ++p)
-    CK(cudaMemcpyAsync(reinterpret_cast<char*>(w.ctl) + int64_t(p) * w.b.stride, &c, sizeof(Ctl),
-                       cudaMemcpyHostToDevice, s));
+  // the median of five launches at step indices 4, 16 and 40 (bounded by
+  // m - 1), summed: early steps whose tensors sit in L2 and a late one whose
+  // basis exceeds it
+  const int ncfg = update_configs();
+  float tot[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int js[3] = {4, 16, 40}, nj = 0;
+  for (int q = 0; q < 3; ++q) {
+    const int j = js[q] < w.m - 1 ? js[q] : w.m - 1;
+    if (nj == 0 || js[nj - 1] != j) js[nj++] = j;
+  }
   StepOpts o{};   // no graph condition, no lock-step count
-  int best = 0;
-  float best_ms = 0.f;
-  for (int cfg = 0; cfg < update_configs(); ++cfg) {
-    w.upcfg = cfg;
-    CK(launch_update(w, o, s));
-    float t[5];
-    for (int r = 0; r < 5; ++r) {
-      CK(cudaEventRecord(cl.e[0], s));
+  for (int q = 0; q < nj; ++q) {
+    Ctl c{};
+    c.j = js[q];
+    c.hnext = 1.0;
+    c.rs_skip = 1;
+    for (int p = 0; p < w.b.n; ++p)
+      CK(cudaMemcpyAsync(reinterpret_cast<char*>(w.ctl) + int64_t(p) * w.b.stride, &c, sizeof(Ctl),
+                         cudaMemcpyHostToDevice, s));
+    for (int cfg = 0; cfg < ncfg && cfg < 8; ++cfg) {
+      w.upcfg = cfg;
       CK(launch_update(w, o, s));
-      CK(cudaEventRecord(cl.e[1], s));
-      CK(cudaEventSynchronize(cl.e[1]));
-      CK(cudaEventElapsedTime(&t[r], cl.e[0], cl.e[1]));
-    }
-    std::sort(t, t + 5);
-    if (cfg == 0 || t[2] < best_ms) {
-      best_ms = t[2];
-      best = cfg;
+      float t[5];
+      for (int r = 0; r < 5; ++r) {
+        CK(cudaEventRecord(cl.e[0], s));
+        CK(launch_update(w, o, s));
+        CK(cudaEventRecord(cl.e[1], s));
+        CK(cudaEventSynchronize(cl.e[1]));
+        CK(cudaEventElapsedTime(&t[r], cl.e[0], cl.e[1]));
+      }
+      std::sort(t, t + 5);
+      tot[cfg] += t[2];
     }
   }
+  int best = 0;
+  for (int cfg = 1; cfg < ncfg && cfg < 8; ++cfg)
+    if (tot[cfg] < tot[best]) best = cfg;
   CK(cudaMemsetAsync(P.mem.p, 0, P.mem.bytes, s));
   CK(cudaStreamSynchronize(s));
   w.upcfg = best;
@@ -1118,7 +1139,7 @@ static rtg_status tune_update(SolvePlan& P, std::map<std::string, int>* cache) {
 // graph solve, its CUDA graph.  Builds only while nothing of the handle runs.
 rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDesc* dhost, InfoDev* ihost,
                      std::shared_ptr<SolvePlan>* out, int nbatch = 0,
-                     std::map<std::string, int>* tune_cache = nullptr) {
+                     std::map<std::string, int>* tune_cache = nullptr, int branches = 1) {
   const rtg_factor* A = ps.A;
   const rtg_factor* B = ps.B;
   const int nA = ps.nA, nB = ps.nB, dtype = ps.dtype, vdtype = ps.vdtype, m = ps.m, mode = ps.mode;
@@ -1181,7 +1202,7 @@ rtg_status make_plan(const PlanSpec& ps, SolveDesc* ddev, InfoDev* idev, SolveDe
     carve_work(P->mem.p, dtype, n, sp, m, tkb, ae, P->w, &P->tA, &P->tB, &P->sk, vdtype, nU);
   }
   P->w.cycles = ps.cycles;
-  RK(tune_update(*P, tune_cache));
+  RK(tune_update(*P, tune_cache, branches));
   if (nbatch > 0) {
   } else if (ddev != nullptr) {   // descriptor and info record in a batch's buffers
     P->ext_desc = true;
@@ -1903,7 +1924,7 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
       std::shared_ptr<SolvePlan> pl;
       const int first = BP->gfirst[k];
       RK(make_plan(specs[members[k][0]], nullptr, nullptr, dh + first, ih + first, &pl,
-                   static_cast<int>(members[k].size()), &h->tuned));
+                   static_cast<int>(members[k].size()), &h->tuned, static_cast<int>(members.size())));
       RK(build_branch(*pl, BP->graph));
       BP->plans.push_back(std::move(pl));
     }
