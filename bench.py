@@ -569,7 +569,7 @@ def reached(res) -> str:
     return f"{sum(bool(r.converged) for r in res)}/{len(res)}"
 
 
-def video_form(h, api, torch, stream, flush, reps: int = 4):
+def video_form(h, api, torch, stream, flush, peaks, reps: int = 4):
     """Precision form on the video workload (256x256x3x64, spatial sigma 2
     radius 6, channel mix, temporal box of width 5, noise 5e-3, m = 40,
     sketch (96, 96, 3, 32), GCV): plain FP32 solves against the BF16 basis,
@@ -602,6 +602,21 @@ def video_form(h, api, torch, stream, flush, reps: int = 4):
                      "ms_per_solve": round(ms, 3),
                      "mean_iters": float(np.mean([r.iters for r in res])), "reached_stop_level": reached(res),
                      "rel_error_to_true_video": round(re, 5)}
+        # the step's operator apply (k_apply_st: reads V_j, writes W, both in the
+        # basis format) against HBM, from one phase-timed solve
+        _, pi = h.gmres_solve(C, p.m, p.sketch_dims, p.seed, p.lam, A, B, X=Xo, tol=tol, mu_grid=p.mu_grid,
+                              max_restarts=RESTARTS, bf16_basis=bf, phase_times=True)
+        la = pi.phase_launches["apply"]
+        if la > 0 and pi.phase_ms["apply"] > 0:
+            n = int(np.prod(p.dims))
+            bpl = 2 * n * (2 if bf else 4)
+            us = 1e3 * pi.phase_ms["apply"] / la
+            gbs = bpl / (us * 1e-6) / 1e9
+            peak = peaks.get("hbm_gbs", 6800.0)
+            out[name]["apply"] = {"kernel": "k_apply_st<%s> (blur 2D + channel mix + temporal box, one pass)"
+                                            % ("bf16, bf16" if bf else "float, float"),
+                                  "bytes_per_launch": bpl, "us_per_launch": round(us, 2), "gbs": round(gbs, 1),
+                                  "frac_of_measured_hbm": round(gbs / peak, 3)}
     out["bf16_vs_fp32_rel_diff"] = round(float(torch.linalg.vector_norm(Xs["bf16_basis"] - Xs["fp32"]) /
                                                torch.linalg.vector_norm(Xs["fp32"])), 5)
     out["speedup_bf16_over_fp32"] = round(out["bf16_basis"]["value"] / out["fp32"]["value"], 3)
@@ -816,7 +831,7 @@ def run_ours(args):
                    "iters_per_problem": [r.iters for r in outs_rs[0]],
                    "note": "every solve runs to rho* (restarted up to 3 times); the batch's time is bound by "
                            "its slowest problem's chain of steps"}
-    vid = video_form(h, api, torch, stream, flush) if extra else None
+    vid = video_form(h, api, torch, stream, flush, peaks) if extra else None
     uneven = uneven_form(h, api, torch, stream, flush, args.uneven) if extra else None
 
     ws_form = None

@@ -110,7 +110,9 @@ def test_bf16_apply_is_one_rounding_of_the_exact_operator(h, I1, I2, F):
 
 @pytest.mark.parametrize("dims,sk", [((64, 64, 3, 9), (24, 24, 3, 4)), ((72, 40, 3), (32, 16, 3)),
                                      ((512, 512, 3), (128, 128, 3)),
-                                     ((64, 512, 20), (32, 64, 20)), ((40, 300, 35), (20, 50, 35))])
+                                     ((64, 512, 20), (32, 64, 20)), ((40, 300, 35), (20, 50, 35)),
+                                     ((150, 37, 3), (40, 16, 3)),      # I_1 % 8 != 0: plain loads
+                                     ((304, 41, 3), (200, 10, 3))])    # s_1 > 128: two row tiles
 def test_bf16_sketch_matches_oracle(h, dims, sk):
     x = np.random.default_rng(5).standard_normal(dims)
     Xb, xb = _bf16(x)
