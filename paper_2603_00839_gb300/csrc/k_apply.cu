@@ -349,11 +349,11 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
 // chunk of output frames.  It walks the input frames in order: each frame's
 // halo tile is loaded into registers (16-byte loads, BF16 or FP32) while
 // the previous frame is being filtered, converted to FP32 in shared memory,
-// filtered along modes 1 and 2 as in the image kernel, and added into a
+// filtered along mode 2 and then mode 1 as in the image kernel, and added into a
 // ring of five partial output frames held in registers; the oldest ring
 // entry is complete after each input frame, is mixed across the channels
 // and stored.  Arithmetic is FP32 in every storage format.
-constexpr int STX = 64, STY = 16, ST_THREADS = 256, ST_RING = 5, ST_SEG = 8, ST_VSEG = 4;
+constexpr int STX = 64, STY = 16, ST_THREADS = 256, ST_RING = 5, ST_VSEG = 4;
 
 struct StArgs {
   int64_t I1, I2, I3, nF;   // mode sizes; nF = 1 for order 3
@@ -396,6 +396,41 @@ __device__ __forceinline__ void st_to_float(const uint4& q, float* dst, __nv_bfl
 }
 __device__ __forceinline__ void st_store(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st_store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+// Four consecutive outputs (plus beta Z, if Z is given): one 16-byte (FP32)
+// or 8-byte (BF16) store when all four lie inside the row (`room` entries
+// left in it) and the address is aligned, else element by element.
+template <typename TO>
+__device__ __forceinline__ void st_store4(TO* p, const float* z, float beta, const float (&v)[4], int room) {
+  float o[4] = {v[0], v[1], v[2], v[3]};
+  const bool vec = room >= 4 && (reinterpret_cast<uintptr_t>(p) % (4 * sizeof(TO))) == 0 &&
+                   (z == nullptr || (reinterpret_cast<uintptr_t>(z) % 16) == 0);
+  if (vec) {
+    if (z != nullptr) {
+      const float4 q = __ldcg(reinterpret_cast<const float4*>(z));
+      o[0] = fmaf(beta, q.x, o[0]);
+      o[1] = fmaf(beta, q.y, o[1]);
+      o[2] = fmaf(beta, q.z, o[2]);
+      o[3] = fmaf(beta, q.w, o[3]);
+    }
+    if constexpr (sizeof(TO) == 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(o[0], o[1]), hi = __floats2bfloat162_rn(o[2], o[3]);
+      uint2 w;
+      w.x = *reinterpret_cast<const uint32_t*>(&lo);
+      w.y = *reinterpret_cast<const uint32_t*>(&hi);
+      *reinterpret_cast<uint2*>(p) = w;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (e >= room) break;
+      float x = o[e];
+      if (z != nullptr) x = fmaf(beta, z[e], x);
+      st_store(p + e, x);
+    }
+  }
+}
 
 template <typename TI, typename TO, int NC, int RR>
 __global__ void __launch_bounds__(ST_THREADS, 2)
@@ -416,7 +451,7 @@ k_apply_st(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, StArgs a, Batch bt)
   constexpr int NPT = (NCH + ST_THREADS - 1) / ST_THREADS;   // per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* in_s = reinterpret_cast<float*>(smem_raw);   // NC x Ht x Wd
-  float* tmp = in_s + NC * Ht * Wd;                   // Ht x STX
+  float* tmp = in_s + NC * Ht * Wd;                   // STY x Wd
   const int x0 = blockIdx.x * STX, y0 = blockIdx.y * STY;
   const int I1 = static_cast<int>(a.I1), I2 = static_cast<int>(a.I2);
   const int64_t plane = a.I1 * a.I2;
@@ -425,8 +460,11 @@ k_apply_st(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, StArgs a, Batch bt)
   const int64_t f0 = static_cast<int64_t>(chunk) * a.F;
   const int64_t f1 = (f0 + a.F < a.nF) ? f0 + a.F : a.nF;
   const int rt = a.rt;
-  const int vx = threadIdx.x & (STX - 1);
-  const int vy = (threadIdx.x / STX) * ST_VSEG;
+  // mode-1 pass and output: row oy, columns ox .. ox + 3 of the tile
+  static_assert(STY * (STX / ST_VSEG) == ST_THREADS, "one output quad per thread");
+  const int oy = threadIdx.x / (STX / ST_VSEG);
+  const int ox = (threadIdx.x % (STX / ST_VSEG)) * ST_VSEG;
+  constexpr int NPAIR = Wd / 2;                       // mode-2 pass: column pairs x 4 output rows
   uint4 pre[NPT];
   auto load_frame = [&](int64_t u) {
 #pragma unroll
@@ -482,12 +520,27 @@ k_apply_st(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, StArgs a, Batch bt)
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const float* ins = in_s + c * Ht * Wd;
-        for (int task = threadIdx.x; task < Ht * (STX / ST_SEG); task += ST_THREADS) {
-          const int yy = task / (STX / ST_SEG);
-          const int xs = (task - yy * (STX / ST_SEG)) * ST_SEG;
+        // mode 2 first over every staged column: task = (column pair, 4 output rows)
+        for (int task = threadIdx.x; task < NPAIR * (STY / ST_VSEG); task += ST_THREADS) {
+          const int pr = task % NPAIR, g = task / NPAIR;
+          float2 win[ST_VSEG + 2 * RR];
+#pragma unroll
+          for (int u2 = 0; u2 < ST_VSEG + 2 * RR; ++u2)
+            win[u2] = *reinterpret_cast<const float2*>(ins + (g * ST_VSEG + u2) * Wd + 2 * pr);
+#pragma unroll
+          for (int o = 0; o < ST_VSEG; ++o) {
+            float2 sacc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int t = 0; t < NT; ++t) sacc = ffma2(make_float2(a.t2[t], a.t2[t]), win[o + t], sacc);
+            *reinterpret_cast<float2*>(tmp + (g * ST_VSEG + o) * Wd + 2 * pr) = sacc;
+          }
+        }
+        __syncthreads();
+        // mode 1: 4 consecutive outputs of row oy
+        {
           constexpr int A0 = OFF & ~3, SH = OFF & 3;
-          constexpr int NV = (SH + ST_SEG + 2 * RR + 3) / 4;
-          const float4* rp = reinterpret_cast<const float4*>(ins + yy * Wd + xs + A0);
+          constexpr int NV = (SH + ST_VSEG + 2 * RR + 3) / 4;
+          const float4* rp = reinterpret_cast<const float4*>(tmp + oy * Wd + ox + A0);
           float buf[NV * 4];
 #pragma unroll
           for (int v4 = 0; v4 < NV; ++v4) {
@@ -498,25 +551,14 @@ k_apply_st(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, StArgs a, Batch bt)
             buf[4 * v4 + 3] = q.w;
           }
 #pragma unroll
-          for (int o = 0; o < ST_SEG; ++o) {
+          for (int o = 0; o < ST_VSEG; ++o) {
             float sacc = 0.f;
 #pragma unroll
             for (int t = 0; t < NT; ++t) sacc = fmaf(a.t1[t], buf[SH + o + t], sacc);
-            tmp[yy * STX + xs + o] = sacc;
+            P[c][o] = sacc;
           }
         }
-        __syncthreads();
-        float win[ST_VSEG + 2 * RR];
-#pragma unroll
-        for (int w2 = 0; w2 < ST_VSEG + 2 * RR; ++w2) win[w2] = tmp[(vy + w2) * STX + vx];
-#pragma unroll
-        for (int o = 0; o < ST_VSEG; ++o) {
-          float sacc = 0.f;
-#pragma unroll
-          for (int t = 0; t < NT; ++t) sacc = fmaf(a.t2[t], win[o + t], sacc);
-          P[c][o] = sacc;
-        }
-        if (c + 1 < NC) __syncthreads();
+        if (c + 1 < NC) __syncthreads();   // the next channel's mode-2 pass rewrites tmp
       }
     }
     // ring[k] is output frame u - rt + k; frame u enters with tap t4[2 + rt - k]
@@ -530,23 +572,21 @@ k_apply_st(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, StArgs a, Batch bt)
         for (int o = 0; o < ST_VSEG; ++o) ring[k][c][o] = fmaf(tk, P[c][o], ring[k][c][o]);
     }
     const int64_t t = u - rt;
-    const int gx = x0 + vx;
-    if (t >= f0 && t < f1 && gx < I1) {
+    const int gy = y0 + oy;
+    if (t >= f0 && t < f1 && gy < I2) {
 #pragma unroll
-      for (int o = 0; o < ST_VSEG; ++o) {
-        const int gy = y0 + vy + o;
-        if (gy >= I2) break;
+      for (int p = 0; p < NC; ++p) {
+        const int64_t base = ((static_cast<int64_t>(group) * NC + p) + a.I3 * t) * plane +
+                             static_cast<int64_t>(gy) * I1 + x0 + ox;
+        float out[ST_VSEG];
 #pragma unroll
-        for (int p = 0; p < NC; ++p) {
+        for (int o = 0; o < ST_VSEG; ++o) {
           float v = 0.f;
 #pragma unroll
           for (int c = 0; c < NC; ++c) v = fmaf(a.M[p + NC * c], ring[0][c][o], v);
-          const int64_t idx = ((static_cast<int64_t>(group) * NC + p) + a.I3 * t) * plane +
-                              static_cast<int64_t>(gy) * I1 + gx;
-          float out = a.alpha * v;
-          if (Z != nullptr) out = fmaf(a.beta, Z[idx], out);
-          st_store(Y + idx, out);
+          out[o] = a.alpha * v;
         }
+        st_store4(Y + base, Z != nullptr ? Z + base : nullptr, a.beta, out, I1 - (x0 + ox));
       }
     }
 #pragma unroll
@@ -850,7 +890,7 @@ static cudaError_t apply_st_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha
 #define RTG_ST_CASE(NC, RR)                                                                         \
   if (nc == NC && rr == RR) {                                                                       \
     using Gm = StGeom<RR, TI>;                                                                      \
-    const size_t smem = static_cast<size_t>(NC * Gm::Ht * Gm::Wd + Gm::Ht * STX) * sizeof(float);   \
+    const size_t smem = static_cast<size_t>(NC * Gm::Ht * Gm::Wd + STY * Gm::Wd) * sizeof(float);   \
     cudaError_t e = set_smem(k_apply_st<TI, TO, NC, RR>, smem);                                     \
     if (e != cudaSuccess) return e;                                                                 \
     k_apply_st<TI, TO, NC, RR><<<grid, ST_THREADS, smem, s>>>(X, Y, Z, stop, a, b);                    \
