@@ -104,17 +104,60 @@ def rho_star(nu_c: float) -> float:
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """SM clock and clock-event (throttle) reasons during the timed region:
+    read-only NVML queries every 10 ms from a thread (libnvidia-ml through
+    ctypes), else nvidia-smi every 200 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, cuda_index: int):
+        # NVML and nvidia-smi number the GPUs physically; CUDA numbers the visible ones
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [t.strip() for t in vis.split(",") if t.strip()]
+        self.gpu = int(ids[cuda_index]) if cuda_index < len(ids) and ids[cuda_index].isdigit() else cuda_index
         self.proc = None
         self.lines = []
+        self.samples = []       # (sm MHz, reason bits) from NVML
+        self.max_mhz = None
+        self.nvml = None
+        self.stop = threading.Event()
+        self.t = None
+
+    def _start_nvml(self) -> bool:
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return False
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) != 0:
+                lib.nvmlShutdown()
+                return False
+            fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        except (OSError, AttributeError):
+            return False
+        mx = ctypes.c_uint(0)
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:   # 1: the SM clock domain
+            self.max_mhz = float(mx.value)
+
+        def loop():
+            c, r = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+            while not self.stop.is_set():
+                if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(c)) == 0 and fn(h, ctypes.byref(r)) == 0:
+                    self.samples.append((float(c.value), int(r.value)))
+                self.stop.wait(0.01)
+        self.nvml = lib
+        self.t = threading.Thread(target=loop, daemon=True)
+        self.t.start()
+        return True
 
     def __enter__(self):
+        if self._start_nvml():
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
@@ -130,6 +173,10 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        if self.nvml is not None:
+            self.stop.set()
+            self.t.join(timeout=2)
+            self.nvml.nvmlShutdown()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -138,6 +185,11 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        if self.nvml is not None:
+            sm = [c for c, _ in self.samples]
+            reasons = sorted({nm for _, r in self.samples for bit, nm in self.REASONS.items() if r & bit})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(sm), "source": "NVML, every 10 ms"}
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
@@ -153,7 +205,7 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, every 200 ms"}
 
 
 # ----------------------------------------------------------------------------- problems
