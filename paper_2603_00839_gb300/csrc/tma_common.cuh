@@ -43,6 +43,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Tiled tensor copy (TMA, cp.async.bulk.tensor) of one box of a 3-D tensor
+// map into shared memory, completing on an mbarrier.  tmap: the generic
+// address of the map (a __grid_constant__ kernel parameter); c0: the
+// innermost coordinate, whose byte offset must be a multiple of 16; boxes
+// reaching past the tensor are filled with zeros.
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Bulk copy shared -> global (bulk-group completion); both addresses
 // 16-byte aligned, size a multiple of 16.  The issuing thread commits the
 // group and waits until the source has been read before the shared memory
