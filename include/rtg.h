@@ -138,7 +138,7 @@ typedef struct rtg_opts {
                                         sketched, and C / X0 16-byte aligned. */
 
 /* Kernel groups of one solve, the index of rtg_info.phase_ms / phase_launches.
- *   SETUP     workspace reset and the sketch signs / Theta fragments (Section 2, Theta_k)
+ *   SETUP     workspace reset and the sketch signs / Theta operand images (Section 2, Theta_k)
  *   INIT      R_0 = C - Phi(X_0), S(R_0), beta, V_1 and its sketch (Algorithm 2 start)
  *   APPLY     W = Phi(V_j)                                  (Eq. 57 operator)
  *   SKETCH    S(W) and, where fused, the sketched dots and Gram-Schmidt finish
@@ -522,7 +522,7 @@ rtg_status rtg_gmres_solve_batched(rtg_handle handle, int32_t nprob, const rtg_p
  * allocates nothing: its scratch (packed signs and the contraction
  * intermediates) lives in one 16 MiB array of the library's static device
  * memory, which every GPU that loads the library holds until the process
- * exits.  Sizes whose scratch (signs, Theta fragments and two partial-sum
+ * exits.  Sizes whose scratch (signs, Theta operand images and two partial-sum
  * intermediates) exceeds 16 MiB are rejected with RTG_ERR_INVALID_ARG and a message in rtg_last_error(),
  * and so are tensors of more than 2^40 elements and an SX that overlaps X (as for rtg_sketch).
  * The first call on a device looks up the array's device address

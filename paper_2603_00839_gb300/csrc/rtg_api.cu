@@ -591,7 +591,7 @@ struct PhaseScope {
 };
 
 // Scratch of rtg_sketch for one (shape, sketch sizes, problem id, dtype,
-// stream): the packed signs, Theta fragments and chain intermediates, and
+// stream): the packed signs, Theta operand images and chain intermediates, and
 // the seed the signs were last drawn for (they are drawn again when a call
 // brings another seed).
 struct SketchCache {

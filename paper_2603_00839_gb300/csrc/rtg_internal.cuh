@@ -262,7 +262,7 @@ struct SketchPlan {
   int stage_in_blocked[kMaxOrder];
   int64_t next_M[kMaxOrder], next_L[kMaxOrder], next_I[kMaxOrder], next_LT[kMaxOrder];
   int64_t stage_out_alloc[kMaxOrder];   // floats the stage output buffer needs
-  int64_t frag_off[kMaxOrder];    // uint32 offset of the stage's Theta fragments
+  int64_t frag_off[kMaxOrder];    // uint32 offset of the stage's Theta images (tcgen05) or fragments (mma.sync)
   int64_t frag_words;
   int64_t part_elems;             // elements of each scratch tensor
   int last_split;                 // partial copies of the final sketch (1)
@@ -270,7 +270,7 @@ struct SketchPlan {
   int64_t dots_blocks;            // CTAs of that last stage (rows of partial sums)
 };
 
-// Scratch of one sketch chain: signs, Theta fragments, two tensors.
+// Scratch of one sketch chain: signs, Theta images / fragments, two tensors.
 struct SketchScratch {
   uint32_t* bits = nullptr;
   uint32_t* frags = nullptr;
@@ -339,7 +339,7 @@ cudaError_t launch_philox_words(uint64_t seed, uint64_t pid, int64_t n_words, ui
 // so one captured graph serves every seed; otherwise sp.seed / sp.pid.
 cudaError_t launch_theta_bits(const SketchPlan& sp, uint32_t* bits, cudaStream_t s,
                               const uint64_t* key_dev = nullptr, Batch b = Batch{});
-// signs, then (FP32 chain) the Theta fragments of every stage
+// signs, then (FP32 chain) the Theta images and fragments of every stage
 cudaError_t launch_theta(const SketchPlan& sp, uint32_t* bits, uint32_t* frags, cudaStream_t s,
                          const uint64_t* key_dev = nullptr, Batch b = Batch{});
 

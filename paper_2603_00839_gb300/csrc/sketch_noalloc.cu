@@ -86,7 +86,7 @@ extern "C" rtg_status rtg_sketch_noalloc(rtg_shape shape, rtg_dtype dtype,
     const char* y = static_cast<const char*>(SX);
     if (x < y + span && y < x + span) return noalloc_fail(RTG_ERR_INVALID_ARG, "SX must not overlap X");
   }
-  // scratch: packed signs, Theta fragments and two contraction intermediates
+  // scratch: packed signs, Theta operand images and two contraction intermediates
   const size_t need = sketch_scratch_bytes(sp);
   if (need > kNoAllocBytes) {
     char msg[256];
@@ -103,7 +103,7 @@ extern "C" rtg_status rtg_sketch_noalloc(rtg_shape shape, rtg_dtype dtype,
   const SketchScratch sc = carve_sketch_scratch(sp, base);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // every byte the chain reads is written first in this call: the signs and
-  // fragments by launch_theta, the intermediates by the contraction that
+  // images by launch_theta, the intermediates by the contraction that
   // produces them, so nothing in the shared scratch needs clearing
   e = launch_theta(sp, sc.bits, sc.frags, s);
   if (e == cudaSuccess) e = launch_sketch(sp, sc, ref(X), SX, nullptr, nullptr, s);
