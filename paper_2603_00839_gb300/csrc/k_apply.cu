@@ -11,7 +11,9 @@
 // product, ping-ponging through scratch tensors.
 #include <cuda_bf16.h>
 
-#include "rtg_internal.cuh"
+#include <cstring>
+
+#include "tma_common.cuh"
 
 namespace rtg {
 
@@ -176,7 +178,8 @@ __device__ __forceinline__ Pair<double> pfma(double t, Pair<double> v, Pair<doub
 
 template <typename T, int NC, int RR>
 __global__ void __launch_bounds__(FTHREADS, (RR <= 7 ? 4 : 1))
-k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch bt) {
+k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a,
+            const __grid_constant__ CUtensorMap xmap, int xtma, Batch bt) {
   const BIdx bi = bidx(bt);
   Xr = Xr.at(bi.off);
   Yr = Yr.at(bi.off);
@@ -194,8 +197,12 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
   constexpr int M1 = 4;                          // mode-1 pass: outputs per thread
   static_assert(Wd % 2 == 0 && NPAIR * (RTY / V2) <= 2 * FTHREADS, "mode-2 tasks");
   static_assert(RTY * (RTX / M1) == FTHREADS, "mode-1 tasks: one per thread");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* in_s = reinterpret_cast<T*>(smem_raw);      // NC x Ht x Wd
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t xbar;
+  // the tiled copy's destination must start on 128 bytes: the tile is placed
+  // there explicitly (the launch adds 128 bytes of slack)
+  const uint32_t raw = static_cast<uint32_t>(__cvta_generic_to_shared(smem_raw));
+  T* in_s = reinterpret_cast<T*>(smem_raw + (((raw + 127u) & ~127u) - raw));   // NC x Ht x Wd
   T* tmp = in_s + NC * Ht * Wd;                  // RTY x Wd
   const int x0 = blockIdx.x * RTX;
   const int y0 = blockIdx.y * RTY;
@@ -203,10 +210,34 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a, Batch
   const int64_t plane = a.I1 * a.I2;
   const int oy = threadIdx.x / (RTX / M1);       // mode-1 pass: output row
   const int ox = (threadIdx.x % (RTX / M1)) * M1; // mode-1 pass: first of 4 outputs
+  // with a tensor map of the input (FP32; the basis slot and the problem as
+  // its outer coordinates), one tiled TMA copy stages the halo tile of all
+  // NC channels, zero filled outside the tensor (the zero boundary of Eq. 57)
+  const int slot = (xtma && Xr.jidx != nullptr) ? *Xr.jidx + Xr.joff : 0;
+  // the copy engine's rules, checked: a 128-byte aligned destination and an
+  // innermost start coordinate on 16 bytes; otherwise the threads stage the tile
+  const bool tma = xtma && (static_cast<uint32_t>(__cvta_generic_to_shared(in_s)) & 127u) == 0 &&
+                   ((static_cast<int64_t>(x0 - RA) * static_cast<int64_t>(sizeof(T))) & 15) == 0;
+  if (tma && threadIdx.x == 0) mbar_init(&xbar);
+  uint32_t xphase = 0;
   for (int64_t slab = bi.z; slab < a.nslab; slab += bi.nz) {
     __syncthreads();
     const T* Xs = X + slab * NC * plane;
-    if (sizeof(T) == 4 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+    if (tma) {
+      if (threadIdx.x == 0) {
+        mbar_expect(&xbar, static_cast<uint32_t>(NC * Ht * Wd * sizeof(T)));
+        tma_load_5d(in_s, &xmap, x0 - RA, y0 - RR, static_cast<int>(slab * NC), slot, bi.p, &xbar);
+      }
+      const bool landed = mbar_wait(&xbar, xphase);
+      xphase ^= 1u;
+      if (__syncthreads_or(!landed)) {
+        // the copy did not land in time: wait once more (bounded) for it, then
+        // poison the tile so that the solve stops with a non-finite status
+        if (threadIdx.x == 0) mbar_wait(&xbar, xphase ^ 1u);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < NC * Ht * Wd; idx += FTHREADS) in_s[idx] = static_cast<T>(__int_as_float(0x7fc00000));
+      }
+    } else if (sizeof(T) == 4 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
       // 16-byte copies; a float4 lies wholly inside or outside (I1 % 4 == 0)
       constexpr int W4 = Wd / 4;
       for (int idx = threadIdx.x; idx < NC * Ht * W4; idx += FTHREADS) {
@@ -727,6 +758,38 @@ int apply_launches(const OpPlan& op, bool combine, int dtype, int tin, int tout)
 
 static bool has_ptr(const PtrRef& r) { return r.base != nullptr || r.ind != nullptr; }
 
+// Tensor map of an FP32 input of the register kernel: dims (I1, I2, planes,
+// slots, problems) where `planes` counts the tensor's I1 x I2 planes, slots
+// the basis slots of a slot-indexed buffer (1 for a direct pointer) and
+// problems the lock-step batch; boxes of the CTA's halo tile (Wd x Ht x NC),
+// zero filled outside.  False for inputs read through a pointer slot or a
+// ring, or that break the copy engine's 16-byte rules.
+static bool make_apply_map(CUtensorMap* m, const PtrRef& X, int64_t I1, int64_t I2, int64_t planes, int Wd, int Ht,
+                           int NC, const Batch& b) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (fn == nullptr || X.base == nullptr || X.ind != nullptr || X.mod != 0) return false;
+  const bool slotted = X.jidx != nullptr;
+  if (slotted && X.nslot <= 0) return false;
+  const uint64_t pitch = static_cast<uint64_t>(I1) * 4, plane = pitch * static_cast<uint64_t>(I2);
+  const uint64_t tens = plane * static_cast<uint64_t>(planes);
+  const uint64_t sstride = slotted ? static_cast<uint64_t>(X.stride) * 4 : ((tens + 15) & ~uint64_t(15));
+  const uint64_t nslot = slotted ? static_cast<uint64_t>(X.nslot) : 1;
+  const uint64_t pstride = b.n > 1 ? static_cast<uint64_t>(b.stride) : ((sstride * nslot + 15) & ~uint64_t(15));
+  const uint64_t lim = uint64_t(1) << 40;
+  if (reinterpret_cast<uintptr_t>(X.base) % 16 || pitch % 16 || plane % 16 || sstride % 16 || pstride % 16 ||
+      sstride < tens || pstride < sstride * nslot || pstride >= lim || I1 > 0x7fffffffll || I2 > 0x7fffffffll ||
+      planes > 0x7fffffffll)
+    return false;
+  const cuuint64_t dims[5] = {static_cast<cuuint64_t>(I1), static_cast<cuuint64_t>(I2),
+                              static_cast<cuuint64_t>(planes), nslot, static_cast<cuuint64_t>(b.n)};
+  const cuuint64_t strides[4] = {pitch, plane, sstride, pstride};
+  const cuuint32_t box[5] = {static_cast<cuuint32_t>(Wd), static_cast<cuuint32_t>(Ht), static_cast<cuuint32_t>(NC), 1u, 1u};
+  const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(X.base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename T>
 static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, double beta,
                            PtrRef Z, T* tmp, T* tmp2, const int* stop, cudaStream_t s, Batch b) {
@@ -779,10 +842,14 @@ static cudaError_t apply_t(const OpPlan& op, PtrRef X, PtrRef Y, double alpha, d
 #define RTG_REG_CASE(NC, RR)                                                                          \
   if (a.nc == NC && rr == RR) {                                                                       \
     using Gm = RegGeom<RR, T>;                                                                        \
-    const size_t smem = static_cast<size_t>(NC * Gm::Ht * Gm::Wd + RTY * Gm::Wd) * sizeof(T);         \
+    const size_t smem = static_cast<size_t>(NC * Gm::Ht * Gm::Wd + RTY * Gm::Wd) * sizeof(T) + 128;   \
     e = set_smem(k_apply_reg<T, NC, RR>, smem);                                                       \
     if (e != cudaSuccess) return e;                                                                   \
-    k_apply_reg<T, NC, RR><<<grid, FTHREADS, smem, s>>>(X, Y, Z, stop, a, b);                            \
+    CUtensorMap xm;                                                                                   \
+    std::memset(&xm, 0, sizeof xm);                                                                   \
+    const int xtma = (sizeof(T) == 4 && make_apply_map(&xm, X, a.I1, a.I2, a.nslab * NC, Gm::Wd, Gm::Ht, NC, b)) \
+                         ? 1 : 0;                                                                     \
+    k_apply_reg<T, NC, RR><<<grid, FTHREADS, smem, s>>>(X, Y, Z, stop, a, xm, xtma, b);                  \
     return cudaGetLastError();                                                                        \
   }
       RTG_REG_CASE(1, 3) RTG_REG_CASE(1, 5) RTG_REG_CASE(1, 7) RTG_REG_CASE(1, 9) RTG_REG_CASE(1, 12) RTG_REG_CASE(1, 16)

@@ -1000,21 +1000,6 @@ static OutMap stage_out_map(const SketchPlan& sp, int t) {
   return om;
 }
 
-// The driver's tensor-map encoder, looked up once (null if unavailable).
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q{};
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }();
-  return fn;
-}
-
 // Tensor map of a first-stage input X (I x R elements of `elt` bytes per
 // problem, problems `b.stride` bytes apart): dims (I, R, problems), boxes of
 // 64 x U_BN x 1, zero fill outside.  False when the encoder refuses it or X

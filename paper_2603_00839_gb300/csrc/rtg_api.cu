@@ -718,6 +718,7 @@ rtg_status enqueue_step(const OpHolder& op, const SketchPlan& sp, const Work& w,
   vj.base = w.V;
   vj.jidx = &w.ctl->j;
   vj.stride = w.n;
+  vj.nslot = w.m + 1;
   const int* stop = &w.ctl->stop;
   {
     PhaseScope ps(pt, RTG_PHASE_APPLY, step, apply_launches(op.op, false, dtype, w.vdtype, w.vdtype));

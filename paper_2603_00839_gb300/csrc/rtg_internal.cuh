@@ -294,6 +294,7 @@ struct PtrRef {
   int64_t stride = 0;
   int joff = 0;
   int mod = 0;      // > 0: slot (*jidx + joff) % mod of a ring
+  int nslot = 0;    // host: slots of the buffer `base` (slot indexing without a ring), 0 unknown
 #ifdef __CUDACC__
   __device__ __forceinline__ PtrRef at(int64_t off) const {
     PtrRef r = *this;
