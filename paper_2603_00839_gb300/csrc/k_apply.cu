@@ -171,6 +171,12 @@ __device__ __forceinline__ Pair<float> pfma(float t, Pair<float> v, Pair<float> 
 __device__ __forceinline__ Pair<double> pfma(double t, Pair<double> v, Pair<double> acc) {
   return {fma(t, v.x, acc.x), fma(t, v.y, acc.y)};
 }
+// Two adjacent values (8-byte aligned for FP32: one 64-bit shared load).
+__device__ __forceinline__ Pair<float> load_pair(const float* p) {
+  const float2 q = *reinterpret_cast<const float2*>(p);
+  return {q.x, q.y};
+}
+__device__ __forceinline__ Pair<double> load_pair(const double* p) { return {p[0], p[1]}; }
 
 // the taps as kernel-parameter (constant-bank) operands, see FusedArgs
 #define t1(t) argT<T>(a.t1p[t], a.t1pf[t])
@@ -197,7 +203,7 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a,
   constexpr int M1 = 4;                          // mode-1 pass: outputs per thread
   static_assert(Wd % 2 == 0 && NPAIR * (RTY / V2) <= 2 * FTHREADS, "mode-2 tasks");
   static_assert(RTY * (RTX / M1) == FTHREADS, "mode-1 tasks: one per thread");
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t xbar;
   // the tiled copy's destination must start on 128 bytes: the tile is placed
   // there explicitly (the launch adds 128 bytes of slack)
@@ -274,13 +280,7 @@ k_apply_reg(PtrRef Xr, PtrRef Yr, PtrRef Zr, const int* stop, FusedArgs a,
         Pair<T> win[V2 + 2 * RR];
 #pragma unroll
         for (int u = 0; u < V2 + 2 * RR; ++u) {
-          const T* p = ins + (g * V2 + u) * Wd + 2 * pr;
-          if constexpr (sizeof(T) == 4) {
-            const float2 q = *reinterpret_cast<const float2*>(p);
-            win[u] = {q.x, q.y};
-          } else {
-            win[u] = {p[0], p[1]};
-          }
+          win[u] = load_pair(ins + (g * V2 + u) * Wd + 2 * pr);
         }
 #pragma unroll
         for (int o = 0; o < V2; ++o) {

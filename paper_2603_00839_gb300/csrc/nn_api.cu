@@ -150,11 +150,8 @@ rtg_status shape_buffers(rtg_warmstart* ws, int N, int H, int W) {
   }
   // largest im2col (rows x 9 c_in) and GEMM output over the layers
   int64_t mk = 0, mn = 0;
-  int h = H, w = W;
   const int hs[NLAYER] = {H, H / 2, H / 4, H / 8, H / 4, H / 2, H, H};
   const int wsz[NLAYER] = {W, W / 2, W / 4, W / 8, W / 4, W / 2, W, W};
-  (void)h;
-  (void)w;
   for (int l = 0; l < NLAYER; ++l) {
     const int64_t M = int64_t(N) * hs[l] * wsz[l];
     mk = std::max<int64_t>(mk, M * 9 * ws->L[l].cin);
@@ -175,7 +172,6 @@ rtg_status shape_buffers(rtg_warmstart* ws, int N, int H, int W) {
   return RTG_OK;
 }
 
-const float* Wf(const rtg_warmstart* ws, int l) { return ws->P.as<float>() + ws->L[l].w; }
 const float* Bf(const rtg_warmstart* ws, int l) { return ws->P.as<float>() + ws->L[l].b; }
 const __nv_bfloat16* Wb(const rtg_warmstart* ws, int l) { return ws->Pb.as<__nv_bfloat16>() + ws->L[l].w; }
 
