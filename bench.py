@@ -41,10 +41,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--problems", type=int, default=16,
+    ap.add_argument("--problems", type=int, default=256,
                     help="distinct seeded problems (the plain form cycles them, the batched form solves "
                          "them together)")
-    ap.add_argument("--batch", type=int, default=16, help="problems per batched launch (chosen form)")
+    ap.add_argument("--batch", type=int, default=256, help="problems per batched launch (chosen form)")
+    ap.add_argument("--queue-slots", type=int, default=8,
+                    help="batched form: graph branches that take the batch's problems from a device work "
+                         "queue (0: one graph branch per problem)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start form")
@@ -736,6 +739,37 @@ def uneven_form(h, api, torch, stream, flush, count: int, reps: int = 2):
                         "lambda 1e-4..1e-1, m 30, sketch min(I_k,128), FP32"}
 
 
+def queue_form(api, torch, stream, flush, batch, grid, slots, reps: int = 3):
+    """The chosen form's batch solved with other graph layouts: every problem
+    its own branch with its own workspace (slots 0), or that many branches
+    taking the problems from the device work queue; and the first 16 problems
+    alone, one branch each (a batch of 16 per launch).  A fresh handle, so
+    that the device memory each plan takes is the change in free memory
+    around its first call."""
+    hq = api.Handle(torch.cuda.current_device())
+    out = {"problems": len(batch)}
+    for name, bt, k in [(f"queue_{k}" if k else "branch_per_problem", batch, k) for k in slots] + \
+                       [("batch_of_16_branch_per_problem", batch[:16], 0)]:
+        def run(_):
+            return hq.gmres_solve_batched(bt, mu_grid=grid, queue_slots=k, max_restarts=RESTARTS)[1]
+        free0 = torch.cuda.mem_get_info()[0]
+        t0 = time.perf_counter()
+        run(0)
+        first = time.perf_counter() - t0
+        mem = free0 - torch.cuda.mem_get_info()[0]
+        run(0)
+        ms, res = device_timed(run, reps, stream, flush)
+        res = res[-1]
+        out[name] = {"value": round(sum(bool(r.converged) for r in res) / (ms / 1e3), 2),
+                     "unit": "solves/s (reaching rho*)", "ms_per_batch": round(ms, 3), "problems": len(bt),
+                     "branches": k if k else len(bt), "device_bytes": int(mem),
+                     "first_call_s": round(first, 2), "reached_stop_level": reached(res),
+                     "mean_iters": float(np.mean([r.iters for r in res]))}
+    hq.close()
+    torch.cuda.synchronize()
+    return out
+
+
 def run_ours(args):
     import torch
     global USE_GRAPH
@@ -776,16 +810,20 @@ def run_ours(args):
                      lam=probs[0]["p"].lam, tol=probs[(k * B + i) % len(probs)]["tol"], X=Xb[i])
                 for i in range(B)]
 
+    slots = args.queue_slots if args.group_max <= 1 else 0
+
     def batched(bt, bf16=False):
         return h.gmres_solve_batched(bt, mu_grid=grid, use_graph=not args.direct, group_max=args.group_max,
-                                     max_restarts=RESTARTS, bf16_basis=bf16)
+                                     queue_slots=slots, max_restarts=RESTARTS, bf16_basis=bf16)
 
-    # ---- plain FP32 form: one solve per step
+    # ---- plain FP32 form: one solve per step, every problem of the batch at
+    # least once (the forms are compared on the same mix of problems)
+    single_steps = max(args.steps, len(probs))
     plain_ms, plain_res = float("nan"), []
     if not only_b:
         for s in range(args.warmup):
             solve(h, probs[s % len(probs)], X)
-        plain_ms, plain_res = device_timed(lambda s: solve(h, probs[s % len(probs)], X)[1], args.steps, stream,
+        plain_ms, plain_res = device_timed(lambda s: solve(h, probs[s % len(probs)], X)[1], single_steps, stream,
                                            flush)
         for r in plain_res:
             if r.device_status != 0:
@@ -800,7 +838,7 @@ def run_ours(args):
     if not only_b:
         for s in range(args.warmup):
             gk(probs[s % len(probs)])
-        gk_ms, gk_res = device_timed(lambda s: gk(probs[s % len(probs)]), args.steps, stream, flush)
+        gk_ms, gk_res = device_timed(lambda s: gk(probs[s % len(probs)]), single_steps, stream, flush)
 
     # ---- chosen form: batched (B problems per CUDA-graph launch), one batch per step
     for s in range(args.warmup):
@@ -872,7 +910,7 @@ def run_ours(args):
     rs_form = None
     if extra:
         def batched_rs(bt):
-            return h.gmres_solve_batched(bt, mu_grid=grid, max_restarts=3)
+            return h.gmres_solve_batched(bt, mu_grid=grid, max_restarts=3, queue_slots=slots)
         for s in range(2):
             batched_rs(batch_of(s % nb))
         ms_rs, outs_rs = device_timed(lambda s: batched_rs(batch_of(s % nb))[1], args.steps, stream, flush)
@@ -881,22 +919,23 @@ def run_ours(args):
                    "ms_per_batch": round(ms_rs, 4), "batch": B, "restarts": 3,
                    "mean_iters": float(np.mean([r.iters for r in rrs])), "reached_stop_level": reached(rrs),
                    "iters_per_problem": [r.iters for r in outs_rs[0]],
-                   "note": "every solve runs to rho* (restarted up to 3 times); the batch's time is bound by "
-                           "its slowest problem's chain of steps"}
+                   "note": "every solve runs to rho* (restarted up to 3 times)"}
     vid = video_form(h, api, torch, stream, flush, peaks) if extra else None
     uneven = uneven_form(h, api, torch, stream, flush, args.uneven) if extra else None
+    queue = queue_form(api, torch, stream, flush, batch_of(0), grid, (0, 16, 32)) if extra and slots else None
 
     ws_form = None
     if rank == 0 and not args.no_warm_start and not only_b:
-        ws_form = (warm_start_form(h, api, torch, probs, train_n=20000, steps=3000, held_out=512)
-                   if args.ws_full else warm_start_form(h, api, torch, probs))
+        ws_form = (warm_start_form(h, api, torch, probs[:16], train_n=20000, steps=3000, held_out=512)
+                   if args.ws_full else warm_start_form(h, api, torch, probs[:16]))
 
     # phase timing holds the stream at gates the host opens; a profiler that
     # serialises every launch would wait on them, so --direct (the profiler
     # mode) leaves it out
     phased = rank == 0 and not args.direct and not only_b
-    roof_plain, phases = phase_report(h, probs, X, peaks, WORKLOAD) if phased else (None, None)
-    roof, phases_b = batched_phase_report(h, batch_of(0), grid, peaks, WORKLOAD) if phased else (None, None)
+    roof_plain, phases = phase_report(h, probs[:16], X, peaks, WORKLOAD) if phased else (None, None)
+    roof, phases_b = (batched_phase_report(h, batch_of(0)[:16], grid, peaks, WORKLOAD) if phased
+                      else (None, None))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not only_b:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -916,9 +955,11 @@ def run_ours(args):
                           "launch": ("direct launches" if args.direct else "cuda graph") +
                                     (f" (lock-step groups of up to {args.group_max} problems)"
                                      if args.group_max > 1 else
+                                     f" ({slots} branches taking the problems from a device work queue, "
+                                     "device-side WHILE loops)" if slots else
                                      " (one branch per problem, device-side WHILE loops)")},
                "forms": {"batched_fp32": {"value": round(value, 2), "ms_per_batch": round(ms_max, 4),
-                                          "batch": B, "reached_stop_level": reached(res_b),
+                                          "batch": B, "queue_slots": slots, "reached_stop_level": reached(res_b),
                                           "vs_plain_fp32": round(value / plain_value, 3) if plain_value else None},
                          "plain_fp32": {"value": round(plain_value, 2), "ms_per_solve": round(plain_max, 4),
                                         "mean_iters": float(np.mean([r.iters for r in plain_res])) if plain_res else None,
@@ -938,6 +979,7 @@ def run_ours(args):
                                               "method": "sketched Golub-Kahan (Algorithm 4), no restarts"},
                          "precision_video": vid,
                          "batched_uneven_256": uneven,
+                         "batched_layouts": queue,
                          "warm_start_fp32": ws_form},
                "e2e": {"value": round(e2e_val, 2), "unit": "solves/s",
                        # per problem: C and X, plus the 328-byte descriptor and the 2376-byte

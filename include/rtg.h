@@ -111,7 +111,11 @@ typedef struct rtg_opts {
                                         graph); calls on one slot are ordered by their stream */
     int32_t group_max;               /* batched solves: most problems in one lock-step group;
                                         0 or 1: every problem its own graph branch */
-    int32_t pad;
+    int32_t queue_slots;             /* batched solves: > 0 serves each class of problems of
+                                        equal structure by at most this many graph branches that
+                                        take the class's problems from a device work queue
+                                        (memory: one workspace per branch, not per problem);
+                                        0: off.  Excludes group_max > 1 */
 } rtg_opts;
 
 #define RTG_MAX_SLOTS 64
@@ -482,7 +486,8 @@ typedef struct rtg_problem {
     double tol;                      /* stop level of rho_j */
 } rtg_problem;
 
-#define RTG_MAX_BATCH 1024
+#define RTG_MAX_BATCH 1024          /* problems of a batch, or graph branches of a queued batch */
+#define RTG_MAX_QUEUE 65536         /* problems of a batch with opts->queue_slots > 0 */
 
 /*
  * Batched form: nprob independent RTG-GMRES solves, of any mix of shapes,
@@ -499,7 +504,21 @@ typedef struct rtg_problem {
  * solved alone.  The groups are independent branches of one CUDA graph, built on
  * the first call for a given list of problem structures and replayed
  * afterwards; descriptors go up in one strided copy per group and the info
- * records come back the same way.  opts (may be NULL) is shared: GCV grid,
+ * records come back the same way.
+ * Work queue (opts->queue_slots = K > 0): the problems of each class of equal
+ * structure (the lock-step key above) go into a device queue, and the class
+ * gets min(K, its problems) graph branches, each with one workspace.  A
+ * branch takes the next problem with an atomic increment of the class's
+ * counter, solves it, returns its info record and takes the next, until the
+ * queue is empty (a device-side WHILE loop around the solve's own), so a
+ * branch whose problem stops early goes on to another, and the device memory
+ * grows with the branches, not the problems: up to RTG_MAX_QUEUE problems,
+ * at most RTG_MAX_BATCH branches in all.  Descriptors go up in one copy and
+ * the info records come back in one.  Which branch solves which problem
+ * depends on timing; the result does not (each equals the same problem
+ * solved alone, bit for bit).  RTG_FLAG_NO_GRAPH runs each class's problems
+ * in order on one workspace; RTG_FLAG_PHASE_TIMES is UNSUPPORTED here, and
+ * group_max > 1 with queue_slots > 0 is INVALID_ARG.  opts (may be NULL) is shared: GCV grid,
  * breakdown level, RTG_FLAG_BF16_BASIS, and RTG_FLAG_NO_GRAPH /
  * RTG_FLAG_PHASE_TIMES (direct launches, one group after another; with
  * PHASE_TIMES each problem's phase_ms / phase_launches are those of its

@@ -17,6 +17,7 @@ MAX_KRYLOV = 256
 MAX_MU = 32
 MAX_SLOTS = 64
 MAX_BATCH = 1024
+MAX_QUEUE = 65536
 
 # rtg_status
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_ALLOC, ERR_TIMEOUT, ERR_NONFINITE = range(7)
@@ -41,7 +42,7 @@ class Factor(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("mu_grid", C.POINTER(C.c_double)), ("n_mu", C.c_int32),
                 ("max_restarts", C.c_int32), ("breakdown_tol", C.c_double), ("flags", C.c_int32),
-                ("slot", C.c_int32), ("group_max", C.c_int32), ("pad", C.c_int32)]
+                ("slot", C.c_int32), ("group_max", C.c_int32), ("queue_slots", C.c_int32)]
 
 
 class Problem(C.Structure):

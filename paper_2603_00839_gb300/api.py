@@ -323,7 +323,7 @@ class Handle:
     def gmres_solve_batched(self, problems: Sequence[dict], mu_grid=None, breakdown_tol: float = 0.0,
                             bf16_basis: bool = False, use_graph: bool = True, phase_times: bool = False,
                             group_max: int = 0, true_residual: bool = False, max_restarts: int = 0,
-                            stream=None):
+                            queue_slots: int = 0, stream=None):
         """Batched form (rtg_gmres_solve_batched): every problem is a dict with
         C (device tensor), m, sketch_dims, seed, lam, and optionally A, B
         (factor lists), tol, X0, X.  All problems share C's dtype; each may
@@ -331,7 +331,10 @@ class Handle:
         use_graph=False / phase_times=True launch directly, one group after
         another (phase_ms: the problem's whole group).  group_max > 1 runs
         problems of equal structure in lock-step groups of up to that many
-        (default: one graph branch per problem).  Returns ([X], [SolveResult])."""
+        (default: one graph branch per problem).  queue_slots = K > 0 serves
+        each class of equal structure by at most K graph branches that take
+        its problems from a device work queue (one workspace per branch).
+        Returns ([X], [SolveResult])."""
         if not problems:
             raise ValueError("no problems")
         arr = (L.Problem * len(problems))()
@@ -370,6 +373,7 @@ class Handle:
             opts.n_mu = len(grid)
         opts.breakdown_tol = float(breakdown_tol)
         opts.group_max = int(group_max)
+        opts.queue_slots = int(queue_slots)
         opts.max_restarts = int(max_restarts)
         opts.flags = ((L.FLAG_BF16_BASIS if bf16_basis else 0) | (0 if use_graph else L.FLAG_NO_GRAPH) |
                       (L.FLAG_PHASE_TIMES if phase_times else 0) | (L.FLAG_TRUE_RESIDUAL if true_residual else 0))

@@ -13,6 +13,7 @@
 // the last CTA to finish picks the smallest GCV (ties: the larger mu).
 // Everything here is FP64.
 #include "gs_common.cuh"
+#include "queue.cuh"
 
 namespace rtg {
 
@@ -506,6 +507,45 @@ cudaError_t launch_ws_zero_if(const WsDecision* dec, float* X, int64_t n, cudaSt
 
 cudaError_t launch_ws_write_desc(const WsDecision* dec, SolveDesc* desc, cudaStream_t s) {
   k_ws_write_desc<<<1, 1, 0, s>>>(dec, desc);
+  return cudaGetLastError();
+}
+
+// Work queue of a batched solve: a graph branch takes the next problem of
+// its class with one atomic increment of the class's counter and copies that
+// problem's descriptor into its own, which its kernels read.  With `done`
+// set, the branch first returns the info record of the problem it has just
+// solved to that problem's place.  The branch's loop condition is 1 while
+// the class has problems left, else 0 (the branch then ends).  A nested loop
+// condition keeps its value from one pass of the outer loop's body to the
+// next, so the solve's own loop condition is set to 1 for the new problem
+// (the first problem of a launch starts from the condition's default, 1).
+__global__ void k_queue_next(QueueArgs q, int done) {
+  __shared__ int next;
+  const int cur = *q.cur;
+  if (done && cur >= 0) {
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(q.my_info);
+    uint64_t* dst = reinterpret_cast<uint64_t*>(q.info + cur);
+    for (int i = threadIdx.x; i < int(sizeof(InfoDev) / 8); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();   // every thread has read *q.cur
+  if (threadIdx.x == 0) {
+    const unsigned k = atomicAdd(q.counter, 1u);
+    next = k < static_cast<unsigned>(q.n) ? static_cast<int>(k) : -1;
+    *q.cur = next;
+    cudaGraphSetConditional(static_cast<cudaGraphConditionalHandle>(q.cond), next >= 0 ? 1u : 0u);
+    if (next >= 0 && q.use_inner) cudaGraphSetConditional(static_cast<cudaGraphConditionalHandle>(q.inner), 1u);
+  }
+  __syncthreads();
+  if (next >= 0) {
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(q.desc + next);
+    uint64_t* dst = reinterpret_cast<uint64_t*>(q.my_desc);
+    for (int i = threadIdx.x; i < int(sizeof(SolveDesc) / 8); i += blockDim.x) dst[i] = src[i];
+  }
+}
+static_assert(sizeof(SolveDesc) % 8 == 0 && sizeof(InfoDev) % 8 == 0, "records are copied as 8-byte words");
+
+cudaError_t launch_queue_next(const QueueArgs& q, int done, cudaStream_t s) {
+  k_queue_next<<<1, 128, 0, s>>>(q, done);
   return cudaGetLastError();
 }
 

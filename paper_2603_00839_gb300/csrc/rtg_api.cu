@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include "queue.cuh"
 #include "rtg_internal.cuh"
 
 using namespace rtg;
@@ -490,7 +491,17 @@ struct BatchPlan {
   std::vector<std::shared_ptr<SolvePlan>> plans;   // one per group
   std::vector<int> group_of, slot_of;              // per problem: its group, its place in the host records
   std::vector<int> gfirst;                         // per group: first host record
+  std::vector<int> gcount;                         // per group: its problems
+  std::vector<int> gplan;                          // per group: its first plan in `plans`
   char* desc_host = nullptr;     // pinned: nprob descriptors, then nprob info records, in group order
+  // work-queue batch (opts.queue_slots > 0): a group is a class of problems of
+  // equal structure served by several one-problem plans (graph branches) that
+  // take the class's problems from a device queue; qmem holds every problem's
+  // descriptor and info record (group order), a counter per class and a
+  // current-problem word per branch
+  bool queued = false;
+  DevBuf qmem;
+  size_t q_info = 0, q_ctr = 0, q_cur = 0;   // byte offsets in qmem
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -903,74 +914,121 @@ rtg_status enqueue_epilogue(SolvePlan& P, cudaStream_t s, PhaseTimer* pt = nullp
   return RTG_OK;
 }
 
-// Captures P's solve (prologue, a WHILE node over one Arnoldi step, epilogue)
-// into g as a branch with no dependencies on the rest of g.
-rtg_status build_branch(SolvePlan& P, cudaGraph_t g) {
-  cudaStream_t cs = nullptr, cs2 = nullptr;
-  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  CK(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
-  struct StreamGuard {
-    cudaStream_t a, b;
-    ~StreamGuard() {
-      cudaStreamDestroy(a);
-      cudaStreamDestroy(b);
-    }
-  } sg{cs, cs2};
-  cudaGraphConditionalHandle hnd;
-  CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
-  StepOpts so = solve_step_opts(P, 1, hnd);
-  CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  rtg_status st = P.method == 1 ? enqueue_gk_prologue(P, so, cs) : enqueue_prologue(P, so, cs);
+// Appends a conditional node of `type` on handle `hnd` to the capture on
+// `cs` (after everything captured so far) and returns its body graph.
+rtg_status add_conditional(cudaStream_t cs, cudaGraphConditionalHandle hnd, cudaGraphConditionalNodeType type,
+                           cudaGraph_t* body) {
   cudaStreamCaptureStatus cst;
   cudaGraph_t gcap = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   size_t nd = 0;
-  if (st == RTG_OK) {
-    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &gcap, &deps, nullptr, &nd);
-    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamGetCaptureInfo");
-  }
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &gcap, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamGetCaptureInfo");
   cudaGraphNode_t cnode = nullptr;
   cudaGraphNodeParams cp{};
-  if (st == RTG_OK) {
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = hnd;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaError_t e = cudaGraphAddNode(&cnode, gcap, deps, nullptr, nd, &cp);
-    if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphAddNode(conditional)");
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hnd;
+  cp.conditional.type = type;
+  cp.conditional.size = 1;
+  e = cudaGraphAddNode(&cnode, gcap, deps, nullptr, nd, &cp);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddNode(conditional)");
+  e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamUpdateCaptureDependencies");
+  *body = cp.conditional.phGraph_out[0];
+  return RTG_OK;
+}
+
+// Captures P's solve (prologue, a WHILE node over one Arnoldi step, epilogue)
+// on `cs`, which is capturing into graph g; cs2 captures the loop's body.
+// The loop's condition handle goes to *loop when loop is not null.
+rtg_status capture_solve(SolvePlan& P, cudaGraph_t g, cudaStream_t cs, cudaStream_t cs2,
+                         cudaGraphConditionalHandle* loop = nullptr) {
+  cudaGraphConditionalHandle hnd;
+  CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
+  if (loop) *loop = hnd;
+  StepOpts so = solve_step_opts(P, 1, hnd);
+  RK(P.method == 1 ? enqueue_gk_prologue(P, so, cs) : enqueue_prologue(P, so, cs));
+  cudaGraph_t body = nullptr;
+  RK(add_conditional(cs, hnd, cudaGraphCondTypeWhile, &body));
+  // restarts: an IF node at the end of the body holds the restart
+  // sequence; the Givens block that ends a cycle sets its condition
+  if (P.w.cycles > 1) {
+    cudaGraphConditionalHandle rh;
+    CK(cudaGraphConditionalHandleCreate(&rh, body, 0, cudaGraphCondAssignDefault));
+    so.use_rs_cond = 1;
+    so.rs_cond = static_cast<unsigned long long>(rh);
   }
-  if (st == RTG_OK) {
-    cudaError_t e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
-    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamUpdateCaptureDependencies");
+  CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  rtg_status st = P.method == 1 ? enqueue_gk_step(P, so, cs2)
+                                : enqueue_step(P.op, P.sp, P.w, P.dtype, P.tA, P.tB, P.sk, so, cs2);
+  if (st == RTG_OK && P.w.cycles > 1) st = capture_restart_if(P, so, cs2);
+  cudaGraph_t bodyout = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs2, &bodyout);
+  RK(st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(body)");
+  return enqueue_epilogue(P, cs);
+}
+
+struct CaptureStreams {
+  cudaStream_t s[3] = {nullptr, nullptr, nullptr};
+  rtg_status create() {
+    for (auto& x : s) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    return RTG_OK;
   }
-  if (st == RTG_OK) {
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    // restarts: an IF node at the end of the body holds the restart
-    // sequence; the Givens block that ends a cycle sets its condition
-    if (P.w.cycles > 1) {
-      cudaGraphConditionalHandle rh;
-      cudaError_t e = cudaGraphConditionalHandleCreate(&rh, body, 0, cudaGraphCondAssignDefault);
-      if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphConditionalHandleCreate(restart)");
-      so.use_rs_cond = 1;
-      so.rs_cond = static_cast<unsigned long long>(rh);
-    }
-    cudaError_t e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCaptureToGraph(body)");
-    if (st == RTG_OK) {
-      st = P.method == 1 ? enqueue_gk_step(P, so, cs2)
-                         : enqueue_step(P.op, P.sp, P.w, P.dtype, P.tA, P.tB, P.sk, so, cs2);
-      if (st == RTG_OK && P.w.cycles > 1) st = capture_restart_if(P, so, cs2);
-      cudaGraph_t bodyout = nullptr;
-      e = cudaStreamEndCapture(cs2, &bodyout);
-      if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture(body)");
-    }
+  ~CaptureStreams() {
+    for (auto x : s)
+      if (x) cudaStreamDestroy(x);
   }
-  if (st == RTG_OK) st = enqueue_epilogue(P, cs);
+};
+
+// Ends the capture on cs whatever happened before, and returns the first error.
+rtg_status end_capture(cudaStream_t cs, rtg_status st) {
   cudaGraph_t gout = nullptr;
-  cudaError_t e = cudaStreamEndCapture(cs, &gout);
+  const cudaError_t e = cudaStreamEndCapture(cs, &gout);
   if (st == RTG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture");
   if (st != RTG_OK) cudaGetLastError();
   return st;
+}
+
+// Captures P's solve into g as a branch with no dependencies on the rest of g.
+rtg_status build_branch(SolvePlan& P, cudaGraph_t g) {
+  CaptureStreams cs;
+  RK(cs.create());
+  CK(cudaStreamBeginCaptureToGraph(cs.s[0], g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  return end_capture(cs.s[0], capture_solve(P, g, cs.s[0], cs.s[1]));
+}
+
+// A branch of a work-queue batch: it takes a problem of its class, then
+// loops (a WHILE node) over solve + hand back + take the next, until the
+// class's queue is empty.  P is a one-problem plan; q names the class's
+// queue and P's descriptor, info record and current-problem word.
+rtg_status build_queue_branch(SolvePlan& P, cudaGraph_t g, QueueArgs q) {
+  CaptureStreams cs;
+  RK(cs.create());
+  cudaGraphConditionalHandle oh;
+  CK(cudaGraphConditionalHandleCreate(&oh, g, 0, cudaGraphCondAssignDefault));
+  q.cond = static_cast<unsigned long long>(oh);
+  CK(cudaStreamBeginCaptureToGraph(cs.s[0], g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  rtg_status st = RTG_OK;
+  cudaGraph_t body = nullptr;
+  if (const cudaError_t e = launch_queue_next(q, 0, cs.s[0]); e != cudaSuccess) st = cuda_fail(e, "queue take");
+  if (st == RTG_OK) st = add_conditional(cs.s[0], oh, cudaGraphCondTypeWhile, &body);
+  if (st == RTG_OK) {
+    if (const cudaError_t e =
+            cudaStreamBeginCaptureToGraph(cs.s[1], body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        e != cudaSuccess) {
+      st = cuda_fail(e, "cudaStreamBeginCaptureToGraph(queue body)");
+    } else {
+      cudaGraphConditionalHandle inner{};
+      st = capture_solve(P, body, cs.s[1], cs.s[2], &inner);
+      q.inner = static_cast<unsigned long long>(inner);
+      q.use_inner = 1;
+      if (st == RTG_OK)
+        if (const cudaError_t e2 = launch_queue_next(q, 1, cs.s[1]); e2 != cudaSuccess) st = cuda_fail(e2, "queue next");
+      st = end_capture(cs.s[1], st);
+    }
+  }
+  return end_capture(cs.s[0], st);
 }
 
 rtg_status build_graph(SolvePlan& P) {
@@ -1816,11 +1874,18 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
                                    rtg_dtype dtype, const rtg_opts* opts_in, rtg_info* infos,
                                    rtg_stream stream) {
   if (h == nullptr) return fail(RTG_ERR_INVALID_ARG, "handle is NULL");
-  if (nprob < 1 || nprob > RTG_MAX_BATCH) return fail(RTG_ERR_INVALID_ARG, "nprob=%d not in 1..%d", nprob, RTG_MAX_BATCH);
-  if (probs == nullptr) return fail(RTG_ERR_INVALID_ARG, "probs is NULL");
-  RK(check_dtype(dtype));
   rtg_opts opts{};
   if (opts_in) opts = *opts_in;
+  if (opts.queue_slots < 0) return fail(RTG_ERR_INVALID_ARG, "opts.queue_slots must be >= 0");
+  const bool queued = opts.queue_slots > 0;
+  if (queued && opts.group_max > 1)
+    return fail(RTG_ERR_INVALID_ARG, "opts.queue_slots and opts.group_max > 1 exclude each other");
+  if (queued && (opts.flags & RTG_FLAG_PHASE_TIMES))
+    return fail(RTG_ERR_UNSUPPORTED, "RTG_FLAG_PHASE_TIMES is not available with opts.queue_slots");
+  const int max_prob = queued ? RTG_MAX_QUEUE : RTG_MAX_BATCH;
+  if (nprob < 1 || nprob > max_prob) return fail(RTG_ERR_INVALID_ARG, "nprob=%d not in 1..%d", nprob, max_prob);
+  if (probs == nullptr) return fail(RTG_ERR_INVALID_ARG, "probs is NULL");
+  RK(check_dtype(dtype));
   if (opts.max_restarts < 0) return fail(RTG_ERR_INVALID_ARG, "opts.max_restarts=%d must be >= 0", opts.max_restarts);
   const bool use_graph = !(opts.flags & (RTG_FLAG_NO_GRAPH | RTG_FLAG_PHASE_TIMES));
   const bool phase_times = (opts.flags & RTG_FLAG_PHASE_TIMES) != 0;
@@ -1836,6 +1901,7 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
   std::string bkey;
   if (opts.group_max < 0) return fail(RTG_ERR_INVALID_ARG, "opts.group_max must be >= 0");
   append_bytes(bkey, &opts.group_max, sizeof opts.group_max);
+  append_bytes(bkey, &opts.queue_slots, sizeof opts.queue_slots);
   const int bflags = opts.flags & RTG_FLAG_TRUE_RESIDUAL;
   append_bytes(bkey, &bflags, sizeof bflags);
   append_bytes(bkey, &opts.max_restarts, sizeof opts.max_restarts);
@@ -1899,7 +1965,8 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
     for (int i = 0; i < nprob; ++i) {
       auto g = gid.find(keys[i]);
       int k = 0;
-      if (g == gid.end() || int(members[g->second].size()) >= (opts.group_max > 1 ? opts.group_max : 1)) {
+      const int cap = queued ? nprob : (opts.group_max > 1 ? opts.group_max : 1);
+      if (g == gid.end() || int(members[g->second].size()) >= cap) {
         k = static_cast<int>(members.size());
         gid[keys[i]] = k;
         members.emplace_back();
@@ -1913,21 +1980,56 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
     int pos = 0;
     for (size_t k = 0; k < members.size(); ++k) {
       BP->gfirst.push_back(pos);
+      BP->gcount.push_back(static_cast<int>(members[k].size()));
       for (int i : members[k]) BP->slot_of[i] = pos++;
     }
+    // branches: one per group, or (queue) up to queue_slots per class
+    std::vector<int> nbr(members.size(), 1);
+    int branches = 0;
+    for (size_t k = 0; k < members.size(); ++k) {
+      if (queued) nbr[k] = std::min(opts.queue_slots, BP->gcount[k]);
+      branches += nbr[k];
+    }
+    if (branches > RTG_MAX_BATCH)
+      return fail(RTG_ERR_INVALID_ARG, "%d graph branches (classes x queue_slots) exceed %d", branches, RTG_MAX_BATCH);
     const size_t total = size_t(nprob) * (sizeof(SolveDesc) + sizeof(InfoDev));
     CK(cudaMallocHost(&BP->desc_host, total));
     std::memset(BP->desc_host, 0, total);
     SolveDesc* dh = reinterpret_cast<SolveDesc*>(BP->desc_host);
     InfoDev* ih = reinterpret_cast<InfoDev*>(BP->desc_host + size_t(nprob) * sizeof(SolveDesc));
+    BP->queued = queued;
+    if (queued) {
+      BP->q_info = (size_t(nprob) * sizeof(SolveDesc) + 255) & ~size_t(255);
+      BP->q_ctr = (BP->q_info + size_t(nprob) * sizeof(InfoDev) + 255) & ~size_t(255);
+      BP->q_cur = (BP->q_ctr + members.size() * sizeof(unsigned) + 255) & ~size_t(255);
+      RK(BP->qmem.ensure(BP->q_cur + size_t(branches) * sizeof(int)));
+      CK(cudaMemset(BP->qmem.p, 0, BP->qmem.bytes));
+    }
+    char* qb = static_cast<char*>(BP->qmem.p);
     CK(cudaGraphCreate(&BP->graph, 0));
+    int bi = 0;
     for (size_t k = 0; k < members.size(); ++k) {
-      std::shared_ptr<SolvePlan> pl;
+      BP->gplan.push_back(static_cast<int>(BP->plans.size()));
       const int first = BP->gfirst[k];
-      RK(make_plan(specs[members[k][0]], nullptr, nullptr, dh + first, ih + first, &pl,
-                   static_cast<int>(members[k].size()), &h->tuned, static_cast<int>(members.size())));
-      RK(build_branch(*pl, BP->graph));
-      BP->plans.push_back(std::move(pl));
+      for (int r = 0; r < nbr[k]; ++r, ++bi) {
+        std::shared_ptr<SolvePlan> pl;
+        RK(make_plan(specs[members[k][0]], nullptr, nullptr, dh + first, ih + first, &pl,
+                     queued ? 1 : BP->gcount[k], &h->tuned, branches));
+        if (queued) {
+          QueueArgs q{};
+          q.desc = reinterpret_cast<const SolveDesc*>(qb) + first;
+          q.info = reinterpret_cast<InfoDev*>(qb + BP->q_info) + first;
+          q.counter = reinterpret_cast<unsigned*>(qb + BP->q_ctr) + k;
+          q.n = BP->gcount[k];
+          q.my_desc = pl->desc_dev;
+          q.my_info = pl->info_dev;
+          q.cur = reinterpret_cast<int*>(qb + BP->q_cur) + bi;
+          RK(build_queue_branch(*pl, BP->graph, q));
+        } else {
+          RK(build_branch(*pl, BP->graph));
+        }
+        BP->plans.push_back(std::move(pl));
+      }
     }
     CK(cudaGraphInstantiate(&BP->exec, BP->graph, 0));
     CK(cudaEventCreate(&BP->ev0));
@@ -1938,9 +2040,10 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
   }
   SolveDesc* dh = reinterpret_cast<SolveDesc*>(BP->desc_host);
   InfoDev* ih = reinterpret_cast<InfoDev*>(BP->desc_host + size_t(nprob) * sizeof(SolveDesc));
+  auto plan_of = [&](int i) -> SolvePlan& { return *BP->plans[BP->gplan[BP->group_of[i]]]; };
   for (int i = 0; i < nprob; ++i) {
     const rtg_problem& q = probs[i];
-    const SolvePlan& P = *BP->plans[BP->group_of[i]];
+    const SolvePlan& P = plan_of(i);
     if (q.X0 && apply_uses_st(P.op.op, dtype, dtype, vdtype) && reinterpret_cast<uintptr_t>(q.X0) % 16 != 0)
       return fail(RTG_ERR_INVALID_ARG, "problem %d: X0 must be 16-byte aligned for this operator", i);
     if (vdtype == RTG_BF16 && reinterpret_cast<uintptr_t>(q.C) % 16 != 0)
@@ -1952,30 +2055,39 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
     fill_desc(dh[BP->slot_of[i]], q.C, q.X0, q.X, q.seed, q.tol, opts.breakdown_tol, dtype, q.lam,
               P.mode == 2 ? opts.n_mu : 0, opts.mu_grid);
   }
-  // one strided copy per group each way: host records are contiguous, device
-  // records sit at the start of each problem's block
-  for (size_t k = 0; k < BP->plans.size(); ++k) {
-    const SolvePlan& P = *BP->plans[k];
-    CK(cudaMemcpy2DAsync(P.desc_dev, size_t(P.w.b.stride), dh + BP->gfirst[k], sizeof(SolveDesc),
-                         sizeof(SolveDesc), size_t(P.w.b.n), cudaMemcpyHostToDevice, s));
+  const size_t ngroups = BP->gfirst.size();
+  char* qb = static_cast<char*>(BP->qmem.p);
+  if (BP->queued && use_graph) {
+    // the whole queue in one copy; the class counters start at zero
+    CK(cudaMemcpyAsync(qb, dh, size_t(nprob) * sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(qb + BP->q_ctr, 0, ngroups * sizeof(unsigned), s));
+  } else if (!BP->queued) {
+    // one strided copy per group each way: host records are contiguous, device
+    // records sit at the start of each problem's block
+    for (size_t k = 0; k < ngroups; ++k) {
+      const SolvePlan& P = *BP->plans[BP->gplan[k]];
+      CK(cudaMemcpy2DAsync(P.desc_dev, size_t(P.w.b.stride), dh + BP->gfirst[k], sizeof(SolveDesc),
+                           sizeof(SolveDesc), size_t(P.w.b.n), cudaMemcpyHostToDevice, s));
+    }
   }
   CK(cudaEventRecord(BP->ev0, s));
-  std::vector<rtg_info> gph(BP->plans.size());   // phase times per group (direct launches)
+  std::vector<rtg_info> gph(ngroups);   // phase times per group (direct launches)
+  std::vector<int> dsteps(nprob, 0);    // steps launched per problem (direct launches)
   if (use_graph) {
     CK(cudaGraphLaunch(BP->exec, s));
   } else {
     // Direct launches, one group after another.  The host reads the group's
     // count of running problems after each step and stops launching when it
-    // reaches zero, so the launch sequence is the one the graph runs.
+    // reaches zero, so the launch sequence is the one the graph runs.  A
+    // queued class runs its problems one after another on its first plan.
     PhaseTimer* pt = nullptr;
     if (phase_times) {
       if (!h->timer) h->timer = std::make_unique<PhaseTimer>();
       CK(h->timer->init());
       pt = h->timer.get();
     }
-    for (size_t k = 0; k < BP->plans.size(); ++k) {
-      SolvePlan& P = *BP->plans[k];
-      if (pt) pt->reset(s);
+    for (size_t k = 0; k < ngroups; ++k) {
+      SolvePlan& P = *BP->plans[BP->gplan[k]];
       auto group = [&](auto&& body) -> rtg_status {
         if (pt) CK(pt->hold());
         rtg_status st = body();
@@ -1988,46 +2100,59 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
         return RTG_OK;
       };
       const StepOpts so = solve_step_opts(P, 0, 0);
-      RK(group([&] { return enqueue_prologue(P, so, s, pt); }));
-      RK(left());
-      int steps = 0;
-      while (steps < P.w.m * P.w.cycles && *P.stop_host != 0) {
-        const int j = steps++;
-        RK(group([&] {
-          RK(enqueue_step(P.op, P.sp, P.w, dtype, P.tA, P.tB, P.sk, so, s, pt, j));
-          if (P.w.cycles > 1) {
-            PhaseScope rs(pt, RTG_PHASE_INIT, j, restart_launches(P.op.op, P.sp, dtype, vdtype));
-            RK(enqueue_restart(P, so, s));
-          }
-          return RTG_OK;
-        }));
+      const int runs = BP->queued ? BP->gcount[k] : 1;
+      for (int r = 0; r < runs; ++r) {
+        const int rec = BP->gfirst[k] + r;
+        if (BP->queued) CK(cudaMemcpyAsync(P.desc_dev, dh + rec, sizeof(SolveDesc), cudaMemcpyHostToDevice, s));
+        if (pt) pt->reset(s);
+        RK(group([&] { return enqueue_prologue(P, so, s, pt); }));
         RK(left());
-      }
-      P.direct_steps = steps;
-      RK(group([&] { return enqueue_epilogue(P, s, pt); }));
-      if (pt) {
-        CK(cudaStreamSynchronize(s));
-        rtg_info& gi = gph[k];
-        for (int q = 0; q < RTG_PHASE_COUNT; ++q) {
-          gi.phase_ms[q] = 0.0;
-          gi.phase_launches[q] = 0;
+        int steps = 0;
+        while (steps < P.w.m * P.w.cycles && *P.stop_host != 0) {
+          const int j = steps++;
+          RK(group([&] {
+            RK(enqueue_step(P.op, P.sp, P.w, dtype, P.tA, P.tB, P.sk, so, s, pt, j));
+            if (P.w.cycles > 1) {
+              PhaseScope rs(pt, RTG_PHASE_INIT, j, restart_launches(P.op.op, P.sp, dtype, vdtype));
+              RK(enqueue_restart(P, so, s));
+            }
+            return RTG_OK;
+          }));
+          RK(left());
         }
-        pt->collect(steps, &gi);
+        P.direct_steps = steps;
+        for (int q = 0; q < (BP->queued ? 1 : BP->gcount[k]); ++q) dsteps[rec + q] = steps;
+        RK(group([&] { return enqueue_epilogue(P, s, pt); }));
+        if (BP->queued) CK(cudaMemcpyAsync(ih + rec, P.info_dev, sizeof(InfoDev), cudaMemcpyDeviceToHost, s));
+        if (pt) {
+          CK(cudaStreamSynchronize(s));
+          rtg_info& gi = gph[k];
+          for (int q = 0; q < RTG_PHASE_COUNT; ++q) {
+            gi.phase_ms[q] = 0.0;
+            gi.phase_launches[q] = 0;
+          }
+          pt->collect(steps, &gi);
+        }
       }
     }
   }
   CK(cudaEventRecord(BP->ev1, s));
-  for (size_t k = 0; k < BP->plans.size(); ++k) {
-    const SolvePlan& P = *BP->plans[k];
-    CK(cudaMemcpy2DAsync(ih + BP->gfirst[k], sizeof(InfoDev), P.info_dev, size_t(P.w.b.stride),
-                         sizeof(InfoDev), size_t(P.w.b.n), cudaMemcpyDeviceToHost, s));
+  if (BP->queued && use_graph) {
+    CK(cudaMemcpyAsync(ih, qb + BP->q_info, size_t(nprob) * sizeof(InfoDev), cudaMemcpyDeviceToHost, s));
+  } else if (!BP->queued) {
+    for (size_t k = 0; k < ngroups; ++k) {
+      const SolvePlan& P = *BP->plans[BP->gplan[k]];
+      CK(cudaMemcpy2DAsync(ih + BP->gfirst[k], sizeof(InfoDev), P.info_dev, size_t(P.w.b.stride),
+                           sizeof(InfoDev), size_t(P.w.b.n), cudaMemcpyDeviceToHost, s));
+    }
   }
   CK(cudaStreamSynchronize(s));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, BP->ev0, BP->ev1);
   if (infos)
     for (int i = 0; i < nprob; ++i) {
-      const SolvePlan& P = *BP->plans[BP->group_of[i]];
+      SolvePlan& P = plan_of(i);
+      P.direct_steps = dsteps[BP->slot_of[i]];
       fill_info(P, ih[BP->slot_of[i]], P.mode, P.n_mu, use_graph, ms, &infos[i]);
       if (phase_times)   // the phase times of the problem's whole group
         for (int q = 0; q < RTG_PHASE_COUNT; ++q) {
