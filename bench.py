@@ -862,6 +862,16 @@ def run_ours(args):
     reach_p = (sum(bool(r.converged) for r in plain_res) / len(plain_res)) if plain_res else 1.0
     value = job_rate(world, reach_b, ms_max / 1e3)
     plain_value = job_rate(world, reach_p, plain_max / 1e3)
+    # every kernel group's algorithmic bytes summed over one batch's solves
+    # (the last timed batch) against the batch's device time
+    nd_n = int(np.prod(probs[0]["p"].dims))
+    nd_d = int(np.prod([min(a, b) for a, b in zip(probs[0]["p"].sketch_dims, probs[0]["p"].dims)]))
+    step_bytes = sum(phase_bytes(k, nd_n, nd_d, r.iters, 4, probs[0]["p"].m)
+                     for r in outs[-1] for k in ("apply", "sketch", "update", "assemble", "init"))
+    whole = {"algorithmic_bytes": int(step_bytes), "gbs": round(step_bytes / (ms / 1e3) / 1e9, 1),
+             "frac_of_measured_hbm": round(step_bytes / (ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0), 4),
+             "note": "apply, sketch, update, assembly and start groups of every solve of the batch (the byte "
+                     "model of the roofline) over the batch's device time"}
 
     # ---- end to end through the C ABI with pinned host buffers, every step:
     # H2D of the batch's observations, the batched solve, D2H of the
@@ -992,6 +1002,7 @@ def run_ours(args):
                                      " (one branch per problem, device-side WHILE loops)")},
                "forms": {"batched_fp32": {"value": round(value, 2), "ms_per_batch": round(ms_max, 4),
                                           "batch": B, "queue_slots": slots, "reached_stop_level": reached(res_b),
+                                          "whole_step": whole,
                                           "vs_plain_fp32": round(value / plain_value, 3) if plain_value else None},
                          "plain_fp32": {"value": round(plain_value, 2), "ms_per_solve": round(plain_max, 4),
                                         "mean_iters": float(np.mean([r.iters for r in plain_res])) if plain_res else None,
