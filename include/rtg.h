@@ -513,7 +513,11 @@ typedef struct rtg_problem {
  * queue is empty (a device-side WHILE loop around the solve's own), so a
  * branch whose problem stops early goes on to another, and the device memory
  * grows with the branches, not the problems: up to RTG_MAX_QUEUE problems,
- * at most RTG_MAX_BATCH branches in all.  Descriptors go up in one copy and
+ * at most RTG_MAX_BATCH branches in all.  When the classes together have
+ * more than K branches (many classes of few problems), the branches run as
+ * K chains (a branch starts when the one before it in its chain has ended):
+ * largest estimated work first (tensor entries x m x problems per branch),
+ * each to the chain with the least estimated work so far.  Descriptors go up in one copy and
  * the info records come back in one.  Which branch solves which problem
  * depends on timing; the result does not (each equals the same problem
  * solved alone, bit for bit).  RTG_FLAG_NO_GRAPH runs each class's problems

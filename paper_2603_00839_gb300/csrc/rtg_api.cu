@@ -990,25 +990,54 @@ rtg_status end_capture(cudaStream_t cs, rtg_status st) {
   return st;
 }
 
-// Captures P's solve into g as a branch with no dependencies on the rest of g.
-rtg_status build_branch(SolvePlan& P, cudaGraph_t g) {
+// Place of a branch in a chain of branches (a batch with a bounded number of
+// branches in flight): `after` holds the nodes its first node waits for
+// (none: it starts with the graph), `tail` receives its last nodes.
+struct ChainLink {
+  const std::vector<cudaGraphNode_t>* after = nullptr;
+  std::vector<cudaGraphNode_t>* tail = nullptr;
+};
+
+rtg_status begin_branch(cudaStream_t cs, cudaGraph_t g, const ChainLink& ch) {
+  const bool dep = ch.after != nullptr && !ch.after->empty();
+  CK(cudaStreamBeginCaptureToGraph(cs, g, dep ? ch.after->data() : nullptr, nullptr, dep ? ch.after->size() : 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  return RTG_OK;
+}
+
+// Records the capture's current last nodes (what the next captured node
+// would depend on) as the branch's tail.
+rtg_status branch_tail(cudaStream_t cs, const ChainLink& ch, rtg_status st) {
+  if (st != RTG_OK || ch.tail == nullptr) return st;
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t gcap = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  const cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &gcap, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamGetCaptureInfo(tail)");
+  ch.tail->assign(deps, deps + nd);
+  return RTG_OK;
+}
+
+// Captures P's solve into g as a branch (after ch.after, if given).
+rtg_status build_branch(SolvePlan& P, cudaGraph_t g, const ChainLink& ch = ChainLink{}) {
   CaptureStreams cs;
   RK(cs.create());
-  CK(cudaStreamBeginCaptureToGraph(cs.s[0], g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  return end_capture(cs.s[0], capture_solve(P, g, cs.s[0], cs.s[1]));
+  RK(begin_branch(cs.s[0], g, ch));
+  return end_capture(cs.s[0], branch_tail(cs.s[0], ch, capture_solve(P, g, cs.s[0], cs.s[1])));
 }
 
 // A branch of a work-queue batch: it takes a problem of its class, then
 // loops (a WHILE node) over solve + hand back + take the next, until the
 // class's queue is empty.  P is a one-problem plan; q names the class's
 // queue and P's descriptor, info record and current-problem word.
-rtg_status build_queue_branch(SolvePlan& P, cudaGraph_t g, QueueArgs q) {
+rtg_status build_queue_branch(SolvePlan& P, cudaGraph_t g, QueueArgs q, const ChainLink& ch = ChainLink{}) {
   CaptureStreams cs;
   RK(cs.create());
   cudaGraphConditionalHandle oh;
   CK(cudaGraphConditionalHandleCreate(&oh, g, 0, cudaGraphCondAssignDefault));
   q.cond = static_cast<unsigned long long>(oh);
-  CK(cudaStreamBeginCaptureToGraph(cs.s[0], g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  RK(begin_branch(cs.s[0], g, ch));
   rtg_status st = RTG_OK;
   cudaGraph_t body = nullptr;
   if (const cudaError_t e = launch_queue_next(q, 0, cs.s[0]); e != cudaSuccess) st = cuda_fail(e, "queue take");
@@ -1028,7 +1057,7 @@ rtg_status build_queue_branch(SolvePlan& P, cudaGraph_t g, QueueArgs q) {
       st = end_capture(cs.s[1], st);
     }
   }
-  return end_capture(cs.s[0], st);
+  return end_capture(cs.s[0], branch_tail(cs.s[0], ch, st));
 }
 
 rtg_status build_graph(SolvePlan& P) {
@@ -2007,28 +2036,62 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
     }
     char* qb = static_cast<char*>(BP->qmem.p);
     CK(cudaGraphCreate(&BP->graph, 0));
-    int bi = 0;
+    // the plans (one per branch), each branch's class and estimated cost
+    // (tensor entries x Krylov dimension x problems it serves)
+    std::vector<int> cls_of;
+    std::vector<double> cost;
     for (size_t k = 0; k < members.size(); ++k) {
       BP->gplan.push_back(static_cast<int>(BP->plans.size()));
       const int first = BP->gfirst[k];
-      for (int r = 0; r < nbr[k]; ++r, ++bi) {
+      const PlanSpec& ps = specs[members[k][0]];
+      for (int r = 0; r < nbr[k]; ++r) {
         std::shared_ptr<SolvePlan> pl;
-        RK(make_plan(specs[members[k][0]], nullptr, nullptr, dh + first, ih + first, &pl,
-                     queued ? 1 : BP->gcount[k], &h->tuned, branches));
+        RK(make_plan(ps, nullptr, nullptr, dh + first, ih + first, &pl, queued ? 1 : BP->gcount[k], &h->tuned,
+                     branches));
+        BP->plans.push_back(std::move(pl));
+        cls_of.push_back(static_cast<int>(k));
+        cost.push_back(double(ps.n) * ps.m * BP->gcount[k] / nbr[k]);
+      }
+    }
+    // queue batch with more branches than queue_slots (classes of few
+    // problems): the branches form queue_slots chains, at most one branch of
+    // a chain in flight; longest first, each to the chain with the least work
+    // so far
+    const int nchain = (queued && branches > opts.queue_slots) ? opts.queue_slots : branches;
+    std::vector<std::vector<int>> chains(nchain);
+    {
+      std::vector<int> order(branches);
+      for (int b = 0; b < branches; ++b) order[b] = b;
+      if (nchain < branches)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+      std::vector<double> load(nchain, 0.0);
+      for (int b : order) {
+        const int c = nchain < branches ? int(std::min_element(load.begin(), load.end()) - load.begin()) : b;
+        chains[c].push_back(b);
+        load[c] += cost[b];
+      }
+    }
+    for (const auto& chain : chains) {
+      std::vector<cudaGraphNode_t> prev, tail;
+      for (int b : chain) {
+        SolvePlan& P = *BP->plans[b];
+        const int k = cls_of[b];
+        const ChainLink link{prev.empty() ? nullptr : &prev, &tail};
         if (queued) {
+          const int first = BP->gfirst[k];
           QueueArgs q{};
           q.desc = reinterpret_cast<const SolveDesc*>(qb) + first;
           q.info = reinterpret_cast<InfoDev*>(qb + BP->q_info) + first;
           q.counter = reinterpret_cast<unsigned*>(qb + BP->q_ctr) + k;
           q.n = BP->gcount[k];
-          q.my_desc = pl->desc_dev;
-          q.my_info = pl->info_dev;
-          q.cur = reinterpret_cast<int*>(qb + BP->q_cur) + bi;
-          RK(build_queue_branch(*pl, BP->graph, q));
+          q.my_desc = P.desc_dev;
+          q.my_info = P.info_dev;
+          q.cur = reinterpret_cast<int*>(qb + BP->q_cur) + b;
+          RK(build_queue_branch(P, BP->graph, q, link));
         } else {
-          RK(build_branch(*pl, BP->graph));
+          RK(build_branch(P, BP->graph, link));
         }
-        BP->plans.push_back(std::move(pl));
+        prev.swap(tail);
       }
     }
     CK(cudaGraphInstantiate(&BP->exec, BP->graph, 0));

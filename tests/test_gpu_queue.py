@@ -171,3 +171,15 @@ def test_queue_rejects_bad_arguments(h):
         h.gmres_solve_batched(probs, queue_slots=2, group_max=2)
     with pytest.raises(L.RtgError, match="PHASE_TIMES"):
         h.gmres_solve_batched(probs, queue_slots=2, phase_times=True)
+
+
+def test_chained_branches_equal_single_solves(h):
+    """More branches than queue slots (classes of one problem each, and a
+    class of four beside them): the branches run as queue_slots chains."""
+    cfgs = w.batched_configs(5, seed=31, side_lo=40, side_hi=140)
+    singles = [_problem(h, c) for c in cfgs]           # five structures
+    four = _class(h, cfgs[0], 4, 500)                   # and a class of four of the first one's
+    probs = [singles[0], four[0], singles[1], singles[2], four[1], singles[3], four[2], singles[4], four[3]]
+    for slots in (2, 3):
+        Xs, res = h.gmres_solve_batched(probs, queue_slots=slots)
+        _assert_equal_to_single(h, probs, Xs, res)
