@@ -37,7 +37,7 @@
 namespace rtg {
 
 constexpr int TC_THREADS = 256;   // 8 warps split K
-constexpr int N_NT = 2;           // later stages: n8 tiles (16 Theta rows) per CTA
+constexpr int N_NT = 4;           // later stages: n8 tiles (32 Theta rows) per CTA
 constexpr int XA = 20;            // blocked row: 16 values of l + 4 pad (conflict-free A loads)
 // ------------------------------------------------------------------ plan
 
