@@ -382,16 +382,20 @@ __device__ __forceinline__ int64_t out_pos(const OutMap& om, int64_t l, int64_t 
 //    TMA copy (cp.async.bulk.tensor) of the 64 x U_BN block per stage, zero
 //    filled past the tensor, issued as soon as the split warps have
 //    released the stage.
-// The copies start before the tensor memory is allocated.
-// Splitting block kb + 1 thus overlaps issuing the MMAs of block kb.  The
+// The copies start before the tensor memory is allocated.  The rings are
+// sized for two CTAs per SM (105 KB of shared memory each): with one limb
+// buffer the split of block kb + 1 waits for the MMAs of block kb, and the
+// other CTA on the SM splits or issues meanwhile (more stages and limb
+// buffers at one CTA per SM overlapped the two inside the CTA, which was
+// faster for one solve alone and slower for many problems at once).  The
 // epilogue (warps 0-7) reads D back (tcgen05.ld, warp w: lanes 32 (w % 4),
 // columns U_BN / 2 (w / 4) ..) and stores through the stage's output map,
 // advancing the output position without divisions.  X not aligned to 16
 // bytes per column block is read with plain loads by the split instead.
 constexpr int U_BN = 64;        // columns of X per CTA (MMA N)
-constexpr int U_TSTAGES = 6;    // Theta ring
-constexpr int U_XSTAGES = 3;    // X ring
-constexpr int U_LBUF = 3;       // limb buffers
+constexpr int U_TSTAGES = 3;    // Theta ring
+constexpr int U_XSTAGES = 2;    // X ring
+constexpr int U_LBUF = 1;       // limb buffers (105 KB in all: two CTAs per SM)
 constexpr uint32_t kTileBlk = 5184;   // epilogue staging pitch per 16-row block (U_BN * 20 floats + 16 floats)
 constexpr int U_SPLIT = 256;    // threads of the split warps
 constexpr int U_THREADS = U_SPLIT + 96;
