@@ -183,3 +183,26 @@ def test_chained_branches_equal_single_solves(h):
     for slots in (2, 3):
         Xs, res = h.gmres_solve_batched(probs, queue_slots=slots)
         _assert_equal_to_single(h, probs, Xs, res)
+
+
+def test_queue_bf16_basis_and_true_residual(h):
+    """The work queue with the BF16 basis, and with the final true residual:
+    each result equals the same problem solved alone with the same options."""
+    cfg = w.batched_configs(1, seed=41, side_lo=64, side_hi=120)[0]
+    I1 = (cfg["dims"][0] // 8) * 8                   # the BF16 basis needs dims[0] % 8 == 0
+    cfg = dict(cfg, dims=(I1,) + tuple(cfg["dims"][1:]),
+               sketch_dims=(min(I1 // 2, 128),) + tuple(cfg["sketch_dims"][1:]))
+    probs = _class(h, cfg, 5, 600)
+    Xs, res = h.gmres_solve_batched(probs, queue_slots=2, bf16_basis=True)
+    for q, X, r in zip(probs, Xs, res):
+        Xr, rr = h.gmres_solve(q["C"], q["m"], q["sketch_dims"], q["seed"], q["lam"], q["A"], q["B"],
+                               tol=q["tol"], bf16_basis=True)
+        assert r.device_status == 0 and r.iters == rr.iters and np.array_equal(r.rho, rr.rho)
+        assert np.array_equal(X.cpu().numpy(), Xr.cpu().numpy())
+    Xs, res = h.gmres_solve_batched(probs, queue_slots=2, true_residual=True)
+    for q, X, r in zip(probs, Xs, res):
+        Xr, rr = h.gmres_solve(q["C"], q["m"], q["sketch_dims"], q["seed"], q["lam"], q["A"], q["B"],
+                               tol=q["tol"], true_residual=True)
+        assert r.device_status == 0 and r.true_rel_resid > 0
+        assert r.true_rel_resid == rr.true_rel_resid and r.true_rel_resid_theta == rr.true_rel_resid_theta
+        assert np.array_equal(X.cpu().numpy(), Xr.cpu().numpy())
