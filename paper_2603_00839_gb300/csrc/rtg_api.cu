@@ -2217,6 +2217,9 @@ rtg_status rtg_gmres_solve_batched(rtg_handle h, int32_t nprob, const rtg_proble
       SolvePlan& P = plan_of(i);
       P.direct_steps = dsteps[BP->slot_of[i]];
       fill_info(P, ih[BP->slot_of[i]], P.mode, P.n_mu, use_graph, ms, &infos[i]);
+      // the queue kernel that handed the problem back and took the next
+      // (each branch's first take is not counted)
+      if (BP->queued && use_graph) infos[i].launches += 1;
       if (phase_times)   // the phase times of the problem's whole group
         for (int q = 0; q < RTG_PHASE_COUNT; ++q) {
           infos[i].phase_ms[q] = gph[BP->group_of[i]].phase_ms[q];
