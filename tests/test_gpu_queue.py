@@ -206,3 +206,36 @@ def test_queue_bf16_basis_and_true_residual(h):
         assert r.device_status == 0 and r.true_rel_resid > 0
         assert r.true_rel_resid == rr.true_rel_resid and r.true_rel_resid_theta == rr.true_rel_resid_theta
         assert np.array_equal(X.cpu().numpy(), Xr.cpu().numpy())
+
+
+def test_queue_full_size_image512_as_the_benchmark_runs_it(h):
+    """The benchmark's launch configuration at full size: 512x512x3 FP32
+    problems (seeds 0..11, GCV over the grid, stop at rho*) through the
+    work queue on eight branches.  Every result equals its single solve bit
+    for bit, and the first problem matches the FP64 oracle (rho history, X
+    at the mu the GPU picked) at the FP32 bar of 1e-4."""
+    api = _api()
+    probs, first = [], None
+    for s in range(12):
+        p = w.image_config(2, seed=s)
+        mats = oracle.factor_matrices(p.dims, p.factors, p.right_factors)
+        C, _, nu_c = oracle.make_observation(p.x_true, mats, p.noise, p.nu)
+        A = [api.banded(m, p.dims[m - 1], t) if k == "banded" else api.dense(m, t) for m, k, t in p.factors]
+        B = [api.banded(m, p.dims[m - 1], t) if k == "banded" else api.dense(m, t) for m, k, t in p.right_factors]
+        probs.append(dict(C=api.to_device(C, torch.float32), A=A, B=B, m=p.m, sketch_dims=p.sketch_dims,
+                          seed=p.seed, lam=p.lam, tol=oracle.rho_star(nu_c)))
+        if s == 0:
+            first = (p, mats, C, oracle.rho_star(nu_c))
+    grid = w.image_config(2).mu_grid
+    Xs, res = h.gmres_solve_batched(probs, mu_grid=grid, queue_slots=8)
+    _assert_equal_to_single(h, probs, Xs, res, mu_grid=grid)
+    p, mats, C, tol = first
+    th = oracle.sketch_matrices(p.dims, p.sketch_dims, p.seed, p.problem_id)
+    ref = oracle.rtg_gmres(mats, C, p.m, th, tol=tol, lam=p.lam, mu_grid=grid)
+    r = res[0]
+    assert r.iters == ref["iters"]
+    assert np.allclose(r.rho, ref["rho"], rtol=1e-4, atol=0)
+    y = oracle.tikhonov_stacked(ref["H"], ref["beta"], r.mu)
+    X_mu = sum(y[i] * ref["V"][i] for i in range(r.iters))
+    Xg = Xs[0].cpu().double().numpy()
+    assert np.linalg.norm(Xg - X_mu) / np.linalg.norm(X_mu) < 1e-4
