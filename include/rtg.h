@@ -517,12 +517,13 @@ typedef struct rtg_problem {
  * more than K branches (many classes of few problems), the branches run as
  * K chains (a branch starts when the one before it in its chain has ended):
  * largest estimated work first (tensor entries x m x problems per branch),
- * each to the chain with the least estimated work so far.  Descriptors go up in one copy and
- * the info records come back in one.  Which branch solves which problem
- * depends on timing; the result does not (each equals the same problem
- * solved alone, bit for bit).  RTG_FLAG_NO_GRAPH runs each class's problems
- * in order on one workspace; RTG_FLAG_PHASE_TIMES is UNSUPPORTED here, and
- * group_max > 1 with queue_slots > 0 is INVALID_ARG.  opts (may be NULL) is shared: GCV grid,
+ * each to the chain with the least estimated work so far.  Descriptors go
+ * up in one copy and the info records come back in one.  Which branch
+ * solves which problem depends on timing; the result does not (each equals
+ * the same problem solved alone, bit for bit).  RTG_FLAG_NO_GRAPH runs each
+ * class's problems in order on one workspace; RTG_FLAG_PHASE_TIMES is
+ * UNSUPPORTED here, and group_max > 1 with queue_slots > 0 is INVALID_ARG.
+ * opts (may be NULL) is shared: GCV grid,
  * breakdown level, RTG_FLAG_BF16_BASIS, and RTG_FLAG_NO_GRAPH /
  * RTG_FLAG_PHASE_TIMES (direct launches, one group after another; with
  * PHASE_TIMES each problem's phase_ms / phase_launches are those of its

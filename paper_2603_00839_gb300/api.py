@@ -333,7 +333,8 @@ class Handle:
         problems of equal structure in lock-step groups of up to that many
         (default: one graph branch per problem).  queue_slots = K > 0 serves
         each class of equal structure by at most K graph branches that take
-        its problems from a device work queue (one workspace per branch).
+        its problems from a device work queue (one workspace per branch);
+        more than K branches in all (many classes) run as K chains.
         Returns ([X], [SolveResult])."""
         if not problems:
             raise ValueError("no problems")
